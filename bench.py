@@ -1,0 +1,351 @@
+"""Benchmark of the generalised geodesic distance transform on GB300.
+
+One step = one forward transform of the 2D large workload (1x3x2048x2048
+float32, three seed disks, lambda = 0.5, v = 1e10, 2 iterations of the four
+passes) through the C ABI, inputs resident in HBM.  Prints one JSON line.
+
+Metric: Mvoxel/s per iteration = elements * iterations / t / 1e6, t = device
+time of the step (CUDA events on the launching stream, L2 flushed between
+steps by a 256 MB write outside the events).  The roofline entry compares the
+algorithmic bytes of the sweep kernel (read D, write D, read the C channels of
+I per element per pass: 8 + 4C bytes) with the measured HBM copy bandwidth.
+
+--impl reference times the CPU oracle (the plain sequential restatement of the
+method, OpenMP over the elements of a line as in the paper's CPU design) on
+this host's cores, on a bounded sample of the same workload.
+
+Multi-GPU: one independent replica per rank (a single transform does not
+shard); value = elements * iterations processed by all ranks / max time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Mvoxel/s per iteration"
+WORKLOAD = "2D large 1x3x2048x2048 fp32, lambda=0.5, v=1e10, iterations=2, 3 seed disks"
+PASSES_2D = 4
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            p = json.load(fh)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def _kernel_hash():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2208_00001_gb300", "csrc")
+    for fn in sorted(os.listdir(csrc)):
+        if fn.endswith((".cu", ".h")):
+            with open(os.path.join(csrc, fn), "rb") as fh:
+                h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def _profile_traffic(name):
+    """Per-launch DRAM bytes of the named kernel from the committed ncu summary
+    (profiles/), or None if absent or taken on a different kernel source."""
+    path = os.path.join(ROOT, "profiles", f"{name}.md")
+    if not os.path.exists(path):
+        return None
+    text = open(path).read()
+    m = re.search(r"kernel_source_hash:\s*([0-9a-f]+)", text)
+    t = re.search(r"traffic_bytes_per_full_launch:\s*([0-9.eE+]+)", text)
+    if not m or not t or m.group(1) != _kernel_hash():
+        return None
+    return float(t.group(1))
+
+
+class ClockSampler:
+    """Samples nvidia-smi clocks and throttle reasons during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[3:7]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _dist_init():
+    import torch
+    import torch.distributed as dist
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        dist.init_process_group(backend)
+    return rank, local, world
+
+
+def _barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def _max_over_ranks(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64,
+                     device="cuda" if torch.cuda.is_available() else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def run_reference(args):
+    """CPU oracle on this host (bounded sample of the workload)."""
+    import numpy as np  # noqa: F401
+    import oracle
+    import workloads
+
+    rank, _, world = _dist_init()
+    if rank != 0:
+        return 0
+    oracle.build()
+    case = workloads.large2d()
+    cores = os.cpu_count() or 1
+    # sample: the first `rows` rows of the image (all passes, both iterations)
+    rows = 512
+    img = case.image[:, :, :rows].copy()
+    m = case.mask[:, :, :rows].copy()
+    for _ in range(args.warmup):
+        oracle.gdt(img, m, case.v, case.lam, case.iterations, threads=cores)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        oracle.gdt(img, m, case.v, case.lam, case.iterations, threads=cores)
+        times.append(time.perf_counter() - t0)
+    t = sum(times) / len(times)
+    units = img.shape[2] * img.shape[3] * case.iterations
+    value = units / t / 1e6
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "Mvoxel/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": t * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "sample": f"first {rows} of 2048 rows"},
+        "cpu_baseline": {"value": value, "unit": "Mvoxel/s", "cores": cores, "kind": "oracle",
+                         "sample": f"rows 0..{rows} of the 2048x2048x3 image, 2 iterations"},
+        "e2e": {"value": value, "unit": "Mvoxel/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+def cpu_baseline_sample(case, budget_s=12.0):
+    """Times the oracle on host cores over a bounded row sample."""
+    import oracle
+    oracle.build()
+    cores = os.cpu_count() or 1
+    rows = 512
+    img = case.image[:, :, :rows].copy()
+    m = case.mask[:, :, :rows].copy()
+    oracle.gdt(img, m, case.v, case.lam, case.iterations, threads=cores)
+    times = []
+    t_start = time.perf_counter()
+    while time.perf_counter() - t_start < budget_s or not times:
+        t0 = time.perf_counter()
+        oracle.gdt(img, m, case.v, case.lam, case.iterations, threads=cores)
+        times.append(time.perf_counter() - t0)
+        if len(times) >= 20:
+            break
+    t = statistics.median(times)
+    return {"value": rows * img.shape[3] * case.iterations / t / 1e6, "unit": "Mvoxel/s",
+            "cores": cores, "kind": "oracle",
+            "sample": f"rows 0..{rows} of the 2048x2048x3 image, 2 iterations, median of "
+                      f"{len(times)} runs, OpenMP over line elements"}
+
+
+def run_fgx(args):
+    import torch
+
+    import paper_2208_00001_gb300 as fgx
+    from paper_2208_00001_gb300 import build
+    import workloads
+
+    rank, local, world = _dist_init()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    build.build()
+    case = workloads.large2d()
+    B, C, H, W = case.image.shape
+    N = B * H * W
+    its = case.iterations
+    img = torch.from_numpy(case.image).to(dev)
+    m = torch.from_numpy(case.mask).to(dev)
+    out = torch.empty_like(m)
+    ws = torch.empty(fgx.workspace_size(2, B, C, 1, H, W), dtype=torch.uint8, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        fgx.geodesic2d(img, m, case.v, case.lam, its, out=out, workspace=ws)
+
+    for _ in range(max(3, args.warmup)):
+        step()
+    torch.cuda.synchronize()
+    if fgx.workspace_status(ws) != 0:
+        raise RuntimeError("device status after warm-up: " + fgx.status_string(
+            fgx.workspace_status(ws)))
+
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    _barrier(world)
+    torch.cuda.synchronize()
+    wall0 = time.perf_counter()
+    with ClockSampler(local) as clk:
+        for i in range(args.steps):
+            flush.fill_(i & 0xFF)           # evict L2 between steps (outside the events)
+            starts[i].record(stream)
+            step()
+            ends[i].record(stream)
+        torch.cuda.synchronize()
+    wall = time.perf_counter() - wall0
+    _barrier(world)
+    status = fgx.workspace_status(ws)
+    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    t_step = statistics.mean(step_ms) / 1e3
+    t_max = _max_over_ranks(t_step, world)
+    value = world * N * its / t_max / 1e6
+
+    # roofline of the sweep kernel: the step is one launch of it (plus a
+    # 4 KB workspace memset)
+    bytes_per_launch = N * its * PASSES_2D * (8 + 4 * C)
+    peak, peak_kind = _peaks()
+    achieved = bytes_per_launch / t_step / 1e9
+    traffic = _profile_traffic("sweep_kernel_2d_large")
+
+    # end-to-end through the public API with host buffers
+    h_img = torch.from_numpy(case.image).pin_memory()
+    h_m = torch.from_numpy(case.mask).pin_memory()
+    h_out = torch.empty(m.shape, dtype=torch.float32).pin_memory()
+    e_img = torch.empty_like(img)
+    e_m = torch.empty_like(m)
+
+    def e2e_step():
+        e_img.copy_(h_img, non_blocking=True)
+        e_m.copy_(h_m, non_blocking=True)
+        fgx.geodesic2d(e_img, e_m, case.v, case.lam, its, out=out, workspace=ws)
+        h_out.copy_(out, non_blocking=True)
+
+    for _ in range(2):
+        e2e_step()
+    torch.cuda.synchronize()
+    e_s = torch.cuda.Event(enable_timing=True)
+    e_e = torch.cuda.Event(enable_timing=True)
+    e_s.record(stream)
+    for _ in range(args.steps):
+        e2e_step()
+    e_e.record(stream)
+    torch.cuda.synchronize()
+    t_e2e = e_s.elapsed_time(e_e) / 1e3 / args.steps
+    t_e2e = _max_over_ranks(t_e2e, world)
+
+    if rank != 0:
+        return 0
+    line = {
+        "metric": METRIC, "value": value, "unit": "Mvoxel/s", "n_gpus": world,
+        "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": t_max * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "parallelism": f"replicas x{world}",
+                   "l2": "flushed between steps (256 MB write outside the timed events)",
+                   "device_status": fgx.status_string(status),
+                   "wall_s_timed_loop": wall},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": traffic,
+                     "peak_source": peak_kind, "kernel": "sweep_kernel",
+                     "algorithmic_bytes_per_launch": bytes_per_launch},
+        "e2e": {"value": world * N * its / t_e2e / 1e6, "unit": "Mvoxel/s",
+                "h2d_bytes_per_step": int(h_img.numel() * 4 + h_m.numel() * 4),
+                "d2h_bytes_per_step": int(h_out.numel() * 4)},
+        "gpu_launches": args.steps,
+        "clocks": clk.summary(),
+    }
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline_sample(case)
+    print(json.dumps(line))
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="fgx", choices=["fgx", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_fgx(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

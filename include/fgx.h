@@ -1,0 +1,179 @@
+/*
+ * fgx.h - C ABI of a GB300 (sm_103a) library for the generalised geodesic
+ * distance transform computed by raster-scan passes.
+ *
+ * Method (FastGeodis, Implementation section; generalised GDT of the
+ * Summary): starting from D0 = v * M (soft seed mask M), every directional
+ * pass updates each element x of a line (a row in 2D, a plane in 3D) from the
+ * already-updated previous line:
+ *     D[x] = min(D[x], min_y D[y] + sqrt((1-lambda)*|x-y|^2_spacing
+ *                                        + lambda*|I(x)-I(y)|^2))
+ * over the 3 (2D) or 9 (3D) neighbours y of x in the previous line.  2D passes
+ * run top-bottom, bottom-top, left-right, right-left; 3D passes run
+ * front-back, back-front, top-bottom, bottom-top, left-right, right-left; the
+ * whole schedule repeats `iterations` times.  Results are bit-exact to a
+ * sequential float32 evaluation with IEEE square root and no fused
+ * multiply-add (arithmetic order:
+ *     s2 = ((dD*sD)^2 + (dH*sH)^2) + (dW*sW)^2, t = (1-lambda)*s2,
+ *     di2 = sum over channels (in order) of (I(x)-I(y))^2,
+ *     c = sqrt(t + lambda*di2), cand = D[y] + c).
+ *
+ * Conventions for every entry point:
+ *  - Tensors are caller-owned, device-resident, float32, contiguous:
+ *    image [B][C][H][W] or [B][C][D][H][W]; mask and dist [B][1][...].
+ *  - The library never allocates device memory.  Entry points that need
+ *    scratch take a caller-owned `workspace` whose size comes from the
+ *    matching *_workspace_size query; its first 256 bytes hold a device
+ *    status word (see fgx_workspace_status).
+ *  - Calls are asynchronous on `stream` (a cudaStream_t; NULL = legacy
+ *    default stream).  The returned status covers argument checks and launch
+ *    errors only; a device-side timeout is reported by fgx_workspace_status
+ *    after the caller synchronises.
+ *  - dist may alias mask (computed in place); dist must not alias image.
+ *  - Inputs must be finite, mask values >= +0 (no -0.0), v > 0 finite,
+ *    0 <= lambda <= 1, iterations >= 0 (0 returns v * M), and squared
+ *    intensity differences must not overflow float32; results for other
+ *    inputs are undefined.
+ *  - Host pointers, null pointers and bad sizes are rejected before any
+ *    launch, with the codes below.
+ */
+#ifndef FGX_H
+#define FGX_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum fgx_status {
+    FGX_OK = 0,
+    FGX_ERR_ARG = -1,             /* null pointer, bad scalar, bad option      */
+    FGX_ERR_NOT_DEVICE_PTR = -2,  /* a tensor pointer is not device memory     */
+    FGX_ERR_SHAPE = -3,           /* negative or unsupported extent            */
+    FGX_ERR_WORKSPACE = -4,       /* workspace/saved buffer missing or small   */
+    FGX_ERR_CUDA = -5,            /* a CUDA runtime call or launch failed      */
+    FGX_ERR_TIMEOUT = -6,         /* (device status) an inter-block wait gave up */
+    FGX_ERR_DEVICE = -7,          /* no usable sm_103 device                   */
+    FGX_ERR_UNSUPPORTED = -8      /* valid request this build does not serve   */
+} fgx_status;
+
+/* Optional tuning knobs; pass NULL for defaults.  `size` must equal
+ * sizeof(fgx_options) (forward compatibility). */
+typedef struct fgx_options {
+    uint32_t size;
+    int32_t tile_lines;   /* lines per exchange block (ring width); 0 = auto */
+    int32_t tile_width;   /* elements per tile along the inner in-line axis; 0 = auto */
+    int32_t tile_height;  /* 3D: elements per tile along the outer in-line axis; 0 = auto */
+    int32_t max_blocks;   /* cap on resident thread blocks; 0 = all that fit */
+    int32_t timeout_ms;   /* inter-block wait limit; 0 = 2000 ms */
+} fgx_options;
+
+/* Human-readable name of a status code (static string). */
+const char* fgx_status_string(int status);
+
+/* Library version as major*10000 + minor*100 + patch. */
+int fgx_version(void);
+
+/* ------------------------------------------------------------ forward ---- */
+
+/* Scratch bytes needed by fgx_geodesic2d / fgx_geodesic3d for this shape
+ * (2D: D = 1, ndim = 2).  Writes *bytes; returns a status. */
+int fgx_geodesic_workspace_size(int ndim, int64_t B, int64_t C, int64_t D, int64_t H, int64_t W,
+                                const fgx_options* opt, size_t* bytes);
+
+/* 2D transform of B images (unit spacing).  image [B][C][H][W], mask and
+ * dist [B][1][H][W].  Four passes per iteration (Implementation section). */
+int fgx_geodesic2d(const float* image, const float* mask, float* dist, int64_t B, int64_t C,
+                   int64_t H, int64_t W, float v, float lambda, int iterations,
+                   void* workspace, size_t workspace_bytes, const fgx_options* opt,
+                   void* stream);
+
+/* 3D transform of B volumes.  image [B][C][D][H][W], mask and dist
+ * [B][1][D][H][W]; spacing = (sD, sH, sW) > 0, read from host memory.  Six
+ * passes per iteration (Implementation section). */
+int fgx_geodesic3d(const float* image, const float* mask, float* dist, int64_t B, int64_t C,
+                   int64_t D, int64_t H, int64_t W, const float spacing[3], float v,
+                   float lambda, int iterations, void* workspace, size_t workspace_bytes,
+                   const fgx_options* opt, void* stream);
+
+/* Device status word held in a workspace: copies it to the host on `stream`,
+ * synchronises the stream, and returns FGX_OK or the recorded device error
+ * (FGX_ERR_TIMEOUT).  Returns FGX_ERR_CUDA if the copy fails. */
+int fgx_workspace_status(const void* workspace, void* stream);
+
+/* ------------------------------------------------------------ batched ---- */
+
+/* One instance of a batched call (B = 1 per instance).  Pointers are device
+ * memory; shapes may differ between instances. */
+typedef struct fgx_instance {
+    int32_t ndim;        /* 2 or 3                                   */
+    int32_t channels;    /* C >= 1                                    */
+    int64_t D, H, W;     /* 2D: D = 1                                 */
+    const float* image;  /* [C][D][H][W]                              */
+    const float* mask;   /* [D][H][W]                                 */
+    float* dist;         /* [D][H][W]                                 */
+    float spacing[3];    /* (sD, sH, sW); 2D uses (1, 1, 1)           */
+    float v, lambda;
+    int32_t iterations;
+} fgx_instance;
+
+int fgx_batched_workspace_size(const fgx_instance* items, int n, const fgx_options* opt,
+                               size_t* bytes);
+
+/* All instances in one persistent launch driven by a work list of
+ * (instance, pass, line tile) items; results equal n separate calls. */
+int fgx_geodesic_batched(const fgx_instance* items, int n, void* workspace,
+                         size_t workspace_bytes, const fgx_options* opt, void* stream);
+
+/* ----------------------------------------------------- differentiable ---- */
+
+/* Bytes of the `saved` buffer written by the training forward and read by
+ * the backward: one parent code byte per element per pass application,
+ * layout [iterations * passes][B][D*H*W] (code 0 = kept its value, k + 1 =
+ * offset k of the pass stencil, offsets numbered row-major over the in-line
+ * axes taken in (D, H, W) order). */
+int fgx_train_saved_size(int ndim, int64_t B, int64_t D, int64_t H, int64_t W, int iterations,
+                         size_t* bytes);
+
+/* Forward that also records the parent codes into `saved`.  Same arguments
+ * as fgx_geodesic2d / fgx_geodesic3d plus the saved buffer. */
+int fgx_geodesic2d_fwd_train(const float* image, const float* mask, float* dist, int64_t B,
+                             int64_t C, int64_t H, int64_t W, float v, float lambda,
+                             int iterations, void* saved, size_t saved_bytes, void* workspace,
+                             size_t workspace_bytes, const fgx_options* opt, void* stream);
+int fgx_geodesic3d_fwd_train(const float* image, const float* mask, float* dist, int64_t B,
+                             int64_t C, int64_t D, int64_t H, int64_t W,
+                             const float spacing[3], float v, float lambda, int iterations,
+                             void* saved, size_t saved_bytes, void* workspace,
+                             size_t workspace_bytes, const fgx_options* opt, void* stream);
+
+/* Scratch bytes for the backward (adjoint G buffer and status). */
+int fgx_backward_workspace_size(int ndim, int64_t B, int64_t C, int64_t D, int64_t H, int64_t W,
+                                const fgx_options* opt, size_t* bytes);
+
+/* Reverse sweep through the recorded codes: pass applications in reverse,
+ * lines in reverse sweep order; each element with a parent pushes its
+ * adjoint into the parent and adds lambda*(I(x)-I(p))/c times it to the
+ * image gradient (0 where c = 0); dL/dM = v * G at the end.  grad_image
+ * [B][C][...] and grad_mask [B][1][...] may each be NULL.  Results are
+ * bit-exact to the sequential float32 order: a parent gathers its children in
+ * offset order, and an element's image gradient receives its parent-side
+ * terms before its own child-side term in each pass. */
+int fgx_geodesic2d_bwd(const float* grad_dist, const float* image, const void* saved,
+                       size_t saved_bytes, float* grad_image, float* grad_mask, int64_t B,
+                       int64_t C, int64_t H, int64_t W, float v, float lambda, int iterations,
+                       void* workspace, size_t workspace_bytes, const fgx_options* opt,
+                       void* stream);
+int fgx_geodesic3d_bwd(const float* grad_dist, const float* image, const void* saved,
+                       size_t saved_bytes, float* grad_image, float* grad_mask, int64_t B,
+                       int64_t C, int64_t D, int64_t H, int64_t W, const float spacing[3],
+                       float v, float lambda, int iterations, void* workspace,
+                       size_t workspace_bytes, const fgx_options* opt, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FGX_H */

@@ -1,0 +1,261 @@
+"""GB300-native generalised geodesic distance transform by raster-scan passes.
+
+Thin Python binding over the C ABI of ``libfgx_gb300.so`` (``include/fgx.h``):
+argument marshalling only.  Every step of the transform runs in the library's
+CUDA kernels; PyTorch supplies device memory and the current stream.  There is
+no CPU path: if the library is missing, every call raises.
+
+Method (FastGeodis, Implementation section; generalised GDT of the Summary):
+D0 = v*M, then 4 (2D) or 6 (3D) directional passes per iteration, each
+updating a line from the already-updated previous line with cost
+sqrt((1-lambda)*|x-y|^2_spacing + lambda*|I(x)-I(y)|^2).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libfgx_gb300.so")
+
+OK = 0
+ERR_ARG = -1
+ERR_NOT_DEVICE_PTR = -2
+ERR_SHAPE = -3
+ERR_WORKSPACE = -4
+ERR_CUDA = -5
+ERR_TIMEOUT = -6
+ERR_DEVICE = -7
+ERR_UNSUPPORTED = -8
+
+_lock = threading.Lock()
+_lib = None
+
+
+class FgxError(RuntimeError):
+    def __init__(self, status, where):
+        self.status = status
+        super().__init__(f"{where}: {status_string(status)} ({status})")
+
+
+class Options(ctypes.Structure):
+    """fgx_options: optional tuning knobs (0 = automatic)."""
+    _fields_ = [("size", ctypes.c_uint32), ("tile_lines", ctypes.c_int32),
+                ("tile_width", ctypes.c_int32), ("tile_height", ctypes.c_int32),
+                ("max_blocks", ctypes.c_int32), ("timeout_ms", ctypes.c_int32)]
+
+    def __init__(self, tile_lines=0, tile_width=0, tile_height=0, max_blocks=0, timeout_ms=0):
+        super().__init__(ctypes.sizeof(Options), tile_lines, tile_width, tile_height, max_blocks,
+                         timeout_ms)
+
+
+class Instance(ctypes.Structure):
+    """fgx_instance: one entry of a batched call."""
+    _fields_ = [("ndim", ctypes.c_int32), ("channels", ctypes.c_int32), ("D", ctypes.c_int64),
+                ("H", ctypes.c_int64), ("W", ctypes.c_int64), ("image", ctypes.c_void_p),
+                ("mask", ctypes.c_void_p), ("dist", ctypes.c_void_p),
+                ("spacing", ctypes.c_float * 3), ("v", ctypes.c_float),
+                ("lambda_", ctypes.c_float), ("iterations", ctypes.c_int32)]
+
+
+_i64, _i32, _f32, _vp, _sz = (ctypes.c_int64, ctypes.c_int, ctypes.c_float, ctypes.c_void_p,
+                              ctypes.c_size_t)
+_SIGS = {
+    "fgx_status_string": ([_i32], ctypes.c_char_p),
+    "fgx_version": ([], _i32),
+    "fgx_geodesic_workspace_size": ([_i32, _i64, _i64, _i64, _i64, _i64, _vp,
+                                     ctypes.POINTER(_sz)], _i32),
+    "fgx_geodesic2d": ([_vp, _vp, _vp, _i64, _i64, _i64, _i64, _f32, _f32, _i32, _vp, _sz, _vp,
+                        _vp], _i32),
+    "fgx_geodesic3d": ([_vp, _vp, _vp, _i64, _i64, _i64, _i64, _i64, _vp, _f32, _f32, _i32, _vp,
+                        _sz, _vp, _vp], _i32),
+    "fgx_workspace_status": ([_vp, _vp], _i32),
+    "fgx_batched_workspace_size": ([_vp, _i32, _vp, ctypes.POINTER(_sz)], _i32),
+    "fgx_geodesic_batched": ([_vp, _i32, _vp, _sz, _vp, _vp], _i32),
+    "fgx_train_saved_size": ([_i32, _i64, _i64, _i64, _i64, _i32, ctypes.POINTER(_sz)], _i32),
+    "fgx_geodesic2d_fwd_train": ([_vp, _vp, _vp, _i64, _i64, _i64, _i64, _f32, _f32, _i32, _vp,
+                                  _sz, _vp, _sz, _vp, _vp], _i32),
+    "fgx_geodesic3d_fwd_train": ([_vp, _vp, _vp, _i64, _i64, _i64, _i64, _i64, _vp, _f32, _f32,
+                                  _i32, _vp, _sz, _vp, _sz, _vp, _vp], _i32),
+    "fgx_backward_workspace_size": ([_i32, _i64, _i64, _i64, _i64, _i64, _vp,
+                                     ctypes.POINTER(_sz)], _i32),
+    "fgx_geodesic2d_bwd": ([_vp, _vp, _vp, _sz, _vp, _vp, _i64, _i64, _i64, _i64, _f32, _f32,
+                            _i32, _vp, _sz, _vp, _vp], _i32),
+    "fgx_geodesic3d_bwd": ([_vp, _vp, _vp, _sz, _vp, _vp, _i64, _i64, _i64, _i64, _i64, _vp,
+                            _f32, _f32, _i32, _vp, _sz, _vp, _vp], _i32),
+}
+
+
+def lib():
+    """Loads the CUDA library (built by ``build.build()``); raises if absent."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError(
+                    f"CUDA library not built: {LIB_PATH} is missing; run "
+                    "paper_2208_00001_gb300.build.build() (there is no CPU fallback)")
+            L = ctypes.CDLL(LIB_PATH)
+            for name, (args, res) in _SIGS.items():
+                f = getattr(L, name)
+                f.argtypes = args
+                f.restype = res
+            _lib = L
+    return _lib
+
+
+def status_string(status: int) -> str:
+    return lib().fgx_status_string(int(status)).decode()
+
+
+def _check(st, where):
+    if st != OK:
+        raise FgxError(st, where)
+
+
+def _stream():
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else None
+
+
+def _opt(options):
+    if options is None:
+        return None
+    if isinstance(options, dict):
+        options = Options(**options)
+    return ctypes.byref(options)
+
+
+def _check_tensor(t, name):
+    if not isinstance(t, torch.Tensor):
+        raise TypeError(f"{name} must be a torch.Tensor")
+    if not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor (there is no CPU path)")
+    if t.dtype != torch.float32:
+        raise TypeError(f"{name} must be float32")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+
+
+def _shape(image, mask, ndim):
+    _check_tensor(image, "image")
+    _check_tensor(mask, "mask")
+    if image.dim() != ndim + 2 or mask.dim() != ndim + 2:
+        raise ValueError(f"expected {ndim + 2}-d image and mask")
+    B, C = image.shape[:2]
+    if mask.shape[0] != B or mask.shape[1] != 1 or mask.shape[2:] != image.shape[2:]:
+        raise ValueError(f"mask shape {tuple(mask.shape)} does not match image "
+                         f"{tuple(image.shape)}")
+    if image.device != mask.device:
+        raise ValueError("image and mask on different devices")
+    spatial = tuple(image.shape[2:])
+    if ndim == 2:
+        return B, C, 1, spatial[0], spatial[1]
+    return (B, C) + spatial
+
+
+def workspace_size(ndim, B, C, D, H, W, options=None):
+    n = ctypes.c_size_t(0)
+    _check(lib().fgx_geodesic_workspace_size(ndim, B, C, D, H, W, _opt(options),
+                                             ctypes.byref(n)), "workspace size")
+    return n.value
+
+
+def workspace_status(ws):
+    """Synchronises the current stream and returns the device status word."""
+    return lib().fgx_workspace_status(_ptr(ws), _stream())
+
+
+def _workspace(nbytes, device):
+    return torch.empty(max(int(nbytes), 256), dtype=torch.uint8, device=device)
+
+
+def geodesic2d(image, mask, v, lam, iterations, out=None, options=None, workspace=None,
+               check=False):
+    """2D transform.  image (B,C,H,W), mask (B,1,H,W), float32 CUDA tensors.
+    Returns dist (B,1,H,W).  check=True synchronises and raises on a device
+    timeout."""
+    B, C, D, H, W = _shape(image, mask, 2)
+    dev = image.device
+    with torch.cuda.device(dev):
+        if out is None:
+            out = torch.empty_like(mask)
+        ws = workspace if workspace is not None else _workspace(
+            workspace_size(2, B, C, 1, H, W, options), dev)
+        _check(lib().fgx_geodesic2d(_ptr(image), _ptr(mask), _ptr(out), B, C, H, W, float(v),
+                                    float(lam), int(iterations), _ptr(ws), ws.numel(),
+                                    _opt(options), _stream()), "fgx_geodesic2d")
+        if check:
+            _check(workspace_status(ws), "fgx_geodesic2d (device)")
+    return out
+
+
+def _spacing(spacing):
+    sp = (ctypes.c_float * 3)(*[float(s) for s in (spacing or (1.0, 1.0, 1.0))])
+    return sp
+
+
+def geodesic3d(image, mask, spacing, v, lam, iterations, out=None, options=None, workspace=None,
+               check=False):
+    """3D transform.  image (B,C,D,H,W), mask (B,1,D,H,W); spacing (sD,sH,sW)."""
+    B, C, D, H, W = _shape(image, mask, 3)
+    dev = image.device
+    with torch.cuda.device(dev):
+        if out is None:
+            out = torch.empty_like(mask)
+        ws = workspace if workspace is not None else _workspace(
+            workspace_size(3, B, C, D, H, W, options), dev)
+        _check(lib().fgx_geodesic3d(_ptr(image), _ptr(mask), _ptr(out), B, C, D, H, W,
+                                    _spacing(spacing), float(v), float(lam), int(iterations),
+                                    _ptr(ws), ws.numel(), _opt(options), _stream()),
+               "fgx_geodesic3d")
+        if check:
+            _check(workspace_status(ws), "fgx_geodesic3d (device)")
+    return out
+
+
+def geodesic(image, mask, v, lam, iterations, spacing=None, **kw):
+    """Dispatches on the image rank: (B,C,H,W) -> 2D, (B,C,D,H,W) -> 3D."""
+    if image.dim() == 4:
+        return geodesic2d(image, mask, v, lam, iterations, **kw)
+    return geodesic3d(image, mask, spacing, v, lam, iterations, **kw)
+
+
+def saved_size(ndim, B, D, H, W, iterations):
+    n = ctypes.c_size_t(0)
+    _check(lib().fgx_train_saved_size(ndim, B, D, H, W, iterations, ctypes.byref(n)),
+           "saved size")
+    return n.value
+
+
+def forward_train(image, mask, v, lam, iterations, spacing=None, options=None, check=False):
+    """Forward that records parent codes.  Returns (dist, saved uint8 tensor
+    [iterations*passes, B, D*H*W])."""
+    ndim = image.dim() - 2
+    B, C, D, H, W = _shape(image, mask, ndim)
+    dev = image.device
+    npass = 6 if ndim == 3 else 4
+    with torch.cuda.device(dev):
+        dist = torch.empty_like(mask)
+        saved = torch.empty((iterations * npass, B, D * H * W), dtype=torch.uint8, device=dev)
+        ws = _workspace(workspace_size(ndim, B, C, D, H, W, options), dev)
+        if ndim == 2:
+            st = lib().fgx_geodesic2d_fwd_train(_ptr(image), _ptr(mask), _ptr(dist), B, C, H, W,
+                                                float(v), float(lam), int(iterations),
+                                                _ptr(saved), saved.numel(), _ptr(ws), ws.numel(),
+                                                _opt(options), _stream())
+        else:
+            st = lib().fgx_geodesic3d_fwd_train(_ptr(image), _ptr(mask), _ptr(dist), B, C, D, H,
+                                                W, _spacing(spacing), float(v), float(lam),
+                                                int(iterations), _ptr(saved), saved.numel(),
+                                                _ptr(ws), ws.numel(), _opt(options), _stream())
+        _check(st, "forward_train")
+        if check:
+            _check(workspace_status(ws), "forward_train (device)")
+    return dist, saved

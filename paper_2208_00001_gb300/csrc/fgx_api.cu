@@ -1,0 +1,347 @@
+// C ABI entry points (include/fgx.h): argument checks, planning of the pass
+// geometry and tiling, workspace layout, launches.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+
+#include "fgx_internal.h"
+
+namespace fgx {
+
+// The paper's pass order (Implementation section): 2D top-bottom,
+// bottom-top, left-right, right-left; 3D front-back, back-front, then the 2D
+// order.  Axis 0 = D, 1 = H, 2 = W.
+static const int kSched2D[4][2] = {{1, +1}, {1, -1}, {2, +1}, {2, -1}};
+static const int kSched3D[6][2] = {{0, +1}, {0, -1}, {1, +1}, {1, -1}, {2, +1}, {2, -1}};
+
+// t_k = (1 - lambda) * s2_k with s2_k = ((dD sD)^2 + (dH sH)^2) + (dW sW)^2 for
+// the stencil offsets of a pass, numbered row-major over the in-line axes
+// (outer p, inner q, in (D, H, W) order); the pass-axis component is 1.
+// Each product and sum is rounded to float separately: the volatile
+// temporaries keep the host compiler from fusing or widening them (the
+// library is also compiled with -ffp-contract=off).
+void pass_offsets_t(int ndim, int axis, const float sp[3], float lambda, float t[9]) {
+    int pa, qa;
+    if (axis == 0) { pa = 1; qa = 2; } else if (axis == 1) { pa = 0; qa = 2; } else { pa = 0; qa = 1; }
+    const int dpmin = ndim == 3 ? -1 : 0, dpmax = ndim == 3 ? 1 : 0;
+    int k = 0;
+    for (int dp = dpmin; dp <= dpmax; ++dp) {
+        for (int dq = -1; dq <= 1; ++dq) {
+            float delta[3] = {0.f, 0.f, 0.f};
+            delta[axis] = 1.f;
+            delta[pa] = (float)dp;
+            delta[qa] = (float)dq;
+            volatile float e0 = delta[0] * sp[0], e1 = delta[1] * sp[1], e2 = delta[2] * sp[2];
+            volatile float a0 = e0 * e0, a1 = e1 * e1, a2 = e2 * e2;
+            volatile float s01 = a0 + a1;
+            volatile float s2 = s01 + a2;
+            volatile float om = 1.0f - lambda;
+            t[k++] = om * s2;
+        }
+    }
+    for (; k < 9; ++k) t[k] = 0.f;
+}
+
+void pass_extents(int axis, const int64_t ext[3], PassGeom* g) {
+    const int64_t st[3] = {ext[1] * ext[2], ext[2], 1};
+    int pa, qa;
+    if (axis == 0) { pa = 1; qa = 2; } else if (axis == 1) { pa = 0; qa = 2; } else { pa = 0; qa = 1; }
+    g->axis = axis;
+    g->L = ext[axis];
+    g->P = ext[pa];
+    g->Q = ext[qa];
+    g->sl = st[axis];
+    g->sp = st[pa];
+    g->sq = st[qa];
+}
+
+namespace {
+
+struct DeviceInfo {
+    int dev = -1, sms = 0, ok = 0;
+};
+
+int current_device(DeviceInfo* info) {
+    static DeviceInfo cache[64];
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return FGX_ERR_DEVICE;
+    if (dev < 0 || dev >= 64) return FGX_ERR_DEVICE;
+    if (cache[dev].dev != dev) {
+        int major = 0, minor = 0, sms = 0;
+        if (cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+            return FGX_ERR_DEVICE;
+        cache[dev].sms = sms;
+        cache[dev].ok = (major == 10 && minor == 3);
+        cache[dev].dev = dev;
+    }
+    *info = cache[dev];
+    return info->ok ? FGX_OK : FGX_ERR_DEVICE;
+}
+
+bool is_device_ptr(const void* p) {
+    if (!p) return false;
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+bool overlaps(const void* a, size_t na, const void* b, size_t nb) {
+    const char* x = (const char*)a;
+    const char* y = (const char*)b;
+    return x < y + nb && y < x + na;
+}
+
+bool finite_pos(float x) { return std::isfinite(x) && x > 0.f; }
+
+// Plan of one forward call.
+struct Plan {
+    SweepArgs args;
+    int grid = 0;
+    size_t smem = 0;
+    size_t ws_bytes = 0;
+};
+
+int plan_forward(int ndim, int64_t B, int64_t C, int64_t D, int64_t H, int64_t W,
+                 const float spacing[3], float lambda, int iterations, const fgx_options* opt,
+                 Plan* pl) {
+    if (opt && opt->size != sizeof(fgx_options)) return FGX_ERR_ARG;
+    if (opt && (opt->tile_lines < 0 || opt->tile_width < 0 || opt->tile_height < 0 ||
+                opt->max_blocks < 0 || opt->timeout_ms < 0))
+        return FGX_ERR_ARG;
+    if (ndim != 2 && ndim != 3) return FGX_ERR_ARG;
+    if (B < 0 || C < 1 || D < 0 || H < 0 || W < 0) return FGX_ERR_SHAPE;
+    if (ndim == 2 && D != 1) return FGX_ERR_SHAPE;
+    if (C > 64) return FGX_ERR_UNSUPPORTED;
+    DeviceInfo dev;
+    int st = current_device(&dev);
+    if (st != FGX_OK) return st;
+    SweepArgs& a = pl->args;
+    std::memset(&a, 0, sizeof(a));
+    a.B = B;
+    a.C = C;
+    a.N = D * H * W;
+    a.ndim = ndim;
+    a.lambda = lambda;
+    a.iterations = iterations;
+    a.npass = ndim == 3 ? 6 : 4;
+    a.timeout_ns = (long long)((opt && opt->timeout_ms) ? opt->timeout_ms : 2000) * 1000000LL;
+    const int64_t ext[3] = {D, H, W};
+    const float unit[3] = {1.f, 1.f, 1.f};
+    const float* sp = ndim == 3 ? spacing : unit;
+    int max_tiles = 1;
+    int64_t region = 1;
+    for (int i = 0; i < a.npass; ++i) {
+        PassGeom& g = a.pass[i];
+        const int axis = ndim == 3 ? kSched3D[i][0] : kSched2D[i][0];
+        g.dir = ndim == 3 ? kSched3D[i][1] : kSched2D[i][1];
+        pass_extents(axis, ext, &g);
+        pass_offsets_t(ndim, axis, sp, lambda, g.t);
+        int K = (opt && opt->tile_lines) ? opt->tile_lines : (ndim == 3 ? 4 : 32);
+        int tq = (opt && opt->tile_width) ? opt->tile_width : (ndim == 3 ? 16 : 256);
+        int tp = ndim == 3 ? ((opt && opt->tile_height) ? opt->tile_height : 16) : 1;
+        tq = (int)std::max<int64_t>(1, std::min<int64_t>(tq, std::max<int64_t>(g.Q, 1)));
+        tp = (int)std::max<int64_t>(1, std::min<int64_t>(tp, std::max<int64_t>(g.P, 1)));
+        // a ring must lie within the neighbouring tiles: full tiles are >= K
+        if (g.Q > tq) K = std::min(K, tq);
+        if (g.P > tp) K = std::min(K, tp);
+        K = std::max(1, K);
+        g.K = K;
+        g.tp = tp;
+        g.tq = tq;
+        g.ntp = (int)std::max<int64_t>(1, (g.P + tp - 1) / tp);
+        g.ntq = (int)std::max<int64_t>(1, (g.Q + tq - 1) / tq);
+        max_tiles = std::max(max_tiles, g.ntp * g.ntq);
+        const int64_t rp = std::min<int64_t>(std::max<int64_t>(g.P, 1), tp + 2 * K);
+        const int64_t rq = std::min<int64_t>(std::max<int64_t>(g.Q, 1), tq + 2 * K);
+        region = std::max(region, rp * rq);
+    }
+    a.max_tiles = max_tiles;
+    a.smem_region = (int)region;
+    pl->smem = (size_t)(2 + 2 * C) * (size_t)region * sizeof(float);
+    if (pl->smem > 200 * 1024) return FGX_ERR_UNSUPPORTED;
+    int per_sm = 0;
+    st = sweep_max_blocks_per_sm(pl->smem, &per_sm);
+    if (st != FGX_OK) return st;
+    if (per_sm < 1) return FGX_ERR_UNSUPPORTED;
+    int64_t grid = (int64_t)per_sm * dev.sms;
+    if (opt && opt->max_blocks) grid = std::min<int64_t>(grid, opt->max_blocks);
+    grid = std::min<int64_t>(grid, std::max<int64_t>(1, B * max_tiles));
+    if (grid < max_tiles) return FGX_ERR_UNSUPPORTED;  // a pass's tiles must be co-resident
+    pl->grid = (int)grid;
+    pl->ws_bytes = kHeaderBytes + (size_t)std::max<int64_t>(B, 1) * max_tiles * 8;
+    return FGX_OK;
+}
+
+int run_forward(int ndim, const float* image, const float* mask, float* dist, int64_t B, int64_t C,
+                int64_t D, int64_t H, int64_t W, const float spacing[3], float v, float lambda,
+                int iterations, uint8_t* codes, size_t codes_bytes, void* workspace,
+                size_t ws_bytes, const fgx_options* opt, void* stream) {
+    if (!(std::isfinite(v) && v > 0.f)) return FGX_ERR_ARG;
+    if (!(lambda >= 0.f && lambda <= 1.f)) return FGX_ERR_ARG;
+    if (iterations < 0) return FGX_ERR_ARG;
+    if (ndim == 3) {
+        if (!spacing) return FGX_ERR_ARG;
+        for (int i = 0; i < 3; ++i)
+            if (!finite_pos(spacing[i])) return FGX_ERR_ARG;
+    }
+    Plan pl;
+    int st = plan_forward(ndim, B, C, D, H, W, spacing, lambda, iterations, opt, &pl);
+    if (st != FGX_OK) return st;
+    const int64_t N = D * H * W;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (B * N == 0) {
+        // nothing to compute; still leave a clean status word for the caller
+        if (workspace && ws_bytes >= sizeof(int) && is_device_ptr(workspace) &&
+            cudaMemsetAsync(workspace, 0, std::min(ws_bytes, kHeaderBytes), s) != cudaSuccess)
+            return FGX_ERR_CUDA;
+        return FGX_OK;
+    }
+    if (!image || !mask || !dist) return FGX_ERR_ARG;
+    if (!is_device_ptr(image) || !is_device_ptr(mask) || !is_device_ptr(dist))
+        return FGX_ERR_NOT_DEVICE_PTR;
+    const size_t nb = (size_t)(B * N) * sizeof(float);
+    if (overlaps(dist, nb, image, (size_t)(B * C * N) * sizeof(float))) return FGX_ERR_ARG;
+    if (!workspace || ws_bytes < pl.ws_bytes) return FGX_ERR_WORKSPACE;
+    if (!is_device_ptr(workspace)) return FGX_ERR_NOT_DEVICE_PTR;
+    const size_t need_codes = (size_t)iterations * pl.args.npass * (size_t)(B * N);
+    if (codes) {
+        if (codes_bytes < need_codes) return FGX_ERR_WORKSPACE;
+        if (!is_device_ptr(codes)) return FGX_ERR_NOT_DEVICE_PTR;
+    }
+    SweepArgs& a = pl.args;
+    a.image = image;
+    a.mask = mask;
+    a.dist = dist;
+    a.v = v;
+    a.codes = codes;
+    a.status = (int*)workspace;
+    a.barrier = (unsigned int*)((char*)workspace + 64);
+    a.flags = (unsigned long long*)((char*)workspace + kHeaderBytes);
+    if (cudaMemsetAsync(workspace, 0, pl.ws_bytes, s) != cudaSuccess) return FGX_ERR_CUDA;
+    if (codes && need_codes && cudaMemsetAsync(codes, 0, need_codes, s) != cudaSuccess)
+        return FGX_ERR_CUDA;
+    return launch_sweep(a, pl.grid, pl.smem, stream);
+}
+
+}  // namespace
+}  // namespace fgx
+
+using namespace fgx;
+
+extern "C" {
+
+const char* fgx_status_string(int status) {
+    switch (status) {
+        case FGX_OK: return "ok";
+        case FGX_ERR_ARG: return "invalid argument";
+        case FGX_ERR_NOT_DEVICE_PTR: return "pointer is not device memory";
+        case FGX_ERR_SHAPE: return "invalid shape";
+        case FGX_ERR_WORKSPACE: return "workspace missing or too small";
+        case FGX_ERR_CUDA: return "CUDA runtime error";
+        case FGX_ERR_TIMEOUT: return "device wait timed out";
+        case FGX_ERR_DEVICE: return "no usable sm_103 device";
+        case FGX_ERR_UNSUPPORTED: return "unsupported request";
+        default: return "unknown status";
+    }
+}
+
+int fgx_version(void) { return 100; }
+
+int fgx_geodesic_workspace_size(int ndim, int64_t B, int64_t C, int64_t D, int64_t H, int64_t W,
+                                const fgx_options* opt, size_t* bytes) {
+    if (!bytes) return FGX_ERR_ARG;
+    const float unit[3] = {1.f, 1.f, 1.f};
+    Plan pl;
+    int st = plan_forward(ndim, B, C, D, H, W, unit, 0.5f, 1, opt, &pl);
+    if (st != FGX_OK) return st;
+    *bytes = pl.ws_bytes;
+    return FGX_OK;
+}
+
+int fgx_geodesic2d(const float* image, const float* mask, float* dist, int64_t B, int64_t C,
+                   int64_t H, int64_t W, float v, float lambda, int iterations, void* workspace,
+                   size_t workspace_bytes, const fgx_options* opt, void* stream) {
+    return run_forward(2, image, mask, dist, B, C, 1, H, W, nullptr, v, lambda, iterations,
+                       nullptr, 0, workspace, workspace_bytes, opt, stream);
+}
+
+int fgx_geodesic3d(const float* image, const float* mask, float* dist, int64_t B, int64_t C,
+                   int64_t D, int64_t H, int64_t W, const float spacing[3], float v,
+                   float lambda, int iterations, void* workspace, size_t workspace_bytes,
+                   const fgx_options* opt, void* stream) {
+    return run_forward(3, image, mask, dist, B, C, D, H, W, spacing, v, lambda, iterations,
+                       nullptr, 0, workspace, workspace_bytes, opt, stream);
+}
+
+int fgx_workspace_status(const void* workspace, void* stream) {
+    if (!workspace) return FGX_ERR_ARG;
+    int h = 0;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (cudaMemcpyAsync(&h, workspace, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess)
+        return FGX_ERR_CUDA;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return FGX_ERR_CUDA;
+    return h;
+}
+
+int fgx_train_saved_size(int ndim, int64_t B, int64_t D, int64_t H, int64_t W, int iterations,
+                         size_t* bytes) {
+    if (!bytes) return FGX_ERR_ARG;
+    if (ndim != 2 && ndim != 3) return FGX_ERR_ARG;
+    if (B < 0 || D < 0 || H < 0 || W < 0 || iterations < 0) return FGX_ERR_SHAPE;
+    if (ndim == 2 && D != 1) return FGX_ERR_SHAPE;
+    *bytes = (size_t)iterations * (ndim == 3 ? 6 : 4) * (size_t)(B * D * H * W);
+    return FGX_OK;
+}
+
+int fgx_geodesic2d_fwd_train(const float* image, const float* mask, float* dist, int64_t B,
+                             int64_t C, int64_t H, int64_t W, float v, float lambda,
+                             int iterations, void* saved, size_t saved_bytes, void* workspace,
+                             size_t workspace_bytes, const fgx_options* opt, void* stream) {
+    if (!saved && (size_t)iterations * B * H * W > 0) return FGX_ERR_WORKSPACE;
+    return run_forward(2, image, mask, dist, B, C, 1, H, W, nullptr, v, lambda, iterations,
+                       (uint8_t*)saved, saved_bytes, workspace, workspace_bytes, opt, stream);
+}
+
+int fgx_geodesic3d_fwd_train(const float* image, const float* mask, float* dist, int64_t B,
+                             int64_t C, int64_t D, int64_t H, int64_t W,
+                             const float spacing[3], float v, float lambda, int iterations,
+                             void* saved, size_t saved_bytes, void* workspace,
+                             size_t workspace_bytes, const fgx_options* opt, void* stream) {
+    if (!saved && (size_t)iterations * B * D * H * W > 0) return FGX_ERR_WORKSPACE;
+    return run_forward(3, image, mask, dist, B, C, D, H, W, spacing, v, lambda, iterations,
+                       (uint8_t*)saved, saved_bytes, workspace, workspace_bytes, opt, stream);
+}
+
+}  // extern "C"
+
+// Entry points served by later translation units are declared in fgx.h; the
+// ones below are not built yet in this version of the library.
+extern "C" {
+int fgx_batched_workspace_size(const fgx_instance*, int, const fgx_options*, size_t*) {
+    return FGX_ERR_UNSUPPORTED;
+}
+int fgx_geodesic_batched(const fgx_instance*, int, void*, size_t, const fgx_options*, void*) {
+    return FGX_ERR_UNSUPPORTED;
+}
+int fgx_backward_workspace_size(int, int64_t, int64_t, int64_t, int64_t, int64_t,
+                                const fgx_options*, size_t*) {
+    return FGX_ERR_UNSUPPORTED;
+}
+int fgx_geodesic2d_bwd(const float*, const float*, const void*, size_t, float*, float*, int64_t,
+                       int64_t, int64_t, int64_t, float, float, int, void*, size_t,
+                       const fgx_options*, void*) {
+    return FGX_ERR_UNSUPPORTED;
+}
+int fgx_geodesic3d_bwd(const float*, const float*, const void*, size_t, float*, float*, int64_t,
+                       int64_t, int64_t, int64_t, int64_t, const float*, float, float, int, void*,
+                       size_t, const fgx_options*, void*) {
+    return FGX_ERR_UNSUPPORTED;
+}
+}

@@ -1,0 +1,55 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+
+#include "fgx.h"
+
+namespace fgx {
+
+constexpr int kMaxPasses = 6;
+// Workspace header: device status word, grid-barrier counter, padding.
+constexpr size_t kHeaderBytes = 256;
+constexpr int kThreads = 256;
+
+// Geometry of one directional pass over an instance of extents (D, H, W).
+// The pass moves along `axis` (0 = D, 1 = H, 2 = W) in direction `dir`; the
+// in-line axes are the other two in (D, H, W) order: p (outer) and q (inner).
+struct PassGeom {
+    int axis, dir;
+    int64_t L, P, Q;     // number of lines, in-line extents
+    int64_t sl, sp, sq;  // element strides of line, p and q
+    int tp, tq;          // tile extents along p and q
+    int ntp, ntq;        // tiles along p and q
+    int K;               // lines per exchange block (= ring width)
+    float t[9];          // (1 - lambda) * |offset|^2 per stencil offset
+};
+
+struct SweepArgs {
+    const float* image;  // [B][C][N]
+    const float* mask;   // [B][N]
+    float* dist;         // [B][N]
+    int64_t B, C, N;
+    int ndim;
+    float v, lambda;
+    int iterations, npass;
+    PassGeom pass[kMaxPasses];
+    uint8_t* codes;               // nullable: [iterations*npass][B][N]
+    unsigned long long* flags;    // [B][max_tiles] block-progress tags
+    unsigned int* barrier;        // grid barrier counter
+    int* status;                  // device status word
+    long long timeout_ns;
+    int max_tiles;
+    int smem_region;              // floats per (D or I-channel) region buffer
+};
+
+// Host helpers (fgx_plan.cu)
+void pass_offsets_t(int ndim, int axis, const float sp[3], float lambda, float t[9]);
+void pass_extents(int axis, const int64_t ext[3], PassGeom* g);
+
+// Launchers (sweep_kernel.cu)
+int launch_sweep(const SweepArgs& a, int grid, size_t smem, void* stream);
+int sweep_max_blocks_per_sm(size_t smem, int* blocks);
+
+}  // namespace fgx

@@ -1,0 +1,208 @@
+"""Parity of the CUDA forward path with the oracle (GPU).
+
+The bar is bit-exact float32 equality with the sequential oracle (IEEE
+square root, no fused multiply-add), element by element, on the seeded
+workloads at full size and on edge cases: ragged and tiny extents, several
+tiles with rings and inter-tile waits, multi-channel images, every lambda
+regime, zero iterations, in-place use and error paths.
+"""
+import ctypes
+import os
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import workloads
+
+pytestmark = pytest.mark.gpu
+THREADS = os.cpu_count() or 1
+
+
+@pytest.fixture(scope="module")
+def fgx():
+    from paper_2208_00001_gb300 import build
+    build.build()
+    import paper_2208_00001_gb300 as m
+    return m
+
+
+def gpu_run(fgx, case, options=None, out=None):
+    img = torch.from_numpy(case.image).cuda()
+    m = torch.from_numpy(case.mask).cuda()
+    if case.ndim == 2:
+        d = fgx.geodesic2d(img, m, case.v, case.lam, case.iterations, options=options,
+                           check=True, out=out)
+    else:
+        d = fgx.geodesic3d(img, m, case.spacing, case.v, case.lam, case.iterations,
+                           options=options, check=True, out=out)
+    return d.cpu().numpy()
+
+
+def oracle_run(case):
+    return oracle.gdt(case.image, case.mask, case.v, case.lam, case.iterations,
+                      spacing=case.spacing, threads=THREADS)
+
+
+def assert_bit_exact(got, want):
+    assert got.shape == want.shape
+    bad = np.flatnonzero(got.view(np.uint32) != want.view(np.uint32))
+    if bad.size:
+        i = bad[0]
+        raise AssertionError(f"{bad.size} of {got.size} elements differ; first at flat index "
+                             f"{i}: gpu {got.reshape(-1)[i]!r} oracle {want.reshape(-1)[i]!r}")
+
+
+# ---------------------------------------------------------- seeded workloads
+
+def test_plain2d_bit_exact(fgx):
+    case = workloads.plain2d()
+    assert_bit_exact(gpu_run(fgx, case), oracle_run(case))
+
+
+@pytest.mark.parametrize("lam", [0.0, 0.5, 1.0])
+@pytest.mark.parametrize("its", [2, 4])
+def test_large2d_bit_exact(fgx, lam, its):
+    case = workloads.large2d(lam=lam, iterations=its)
+    assert_bit_exact(gpu_run(fgx, case), oracle_run(case))
+
+
+def test_volume3d_bit_exact(fgx):
+    case = workloads.volume3d()
+    assert_bit_exact(gpu_run(fgx, case), oracle_run(case))
+
+
+def test_differentiable_configs_forward_bit_exact(fgx):
+    for case in (workloads.diff2d(), workloads.diff3d()):
+        assert_bit_exact(gpu_run(fgx, case), oracle_run(case))
+
+
+# ------------------------------------------------------------------ edges
+
+SIDES = [1, 2, 31, 32, 33, 127, 129, 1000]
+
+
+@pytest.mark.parametrize("H", SIDES)
+def test_edge_shapes_2d(fgx, H):
+    rng = np.random.default_rng(H)
+    for W in SIDES:
+        if H * W > 200_000:
+            continue
+        C = int(rng.integers(1, 5))
+        lam = [0.0, 0.3, 1.0][int(rng.integers(0, 3))]
+        case = workloads.random_case(rng, 2, (H, W), channels=C, lam=lam,
+                                     iterations=int(rng.integers(1, 3)), soft=bool(H % 2),
+                                     v=1e10 if W % 2 else 7.5)
+        want = oracle_run(case)
+        assert_bit_exact(gpu_run(fgx, case), want)
+        # many small tiles: rings and neighbour waits on every block
+        assert_bit_exact(gpu_run(fgx, case, options=dict(tile_width=8, tile_lines=3)), want)
+
+
+@pytest.mark.parametrize("shape", [(1, 1, 1), (1, 5, 7), (6, 1, 9), (7, 8, 1), (9, 17, 33),
+                                   (33, 31, 2), (16, 40, 24)])
+def test_edge_shapes_3d(fgx, shape):
+    rng = np.random.default_rng(sum(shape))
+    for C, lam in [(1, 1.0), (2, 0.4), (3, 0.0)]:
+        sp = tuple(float(x) for x in rng.uniform(0.5, 3.0, size=3))
+        case = workloads.random_case(rng, 3, shape, channels=C, lam=lam, iterations=2,
+                                     soft=True, v=20.0, spacing=sp)
+        want = oracle_run(case)
+        assert_bit_exact(gpu_run(fgx, case), want)
+        assert_bit_exact(gpu_run(fgx, case, options=dict(tile_width=4, tile_height=3,
+                                                          tile_lines=2)), want)
+
+
+def test_batch_of_images_bit_exact(fgx):
+    rng = np.random.default_rng(7)
+    img = rng.uniform(0, 1, (5, 2, 70, 90)).astype(np.float32)
+    m = rng.uniform(0, 1, (5, 1, 70, 90)).astype(np.float32)
+    m[:, :, 10, 20] = 0
+    case = workloads.Case("batch", img, m, 3.0, 0.6, 3)
+    want = oracle_run(case)
+    assert_bit_exact(gpu_run(fgx, case), want)
+    # few resident blocks: instances run in waves
+    assert_bit_exact(gpu_run(fgx, case, options=dict(tile_width=16, tile_lines=4,
+                                                     max_blocks=12)), want)
+
+
+def test_zero_iterations_returns_v_times_mask(fgx):
+    case = workloads.plain2d(iterations=0)
+    got = gpu_run(fgx, case)
+    assert_bit_exact(got, (np.float32(case.v) * case.mask).astype(np.float32))
+
+
+def test_in_place_on_mask(fgx):
+    case = workloads.plain2d()
+    img = torch.from_numpy(case.image).cuda()
+    m = torch.from_numpy(case.mask).cuda()
+    d = fgx.geodesic2d(img, m, case.v, case.lam, case.iterations, out=m, check=True)
+    assert d.data_ptr() == m.data_ptr()
+    assert_bit_exact(m.cpu().numpy(), oracle_run(case))
+
+
+def test_empty_inputs(fgx):
+    for shape in [(0, 1, 8, 8), (1, 1, 0, 8), (1, 1, 8, 0)]:
+        img = torch.zeros(shape, device="cuda")
+        m = torch.zeros((shape[0], 1) + shape[2:], device="cuda")
+        d = fgx.geodesic2d(img, m, 1.0, 0.5, 2, check=True)
+        assert d.shape == m.shape
+
+
+def test_repeated_calls_are_identical(fgx):
+    case = workloads.volume3d(shape=(40, 50, 60))
+    a = gpu_run(fgx, case)
+    b = gpu_run(fgx, case)
+    assert_bit_exact(a, b)
+
+
+def test_fwd_train_codes_match_oracle(fgx):
+    for case in (workloads.diff2d(batch=2, size=96), workloads.diff3d(shape=(20, 24, 28))):
+        img = torch.from_numpy(case.image).cuda()
+        m = torch.from_numpy(case.mask).cuda()
+        d, saved = fgx.forward_train(img, m, case.v, case.lam, case.iterations,
+                                     spacing=case.spacing, check=True)
+        want_d, want_codes = oracle.gdt(case.image, case.mask, case.v, case.lam,
+                                        case.iterations, spacing=case.spacing,
+                                        return_codes=True, threads=THREADS)
+        assert_bit_exact(d.cpu().numpy(), want_d)
+        np.testing.assert_array_equal(saved.cpu().numpy(), want_codes)
+
+
+# ----------------------------------------------------------------- errors
+
+def test_error_codes(fgx):
+    L = fgx.lib()
+    dev = torch.zeros((1, 1, 8, 8), device="cuda")
+    host = torch.zeros((1, 1, 8, 8))
+    ws = torch.zeros(4096, dtype=torch.uint8, device="cuda")
+    s = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    P = lambda t: ctypes.c_void_p(t.data_ptr())  # noqa: E731
+
+    def call(img, m, d, lam=0.5, v=1.0, its=2, wsb=4096, H=8, W=8):
+        return L.fgx_geodesic2d(P(img), P(m), P(d), 1, 1, H, W, v, lam, its, P(ws), wsb, None, s)
+
+    out = torch.zeros_like(dev)
+    assert call(dev, dev, out) == fgx.OK
+    assert call(host, dev, out) == fgx.ERR_NOT_DEVICE_PTR
+    assert call(dev, dev, out, lam=1.5) == fgx.ERR_ARG
+    assert call(dev, dev, out, lam=float("nan")) == fgx.ERR_ARG
+    assert call(dev, dev, out, v=0.0) == fgx.ERR_ARG
+    assert call(dev, dev, out, v=float("inf")) == fgx.ERR_ARG
+    assert call(dev, dev, out, its=-1) == fgx.ERR_ARG
+    assert call(dev, dev, out, wsb=8) == fgx.ERR_WORKSPACE
+    assert call(dev, dev, dev) == fgx.ERR_ARG  # dist aliases image
+    assert call(dev, dev, out, H=-1) == fgx.ERR_SHAPE
+    assert L.fgx_geodesic2d(None, P(dev), P(out), 1, 1, 8, 8, 1.0, 0.5, 1, P(ws), 4096, None,
+                            s) == fgx.ERR_ARG
+    bad = fgx.Options()
+    bad.size = 3
+    assert L.fgx_geodesic2d(P(dev), P(dev), P(out), 1, 1, 8, 8, 1.0, 0.5, 1, P(ws), 4096,
+                            ctypes.byref(bad), s) == fgx.ERR_ARG
+    sp = (ctypes.c_float * 3)(1.0, 0.0, 1.0)
+    d3 = torch.zeros((1, 1, 2, 8, 8), device="cuda")
+    o3 = torch.zeros_like(d3)
+    assert L.fgx_geodesic3d(P(d3), P(d3), P(o3), 1, 1, 2, 8, 8, sp, 1.0, 0.5, 1, P(ws), 4096,
+                            None, s) == fgx.ERR_ARG
+    torch.cuda.synchronize()
