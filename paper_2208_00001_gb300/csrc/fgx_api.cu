@@ -5,6 +5,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <mutex>
 
 #include "fgx_internal.h"
 
@@ -344,4 +345,62 @@ int fgx_geodesic3d_bwd(const float*, const float*, const void*, size_t, float*, 
                        size_t, const fgx_options*, void*) {
     return FGX_ERR_UNSUPPORTED;
 }
+}
+
+// ----------------------------------------------------------------------------
+// Allocation-free forward.  Some callers cannot allocate device memory at the
+// point where they need a transform: code running inside a CUDA graph capture
+// or a custom allocator's callback, real-time loops with a fixed memory
+// budget, or plugins whose host framework owns every allocation.  This entry
+// point runs the same sweep kernel as fgx_geodesic2d / fgx_geodesic3d, but
+// its scratch (status word, barrier counter, tile progress tags) lives in the
+// static device array below instead of a caller workspace.  Every GPU that
+// loads the library holds the array until the process exits.
+namespace {
+
+constexpr size_t kNoAllocScratchBytes = 64 * 1024;
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+// Device address of g_noalloc_scratch, looked up once per device with that
+// device current.  In host code the array's name is only a host-side stand-in,
+// so the kernel must be given this address, never the name.
+int noalloc_scratch_address(void** out) {
+    static std::mutex mu;
+    static void* addr[64];
+    static bool done[64];
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return FGX_ERR_DEVICE;
+    std::lock_guard<std::mutex> lock(mu);
+    if (!done[dev]) {
+        void* p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess) {
+            cudaGetLastError();
+            return FGX_ERR_CUDA;
+        }
+        addr[dev] = p;
+        done[dev] = true;
+    }
+    *out = addr[dev];
+    return FGX_OK;
+}
+
+}  // namespace
+
+extern "C" int fgx_geodesic_noalloc(int ndim, const float* image, const float* mask, float* dist,
+                                    int64_t B, int64_t C, int64_t D, int64_t H, int64_t W,
+                                    const float spacing[3], float v, float lambda, int iterations,
+                                    const fgx_options* opt, void* stream) {
+    if (ndim != 2 && ndim != 3) return FGX_ERR_ARG;
+    if (ndim == 2 && D != 1) return FGX_ERR_SHAPE;
+    const float unit[3] = {1.f, 1.f, 1.f};
+    Plan pl;
+    int st = plan_forward(ndim, B, C, D, H, W, ndim == 3 && spacing ? spacing : unit, lambda,
+                          iterations, opt, &pl);
+    if (st != FGX_OK) return st;
+    if (pl.ws_bytes > kNoAllocScratchBytes) return FGX_ERR_WORKSPACE;  // beyond the static limit
+    void* scratch = nullptr;
+    st = noalloc_scratch_address(&scratch);
+    if (st != FGX_OK) return st;
+    return run_forward(ndim, image, mask, dist, B, C, D, H, W, spacing, v, lambda, iterations,
+                       nullptr, 0, scratch, kNoAllocScratchBytes, opt, stream);
 }
