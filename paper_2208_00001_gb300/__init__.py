@@ -259,3 +259,12 @@ def forward_train(image, mask, v, lam, iterations, spacing=None, options=None, c
         if check:
             _check(workspace_status(ws), "forward_train (device)")
     return dist, saved
+
+
+def workspace_timeline(ws):
+    """Phase timestamps (ns, device globaltimer) recorded by the persistent
+    kernels in the workspace header: [start of first barrier, after it, after
+    each pass ...]; zeros where nothing was recorded."""
+    torch.cuda.synchronize()
+    hdr = ws[128:256].cpu().view(torch.int64)
+    return [int(x) for x in hdr.tolist()]

@@ -106,7 +106,9 @@ struct Plan {
     SweepArgs args;
     int grid = 0;
     size_t smem = 0;
-    size_t ws_bytes = 0;
+    size_t ws_bytes = 0;      // tiled sweep kernel
+    size_t chain_bytes = 0;   // 2D warp-chain kernel (0 when not applicable)
+    int sms = 0;
 };
 
 int plan_forward(int ndim, int64_t B, int64_t C, int64_t D, int64_t H, int64_t W,
@@ -176,14 +178,22 @@ int plan_forward(int ndim, int64_t B, int64_t C, int64_t D, int64_t H, int64_t W
     grid = std::min<int64_t>(grid, std::max<int64_t>(1, B * max_tiles));
     if (grid < max_tiles) return FGX_ERR_UNSUPPORTED;  // a pass's tiles must be co-resident
     pl->grid = (int)grid;
+    pl->sms = dev.sms;
     pl->ws_bytes = kHeaderBytes + (size_t)std::max<int64_t>(B, 1) * max_tiles * 8;
+    pl->chain_bytes = 0;
+    if (ndim == 2) {
+        int K, T, tv, th;
+        chain2d_geometry(H, W, opt, &K, &T, &tv, &th);
+        pl->chain_bytes = chain2d_workspace_bytes(B, C, H, W, std::max(tv, th));
+    }
     return FGX_OK;
 }
 
 int run_forward(int ndim, const float* image, const float* mask, float* dist, int64_t B, int64_t C,
                 int64_t D, int64_t H, int64_t W, const float spacing[3], float v, float lambda,
                 int iterations, uint8_t* codes, size_t codes_bytes, void* workspace,
-                size_t ws_bytes, const fgx_options* opt, void* stream) {
+                size_t ws_bytes, const fgx_options* opt, void* stream,
+                bool use_chain2d = false) {
     if (!(std::isfinite(v) && v > 0.f)) return FGX_ERR_ARG;
     if (!(lambda >= 0.f && lambda <= 1.f)) return FGX_ERR_ARG;
     if (iterations < 0) return FGX_ERR_ARG;
@@ -209,6 +219,12 @@ int run_forward(int ndim, const float* image, const float* mask, float* dist, in
         return FGX_ERR_NOT_DEVICE_PTR;
     const size_t nb = (size_t)(B * N) * sizeof(float);
     if (overlaps(dist, nb, image, (size_t)(B * C * N) * sizeof(float))) return FGX_ERR_ARG;
+    if (use_chain2d && ndim == 2 && !codes) {
+        if (!workspace || ws_bytes < pl.chain_bytes) return FGX_ERR_WORKSPACE;
+        if (!is_device_ptr(workspace)) return FGX_ERR_NOT_DEVICE_PTR;
+        return run_chain2d(image, mask, dist, B, C, H, W, v, lambda, iterations, workspace,
+                           ws_bytes, opt, pl.sms, stream);
+    }
     if (!workspace || ws_bytes < pl.ws_bytes) return FGX_ERR_WORKSPACE;
     if (!is_device_ptr(workspace)) return FGX_ERR_NOT_DEVICE_PTR;
     const size_t need_codes = (size_t)iterations * pl.args.npass * (size_t)(B * N);
@@ -262,7 +278,7 @@ int fgx_geodesic_workspace_size(int ndim, int64_t B, int64_t C, int64_t D, int64
     Plan pl;
     int st = plan_forward(ndim, B, C, D, H, W, unit, 0.5f, 1, opt, &pl);
     if (st != FGX_OK) return st;
-    *bytes = pl.ws_bytes;
+    *bytes = std::max(pl.ws_bytes, pl.chain_bytes);
     return FGX_OK;
 }
 
@@ -270,7 +286,7 @@ int fgx_geodesic2d(const float* image, const float* mask, float* dist, int64_t B
                    int64_t H, int64_t W, float v, float lambda, int iterations, void* workspace,
                    size_t workspace_bytes, const fgx_options* opt, void* stream) {
     return run_forward(2, image, mask, dist, B, C, 1, H, W, nullptr, v, lambda, iterations,
-                       nullptr, 0, workspace, workspace_bytes, opt, stream);
+                       nullptr, 0, workspace, workspace_bytes, opt, stream, true);
 }
 
 int fgx_geodesic3d(const float* image, const float* mask, float* dist, int64_t B, int64_t C,

@@ -9,7 +9,8 @@
 namespace fgx {
 
 constexpr int kMaxPasses = 6;
-// Workspace header: device status word, grid-barrier counter, padding.
+// Workspace header: device status word (offset 0), grid-barrier counter
+// (offset 64), phase timeline of 16 globaltimer stamps (offset 128).
 constexpr size_t kHeaderBytes = 256;
 constexpr int kThreads = 256;
 
@@ -44,9 +45,17 @@ struct SweepArgs {
     int smem_region;              // floats per (D or I-channel) region buffer
 };
 
-// Host helpers (fgx_plan.cu)
+// Host helpers (fgx_api.cu)
 void pass_offsets_t(int ndim, int axis, const float sp[3], float lambda, float t[9]);
 void pass_extents(int axis, const int64_t ext[3], PassGeom* g);
+
+// 2D warp-chain forward (chain2d.cu)
+size_t chain2d_workspace_bytes(int64_t B, int64_t C, int64_t H, int64_t W, int tiles);
+int chain2d_geometry(int64_t H, int64_t W, const fgx_options* opt, int* K, int* T, int* tv,
+                     int* th);
+int run_chain2d(const float* image, const float* mask, float* dist, int64_t B, int64_t C,
+                int64_t H, int64_t W, float v, float lambda, int iterations, void* workspace,
+                size_t ws_bytes, const fgx_options* opt, int sms, void* stream);
 
 // Launchers (sweep_kernel.cu)
 int launch_sweep(const SweepArgs& a, int grid, size_t smem, void* stream);
