@@ -268,3 +268,68 @@ def workspace_timeline(ws):
     torch.cuda.synchronize()
     hdr = ws[128:256].cpu().view(torch.int64)
     return [int(x) for x in hdr.tolist()]
+
+
+def backward_workspace_size(ndim, B, C, D, H, W, options=None):
+    n = ctypes.c_size_t(0)
+    _check(lib().fgx_backward_workspace_size(ndim, B, C, D, H, W, _opt(options),
+                                             ctypes.byref(n)), "backward workspace size")
+    return n.value
+
+
+def backward(grad_dist, image, saved, v, lam, iterations, spacing=None, need_image=True,
+             need_mask=True, options=None, check=False):
+    """Reverse sweep through the codes recorded by :func:`forward_train`.
+    Returns (grad_image or None, grad_mask or None)."""
+    ndim = image.dim() - 2
+    _check_tensor(grad_dist, "grad_dist")
+    B, C, D, H, W = _shape(image, grad_dist, ndim)
+    dev = image.device
+    with torch.cuda.device(dev):
+        gi = torch.empty_like(image) if need_image else None
+        gm = torch.empty_like(grad_dist) if need_mask else None
+        if gi is None and gm is None:
+            return None, None
+        ws = _workspace(backward_workspace_size(ndim, B, C, D, H, W, options), dev)
+        if ndim == 2:
+            st = lib().fgx_geodesic2d_bwd(_ptr(grad_dist), _ptr(image), _ptr(saved),
+                                          saved.numel(), _ptr(gi), _ptr(gm), B, C, H, W,
+                                          float(v), float(lam), int(iterations), _ptr(ws),
+                                          ws.numel(), _opt(options), _stream())
+        else:
+            st = lib().fgx_geodesic3d_bwd(_ptr(grad_dist), _ptr(image), _ptr(saved),
+                                          saved.numel(), _ptr(gi), _ptr(gm), B, C, D, H, W,
+                                          _spacing(spacing), float(v), float(lam),
+                                          int(iterations), _ptr(ws), ws.numel(), _opt(options),
+                                          _stream())
+        _check(st, "backward")
+        if check:
+            _check(workspace_status(ws), "backward (device)")
+    return gi, gm
+
+
+class GeodesicFn(torch.autograd.Function):
+    """Differentiable transform: the forward records argmin parent codes, the
+    backward runs the reverse sweep through them (dL/dimage, dL/dmask)."""
+
+    @staticmethod
+    def forward(ctx, image, mask, v, lam, iterations, spacing=None, options=None):
+        dist, saved = forward_train(image.detach().contiguous(), mask.detach().contiguous(), v,
+                                    lam, iterations, spacing=spacing, options=options)
+        ctx.save_for_backward(image.detach(), saved)
+        ctx.params = (v, lam, iterations, spacing, options)
+        return dist
+
+    @staticmethod
+    def backward(ctx, grad_dist):
+        image, saved = ctx.saved_tensors
+        v, lam, iterations, spacing, options = ctx.params
+        gi, gm = backward(grad_dist.contiguous(), image, saved, v, lam, iterations,
+                          spacing=spacing, need_image=ctx.needs_input_grad[0],
+                          need_mask=ctx.needs_input_grad[1], options=options)
+        return gi, gm, None, None, None, None, None
+
+
+def geodesic_autograd(image, mask, v, lam, iterations, spacing=None, options=None):
+    """Autograd entry point: dist = GeodesicFn(image, mask, ...)."""
+    return GeodesicFn.apply(image, mask, v, lam, iterations, spacing, options)

@@ -32,6 +32,7 @@
 #include <cmath>
 #include <cstring>
 
+#include "device_sync.cuh"
 #include "fgx_internal.h"
 
 namespace fgx {
@@ -68,30 +69,7 @@ struct Chain2DArgs {
     int max_tiles;
 };
 
-__device__ __forceinline__ long long gtimer() {
-    long long t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-__device__ __forceinline__ unsigned int ld_acq_u32(const unsigned int* p) {
-    unsigned int v;
-    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-    return v;
-}
-__device__ __forceinline__ unsigned int ld_relaxed_u32(const unsigned int* p) {
-    unsigned int v;
-    asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-    return v;
-}
-__device__ __forceinline__ unsigned long long ld_relaxed_u64(const unsigned long long* p) {
-    unsigned long long v;
-    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
-    return v;
-}
-__device__ __forceinline__ void st_relaxed_u64(unsigned long long* p, unsigned long long v) {
-    asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
-}
-__device__ __forceinline__ int status_of(const int* s) { return *(volatile const int*)s; }
+using namespace dev;
 
 __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
     const unsigned int sa = (unsigned int)__cvta_generic_to_shared(smem);
@@ -103,32 +81,6 @@ __device__ __forceinline__ void cp_async_commit() {
 template <int N>
 __device__ __forceinline__ void cp_async_wait() {
     asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
-}
-
-__device__ bool grid_sync(unsigned int* ctr, unsigned int epoch, int* status, long long tmo) {
-    __shared__ int ok;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        __threadfence();
-        atomicAdd(ctr, 1u);
-        const unsigned int target = epoch * gridDim.x;
-        ok = status_of(status) == 0;
-        // poll with relaxed loads and back-off (an acquiring load in a tight
-        // loop disturbs the working warps that share this SM), then one fence
-        const long long t0 = gtimer();
-        while (ok && ld_relaxed_u32(ctr) < target) {
-            if (status_of(status) != 0) { ok = 0; break; }
-            if (gtimer() - t0 > tmo) {
-                atomicCAS(status, 0, (int)FGX_ERR_TIMEOUT);
-                ok = 0;
-                break;
-            }
-            __nanosleep(256);
-        }
-        __threadfence();
-    }
-    __syncthreads();
-    return ok != 0;
 }
 
 // Cost of the undirected edge between a and b (same channel stride n), in the
@@ -358,7 +310,7 @@ __device__ bool chain_tile(const Chain2DArgs& a, int t_app, int pass, int b, int
                 if (lane == 0) {
                     if (status_of(a.status) != 0) fail = 1;
                     else if (gtimer() - t0 > a.timeout_ns) {
-                        atomicCAS(a.status, 0, (int)FGX_ERR_TIMEOUT);
+                        record_timeout(a.status);
                         fail = 1;
                     }
                 }
@@ -473,7 +425,7 @@ __global__ void __launch_bounds__(kWarps * 32, 1) chain2d_kernel(const Chain2DAr
     }
     unsigned long long* timeline = (unsigned long long*)((char*)a.status + 128);
     if (blockIdx.x == 0 && threadIdx.x == 0) timeline[0] = (unsigned long long)gtimer();
-    bool alive = grid_sync(a.barrier, epoch++, a.status, a.timeout_ns);
+    bool alive = grid_barrier(a.barrier, epoch++, a.status, a.timeout_ns);
     if (blockIdx.x == 0 && threadIdx.x == 0) timeline[1] = (unsigned long long)gtimer();
     const int gwarp = blockIdx.x * kWarps + (threadIdx.x >> 5);
     const int nwarps = gridDim.x * kWarps;
@@ -497,7 +449,7 @@ __global__ void __launch_bounds__(kWarps * 32, 1) chain2d_kernel(const Chain2DAr
                 }
             }
         }
-        alive = grid_sync(a.barrier, epoch++, a.status, a.timeout_ns);
+        alive = grid_barrier(a.barrier, epoch++, a.status, a.timeout_ns);
         if (blockIdx.x == 0 && threadIdx.x == 0 && t_app + 2 < 16)
             timeline[t_app + 2] = (unsigned long long)gtimer();
     }

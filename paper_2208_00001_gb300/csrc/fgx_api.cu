@@ -338,30 +338,156 @@ int fgx_geodesic3d_fwd_train(const float* image, const float* mask, float* dist,
 
 }  // extern "C"
 
-// Entry points served by later translation units are declared in fgx.h; the
-// ones below are not built yet in this version of the library.
+// ---------------------------------------------------------------- backward
+
+namespace fgx {
+namespace {
+
+struct BwdPlan {
+    AdjointArgs args;
+    int grid = 0;
+    size_t smem = 0;
+    size_t ws_bytes = 0;
+    size_t flags_bytes = 0;
+};
+
+size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+int plan_backward(int ndim, int64_t B, int64_t C, int64_t D, int64_t H, int64_t W,
+                  const float spacing[3], float lambda, int iterations, const fgx_options* opt,
+                  BwdPlan* bp) {
+    Plan pl;
+    int st = plan_forward(ndim, B, C, D, H, W, spacing, lambda, iterations, opt, &pl);
+    if (st != FGX_OK) return st;
+    AdjointArgs& a = bp->args;
+    std::memset(&a, 0, sizeof(a));
+    const SweepArgs& f = pl.args;
+    a.B = B;
+    a.C = C;
+    a.N = f.N;
+    a.ndim = ndim;
+    a.lambda = lambda;
+    a.iterations = iterations;
+    a.npass = f.npass;
+    for (int i = 0; i < kMaxPasses; ++i) a.pass[i] = f.pass[i];
+    a.timeout_ns = f.timeout_ns;
+    a.max_tiles = f.max_tiles;
+    a.smem_region = f.smem_region;
+    bp->smem = (size_t)(4 + 2 * C) * (size_t)f.smem_region * sizeof(float);
+    if (bp->smem > 200 * 1024) return FGX_ERR_UNSUPPORTED;
+    int per_sm = 0;
+    st = adjoint_max_blocks_per_sm(bp->smem, &per_sm);
+    if (st != FGX_OK) return st;
+    if (per_sm < 1) return FGX_ERR_UNSUPPORTED;
+    int64_t grid = (int64_t)per_sm * pl.sms;
+    if (opt && opt->max_blocks) grid = std::min<int64_t>(grid, opt->max_blocks);
+    grid = std::min<int64_t>(grid, std::max<int64_t>(1, B * f.max_tiles));
+    if (grid < f.max_tiles) return FGX_ERR_UNSUPPORTED;
+    bp->grid = (int)grid;
+    bp->flags_bytes = align256((size_t)std::max<int64_t>(B, 1) * f.max_tiles * 8);
+    bp->ws_bytes = kHeaderBytes + bp->flags_bytes + 2 * align256((size_t)(B * f.N) * 4);
+    return FGX_OK;
+}
+
+int run_backward(int ndim, const float* grad_dist, const float* image, const void* saved,
+                 size_t saved_bytes, float* grad_image, float* grad_mask, int64_t B, int64_t C,
+                 int64_t D, int64_t H, int64_t W, const float spacing[3], float v, float lambda,
+                 int iterations, void* workspace, size_t ws_bytes, const fgx_options* opt,
+                 void* stream) {
+    if (!(std::isfinite(v) && v > 0.f)) return FGX_ERR_ARG;
+    if (!(lambda >= 0.f && lambda <= 1.f)) return FGX_ERR_ARG;
+    if (iterations < 0) return FGX_ERR_ARG;
+    if (ndim == 3) {
+        if (!spacing) return FGX_ERR_ARG;
+        for (int i = 0; i < 3; ++i)
+            if (!finite_pos(spacing[i])) return FGX_ERR_ARG;
+    }
+    BwdPlan bp;
+    int st = plan_backward(ndim, B, C, D, H, W, spacing, lambda, iterations, opt, &bp);
+    if (st != FGX_OK) return st;
+    const int64_t N = D * H * W;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (B * N == 0) {
+        if (workspace && ws_bytes >= sizeof(int) && is_device_ptr(workspace) &&
+            cudaMemsetAsync(workspace, 0, std::min(ws_bytes, kHeaderBytes), s) != cudaSuccess)
+            return FGX_ERR_CUDA;
+        return FGX_OK;
+    }
+    if (!grad_dist || !image) return FGX_ERR_ARG;
+    if (!grad_image && !grad_mask) return FGX_ERR_ARG;
+    if (!is_device_ptr(grad_dist) || !is_device_ptr(image)) return FGX_ERR_NOT_DEVICE_PTR;
+    if (grad_image && !is_device_ptr(grad_image)) return FGX_ERR_NOT_DEVICE_PTR;
+    if (grad_mask && !is_device_ptr(grad_mask)) return FGX_ERR_NOT_DEVICE_PTR;
+    const size_t need_codes = (size_t)iterations * bp.args.npass * (size_t)(B * N);
+    if (need_codes) {
+        if (!saved || saved_bytes < need_codes) return FGX_ERR_WORKSPACE;
+        if (!is_device_ptr(saved)) return FGX_ERR_NOT_DEVICE_PTR;
+    }
+    if (!workspace || ws_bytes < bp.ws_bytes) return FGX_ERR_WORKSPACE;
+    if (!is_device_ptr(workspace)) return FGX_ERR_NOT_DEVICE_PTR;
+    AdjointArgs& a = bp.args;
+    char* w = (char*)workspace;
+    a.image = image;
+    a.codes = (const uint8_t*)saved;
+    a.grad_dist = grad_dist;
+    a.grad_image = grad_image;
+    a.grad_mask = grad_mask;
+    a.v = v;
+    a.status = (int*)w;
+    a.barrier = (unsigned int*)(w + 64);
+    a.flags = (unsigned long long*)(w + kHeaderBytes);
+    a.G[0] = (float*)(w + kHeaderBytes + bp.flags_bytes);
+    a.G[1] = (float*)(w + kHeaderBytes + bp.flags_bytes + align256((size_t)(B * N) * 4));
+    if (cudaMemsetAsync(workspace, 0, kHeaderBytes + bp.flags_bytes, s) != cudaSuccess)
+        return FGX_ERR_CUDA;
+    return launch_adjoint(a, bp.grid, bp.smem, stream);
+}
+
+}  // namespace
+}  // namespace fgx
+
 extern "C" {
+
+int fgx_backward_workspace_size(int ndim, int64_t B, int64_t C, int64_t D, int64_t H, int64_t W,
+                                const fgx_options* opt, size_t* bytes) {
+    if (!bytes) return FGX_ERR_ARG;
+    const float unit[3] = {1.f, 1.f, 1.f};
+    BwdPlan bp;
+    int st = plan_backward(ndim, B, C, D, H, W, unit, 0.5f, 1, opt, &bp);
+    if (st != FGX_OK) return st;
+    *bytes = bp.ws_bytes;
+    return FGX_OK;
+}
+
+int fgx_geodesic2d_bwd(const float* grad_dist, const float* image, const void* saved,
+                       size_t saved_bytes, float* grad_image, float* grad_mask, int64_t B,
+                       int64_t C, int64_t H, int64_t W, float v, float lambda, int iterations,
+                       void* workspace, size_t workspace_bytes, const fgx_options* opt,
+                       void* stream) {
+    return run_backward(2, grad_dist, image, saved, saved_bytes, grad_image, grad_mask, B, C, 1,
+                        H, W, nullptr, v, lambda, iterations, workspace, workspace_bytes, opt,
+                        stream);
+}
+
+int fgx_geodesic3d_bwd(const float* grad_dist, const float* image, const void* saved,
+                       size_t saved_bytes, float* grad_image, float* grad_mask, int64_t B,
+                       int64_t C, int64_t D, int64_t H, int64_t W, const float spacing[3],
+                       float v, float lambda, int iterations, void* workspace,
+                       size_t workspace_bytes, const fgx_options* opt, void* stream) {
+    return run_backward(3, grad_dist, image, saved, saved_bytes, grad_image, grad_mask, B, C, D,
+                        H, W, spacing, v, lambda, iterations, workspace, workspace_bytes, opt,
+                        stream);
+}
+
+// Batched entry points are served by a later version of the library.
 int fgx_batched_workspace_size(const fgx_instance*, int, const fgx_options*, size_t*) {
     return FGX_ERR_UNSUPPORTED;
 }
 int fgx_geodesic_batched(const fgx_instance*, int, void*, size_t, const fgx_options*, void*) {
     return FGX_ERR_UNSUPPORTED;
 }
-int fgx_backward_workspace_size(int, int64_t, int64_t, int64_t, int64_t, int64_t,
-                                const fgx_options*, size_t*) {
-    return FGX_ERR_UNSUPPORTED;
-}
-int fgx_geodesic2d_bwd(const float*, const float*, const void*, size_t, float*, float*, int64_t,
-                       int64_t, int64_t, int64_t, float, float, int, void*, size_t,
-                       const fgx_options*, void*) {
-    return FGX_ERR_UNSUPPORTED;
-}
-int fgx_geodesic3d_bwd(const float*, const float*, const void*, size_t, float*, float*, int64_t,
-                       int64_t, int64_t, int64_t, int64_t, const float*, float, float, int, void*,
-                       size_t, const fgx_options*, void*) {
-    return FGX_ERR_UNSUPPORTED;
-}
-}
+
+}  // extern "C"
 
 // ----------------------------------------------------------------------------
 // Allocation-free forward.  Some callers cannot allocate device memory at the

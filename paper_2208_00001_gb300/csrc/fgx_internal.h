@@ -45,6 +45,28 @@ struct SweepArgs {
     int smem_region;              // floats per (D or I-channel) region buffer
 };
 
+// Reverse sweep through recorded parent codes (adjoint_kernel.cu).  Uses the
+// same pass geometry and tiling as SweepArgs.
+struct AdjointArgs {
+    const float* image;      // [B][C][N]
+    const uint8_t* codes;    // [iterations*npass][B][N]
+    const float* grad_dist;  // [B][N]  dL/dD of the final distance
+    float* G[2];             // [B][N]  adjoint ping-pong buffers (workspace)
+    float* grad_image;       // [B][C][N] or null
+    float* grad_mask;        // [B][N] or null
+    int64_t B, C, N;
+    int ndim;
+    float v, lambda;
+    int iterations, npass;
+    PassGeom pass[kMaxPasses];
+    unsigned long long* flags;
+    unsigned int* barrier;
+    int* status;
+    long long timeout_ns;
+    int max_tiles;
+    int smem_region;
+};
+
 // Host helpers (fgx_api.cu)
 void pass_offsets_t(int ndim, int axis, const float sp[3], float lambda, float t[9]);
 void pass_extents(int axis, const int64_t ext[3], PassGeom* g);
@@ -56,6 +78,10 @@ int chain2d_geometry(int64_t H, int64_t W, const fgx_options* opt, int* K, int* 
 int run_chain2d(const float* image, const float* mask, float* dist, int64_t B, int64_t C,
                 int64_t H, int64_t W, float v, float lambda, int iterations, void* workspace,
                 size_t ws_bytes, const fgx_options* opt, int sms, void* stream);
+
+// Adjoint launchers (adjoint_kernel.cu)
+int launch_adjoint(const AdjointArgs& a, int grid, size_t smem, void* stream);
+int adjoint_max_blocks_per_sm(size_t smem, int* blocks);
 
 // Launchers (sweep_kernel.cu)
 int launch_sweep(const SweepArgs& a, int grid, size_t smem, void* stream);

@@ -15,80 +15,16 @@
 // bit-exact.  Passes are separated by a grid barrier.
 #include <cuda_runtime.h>
 
+#include "device_sync.cuh"
 #include "fgx_internal.h"
 
 namespace fgx {
 namespace {
 
-__device__ __forceinline__ int64_t mn64(int64_t x, int64_t y) { return x < y ? x : y; }
-__device__ __forceinline__ int64_t mx64(int64_t x, int64_t y) { return x > y ? x : y; }
-
-__device__ __forceinline__ unsigned long long ld_acquire(const unsigned long long* p) {
-    unsigned long long v;
-    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
-    return v;
-}
-__device__ __forceinline__ unsigned int ld_acquire_u32(const unsigned int* p) {
-    unsigned int v;
-    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-    return v;
-}
-__device__ __forceinline__ void st_release(unsigned long long* p, unsigned long long v) {
-    asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
-}
-__device__ __forceinline__ long long globaltimer() {
-    long long t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-__device__ __forceinline__ int ld_status(const int* s) {
-    return *(volatile const int*)s;
-}
+using namespace dev;
 
 __device__ __forceinline__ unsigned long long tag(int t_app, int blk) {
     return ((unsigned long long)(t_app + 1) << 32) | (unsigned int)blk;
-}
-
-// Thread 0 waits until *f >= target.  Returns false (and records a timeout in
-// the status word) when the limit passes or another block already failed.
-__device__ bool wait_tag(const unsigned long long* f, unsigned long long target, int* status,
-                         long long timeout_ns) {
-    if (ld_acquire(f) >= target) return true;
-    const long long t0 = globaltimer();
-    for (;;) {
-        if (ld_acquire(f) >= target) return true;
-        if (ld_status(status) != 0) return false;
-        if (globaltimer() - t0 > timeout_ns) {
-            atomicCAS(status, 0, (int)FGX_ERR_TIMEOUT);
-            return false;
-        }
-        __nanosleep(64);
-    }
-}
-
-// Grid barrier; `epoch` counts barriers passed so far (1-based target).
-__device__ bool grid_barrier(unsigned int* ctr, unsigned int epoch, int* status,
-                             long long timeout_ns) {
-    __shared__ int ok;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        __threadfence();
-        atomicAdd(ctr, 1u);
-        const unsigned int target = epoch * gridDim.x;
-        ok = 1;
-        const long long t0 = globaltimer();
-        while (ld_acquire_u32(ctr) < target) {
-            if (ld_status(status) != 0) { ok = 0; break; }
-            if (globaltimer() - t0 > timeout_ns) {
-                atomicCAS(status, 0, (int)FGX_ERR_TIMEOUT);
-                ok = 0;
-                break;
-            }
-            __nanosleep(64);
-        }
-    }
-    __syncthreads();
-    return ok != 0;
 }
 
 // One tile of one instance for one pass application.  Returns false if a
@@ -195,7 +131,7 @@ __device__ bool sweep_tile(const SweepArgs& a, const PassGeom& g, int t_app, int
         }
         if (threadIdx.x == 0) {
             __threadfence();
-            st_release(myflag, tag(t_app, blk + 1));
+            st_release_u64(myflag, tag(t_app, blk + 1));
         }
     }
     return true;

@@ -1,0 +1,165 @@
+"""Parity of the CUDA reverse sweep with the oracle's (GPU).
+
+The GPU records parent codes in the forward (checked equal to the oracle's
+codes in the forward tests) and runs the adjoint through them; with identical
+codes the float32 gradients must match the oracle's float32 reverse sweep bit
+for bit (same accumulation order: children in offset order, parent-side image
+terms before the child-side term).
+"""
+import os
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import workloads
+
+pytestmark = pytest.mark.gpu
+THREADS = os.cpu_count() or 1
+
+
+@pytest.fixture(scope="module")
+def fgx():
+    from paper_2208_00001_gb300 import build
+    build.build()
+    import paper_2208_00001_gb300 as m
+    return m
+
+
+def _bits_equal(got, want, what):
+    got = np.ascontiguousarray(got, np.float32)
+    want = np.ascontiguousarray(want, np.float32)
+    assert got.shape == want.shape, what
+    bad = np.flatnonzero(got.view(np.uint32) != want.view(np.uint32))
+    if bad.size:
+        i = bad[0]
+        raise AssertionError(f"{what}: {bad.size}/{got.size} differ; first {i}: "
+                             f"gpu {got.reshape(-1)[i]!r} oracle {want.reshape(-1)[i]!r}")
+
+
+def _run(fgx, case, w, options=None, need_image=True, need_mask=True):
+    img = torch.from_numpy(case.image).cuda()
+    m = torch.from_numpy(case.mask).cuda()
+    d, saved = fgx.forward_train(img, m, case.v, case.lam, case.iterations,
+                                 spacing=case.spacing, options=options, check=True)
+    g = torch.from_numpy(w).cuda()
+    gi, gm = fgx.backward(g, img, saved, case.v, case.lam, case.iterations,
+                          spacing=case.spacing, need_image=need_image, need_mask=need_mask,
+                          options=options, check=True)
+    return (d.cpu().numpy(), saved.cpu().numpy(), None if gi is None else gi.cpu().numpy(),
+            None if gm is None else gm.cpu().numpy())
+
+
+def _oracle(case, w, codes):
+    return oracle.backward(w, case.image, codes, case.v, case.lam, case.iterations,
+                           spacing=case.spacing)
+
+
+@pytest.mark.parametrize("v", [1e10, 10.0])
+def test_backward_2d_bit_exact(fgx, v):
+    case = workloads.diff2d(batch=2, size=96, v=v)
+    w = case.extra["w"]
+    d, codes, gi, gm = _run(fgx, case, w)
+    want_d, want_codes = oracle.gdt(case.image, case.mask, case.v, case.lam, case.iterations,
+                                    return_codes=True, threads=THREADS)
+    np.testing.assert_array_equal(codes, want_codes)
+    wi, wm = _oracle(case, w, want_codes)
+    _bits_equal(gi, wi, "grad_image")
+    _bits_equal(gm, wm, "grad_mask")
+    assert np.abs(gi).sum() > 0
+
+
+def test_backward_2d_many_tiles_and_channels(fgx):
+    rng = np.random.default_rng(21)
+    img = rng.uniform(0, 1, (3, 2, 45, 70)).astype(np.float32)
+    m = rng.uniform(0, 1, (3, 1, 45, 70)).astype(np.float32)
+    m[:, :, 10, 20] = 0
+    case = workloads.Case("mc", img, m, 5.0, 0.6, 2)
+    w = rng.uniform(0, 1, m.shape).astype(np.float32)
+    for opts in (None, dict(tile_width=8, tile_lines=3), dict(tile_width=16, tile_lines=5,
+                                                             max_blocks=12)):
+        d, codes, gi, gm = _run(fgx, case, w, options=opts)
+        wi, wm = _oracle(case, w, codes)
+        _bits_equal(gi, wi, f"grad_image {opts}")
+        _bits_equal(gm, wm, f"grad_mask {opts}")
+
+
+def test_backward_3d_bit_exact(fgx):
+    case = workloads.diff3d(shape=(14, 19, 23), v=10.0)
+    w = case.extra["w"]
+    for opts in (None, dict(tile_width=4, tile_height=3, tile_lines=2)):
+        d, codes, gi, gm = _run(fgx, case, w, options=opts)
+        wi, wm = _oracle(case, w, codes)
+        _bits_equal(gi, wi, f"grad_image {opts}")
+        _bits_equal(gm, wm, f"grad_mask {opts}")
+
+
+def test_backward_3d_anisotropic_multichannel(fgx):
+    rng = np.random.default_rng(5)
+    img = rng.uniform(0, 1, (1, 2, 9, 12, 10)).astype(np.float32)
+    m = rng.uniform(0, 1, (1, 1, 9, 12, 10)).astype(np.float32)
+    m[0, 0, 4, 5, 6] = 0
+    case = workloads.Case("3d", img, m, 4.0, 0.3, 2, (2.5, 1.0, 0.75))
+    w = rng.uniform(0, 1, m.shape).astype(np.float32)
+    d, codes, gi, gm = _run(fgx, case, w)
+    wi, wm = _oracle(case, w, codes)
+    _bits_equal(gi, wi, "grad_image")
+    _bits_equal(gm, wm, "grad_mask")
+
+
+@pytest.mark.parametrize("which", ["image", "mask"])
+def test_backward_single_output(fgx, which):
+    case = workloads.diff2d(batch=1, size=40, v=10.0)
+    w = case.extra["w"]
+    d, codes, gi, gm = _run(fgx, case, w, need_image=which == "image",
+                            need_mask=which == "mask")
+    wi, wm = _oracle(case, w, codes)
+    if which == "image":
+        assert gm is None
+        _bits_equal(gi, wi, "grad_image")
+    else:
+        assert gi is None
+        _bits_equal(gm, wm, "grad_mask")
+
+
+def test_backward_zero_iterations(fgx):
+    case = workloads.diff2d(batch=1, size=24, iterations=0)
+    w = case.extra["w"]
+    d, codes, gi, gm = _run(fgx, case, w)
+    assert np.all(gi == 0)
+    _bits_equal(gm, (np.float32(case.v) * w).astype(np.float32), "grad_mask")
+
+
+def test_differentiable_configs_full_size(fgx):
+    """The differentiable workloads at their stated sizes (8x512x512 2D batch,
+    96x160x160 volume): gradients bit-exact to the oracle."""
+    for case in (workloads.diff2d(), workloads.diff3d()):
+        w = case.extra["w"]
+        d, codes, gi, gm = _run(fgx, case, w)
+        want_d, want_codes = oracle.gdt(case.image, case.mask, case.v, case.lam,
+                                        case.iterations, spacing=case.spacing,
+                                        return_codes=True, threads=THREADS)
+        _bits_equal(d, want_d, "dist")
+        np.testing.assert_array_equal(codes, want_codes)
+        wi, wm = _oracle(case, w, codes)
+        _bits_equal(gi, wi, "grad_image")
+        _bits_equal(gm, wm, "grad_mask")
+
+
+def test_autograd_function(fgx):
+    case = workloads.diff2d(batch=2, size=48, v=10.0)
+    img = torch.from_numpy(case.image).cuda().requires_grad_(True)
+    m = torch.from_numpy(case.mask).cuda().requires_grad_(True)
+    w = torch.from_numpy(case.extra["w"]).cuda()
+    d = fgx.geodesic_autograd(img, m, case.v, case.lam, case.iterations)
+    loss = (w * d).sum()
+    loss.backward()
+    _, codes = oracle.gdt(case.image, case.mask, case.v, case.lam, case.iterations,
+                          return_codes=True)
+    wi, wm = _oracle(case, case.extra["w"], codes)
+    _bits_equal(img.grad.cpu().numpy(), wi, "autograd grad_image")
+    _bits_equal(m.grad.cpu().numpy(), wm, "autograd grad_mask")
+    # forward value equals the plain forward
+    plain = fgx.geodesic2d(img.detach(), m.detach(), case.v, case.lam, case.iterations)
+    _bits_equal(d.detach().cpu().numpy(), plain.cpu().numpy(), "autograd forward")
