@@ -144,11 +144,44 @@ typedef struct fgx_instance {
     int32_t iterations;
 } fgx_instance;
 
+/* Plan of a batched launch, filled by fgx_batched_prepare.  Plain data: the
+ * caller keeps it and may replay fgx_batched_run with it as often as it likes
+ * (for example inside a captured CUDA graph) while the workspace and the
+ * instances' buffers stay valid. */
+typedef struct fgx_batched_plan {
+    uint32_t size;          /* sizeof(fgx_batched_plan)                      */
+    int32_t n;              /* instances scheduled                           */
+    int32_t grid;           /* thread blocks of the persistent launch        */
+    int32_t smem_bytes;     /* dynamic shared memory per block               */
+    int32_t rounds;         /* pass-application rounds                       */
+    int32_t region, kmax;   /* tile buffer geometry                          */
+    int32_t timeout_ms;
+    uint64_t clear_bytes;   /* workspace prefix cleared before every run     */
+    uint64_t desc_off, waves_off, items_off;  /* table offsets in workspace  */
+    void* workspace;
+    uint64_t workspace_bytes;
+} fgx_batched_plan;
+
+/* Workspace bytes for a batched launch of these instances. */
 int fgx_batched_workspace_size(const fgx_instance* items, int n, const fgx_options* opt,
                                size_t* bytes);
 
-/* All instances in one persistent launch driven by a work list of
- * (instance, pass, line tile) items; results equal n separate calls. */
+/* Checks the instances, builds the work list of (instance, pass, line tile)
+ * items - instances advance one pass application per round; each round packs
+ * whole instances into waves of co-resident thread blocks - and uploads it
+ * with the instance descriptors into `workspace` (a copy from host memory on
+ * `stream`; `items` may be freed on return).  Writes `plan`. */
+int fgx_batched_prepare(const fgx_instance* items, int n, void* workspace,
+                        size_t workspace_bytes, const fgx_options* opt,
+                        fgx_batched_plan* plan, void* stream);
+
+/* Runs a prepared plan: clears the plan's progress tags and launches the one
+ * persistent kernel that computes every instance.  Allocates nothing and
+ * copies nothing from the host, so it can be captured in a CUDA graph. */
+int fgx_batched_run(const fgx_batched_plan* plan, void* stream);
+
+/* fgx_batched_prepare followed by fgx_batched_run.  Results equal n separate
+ * fgx_geodesic2d / fgx_geodesic3d calls bit for bit. */
 int fgx_geodesic_batched(const fgx_instance* items, int n, void* workspace,
                          size_t workspace_bytes, const fgx_options* opt, void* stream);
 

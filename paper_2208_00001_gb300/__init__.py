@@ -61,6 +61,17 @@ class Instance(ctypes.Structure):
                 ("lambda_", ctypes.c_float), ("iterations", ctypes.c_int32)]
 
 
+class BatchedPlanC(ctypes.Structure):
+    """fgx_batched_plan: plain data describing a prepared batched launch."""
+    _fields_ = [("size", ctypes.c_uint32), ("n", ctypes.c_int32), ("grid", ctypes.c_int32),
+                ("smem_bytes", ctypes.c_int32), ("rounds", ctypes.c_int32),
+                ("region", ctypes.c_int32), ("kmax", ctypes.c_int32),
+                ("timeout_ms", ctypes.c_int32), ("clear_bytes", ctypes.c_uint64),
+                ("desc_off", ctypes.c_uint64), ("waves_off", ctypes.c_uint64),
+                ("items_off", ctypes.c_uint64), ("workspace", ctypes.c_void_p),
+                ("workspace_bytes", ctypes.c_uint64)]
+
+
 _i64, _i32, _f32, _vp, _sz = (ctypes.c_int64, ctypes.c_int, ctypes.c_float, ctypes.c_void_p,
                               ctypes.c_size_t)
 _SIGS = {
@@ -75,6 +86,8 @@ _SIGS = {
     "fgx_workspace_status": ([_vp, _vp], _i32),
     "fgx_batched_workspace_size": ([_vp, _i32, _vp, ctypes.POINTER(_sz)], _i32),
     "fgx_geodesic_batched": ([_vp, _i32, _vp, _sz, _vp, _vp], _i32),
+    "fgx_batched_prepare": ([_vp, _i32, _vp, _sz, _vp, _vp, _vp], _i32),
+    "fgx_batched_run": ([_vp, _vp], _i32),
     "fgx_train_saved_size": ([_i32, _i64, _i64, _i64, _i64, _i32, ctypes.POINTER(_sz)], _i32),
     "fgx_geodesic2d_fwd_train": ([_vp, _vp, _vp, _i64, _i64, _i64, _i64, _f32, _f32, _i32, _vp,
                                   _sz, _vp, _sz, _vp, _vp], _i32),
@@ -333,3 +346,56 @@ class GeodesicFn(torch.autograd.Function):
 def geodesic_autograd(image, mask, v, lam, iterations, spacing=None, options=None):
     """Autograd entry point: dist = GeodesicFn(image, mask, ...)."""
     return GeodesicFn.apply(image, mask, v, lam, iterations, spacing, options)
+
+
+class BatchedPlan:
+    """A prepared batched launch over instances of uneven shapes (2D and 3D
+    mixed).  ``instances`` is a list of (image, mask, v, lam, iterations,
+    spacing) with image (1, C, ...) and mask (1, 1, ...) CUDA float32
+    tensors.  :meth:`run` launches the one persistent kernel (replayable, also
+    inside a captured CUDA graph); results are in :attr:`outputs`."""
+
+    def __init__(self, instances, options=None):
+        self.instances = list(instances)
+        self.outputs = []
+        arr = (Instance * max(1, len(self.instances)))()
+        dev = None
+        for i, (img, m, v, lam, its, sp) in enumerate(self.instances):
+            ndim = img.dim() - 2
+            B, C, D, H, W = _shape(img, m, ndim)
+            if B != 1:
+                raise ValueError("batched instances have B = 1")
+            out = torch.empty_like(m)
+            self.outputs.append(out)
+            dev = img.device
+            sp3 = (1.0, 1.0, 1.0) if ndim == 2 else tuple(float(x) for x in sp)
+            arr[i] = Instance(ndim, C, D, H, W, img.data_ptr(), m.data_ptr(), out.data_ptr(),
+                              (ctypes.c_float * 3)(*sp3), float(v), float(lam), int(its))
+        self._arr = arr
+        self._opt = options if not isinstance(options, dict) else Options(**options)
+        n = ctypes.c_size_t(0)
+        _check(lib().fgx_batched_workspace_size(ctypes.byref(arr), len(self.instances),
+                                                _opt(self._opt), ctypes.byref(n)),
+               "batched workspace size")
+        dev = dev or torch.device("cuda")
+        self.workspace = _workspace(n.value, dev)
+        self.plan = BatchedPlanC()
+        with torch.cuda.device(dev):
+            _check(lib().fgx_batched_prepare(ctypes.byref(arr), len(self.instances),
+                                             _ptr(self.workspace), self.workspace.numel(),
+                                             _opt(self._opt), ctypes.byref(self.plan), _stream()),
+                   "fgx_batched_prepare")
+        self.device = dev
+
+    def run(self, check=False):
+        with torch.cuda.device(self.device):
+            _check(lib().fgx_batched_run(ctypes.byref(self.plan), _stream()), "fgx_batched_run")
+            if check:
+                _check(workspace_status(self.workspace), "fgx_batched_run (device)")
+        return self.outputs
+
+
+def geodesic_batched(instances, options=None, check=False):
+    """One persistent launch over all instances; returns their distance maps."""
+    plan = BatchedPlan(instances, options)
+    return plan.run(check=check)

@@ -189,7 +189,7 @@ __device__ bool adjoint_tile(const AdjointArgs& a, const PassGeom& g, int t_app,
     return true;
 }
 
-__global__ void __launch_bounds__(kThreads) adjoint_kernel(const AdjointArgs a) {
+__global__ void __launch_bounds__(kThreads, 2) adjoint_kernel(const AdjointArgs a) {
     extern __shared__ float smem[];
     const int T = a.iterations * a.npass;
     const int64_t total = a.B * a.N;

@@ -146,8 +146,9 @@ int plan_forward(int ndim, int64_t B, int64_t C, int64_t D, int64_t H, int64_t W
         g.dir = ndim == 3 ? kSched3D[i][1] : kSched2D[i][1];
         pass_extents(axis, ext, &g);
         pass_offsets_t(ndim, axis, sp, lambda, g.t);
-        int K = (opt && opt->tile_lines) ? opt->tile_lines : (ndim == 3 ? 4 : 32);
-        int tq = (opt && opt->tile_width) ? opt->tile_width : (ndim == 3 ? 16 : 256);
+        for (int k = 0; k < 9; ++k) g.c[k] = std::sqrt(g.t[k]);  // IEEE square root
+        int K = (opt && opt->tile_lines) ? opt->tile_lines : (ndim == 3 ? 4 : 16);
+        int tq = (opt && opt->tile_width) ? opt->tile_width : (ndim == 3 ? 16 : 128);
         int tp = ndim == 3 ? ((opt && opt->tile_height) ? opt->tile_height : 16) : 1;
         tq = (int)std::max<int64_t>(1, std::min<int64_t>(tq, std::max<int64_t>(g.Q, 1)));
         tp = (int)std::max<int64_t>(1, std::min<int64_t>(tp, std::max<int64_t>(g.P, 1)));
@@ -163,11 +164,18 @@ int plan_forward(int ndim, int64_t B, int64_t C, int64_t D, int64_t H, int64_t W
         max_tiles = std::max(max_tiles, g.ntp * g.ntq);
         const int64_t rp = std::min<int64_t>(std::max<int64_t>(g.P, 1), tp + 2 * K);
         const int64_t rq = std::min<int64_t>(std::max<int64_t>(g.Q, 1), tq + 2 * K);
-        region = std::max(region, rp * rq);
+        if (rp * rq > kMaxRegion) return FGX_ERR_UNSUPPORTED;
+        // shared buffers carry a one-element border (none along p in 2D)
+        region = std::max(region, (rp + (ndim == 3 ? 2 : 0)) * (rq + 2));
     }
+    int kmax = 1;
+    for (int i = 0; i < a.npass; ++i) kmax = std::max(kmax, a.pass[i].K);
     a.max_tiles = max_tiles;
     a.smem_region = (int)region;
-    pl->smem = (size_t)(2 + 2 * C) * (size_t)region * sizeof(float);
+    a.kmax = kmax;
+    a.cost_mode = lambda == 0.0f ? kCostConst
+                  : (lambda == 1.0f && C == 1) ? kCostAbs : kCostGeneral;
+    pl->smem = sweep_smem_bytes(a.cost_mode == kCostConst ? 0 : C, (int)region, kmax);
     if (pl->smem > 200 * 1024) return FGX_ERR_UNSUPPORTED;
     int per_sm = 0;
     st = sweep_max_blocks_per_sm(pl->smem, &per_sm);
@@ -248,6 +256,19 @@ int run_forward(int ndim, const float* image, const float* mask, float* dist, in
 }
 
 }  // namespace
+
+int plan_instance(int ndim, int64_t C, int64_t D, int64_t H, int64_t W, const float spacing[3],
+                  float lambda, const fgx_options* opt, SweepArgs* args, int* sms) {
+    Plan pl;
+    const int st = plan_forward(ndim, 1, C, D, H, W, spacing, lambda, 1, opt, &pl);
+    if (st != FGX_OK) return st;
+    *args = pl.args;
+    *sms = pl.sms;
+    return FGX_OK;
+}
+
+bool device_pointer(const void* p) { return is_device_ptr(p); }
+
 }  // namespace fgx
 
 using namespace fgx;
@@ -479,13 +500,6 @@ int fgx_geodesic3d_bwd(const float* grad_dist, const float* image, const void* s
                         stream);
 }
 
-// Batched entry points are served by a later version of the library.
-int fgx_batched_workspace_size(const fgx_instance*, int, const fgx_options*, size_t*) {
-    return FGX_ERR_UNSUPPORTED;
-}
-int fgx_geodesic_batched(const fgx_instance*, int, void*, size_t, const fgx_options*, void*) {
-    return FGX_ERR_UNSUPPORTED;
-}
 
 }  // extern "C"
 

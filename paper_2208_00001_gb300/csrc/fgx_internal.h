@@ -12,7 +12,9 @@ constexpr int kMaxPasses = 6;
 // Workspace header: device status word (offset 0), grid-barrier counter
 // (offset 64), phase timeline of 16 globaltimer stamps (offset 128).
 constexpr size_t kHeaderBytes = 256;
-constexpr int kThreads = 256;
+constexpr int kThreads = 512;
+// Largest tile region (tile + ring) of the tiled engine, in elements.
+constexpr int kMaxRegion = 1024;
 
 // Geometry of one directional pass over an instance of extents (D, H, W).
 // The pass moves along `axis` (0 = D, 1 = H, 2 = W) in direction `dir`; the
@@ -25,7 +27,11 @@ struct PassGeom {
     int ntp, ntq;        // tiles along p and q
     int K;               // lines per exchange block (= ring width)
     float t[9];          // (1 - lambda) * |offset|^2 per stencil offset
+    float c[9];          // sqrt(t) (the cost itself when lambda = 0)
 };
+
+// Edge-cost evaluation modes of the tiled engine (see sweep_kernel.cu).
+enum { kCostGeneral = 0, kCostAbs = 1, kCostConst = 2 };
 
 struct SweepArgs {
     const float* image;  // [B][C][N]
@@ -43,6 +49,55 @@ struct SweepArgs {
     long long timeout_ns;
     int max_tiles;
     int smem_region;              // floats per (D or I-channel) region buffer
+    int kmax;                     // most lines per exchange block over the passes
+    int cost_mode;                // kCostGeneral / kCostAbs / kCostConst
+};
+
+// One tile of one instance for one pass application of the tiled engine.
+struct TileJob {
+    const float* img;             // instance image [C][N]
+    float* dist;                  // instance distance map [N]
+    uint8_t* codes;               // this pass application's codes [N] or null
+    unsigned long long* flags;    // the instance's tile progress tags
+    int64_t N;
+    int C, ndim;
+    float lambda;
+    int seq;                      // increasing pass-application counter (tags)
+    int tile;
+    int region, kmax;
+    int* status;
+    long long timeout_ns;
+};
+
+// One instance of a batched launch (device-side descriptor).
+struct InstDesc {
+    const float* image;  // [C][N]
+    const float* mask;   // [N]
+    float* dist;         // [N]
+    int64_t N;
+    int C, ndim;
+    float v, lambda;
+    int napps;           // pass applications: iterations * passes
+    int npass;
+    int cost_mode;
+    int flags_off;       // first progress tag of this instance in the tag array
+    int region, kmax;    // this instance's tile buffer geometry
+    PassGeom pass[kMaxPasses];
+};
+
+// Batched launch: instances advance one pass application per round; within a
+// round, each wave assigns whole instances to consecutive thread blocks
+// (wave_items[w * grid + block] = instance << 16 | tile, or -1).
+struct BatchedArgs {
+    const InstDesc* desc;
+    int n;
+    int rounds;
+    const int* round_waves;  // [rounds + 1] first wave of each round
+    const int* wave_items;   // [waves][grid]
+    unsigned long long* flags;
+    unsigned int* barrier;
+    int* status;
+    long long timeout_ns;
 };
 
 // Reverse sweep through recorded parent codes (adjoint_kernel.cu).  Uses the
@@ -68,6 +123,11 @@ struct AdjointArgs {
 };
 
 // Host helpers (fgx_api.cu)
+// Geometry, tiling and buffer sizes of one instance (B = 1) on the tiled
+// engine; fills args (pointers unset) and the device's SM count.
+int plan_instance(int ndim, int64_t C, int64_t D, int64_t H, int64_t W, const float spacing[3],
+                  float lambda, const fgx_options* opt, SweepArgs* args, int* sms);
+bool device_pointer(const void* p);
 void pass_offsets_t(int ndim, int axis, const float sp[3], float lambda, float t[9]);
 void pass_extents(int axis, const int64_t ext[3], PassGeom* g);
 
@@ -84,7 +144,10 @@ int launch_adjoint(const AdjointArgs& a, int grid, size_t smem, void* stream);
 int adjoint_max_blocks_per_sm(size_t smem, int* blocks);
 
 // Launchers (sweep_kernel.cu)
+size_t sweep_smem_bytes(int64_t C, int region, int kmax);
 int launch_sweep(const SweepArgs& a, int grid, size_t smem, void* stream);
+int launch_batched(const BatchedArgs& a, int grid, size_t smem, void* stream);
+int batched_max_blocks_per_sm(size_t smem, int* blocks);
 int sweep_max_blocks_per_sm(size_t smem, int* blocks);
 
 }  // namespace fgx
