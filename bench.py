@@ -222,6 +222,116 @@ def cpu_baseline_sample(case, budget_s=12.0):
                       f"{len(times)} runs, OpenMP over line elements"}
 
 
+def _device_time(fn, steps, flush, stream):
+    """Mean device time (s) of fn() over `steps` runs, L2 flushed between
+    runs outside the timed events."""
+    import torch
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    for i in range(steps):
+        flush.fill_(i & 0xFF)
+        starts[i].record(stream)
+        fn()
+        ends[i].record(stream)
+    torch.cuda.synchronize()
+    return statistics.mean(s.elapsed_time(e) for s, e in zip(starts, ends)) / 1e3
+
+
+def _roof(bytes_, t, peak):
+    gbs = bytes_ / t / 1e9
+    return {"achieved_gbs": gbs, "frac": gbs / peak, "algorithmic_bytes": bytes_}
+
+
+def measure_extras(fgx, dev, flush, stream, peak, steps=5):
+    """The other workloads of the method on this GPU, each timed like the
+    headline (warm-up, L2 flush between steps, CUDA events)."""
+    import torch
+    import workloads
+    out = {}
+
+    def fwd_bytes(c):
+        npass = 6 if c.ndim == 3 else 4
+        per = 8 if c.lam == 0 else 8 + 4 * c.image.shape[1]
+        return c.voxels * c.iterations * npass * per
+
+    def run_case(c, warm=2):
+        img = torch.from_numpy(c.image).to(dev)
+        m = torch.from_numpy(c.mask).to(dev)
+        o = torch.empty_like(m)
+        ws = torch.empty(fgx.workspace_size(c.ndim, *([img.shape[0], img.shape[1]] + (
+            [1] if c.ndim == 2 else []) + list(img.shape[2:]))), dtype=torch.uint8, device=dev)
+        fn = lambda: fgx.geodesic(img, m, c.v, c.lam, c.iterations, spacing=c.spacing,  # noqa
+                                  out=o, workspace=ws)
+        for _ in range(warm):
+            fn()
+        t = _device_time(fn, steps, flush, stream)
+        st = fgx.workspace_status(ws)
+        return t, st
+
+    for name, c in [("2d_plain_256", workloads.plain2d()),
+                    ("2d_large_lambda0", workloads.large2d(lam=0.0)),
+                    ("2d_large_lambda1", workloads.large2d(lam=1.0)),
+                    ("2d_large_lambda0.5_it4", workloads.large2d(iterations=4)),
+                    ("3d_volume_128x256x256", workloads.volume3d())]:
+        t, st = run_case(c)
+        out[name] = {"ms": t * 1e3, "mvox_per_s_per_iter": c.voxels * c.iterations / t / 1e6,
+                     "roofline": _roof(fwd_bytes(c), t, peak),
+                     "device_status": fgx.status_string(st)}
+
+    # batched: one persistent launch vs the same instances as sequential calls
+    cases = workloads.batched()
+    gpu = [(torch.from_numpy(c.image).to(dev), torch.from_numpy(c.mask).to(dev), c.v, c.lam,
+            c.iterations, c.spacing or (1.0, 1.0, 1.0)) for c in cases]
+    plan = fgx.BatchedPlan(gpu)
+    plan.run()
+    t_b = _device_time(plan.run, steps, flush, stream)
+    st_b = fgx.workspace_status(plan.workspace)
+    seq_outs = [torch.empty_like(g[1]) for g in gpu]
+
+    def sequential():
+        for g, o in zip(gpu, seq_outs):
+            fgx.geodesic(g[0], g[1], g[2], g[3], g[4], spacing=g[5], out=o)
+    sequential()
+    t_s = _device_time(sequential, max(2, steps // 2), flush, stream)
+    units = sum(c.voxels * c.iterations for c in cases)
+    bbytes = sum(fwd_bytes(c) for c in cases)
+    out["batched_64x2d_16x3d"] = {
+        "instances": len(cases), "voxel_iterations": units,
+        "one_launch_ms": t_b * 1e3, "one_launch_mvox_per_s_per_iter": units / t_b / 1e6,
+        "sequential_80_calls_ms": t_s * 1e3,
+        "sequential_mvox_per_s_per_iter": units / t_s / 1e6,
+        "roofline_one_launch": _roof(bbytes, t_b, peak),
+        "device_status": fgx.status_string(st_b)}
+
+    # differentiable: forward, forward with codes, backward
+    for name, c in [("diff_2d_8x512x512", workloads.diff2d()),
+                    ("diff_3d_96x160x160", workloads.diff3d())]:
+        img = torch.from_numpy(c.image).to(dev)
+        m = torch.from_numpy(c.mask).to(dev)
+        w = torch.from_numpy(c.extra["w"]).to(dev)
+        f_plain = lambda: fgx.geodesic(img, m, c.v, c.lam, c.iterations, spacing=c.spacing)  # noqa
+        f_train = lambda: fgx.forward_train(img, m, c.v, c.lam, c.iterations,  # noqa
+                                            spacing=c.spacing)
+        d, saved = f_train()
+        f_bwd = lambda: fgx.backward(w, img, saved, c.v, c.lam, c.iterations,  # noqa
+                                     spacing=c.spacing)
+        for f in (f_plain, f_train, f_bwd):
+            f()
+        tp = _device_time(f_plain, steps, flush, stream)
+        tt = _device_time(f_train, steps, flush, stream)
+        tb = _device_time(f_bwd, steps, flush, stream)
+        units = c.voxels * c.iterations
+        C = c.image.shape[1]
+        npass = 6 if c.ndim == 3 else 4
+        bwd_bytes = c.voxels * c.iterations * npass * (8 + 2 + 4 * C + 8 * C)
+        out[name] = {"fwd_ms": tp * 1e3, "fwd_train_ms": tt * 1e3, "bwd_ms": tb * 1e3,
+                     "fwd_plus_bwd_ms": (tt + tb) * 1e3,
+                     "fwd_mvox_per_s_per_iter": units / tp / 1e6,
+                     "fwd_plus_bwd_mvox_per_s_per_iter": units / (tt + tb) / 1e6,
+                     "bwd_roofline": _roof(bwd_bytes, tb, peak)}
+    return out
+
+
 def run_fgx(args):
     import torch
 
@@ -279,7 +389,7 @@ def run_fgx(args):
     bytes_per_launch = N * its * PASSES_2D * (8 + 4 * C)
     peak, peak_kind = _peaks()
     achieved = bytes_per_launch / t_step / 1e9
-    traffic = _profile_traffic("sweep_kernel_2d_large")
+    traffic = _profile_traffic("chain2d_kernel_2d_large")
 
     # end-to-end through the public API with host buffers
     h_img = torch.from_numpy(case.image).pin_memory()
@@ -307,6 +417,9 @@ def run_fgx(args):
     t_e2e = e_s.elapsed_time(e_e) / 1e3 / args.steps
     t_e2e = _max_over_ranks(t_e2e, world)
 
+    extras = None
+    if not args.no_extras and rank == 0:
+        extras = measure_extras(fgx, dev, flush, stream, peak)
     if rank != 0:
         return 0
     line = {
@@ -320,7 +433,7 @@ def run_fgx(args):
                    "wall_s_timed_loop": wall},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic,
-                     "peak_source": peak_kind, "kernel": "sweep_kernel",
+                     "peak_source": peak_kind, "kernel": "chain2d_kernel",
                      "algorithmic_bytes_per_launch": bytes_per_launch},
         "e2e": {"value": world * N * its / t_e2e / 1e6, "unit": "Mvoxel/s",
                 "h2d_bytes_per_step": int(h_img.numel() * 4 + h_m.numel() * 4),
@@ -330,6 +443,8 @@ def run_fgx(args):
     }
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline_sample(case)
+    if extras is not None:
+        line["extras"] = extras
     print(json.dumps(line))
     return 0
 
@@ -341,6 +456,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="fgx", choices=["fgx", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the other workloads (3D, batched, differentiable)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
