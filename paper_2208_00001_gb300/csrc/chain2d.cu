@@ -15,17 +15,19 @@
 // edges between columns w and w+1.  With lambda = 0 the costs are the
 // constants sqrt(t_k) and no table is built.
 //
-// Work decomposition.  One cooperative persistent launch.  Each warp owns a
-// tile of T columns of one line plus a ring of K columns on each side
-// (T + 2K = 128, four columns per lane).  Per line a lane reads its prefetched
-// slice of the previous-line distances, costs and old values, gets the two
-// neighbouring columns across lanes by shuffle and applies the min-plus
-// update; the dependency cone shrinks the valid part of the ring by one column
-// per line, so after K lines the owned columns are exact.  Every K lines a
-// warp publishes the 2K owned columns its neighbours need as 64-bit words
-// (value, tag) and polls the neighbours' words until the tags match (bounded
-// wait); the ring is then refreshed.  Rows are prefetched kStages lines ahead
-// with cp.async.  Passes are separated by a grid barrier.
+// Work decomposition.  One cooperative persistent launch; each thread block
+// owns a tile of T columns of one line plus a ring of K columns on each side
+// (T + 2K = 128, four columns per lane of the chain warp).  Three warps per
+// block: the chain warp applies the min-plus update line after line, getting
+// the two neighbouring columns across lanes by shuffle; a producer warp
+// copies old values and edge costs into a shared-memory ring of 8-line
+// chunks ahead of it; a flusher warp writes finished chunks out.  The
+// dependency cone shrinks the valid part of the ring by one column per line,
+// so after K lines the owned columns are exact; every K lines (a whole number
+// of chunks) the chain warp publishes the 2K owned columns its neighbours
+// need as 64-bit words (value, tag) and polls the neighbours' words until the
+// tags match (bounded wait); the ring is then refreshed.  Passes are
+// separated by a grid barrier.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -39,11 +41,9 @@ namespace fgx {
 
 namespace {
 
-constexpr int kWarps = 2;              // warps per thread block
-constexpr int kStages = 16;            // prefetch depth in lines
-constexpr int kRegion = 128;           // columns per warp (4 per lane)
+constexpr int kRegion = 128;           // columns per tile region (4 per lane)
+constexpr int kBlockThreads = 96;      // chain, producer and flusher warps
 constexpr int kMaxRing = 48;           // words per exchanged strip
-constexpr int kStageDepth = 32;        // lines per transposed-output flush
 #define kInf __int_as_float(0x7f800000)
 
 struct Chain2DArgs {
@@ -75,14 +75,6 @@ __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
     const unsigned int sa = (unsigned int)__cvta_generic_to_shared(smem);
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sa), "l"(gmem) : "memory");
 }
-__device__ __forceinline__ void cp_async_commit() {
-    asm volatile("cp.async.commit_group;" ::: "memory");
-}
-template <int N>
-__device__ __forceinline__ void cp_async_wait() {
-    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
-}
-
 // Cost of the undirected edge between a and b (same channel stride n), in the
 // fixed arithmetic order: di2 = sum_ch (I(a)-I(b))^2, c = sqrt(t + lambda*di2).
 __device__ __forceinline__ float edge_cost(const float* ia, const float* ib, int C, int64_t n,
@@ -95,310 +87,485 @@ __device__ __forceinline__ float edge_cost(const float* ia, const float* ib, int
     return __fsqrt_rn(__fadd_rn(t, __fmul_rn(lam, di2)));
 }
 
-struct WarpSmem {
-    float D[kStages][kRegion];
-    float E[kStages][3][kRegion];
-    float stage[kRegion][kStageDepth + 1];  // transposed-output staging [owned col][line]
-};
+// Producer/consumer organisation of one tile, three warps.  The chain warp
+// holds four columns per lane in registers and applies the min-plus update
+// in fully unrolled chunks of kCh lines; the producer warp copies the rows of
+// old distances and edge costs into a ring of chunks ahead of it (cp.async,
+// completion tracked by one mbarrier per chunk); the flusher warp writes the
+// finished chunks to global memory, transposed where the pass requires.
+// Waits, ring exchanges and hand-overs happen only between chunks, so the
+// per-line code has no branches.
+constexpr int kCh = 8;              // lines per chunk
+constexpr int kNci = 5;             // chunks in the input ring
+constexpr int kNo = 3;              // chunks in the output ring
+constexpr int kRow = kRegion + 8;   // floats per input row: 4 pad | 128 | 4 pad
+constexpr int kOutLd = kRegion + 4; // floats per output row (conflict-free transposes)
 
-// One warp sweeps one tile of one pass.  Returns false once the device status
-// records a failure (the warp then skips the rest of its work).
-template <bool fwd, bool table>
-__device__ bool chain_tile(const Chain2DArgs& a, int t_app, int pass, int b, int tile,
-                           WarpSmem& sm) {
-    const int lane = threadIdx.x & 31;
-    const bool vert = pass < 2;          // rows of Dw (TB/BT) or rows of Dt (LR/RL)
-    const int L = vert ? a.H : a.W;       // number of lines
-    const int Q = vert ? a.W : a.H;       // line length
-    const int ld = vert ? a.Wp : a.Hp;    // row stride of the source array
-    const int ntiles = vert ? a.tiles_v : a.tiles_h;
-    const bool multi = ntiles > 1;
-    const int K = multi ? a.K : 0;
-    const int T = multi ? a.T : Q;
-    const int q0 = multi ? tile * T : 0;
-    const int q1 = min(Q, q0 + T);
-    const int r0 = q0 - K;
-    const int c0 = r0 + 4 * lane;
-    const float* src = vert ? a.Dw + (int64_t)b * a.H * a.Wp : a.Dt + (int64_t)b * a.W * a.Hp;
-    const float* E = vert ? a.Ev + (int64_t)b * 3 * a.H * a.Wp : a.Eh + (int64_t)b * 3 * a.W * a.Hp;
-    const int64_t eplane = (int64_t)L * ld;
-    const float tc0 = vert ? a.cv[0] : a.chh[0];
-    const float tc1 = vert ? a.cv[1] : a.chh[1];
-    const float tc2 = vert ? a.cv[2] : a.chh[2];
-    // output
-    const bool transposed_out = !fwd;  // BT -> Dt, RL -> Dw or dist
-    const bool last_rl = (pass == 3) && (t_app == a.iterations * 4 - 1);
+struct TileSmem {
+    unsigned long long in_full[kNci], in_empty[kNci], out_full[kNo], out_empty[kNo];
+    float in[kNci][kCh][4][kRow];   // per line: old values, edge rows E0, E1, E2
+    float out[kNo][kCh][kOutLd];    // chain results per line
+};
+static_assert((2 * kNci + 2 * kNo) * 8 % 16 == 0, "ring rows must stay 16-byte aligned");
+
+__device__ __forceinline__ unsigned int saddr(const void* p) {
+    return (unsigned int)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(unsigned long long* b, unsigned int count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(saddr(b)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(unsigned long long* b) {
+    asm volatile("mbarrier.arrive.release.cta.shared::cta.b64 _, [%0];" ::"r"(saddr(b)) : "memory");
+}
+// One arrival on *b once every cp.async this thread issued so far has landed.
+__device__ __forceinline__ void cp_async_arrive_noinc(unsigned long long* b) {
+    asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(saddr(b)) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+    asm volatile("cp.async.wait_all;" ::: "memory");
+}
+__device__ __forceinline__ bool mbar_test(unsigned long long* b, unsigned int parity) {
+    unsigned int ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.acquire.cta.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(saddr(b)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// Non-blocking test of the same phase.
+__device__ __forceinline__ bool mbar_peek(unsigned long long* b, unsigned int parity) {
+    unsigned int ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.test_wait.parity.acquire.cta.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(saddr(b)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// Waits (bounded) for the completion of the phase of parity `parity` of *b;
+// false on timeout or an earlier failure recorded in the status word.
+__device__ __noinline__ bool mbar_wait_slow(unsigned long long* b, unsigned int parity,
+                                            int* status, long long timeout_ns) {
+    const long long t0 = gtimer();
+    for (;;) {
+        if (mbar_test(b, parity)) return true;
+        if (status_of(status) != 0) return false;
+        if (gtimer() - t0 > timeout_ns) {
+            record_timeout(status);
+            return false;
+        }
+    }
+}
+__device__ __forceinline__ bool mbar_wait(unsigned long long* b, unsigned int parity,
+                                          const Chain2DArgs& a) {
+    if (mbar_test(b, parity)) return true;
+    return mbar_wait_slow(b, parity, a.status, a.timeout_ns);
+}
+// Chunk gc of a ring of n slots: slot, parity of its "full" phase, and parity
+// of the "empty" phase that frees the slot (the release of chunk gc - n).
+__device__ __forceinline__ int slot_of(unsigned int gc, int n) { return (int)(gc % (unsigned)n); }
+__device__ __forceinline__ unsigned int full_parity(unsigned int gc, int n) {
+    return (gc / (unsigned)n) & 1u;
+}
+__device__ __forceinline__ unsigned int empty_parity(unsigned int gc, int n) {
+    return ((gc / (unsigned)n) & 1u) ^ 1u;
+}
+
+// Geometry of one tile of one pass, identical in the three warps.
+struct TileGeo {
+    int L, Q, ld, ntiles, K, T, q0, q1, r0, nch;
+    bool multi;
+    const float* src;
+    const float* E;
+    int64_t eplane;
     float* out;
     int out_ld;
-    if (pass == 0) { out = a.Dw + (int64_t)b * a.H * a.Wp; out_ld = a.Wp; }
-    else if (pass == 1) { out = a.Dt + (int64_t)b * a.W * a.Hp; out_ld = a.Hp; }
-    else if (pass == 2) { out = a.Dt + (int64_t)b * a.W * a.Hp; out_ld = a.Hp; }
-    else if (last_rl) { out = a.dist + (int64_t)b * a.H * a.W; out_ld = a.W; }
-    else { out = a.Dw + (int64_t)b * a.H * a.Wp; out_ld = a.Wp; }
+};
 
-    bool valid[4], owned[4];
+__device__ __forceinline__ TileGeo tile_geo(const Chain2DArgs& a, int t_app, int pass, int b,
+                                            int tile) {
+    TileGeo g;
+    const bool vert = pass < 2;  // rows of Dw (TB/BT) or rows of Dt (LR/RL)
+    g.L = vert ? a.H : a.W;
+    g.Q = vert ? a.W : a.H;
+    g.ld = vert ? a.Wp : a.Hp;
+    g.ntiles = vert ? a.tiles_v : a.tiles_h;
+    g.multi = g.ntiles > 1;
+    g.K = g.multi ? a.K : 0;
+    g.T = g.multi ? a.T : g.Q;
+    g.q0 = g.multi ? tile * g.T : 0;
+    g.q1 = min(g.Q, g.q0 + g.T);
+    g.r0 = g.q0 - g.K;
+    g.nch = (g.L + kCh - 1) / kCh;
+    g.src = vert ? a.Dw + (int64_t)b * a.H * a.Wp : a.Dt + (int64_t)b * a.W * a.Hp;
+    g.E = vert ? a.Ev + (int64_t)b * 3 * a.H * a.Wp : a.Eh + (int64_t)b * 3 * a.W * a.Hp;
+    g.eplane = (int64_t)g.L * g.ld;
+    const bool last_rl = (pass == 3) && (t_app == a.iterations * 4 - 1);
+    if (pass == 0) { g.out = a.Dw + (int64_t)b * a.H * a.Wp; g.out_ld = a.Wp; }
+    else if (pass == 1) { g.out = a.Dt + (int64_t)b * a.W * a.Hp; g.out_ld = a.Hp; }
+    else if (pass == 2) { g.out = a.Dt + (int64_t)b * a.W * a.Hp; g.out_ld = a.Hp; }
+    else if (last_rl) { g.out = a.dist + (int64_t)b * a.H * a.W; g.out_ld = a.W; }
+    else { g.out = a.Dw + (int64_t)b * a.H * a.Wp; g.out_ld = a.Wp; }
+    return g;
+}
+
+// Producer warp: chunk c of the tile goes to ring slot (cb + c) % kNci once
+// the chain has released that slot.  The edge row between steps s-1 and s is
+// row s-1 of the table in a forward pass and row L-1-s in a backward one;
+// the first line of a sweep has no parents and gets no edge row.
+template <bool fwd, bool table>
+__device__ bool producer_tile(const Chain2DArgs& a, const TileGeo& g, TileSmem& sm,
+                              unsigned int cb) {
+    const int lane = threadIdx.x & 31;
+    const int c0 = g.r0 + 4 * lane;
+    const bool lane_loads = (c0 >= 0) && (c0 < g.Q);
+    const int L = g.L;
+    for (int c = 0; c < g.nch; ++c) {
+        const unsigned int gc = cb + c;
+        const int slot = slot_of(gc, kNci);
+        if (gc >= (unsigned)kNci &&
+            !__all_sync(0xffffffffu, mbar_wait(&sm.in_empty[slot], empty_parity(gc, kNci), a))) {
+            cp_async_wait_all();
+            return false;
+        }
+        if (lane_loads) {
+            const int jn = min(kCh, L - c * kCh);
+            for (int j = 0; j < jn; ++j) {
+                const int s = c * kCh + j;
+                const int line = fwd ? s : (L - 1 - s);
+                float(*row)[kRow] = sm.in[slot][j];
+                cp_async16(&row[0][4 + 4 * lane], g.src + (int64_t)line * g.ld + c0);
+                if (table && s >= 1) {
+                    const float* ep = g.E + (int64_t)(fwd ? s - 1 : line) * g.ld + c0;
+                    cp_async16(&row[1][4 + 4 * lane], ep);
+                    cp_async16(&row[2][4 + 4 * lane], ep + g.eplane);
+                    cp_async16(&row[3][4 + 4 * lane], ep + 2 * g.eplane);
+                }
+            }
+        }
+        cp_async_arrive_noinc(&sm.in_full[slot]);
+    }
+    return true;
+}
+
+// Flusher warp: writes the owned columns of each finished chunk.
+template <bool fwd>
+__device__ bool flusher_tile(const Chain2DArgs& a, const TileGeo& g, TileSmem& sm,
+                             unsigned int cb) {
+    const int lane = threadIdx.x & 31;
+    const int c0 = g.r0 + 4 * lane;
+    const int L = g.L;
+    bool owned[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) owned[i] = (c0 + i >= g.q0) && (c0 + i < g.q1);
+    const bool all_owned = owned[0] && owned[3];
+    const int ncol = g.q1 - g.q0;
+    const int off = g.q0 - g.r0;
+    for (int c = 0; c < g.nch; ++c) {
+        const unsigned int gc = cb + c;
+        const int slot = slot_of(gc, kNo);
+        if (!__all_sync(0xffffffffu, mbar_wait(&sm.out_full[slot], full_parity(gc, kNo), a)))
+            return false;
+        const int s0 = c * kCh;
+        const int nl = min(kCh, L - s0);
+        if (fwd) {
+            // rows of the output array: each lane writes its own four columns
+            float4 v[kCh];
+#pragma unroll
+            for (int j = 0; j < kCh; ++j)
+                v[j] = *reinterpret_cast<const float4*>(&sm.out[slot][j][4 * lane]);
+#pragma unroll
+            for (int j = 0; j < kCh; ++j) {
+                if (j >= nl) break;
+                float* row = g.out + (int64_t)(s0 + j) * g.out_ld + c0;
+                if (all_owned) {
+                    *reinterpret_cast<float4*>(row) = v[j];
+                } else {
+                    if (owned[0]) row[0] = v[j].x;
+                    if (owned[1]) row[1] = v[j].y;
+                    if (owned[2]) row[2] = v[j].z;
+                    if (owned[3]) row[3] = v[j].w;
+                }
+            }
+        } else {
+            // transposed: consecutive lanes write consecutive lines of a column
+            // (four columns per warp-wide store, four stores in flight)
+            const int jj = lane & (kCh - 1);
+            const int line = L - 1 - (s0 + jj);
+            for (int col0 = lane >> 3; col0 < ncol; col0 += 16) {
+                float v[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int col = col0 + 4 * u;
+                    v[u] = col < ncol ? sm.out[slot][jj][off + col] : 0.0f;
+                }
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int col = col0 + 4 * u;
+                    if (col < ncol && jj < nl)
+                        g.out[(int64_t)(g.q0 + col) * g.out_ld + line] = v[u];
+                }
+            }
+        }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&sm.out_empty[slot]);
+    }
+    return true;
+}
+
+// One line of chain input in registers: old values and the costs of the
+// three parents (column offsets -1, 0, +1) of each of the lane's columns.
+struct LineIn {
+    float dold[4];
+    float c0[4], c1[4], c2[4];
+};
+
+// Reads line j of a ring chunk.  Ring row k+1 holds E_k[e][x], the cost of
+// the edge from column x of one line to column x+k-1 of the next.  In a
+// forward step the parent of x at offset k-1 sits on the previous line, so
+// its cost is E_{2-k}[x+k-1] (the two shifted rows need one extra element
+// from the padding or the neighbouring lane's range); in a backward step the
+// parent sits on the next line and the cost is E_k[x].
+template <bool fwd, bool table>
+__device__ __forceinline__ void load_line(const float (*p)[kRow], int lane, LineIn& r, float k0,
+                                          float k1, float k2) {
+    const float4 o = *reinterpret_cast<const float4*>(&p[0][4 + 4 * lane]);
+    r.dold[0] = o.x; r.dold[1] = o.y; r.dold[2] = o.z; r.dold[3] = o.w;
+    if (!table) {
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            r.c0[i] = k0;
+            r.c1[i] = k1;
+            r.c2[i] = k2;
+        }
+        return;
+    }
+    const float4 e0 = *reinterpret_cast<const float4*>(&p[1][4 + 4 * lane]);
+    const float4 e1 = *reinterpret_cast<const float4*>(&p[2][4 + 4 * lane]);
+    const float4 e2 = *reinterpret_cast<const float4*>(&p[3][4 + 4 * lane]);
+    if (fwd) {
+        const float e2m = p[3][3 + 4 * lane];
+        const float e0p = p[1][8 + 4 * lane];
+        r.c0[0] = e2m;  r.c0[1] = e2.x; r.c0[2] = e2.y; r.c0[3] = e2.z;
+        r.c2[0] = e0.y; r.c2[1] = e0.z; r.c2[2] = e0.w; r.c2[3] = e0p;
+    } else {
+        r.c0[0] = e0.x; r.c0[1] = e0.y; r.c0[2] = e0.z; r.c0[3] = e0.w;
+        r.c2[0] = e2.x; r.c2[1] = e2.y; r.c2[2] = e2.z; r.c2[3] = e2.w;
+    }
+    r.c1[0] = e1.x; r.c1[1] = e1.y; r.c1[2] = e1.z; r.c1[3] = e1.w;
+}
+
+// One min-plus line update (Jacobi within the line): candidates in the fixed
+// order old value, own parents, then the parents held by the neighbouring
+// lanes; columns outside the array stay at +inf.
+__device__ __forceinline__ void chain_step(float (&dp)[4], const LineIn& c, const bool (&valid)[4],
+                                           int lane, float* out) {
+    float left = __shfl_up_sync(0xffffffffu, dp[3], 1);
+    float right = __shfl_down_sync(0xffffffffu, dp[0], 1);
+    if (lane == 0) left = kInf;
+    if (lane == 31) right = kInf;
+    float nd[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        float best = c.dold[i];
+        if (i > 0) best = fminf(best, __fadd_rn(dp[i - 1], c.c0[i]));
+        best = fminf(best, __fadd_rn(dp[i], c.c1[i]));
+        if (i < 3) best = fminf(best, __fadd_rn(dp[i + 1], c.c2[i]));
+        if (i == 0) best = fminf(best, __fadd_rn(left, c.c0[0]));
+        if (i == 3) best = fminf(best, __fadd_rn(right, c.c2[3]));
+        nd[i] = valid[i] ? best : kInf;
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) dp[i] = nd[i];
+    *reinterpret_cast<float4*>(out) = make_float4(nd[0], nd[1], nd[2], nd[3]);
+}
+
+// Ring refresh of a multi-tile pass before step s (dp holds line s-1):
+// publish the owned columns the neighbours' rings cover, then take the ring
+// columns from the neighbours (bounded wait on the tags).
+__device__ __forceinline__ bool exchange(const Chain2DArgs& a, const TileGeo& g, int b, int tile,
+                                         unsigned int tg, int par, float (&dp)[4],
+                                         const bool (&valid)[4]) {
+    const int lane = threadIdx.x & 31;
+    const int c0 = g.r0 + 4 * lane;
+    const int q0 = g.q0, K = g.K, T = g.T;
+    unsigned long long* mine =
+        a.xbuf + ((int64_t)b * a.max_tiles + tile) * (4 * kMaxRing) + par * (2 * kMaxRing);
+    const int rq = q0 + T - K;
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
         const int c = c0 + i;
-        valid[i] = c >= 0 && c < Q;
-        owned[i] = c >= q0 && c < q1;
+        const unsigned long long w =
+            ((unsigned long long)tg << 32) | (unsigned int)__float_as_uint(dp[i]);
+        if (c >= q0 && c < q0 + K) st_relaxed_u64(mine + (c - q0), w);
+        if (c >= rq && c < q0 + T) st_relaxed_u64(mine + kMaxRing + (c - rq), w);
     }
-    // each lane prefetches (and later reads) only its own 16-byte slice of
-    // every row, so no cross-lane synchronisation is needed for the ring
-    const bool lane_loads = (c0 >= 0) && (c0 < Q);
-
-    auto line_of = [&](int s) { return fwd ? s : (L - 1 - s); };
-
-    // prefetch cursors: the next item to fetch, its source rows and stage
-    const int64_t step = fwd ? (int64_t)ld : -(int64_t)ld;
-    const float* pf_d = src + (int64_t)line_of(0) * ld + c0;
-    const float* pf_e = E + (int64_t)(fwd ? 0 : (L - 2)) * ld + c0 - step;  // edge row of item 0 (unused)
-    int pf_next = 0;
-    auto prefetch = [&]() {
-        const int s = pf_next++;
-        if (s < L && lane_loads) {
-            const int slot = s & (kStages - 1);
-            cp_async16(&sm.D[slot][4 * lane], pf_d);
-            if (table && s >= 1) {
-                cp_async16(&sm.E[slot][0][4 * lane], pf_e);
-                cp_async16(&sm.E[slot][1][4 * lane], pf_e + eplane);
-                cp_async16(&sm.E[slot][2][4 * lane], pf_e + 2 * eplane);
-            }
-        }
-        pf_d += step;
-        pf_e += step;
-        cp_async_commit();  // one group per item, possibly empty
-    };
-
-    // Registers of one line: old values and the parent costs of the lane's
-    // four columns (cost shifts across lanes done at load time, off the chain).
-    struct LineRegs {
-        float dold[4];
-        float cst[3][4];
-    };
-    auto load_line = [&](int s, LineRegs& r) {
-        const int slot = s & (kStages - 1);
-        const float4 o4 = *reinterpret_cast<const float4*>(&sm.D[slot][4 * lane]);
-        r.dold[0] = o4.x; r.dold[1] = o4.y; r.dold[2] = o4.z; r.dold[3] = o4.w;
-        if (s == 0) return;
-        if constexpr (table) {
-            float e[3][4];
-#pragma unroll
-            for (int k = 0; k < 3; ++k) {
-                const float4 v4 = *reinterpret_cast<const float4*>(&sm.E[slot][k][4 * lane]);
-                e[k][0] = v4.x; e[k][1] = v4.y; e[k][2] = v4.z; e[k][3] = v4.w;
-            }
-            if constexpr (fwd) {
-                // parent at column c+k-1 of the previous line: edge E_{2-k}[line-1][c+k-1]
-                const float e2l = __shfl_up_sync(0xffffffffu, e[2][3], 1);
-                const float e0r = __shfl_down_sync(0xffffffffu, e[0][0], 1);
-#pragma unroll
-                for (int i = 0; i < 4; ++i) {
-                    r.cst[0][i] = (i == 0) ? e2l : e[2][i - 1];
-                    r.cst[1][i] = e[1][i];
-                    r.cst[2][i] = (i == 3) ? e0r : e[0][i + 1];
-                }
-            } else {
-                // parent at column c+k-1 of line+1: edge E_k[line][c]
-#pragma unroll
-                for (int k = 0; k < 3; ++k)
-#pragma unroll
-                    for (int i = 0; i < 4; ++i) r.cst[k][i] = e[k][i];
-            }
-        } else {
+    // ring lanes [q0-K, q0) and [q0+T, q0+T+K); lanes beyond the right ring
+    // hold columns outside the cone and are never refreshed
+    const bool left_ring = c0 < q0 && tile > 0;
+    const bool right_ring = c0 >= q0 + T && c0 < q0 + T + K && tile + 1 < g.ntiles;
+    const unsigned long long* nb = nullptr;
+    int base = 0;
+    if (left_ring) {
+        nb = a.xbuf + ((int64_t)b * a.max_tiles + tile - 1) * (4 * kMaxRing) +
+             par * (2 * kMaxRing) + kMaxRing;
+        base = c0 - (q0 - K);
+    } else if (right_ring) {
+        nb = a.xbuf + ((int64_t)b * a.max_tiles + tile + 1) * (4 * kMaxRing) +
+             par * (2 * kMaxRing);
+        base = c0 - (q0 + T);
+    }
+    float got[4] = {dp[0], dp[1], dp[2], dp[3]};
+    bool ok = (nb == nullptr);
+    long long t0 = 0;
+    for (unsigned int it = 0;; ++it) {
+        if (!ok) {
+            bool all = true;
 #pragma unroll
             for (int i = 0; i < 4; ++i) {
-                r.cst[0][i] = tc0;
-                r.cst[1][i] = tc1;
-                r.cst[2][i] = tc2;
+                const unsigned long long w = ld_relaxed_u64(nb + base + i);
+                if ((unsigned int)(w >> 32) != tg) all = false;
+                got[i] = __uint_as_float((unsigned int)w);
             }
+            ok = all;
         }
-    };
-
-    // items 0 .. kStages-2 in flight; item s is complete once at most
-    // kStages-2 younger groups are pending
-    for (int s = 0; s < kStages - 1; ++s) prefetch();
-
-    unsigned long long* xb = a.xbuf + ((int64_t)b * a.max_tiles + tile) * (4 * kMaxRing);
-    const unsigned int tag_base = ((unsigned int)(t_app + 1)) << 16;
-
-    float dp[4];
-    bool alive = true;
-    int stage_start = 1;  // first step whose output sits in the staging buffer
-    LineRegs cur, nxt;
-
-    // line 0 of the sweep: not updated; it seeds the chain
-    cp_async_wait<kStages - 2>();
-    load_line(0, cur);
-#pragma unroll
-    for (int i = 0; i < 4; ++i) dp[i] = valid[i] ? cur.dold[i] : kInf;
-    if (transposed_out) {
-        const int x0 = line_of(0);
-#pragma unroll
-        for (int i = 0; i < 4; ++i)
-            if (owned[i]) out[(int64_t)(c0 + i) * out_ld + x0] = dp[i];
-    }
-    prefetch();
-    if (L > 1) {
-        cp_async_wait<kStages - 2>();
-        load_line(1, cur);
-    }
-    int s = 1;
-    int next_refresh = multi ? 1 + K : L;  // first step of the next exchange block
-    int blk = 0;                           // exchange blocks finished so far
-    int x = line_of(1);
-    float* out_row = out + (int64_t)x * out_ld + c0;  // normal output cursor
-    const int64_t out_step = fwd ? (int64_t)out_ld : -(int64_t)out_ld;
-#pragma unroll 2
-    for (; s < L; ++s, x += fwd ? 1 : -1, out_row += out_step) {
-        // keep the pipeline full, then fetch the next line's registers so that
-        // their shared-memory latency overlaps this line's chain
-        prefetch();
-        if (s + 1 < L) {
-            cp_async_wait<kStages - 2>();
-            load_line(s + 1, nxt);
-        }
-        // ring refresh every K lines (multi-tile passes)
-        if (s == next_refresh) {
-            next_refresh += K;
-            const unsigned int tg = tag_base | (unsigned int)(blk + 1);
-            const int par = blk & 1;
-            unsigned long long* mine = xb + par * (2 * kMaxRing);
-            // publish: left-facing strip = owned columns [q0, q0+K), right-facing
-            // strip = owned columns [q0+T-K, q0+T)
-            const int rq = q0 + T - K;
-#pragma unroll
-            for (int i = 0; i < 4; ++i) {
-                const int c = c0 + i;
-                const unsigned long long w =
-                    ((unsigned long long)tg << 32) | (unsigned int)__float_as_uint(dp[i]);
-                if (c >= q0 && c < q0 + K) st_relaxed_u64(mine + (c - q0), w);
-                if (c >= rq && c < q0 + T) st_relaxed_u64(mine + kMaxRing + (c - rq), w);
-            }
-            // ring lanes: [q0-K, q0) and [q0+T, q0+T+K); lanes beyond the right
-            // ring (when T + 2K < 128) hold columns outside the cone and are
-            // never refreshed
-            const bool left_ring = c0 < q0 && tile > 0;
-            const bool right_ring = c0 >= q0 + T && c0 < q0 + T + K && tile + 1 < ntiles;
-            const unsigned long long* nb = nullptr;
-            int base = 0;
-            if (left_ring) {
-                nb = a.xbuf + ((int64_t)b * a.max_tiles + tile - 1) * (4 * kMaxRing) +
-                     par * (2 * kMaxRing) + kMaxRing;  // left neighbour's right-facing strip
-                base = c0 - (q0 - K);
-            } else if (right_ring) {
-                nb = a.xbuf + ((int64_t)b * a.max_tiles + tile + 1) * (4 * kMaxRing) +
-                     par * (2 * kMaxRing);             // right neighbour's left-facing strip
-                base = c0 - (q0 + T);
-            }
-            float got[4] = {dp[0], dp[1], dp[2], dp[3]};
-            bool ok = (nb == nullptr);
-            const long long t0 = gtimer();
-            for (;;) {
-                if (!ok) {
-                    bool all = true;
-#pragma unroll
-                    for (int i = 0; i < 4; ++i) {
-                        const unsigned long long w = ld_relaxed_u64(nb + base + i);
-                        if ((unsigned int)(w >> 32) != tg) all = false;
-                        got[i] = __uint_as_float((unsigned int)w);
-                    }
-                    ok = all;
+        if (__all_sync(0xffffffffu, ok)) break;
+        // the status word and the clock are read every 16th poll only
+        if ((it & 15u) == 15u) {
+            int fail = 0;
+            if (lane == 0) {
+                const long long now = gtimer();
+                if (t0 == 0) t0 = now;
+                if (status_of(a.status) != 0) fail = 1;
+                else if (now - t0 > a.timeout_ns) {
+                    record_timeout(a.status);
+                    fail = 1;
                 }
-                if (__all_sync(0xffffffffu, ok)) break;
-                int fail = 0;
-                if (lane == 0) {
-                    if (status_of(a.status) != 0) fail = 1;
-                    else if (gtimer() - t0 > a.timeout_ns) {
-                        record_timeout(a.status);
-                        fail = 1;
-                    }
-                }
-                if (__shfl_sync(0xffffffffu, fail, 0)) { alive = false; break; }
-                __nanosleep(20);
             }
-            if (!alive) break;
-            if (nb) {
-#pragma unroll
-                for (int i = 0; i < 4; ++i) dp[i] = valid[i] ? got[i] : kInf;
-            }
-            ++blk;
+            if (__shfl_sync(0xffffffffu, fail, 0)) return false;
         }
-        // min-plus update; the shuffled neighbours enter last so the chain
-        // through the lanes is shuffle -> add -> min
-        float left = __shfl_up_sync(0xffffffffu, dp[3], 1);
-        float right = __shfl_down_sync(0xffffffffu, dp[0], 1);
-        if (lane == 0) left = kInf;
-        if (lane == 31) right = kInf;
-        float nd[4];
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            float best = cur.dold[i];
-            // parents in the lane's own registers first
-            if (i > 0) best = fminf(best, __fadd_rn(dp[i - 1], cur.cst[0][i]));
-            best = fminf(best, __fadd_rn(dp[i], cur.cst[1][i]));
-            if (i < 3) best = fminf(best, __fadd_rn(dp[i + 1], cur.cst[2][i]));
-            if (i == 0) best = fminf(best, __fadd_rn(left, cur.cst[0][0]));
-            if (i == 3) best = fminf(best, __fadd_rn(right, cur.cst[2][3]));
-            nd[i] = valid[i] ? best : kInf;
-        }
-#pragma unroll
-        for (int i = 0; i < 4; ++i) dp[i] = nd[i];
-        // owned outputs
-        if (!transposed_out) {
-            if (owned[0] && owned[3]) {
-                *reinterpret_cast<float4*>(out_row) = make_float4(nd[0], nd[1], nd[2], nd[3]);
-            } else {
-#pragma unroll
-                for (int i = 0; i < 4; ++i)
-                    if (owned[i]) out_row[i] = nd[i];
-            }
-        } else {
-            const int j = s - stage_start;  // line slot in the staging buffer
-#pragma unroll
-            for (int i = 0; i < 4; ++i)
-                if (owned[i]) sm.stage[c0 + i - q0][j] = nd[i];
-            if (j + 1 == kStageDepth || s == L - 1) {
-                __syncwarp();
-                const int nl = j + 1;
-                const int ncol = q1 - q0;
-                // slot jj holds step stage_start + jj; consecutive lanes write
-                // consecutive lines of one owned column (one output row)
-                if (nl == 32) {
-                    const int xx = line_of(stage_start + lane);
-                    for (int col = 0; col < ncol; ++col)
-                        out[(int64_t)(q0 + col) * out_ld + xx] = sm.stage[col][lane];
-                } else {
-                    for (int e = lane; e < ncol * nl; e += 32) {
-                        const int col = e / nl, jj = e % nl;
-                        const int xx = line_of(stage_start + jj);
-                        out[(int64_t)(q0 + col) * out_ld + xx] = sm.stage[col][jj];
-                    }
-                }
-                __syncwarp();
-                stage_start = s + 1;
-            }
-        }
-        cur = nxt;
     }
-    // no copy may still target the staging ring when the next tile starts
-    cp_async_wait<0>();
-    __syncwarp();
-    return alive;
+    if (nb) {
+#pragma unroll
+        for (int i = 0; i < 4; ++i) dp[i] = valid[i] ? got[i] : kInf;
+    }
+    return true;
 }
 
-__global__ void __launch_bounds__(kWarps * 32, 1) chain2d_kernel(const Chain2DArgs a) {
+// Chain warp.  Line j of chunk c is step s = kCh*c + j; the first step (the
+// first line of the sweep, which has no parents) runs with +inf parents and
+// so keeps the old values.  AHEAD lines of input are held in registers ahead
+// of the step that uses them.
+template <bool fwd, bool table, int AHEAD>
+__device__ bool chain_tile(const Chain2DArgs& a, const TileGeo& g, int t_app, int b, int tile,
+                           TileSmem& sm, unsigned int cb, float k0, float k1, float k2) {
+    constexpr int NB = AHEAD == 1 ? 2 : 4;  // register buffers (divides kCh)
+    const int lane = threadIdx.x & 31;
+    const int c0 = g.r0 + 4 * lane;
+    bool valid[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) valid[i] = (c0 + i >= 0) && (c0 + i < g.Q);
+    const unsigned int tag_base = ((unsigned int)(t_app + 1)) << 16;
+    float dp[4] = {kInf, kInf, kInf, kInf};
+    LineIn buf[NB];
+    if (!__all_sync(0xffffffffu, mbar_wait(&sm.in_full[slot_of(cb, kNci)], full_parity(cb, kNci), a)))
+        return false;
+#pragma unroll
+    for (int j = 0; j < AHEAD; ++j)
+        load_line<fwd, table>(sm.in[slot_of(cb, kNci)][j], lane, buf[j], k0, k1, k2);
+    int next_refresh = g.multi ? g.K : 0x7fffffff;
+    int blk = 0;
+    // Hand-overs are tested one chunk in advance (non-blocking) so the test's
+    // latency overlaps a chunk of work; a blocking wait follows only when the
+    // test found the chunk not ready yet.
+    bool in_ready = g.nch < 2 || mbar_peek(&sm.in_full[slot_of(cb + 1, kNci)],
+                                           full_parity(cb + 1, kNci));
+    bool out_ready = cb < (unsigned)kNo || mbar_peek(&sm.out_empty[slot_of(cb, kNo)],
+                                                     empty_parity(cb, kNo));
+    for (int c = 0; c < g.nch; ++c) {
+        const unsigned int gc = cb + c;
+        const int slot = slot_of(gc, kNci), nslot = slot_of(gc + 1, kNci);
+        const int oslot = slot_of(gc, kNo);
+        if (!__all_sync(0xffffffffu, in_ready) &&
+            !__all_sync(0xffffffffu, mbar_wait(&sm.in_full[nslot], full_parity(gc + 1, kNci), a)))
+            return false;
+        if (!__all_sync(0xffffffffu, out_ready) &&
+            !__all_sync(0xffffffffu, mbar_wait(&sm.out_empty[oslot], empty_parity(gc, kNo), a)))
+            return false;
+        in_ready = c + 2 >= g.nch || mbar_peek(&sm.in_full[slot_of(gc + 2, kNci)],
+                                               full_parity(gc + 2, kNci));
+        out_ready = gc + 1 < (unsigned)kNo || mbar_peek(&sm.out_empty[slot_of(gc + 1, kNo)],
+                                                        empty_parity(gc + 1, kNo));
+        if (c * kCh == next_refresh) {
+            if (!exchange(a, g, b, tile, tag_base | (unsigned int)(blk + 1), blk & 1, dp, valid))
+                return false;
+            next_refresh += g.K;
+            ++blk;
+        }
+        const float(*cur)[4][kRow] = sm.in[slot];
+        const float(*nxt)[4][kRow] = sm.in[nslot];
+#pragma unroll
+        for (int j = 0; j < kCh; ++j) {
+            const int nj = j + AHEAD;
+            load_line<fwd, table>(nj < kCh ? cur[nj] : nxt[nj - kCh], lane, buf[nj % NB], k0, k1,
+                                  k2);
+            chain_step(dp, buf[j % NB], valid, lane, &sm.out[oslot][j][4 * lane]);
+        }
+        __syncwarp();
+        if (lane == 0) {
+            mbar_arrive(&sm.in_empty[slot]);
+            mbar_arrive(&sm.out_full[oslot]);
+        }
+    }
+    return true;
+}
+
+template <bool fwd, bool table>
+__device__ bool run_tile(const Chain2DArgs& a, int t_app, int pass, int b, int tile,
+                         TileSmem& sm, unsigned int cb) {
+    const TileGeo g = tile_geo(a, t_app, pass, b, tile);
+    const int warp = threadIdx.x >> 5;
+    if (warp == 0) {
+        const bool vert = pass < 2;
+        const float k0 = vert ? a.cv[0] : a.chh[0];
+        const float k1 = vert ? a.cv[1] : a.chh[1];
+        const float k2 = vert ? a.cv[2] : a.chh[2];
+        return chain_tile<fwd, table, table ? 2 : 1>(a, g, t_app, b, tile, sm, cb, k0, k1, k2);
+    }
+    if (warp == 1) return producer_tile<fwd, table>(a, g, sm, cb);
+    return flusher_tile<fwd>(a, g, sm, cb);
+}
+
+__global__ void __launch_bounds__(kBlockThreads, 1) chain2d_kernel(const Chain2DArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    WarpSmem& sm = reinterpret_cast<WarpSmem*>(smem_raw)[threadIdx.x >> 5];
+    TileSmem& sm = *reinterpret_cast<TileSmem*>(smem_raw);
     const int64_t N = (int64_t)a.H * a.W;
     const int64_t nthreads = (int64_t)gridDim.x * blockDim.x;
     const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     unsigned int epoch = 1;
-    // D0 = v * M (and the cost tables)
     if (a.iterations == 0) {
         for (int64_t i = tid; i < a.B * N; i += nthreads) a.dist[i] = __fmul_rn(a.v, a.mask[i]);
         return;
     }
+    // ring rows start at +inf (the padding columns are never written again)
+    for (int i = threadIdx.x; i < kNci * kCh * 4 * kRow; i += blockDim.x)
+        (&sm.in[0][0][0][0])[i] = kInf;
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < kNci; ++i) {
+            mbar_init(&sm.in_full[i], 32);  // one asynchronous arrival per producer lane
+            mbar_init(&sm.in_empty[i], 1);
+        }
+        for (int i = 0; i < kNo; ++i) {
+            mbar_init(&sm.out_full[i], 1);
+            mbar_init(&sm.out_empty[i], 1);
+        }
+    }
+    // D0 = v * M (and the cost tables)
     for (int64_t i = tid; i < a.B * N; i += nthreads) {
         const int64_t b = i / N, r = i % N;
         const int h = (int)(r / a.W), w = (int)(r % a.W);
@@ -427,25 +594,26 @@ __global__ void __launch_bounds__(kWarps * 32, 1) chain2d_kernel(const Chain2DAr
     if (blockIdx.x == 0 && threadIdx.x == 0) timeline[0] = (unsigned long long)gtimer();
     bool alive = grid_barrier(a.barrier, epoch++, a.status, a.timeout_ns);
     if (blockIdx.x == 0 && threadIdx.x == 0) timeline[1] = (unsigned long long)gtimer();
-    const int gwarp = blockIdx.x * kWarps + (threadIdx.x >> 5);
-    const int nwarps = gridDim.x * kWarps;
+    unsigned int cb = 0;  // chunks handed over so far in this block
     const int napps = a.iterations * 4;
     for (int t_app = 0; t_app < napps && alive; ++t_app) {
         const int pass = t_app % 4;
         const int ntiles = pass < 2 ? a.tiles_v : a.tiles_h;
-        const int per_wave = nwarps / ntiles;
+        const int L = pass < 2 ? a.H : a.W;
+        const int per_wave = gridDim.x / ntiles;
         const int nwaves = (a.B + per_wave - 1) / per_wave;
         bool ok = true;
         for (int wv = 0; wv < nwaves && ok; ++wv) {
-            if (gwarp < per_wave * ntiles) {
-                const int b = wv * per_wave + gwarp / ntiles;
+            if ((int)blockIdx.x < per_wave * ntiles) {
+                const int b = wv * per_wave + blockIdx.x / ntiles;
                 if (b < a.B) {
-                    const int tile = gwarp % ntiles;
+                    const int tile = blockIdx.x % ntiles;
                     const bool fwd = (pass == 0 || pass == 2);
-                    if (fwd && a.table) ok = chain_tile<true, true>(a, t_app, pass, b, tile, sm);
-                    else if (fwd) ok = chain_tile<true, false>(a, t_app, pass, b, tile, sm);
-                    else if (a.table) ok = chain_tile<false, true>(a, t_app, pass, b, tile, sm);
-                    else ok = chain_tile<false, false>(a, t_app, pass, b, tile, sm);
+                    if (fwd && a.table) ok = run_tile<true, true>(a, t_app, pass, b, tile, sm, cb);
+                    else if (fwd) ok = run_tile<true, false>(a, t_app, pass, b, tile, sm, cb);
+                    else if (a.table) ok = run_tile<false, true>(a, t_app, pass, b, tile, sm, cb);
+                    else ok = run_tile<false, false>(a, t_app, pass, b, tile, sm, cb);
+                    cb += (unsigned int)((L + kCh - 1) / kCh);
                 }
             }
         }
@@ -474,14 +642,16 @@ size_t chain2d_workspace_bytes(int64_t B, int64_t C, int64_t H, int64_t W, int t
 
 int chain2d_geometry(int64_t H, int64_t W, const fgx_options* opt, int* K, int* T, int* tv,
                      int* th) {
+    // K: lines between ring refreshes, a whole number of chunks; T >= K so a
+    // ring never reaches past the neighbouring tile
     int k = (opt && opt->tile_lines) ? opt->tile_lines : 40;
-    k = std::max(4, std::min(kMaxRing, (k + 3) & ~3));
+    k = std::max(kCh, std::min(40, (k + kCh - 1) / kCh * kCh));
     int t = kRegion - 2 * k;
-    if (opt && opt->tile_width) t = std::min(t, std::max(4, opt->tile_width & ~3));
-    if (t < k) { k = std::max(4, (kRegion / 3) & ~3); t = kRegion - 2 * k; }
+    if (opt && opt->tile_width) t = std::min(t, std::max(kCh, opt->tile_width & ~3));
+    if (t < k) k = t / kCh * kCh;
     *K = k;
     *T = t;
-    // a line that fits one warp region is one tile, unless a tile width is forced
+    // a line that fits one region is one tile, unless a tile width is forced
     const int64_t single = (opt && opt->tile_width) ? t : kRegion;
     *tv = W <= single ? 1 : (int)((W + t - 1) / t);
     *th = H <= single ? 1 : (int)((H + t - 1) / t);
@@ -539,25 +709,26 @@ int run_chain2d(const float* image, const float* mask, float* dist, int64_t B, i
     off += al((size_t)B * 3 * H * a.Wp * 4);
     a.Eh = (float*)(p + off);
 
-    const size_t smem = sizeof(WarpSmem) * kWarps;
+    const size_t smem = sizeof(TileSmem);
     if (cudaFuncSetAttribute(chain2d_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)smem) != cudaSuccess)
         return FGX_ERR_CUDA;
     int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, chain2d_kernel, kWarps * 32,
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, chain2d_kernel, kBlockThreads,
                                                       smem) != cudaSuccess || per_sm < 1)
         return FGX_ERR_CUDA;
+    // one tile per block; blocks beyond the tiles of one wave of images only
+    // help with the cost tables
     int64_t grid = (int64_t)per_sm * sms;
     if (opt && opt->max_blocks) grid = std::min<int64_t>(grid, opt->max_blocks);
-    const int64_t want = (B * max_tiles + kWarps - 1) / kWarps;
-    grid = std::max<int64_t>(1, std::min<int64_t>(grid, std::max<int64_t>(want, sms)));
-    if (grid * kWarps < max_tiles) return FGX_ERR_UNSUPPORTED;
+    grid = std::max<int64_t>(1, std::min<int64_t>(grid, std::max<int64_t>(B * max_tiles, sms)));
+    if (grid < max_tiles) return FGX_ERR_UNSUPPORTED;
     cudaStream_t s = (cudaStream_t)stream;
     if (cudaMemsetAsync(workspace, 0, kHeaderBytes + xbytes, s) != cudaSuccess) return FGX_ERR_CUDA;
     cudaLaunchConfig_t cfg = {};
     cudaLaunchAttribute attr[1];
     cfg.gridDim = dim3((unsigned)grid);
-    cfg.blockDim = dim3(kWarps * 32);
+    cfg.blockDim = dim3(kBlockThreads);
     cfg.dynamicSmemBytes = smem;
     cfg.stream = s;
     attr[0].id = cudaLaunchAttributeCooperative;
