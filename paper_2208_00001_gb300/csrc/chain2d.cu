@@ -102,11 +102,18 @@ constexpr int kRow = kRegion + 8;   // floats per input row: 4 pad | 128 | 4 pad
 constexpr int kOutLd = kRegion + 4; // floats per output row (conflict-free transposes)
 
 struct TileSmem {
-    unsigned long long in_full[kNci], in_empty[kNci], out_full[kNo], out_empty[kNo];
+    // in_full: the producer's copies of a chunk have landed; done: the chain
+    // has finished a chunk (its input slot is free, its output is ready);
+    // out_empty: the flusher has written an output slot out
+    unsigned long long in_full[kNci], done[kNci], out_empty[kNo];
+    unsigned long long pad_[16 - 2 * kNci - kNo];
     float in[kNci][kCh][4][kRow];   // per line: old values, edge rows E0, E1, E2
     float out[kNo][kCh][kOutLd];    // chain results per line
 };
-static_assert((2 * kNci + 2 * kNo) * 8 % 16 == 0, "ring rows must stay 16-byte aligned");
+
+// Source of the +inf rows copied into the ring for lanes outside the array.
+__device__ __align__(16) unsigned int g_inf_row[4] = {0x7f800000u, 0x7f800000u, 0x7f800000u,
+                                                      0x7f800000u};
 
 __device__ __forceinline__ unsigned int saddr(const void* p) {
     return (unsigned int)__cvta_generic_to_shared(p);
@@ -166,6 +173,17 @@ __device__ __forceinline__ bool mbar_wait(unsigned long long* b, unsigned int pa
     if (mbar_test(b, parity)) return true;
     return mbar_wait_slow(b, parity, a.status, a.timeout_ns);
 }
+// Position of chunk gc in a ring of n slots: the slot and the parity of the
+// slot's phase that the chunk fills.
+struct RingPos {
+    int slot;
+    unsigned int par;
+    __device__ RingPos(unsigned int gc, int n) : slot((int)(gc % (unsigned)n)), par((gc / (unsigned)n) & 1u) {}
+    __device__ RingPos(int s, unsigned int p) : slot(s), par(p) {}
+    __device__ __forceinline__ RingPos next(int n) const {
+        return slot + 1 == n ? RingPos(0, par ^ 1u) : RingPos(slot + 1, par);
+    }
+};
 // Chunk gc of a ring of n slots: slot, parity of its "full" phase, and parity
 // of the "empty" phase that frees the slot (the release of chunk gc - n).
 __device__ __forceinline__ int slot_of(unsigned int gc, int n) { return (int)(gc % (unsigned)n); }
@@ -229,23 +247,25 @@ __device__ bool producer_tile(const Chain2DArgs& a, const TileGeo& g, TileSmem& 
         const unsigned int gc = cb + c;
         const int slot = slot_of(gc, kNci);
         if (gc >= (unsigned)kNci &&
-            !__all_sync(0xffffffffu, mbar_wait(&sm.in_empty[slot], empty_parity(gc, kNci), a))) {
+            !__all_sync(0xffffffffu, mbar_wait(&sm.done[slot], empty_parity(gc, kNci), a))) {
             cp_async_wait_all();
             return false;
         }
-        if (lane_loads) {
-            const int jn = min(kCh, L - c * kCh);
-            for (int j = 0; j < jn; ++j) {
-                const int s = c * kCh + j;
-                const int line = fwd ? s : (L - 1 - s);
-                float(*row)[kRow] = sm.in[slot][j];
-                cp_async16(&row[0][4 + 4 * lane], g.src + (int64_t)line * g.ld + c0);
-                if (table && s >= 1) {
-                    const float* ep = g.E + (int64_t)(fwd ? s - 1 : line) * g.ld + c0;
-                    cp_async16(&row[1][4 + 4 * lane], ep);
-                    cp_async16(&row[2][4 + 4 * lane], ep + g.eplane);
-                    cp_async16(&row[3][4 + 4 * lane], ep + 2 * g.eplane);
-                }
+        const int jn = min(kCh, L - c * kCh);
+        for (int j = 0; j < jn; ++j) {
+            const int s = c * kCh + j;
+            const int line = fwd ? s : (L - 1 - s);
+            float(*row)[kRow] = sm.in[slot][j];
+            // lanes outside the array get +inf rows: their columns stay at
+            // +inf and cost nothing to the columns next to them
+            cp_async16(&row[0][4 + 4 * lane],
+                       lane_loads ? (const void*)(g.src + (int64_t)line * g.ld + c0) : g_inf_row);
+            if (table && s >= 1) {
+                const float* ep = g.E + (int64_t)(fwd ? s - 1 : line) * g.ld + c0;
+                cp_async16(&row[1][4 + 4 * lane], lane_loads ? (const void*)ep : g_inf_row);
+                cp_async16(&row[2][4 + 4 * lane], lane_loads ? (const void*)(ep + g.eplane) : g_inf_row);
+                cp_async16(&row[3][4 + 4 * lane],
+                           lane_loads ? (const void*)(ep + 2 * g.eplane) : g_inf_row);
             }
         }
         cp_async_arrive_noinc(&sm.in_full[slot]);
@@ -269,7 +289,8 @@ __device__ bool flusher_tile(const Chain2DArgs& a, const TileGeo& g, TileSmem& s
     for (int c = 0; c < g.nch; ++c) {
         const unsigned int gc = cb + c;
         const int slot = slot_of(gc, kNo);
-        if (!__all_sync(0xffffffffu, mbar_wait(&sm.out_full[slot], full_parity(gc, kNo), a)))
+        if (!__all_sync(0xffffffffu,
+                        mbar_wait(&sm.done[slot_of(gc, kNci)], full_parity(gc, kNci), a)))
             return false;
         const int s0 = c * kCh;
         const int nl = min(kCh, L - s0);
@@ -362,7 +383,10 @@ __device__ __forceinline__ void load_line(const float (*p)[kRow], int lane, Line
 
 // One min-plus line update (Jacobi within the line): candidates in the fixed
 // order old value, own parents, then the parents held by the neighbouring
-// lanes; columns outside the array stay at +inf.
+// lanes.  Columns outside the array stay at +inf: with cost tables their old
+// values and the costs of every edge into them are +inf already (table and
+// array padding, +inf ring rows), with constant costs they are masked.
+template <bool masked>
 __device__ __forceinline__ void chain_step(float (&dp)[4], const LineIn& c, const bool (&valid)[4],
                                            int lane, float* out) {
     float left = __shfl_up_sync(0xffffffffu, dp[3], 1);
@@ -378,7 +402,7 @@ __device__ __forceinline__ void chain_step(float (&dp)[4], const LineIn& c, cons
         if (i < 3) best = fminf(best, __fadd_rn(dp[i + 1], c.c2[i]));
         if (i == 0) best = fminf(best, __fadd_rn(left, c.c0[0]));
         if (i == 3) best = fminf(best, __fadd_rn(right, c.c2[3]));
-        nd[i] = valid[i] ? best : kInf;
+        nd[i] = (!masked || valid[i]) ? best : kInf;
     }
 #pragma unroll
     for (int i = 0; i < 4; ++i) dp[i] = nd[i];
@@ -420,23 +444,43 @@ __device__ __forceinline__ bool exchange(const Chain2DArgs& a, const TileGeo& g,
              par * (2 * kMaxRing);
         base = c0 - (q0 + T);
     }
+    // Two polls stay in flight, the second issued ~100 ns after the first,
+    // so one of them tends to reach the cache just after the neighbour's
+    // store instead of a full round trip later.
     float got[4] = {dp[0], dp[1], dp[2], dp[3]};
-    bool ok = (nb == nullptr);
+    bool done = (nb == nullptr);
+    unsigned long long wa[4], wb[4];
+    auto issue = [&](unsigned long long (&w)[4]) {
+#pragma unroll
+        for (int i = 0; i < 4; ++i) w[i] = ld_relaxed_u64(nb + base + i);
+    };
+    auto take = [&](const unsigned long long (&w)[4]) {
+        bool all = true;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) all = all && (unsigned int)(w[i] >> 32) == tg;
+        if (all) {
+#pragma unroll
+            for (int i = 0; i < 4; ++i) got[i] = __uint_as_float((unsigned int)w[i]);
+        }
+        return all;
+    };
+    if (!done) issue(wa);
+    __nanosleep(50);
+    if (!done) issue(wb);
     long long t0 = 0;
     for (unsigned int it = 0;; ++it) {
-        if (!ok) {
-            bool all = true;
-#pragma unroll
-            for (int i = 0; i < 4; ++i) {
-                const unsigned long long w = ld_relaxed_u64(nb + base + i);
-                if ((unsigned int)(w >> 32) != tg) all = false;
-                got[i] = __uint_as_float((unsigned int)w);
-            }
-            ok = all;
+        if (!done) {
+            done = take(wa);
+            if (!done) issue(wa);
         }
-        if (__all_sync(0xffffffffu, ok)) break;
-        // the status word and the clock are read every 16th poll only
-        if ((it & 15u) == 15u) {
+        if (__all_sync(0xffffffffu, done)) break;
+        if (!done) {
+            done = take(wb);
+            if (!done) issue(wb);
+        }
+        if (__all_sync(0xffffffffu, done)) break;
+        // the status word and the clock are read every 8th round only
+        if ((it & 7u) == 7u) {
             int fail = 0;
             if (lane == 0) {
                 const long long now = gtimer();
@@ -473,34 +517,37 @@ __device__ bool chain_tile(const Chain2DArgs& a, const TileGeo& g, int t_app, in
     const unsigned int tag_base = ((unsigned int)(t_app + 1)) << 16;
     float dp[4] = {kInf, kInf, kInf, kInf};
     LineIn buf[NB];
-    if (!__all_sync(0xffffffffu, mbar_wait(&sm.in_full[slot_of(cb, kNci)], full_parity(cb, kNci), a)))
-        return false;
+    // ring positions (slot, phase parity) of chunks gc, gc+1, gc+2 of the
+    // input ring and gc, gc+1 of the output ring, advanced without divisions
+    RingPos i0(cb, kNci), i1 = i0.next(kNci), i2 = i1.next(kNci);
+    RingPos o0(cb, kNo), o1 = o0.next(kNo);
+    if (!__all_sync(0xffffffffu, mbar_wait(&sm.in_full[i0.slot], i0.par, a))) return false;
 #pragma unroll
     for (int j = 0; j < AHEAD; ++j)
-        load_line<fwd, table>(sm.in[slot_of(cb, kNci)][j], lane, buf[j], k0, k1, k2);
+        load_line<fwd, table>(sm.in[i0.slot][j], lane, buf[j], k0, k1, k2);
     int next_refresh = g.multi ? g.K : 0x7fffffff;
     int blk = 0;
     // Hand-overs are tested one chunk in advance (non-blocking) so the test's
     // latency overlaps a chunk of work; a blocking wait follows only when the
     // test found the chunk not ready yet.
-    bool in_ready = g.nch < 2 || mbar_peek(&sm.in_full[slot_of(cb + 1, kNci)],
-                                           full_parity(cb + 1, kNci));
-    bool out_ready = cb < (unsigned)kNo || mbar_peek(&sm.out_empty[slot_of(cb, kNo)],
-                                                     empty_parity(cb, kNo));
+    bool in_ready = g.nch < 2 || mbar_peek(&sm.in_full[i1.slot], i1.par);
+    bool out_ready = cb < (unsigned)kNo || mbar_peek(&sm.out_empty[o0.slot], o0.par ^ 1u);
     for (int c = 0; c < g.nch; ++c) {
         const unsigned int gc = cb + c;
-        const int slot = slot_of(gc, kNci), nslot = slot_of(gc + 1, kNci);
-        const int oslot = slot_of(gc, kNo);
+        const int slot = i0.slot, nslot = i1.slot, oslot = o0.slot;
         if (!__all_sync(0xffffffffu, in_ready) &&
-            !__all_sync(0xffffffffu, mbar_wait(&sm.in_full[nslot], full_parity(gc + 1, kNci), a)))
+            !__all_sync(0xffffffffu, mbar_wait(&sm.in_full[nslot], i1.par, a)))
             return false;
         if (!__all_sync(0xffffffffu, out_ready) &&
-            !__all_sync(0xffffffffu, mbar_wait(&sm.out_empty[oslot], empty_parity(gc, kNo), a)))
+            !__all_sync(0xffffffffu, mbar_wait(&sm.out_empty[oslot], o0.par ^ 1u, a)))
             return false;
-        in_ready = c + 2 >= g.nch || mbar_peek(&sm.in_full[slot_of(gc + 2, kNci)],
-                                               full_parity(gc + 2, kNci));
-        out_ready = gc + 1 < (unsigned)kNo || mbar_peek(&sm.out_empty[slot_of(gc + 1, kNo)],
-                                                        empty_parity(gc + 1, kNo));
+        in_ready = c + 2 >= g.nch || mbar_peek(&sm.in_full[i2.slot], i2.par);
+        out_ready = gc + 1 < (unsigned)kNo || mbar_peek(&sm.out_empty[o1.slot], o1.par ^ 1u);
+        i0 = i1;
+        i1 = i2;
+        i2 = i2.next(kNci);
+        o0 = o1;
+        o1 = o1.next(kNo);
         if (c * kCh == next_refresh) {
             if (!exchange(a, g, b, tile, tag_base | (unsigned int)(blk + 1), blk & 1, dp, valid))
                 return false;
@@ -514,13 +561,10 @@ __device__ bool chain_tile(const Chain2DArgs& a, const TileGeo& g, int t_app, in
             const int nj = j + AHEAD;
             load_line<fwd, table>(nj < kCh ? cur[nj] : nxt[nj - kCh], lane, buf[nj % NB], k0, k1,
                                   k2);
-            chain_step(dp, buf[j % NB], valid, lane, &sm.out[oslot][j][4 * lane]);
+            chain_step<!table>(dp, buf[j % NB], valid, lane, &sm.out[oslot][j][4 * lane]);
         }
         __syncwarp();
-        if (lane == 0) {
-            mbar_arrive(&sm.in_empty[slot]);
-            mbar_arrive(&sm.out_full[oslot]);
-        }
+        if (lane == 0) mbar_arrive(&sm.done[slot]);
     }
     return true;
 }
@@ -558,35 +602,43 @@ __global__ void __launch_bounds__(kBlockThreads, 1) chain2d_kernel(const Chain2D
     if (threadIdx.x == 0) {
         for (int i = 0; i < kNci; ++i) {
             mbar_init(&sm.in_full[i], 32);  // one asynchronous arrival per producer lane
-            mbar_init(&sm.in_empty[i], 1);
+            mbar_init(&sm.done[i], 1);
         }
-        for (int i = 0; i < kNo; ++i) {
-            mbar_init(&sm.out_full[i], 1);
-            mbar_init(&sm.out_empty[i], 1);
-        }
+        for (int i = 0; i < kNo; ++i) mbar_init(&sm.out_empty[i], 1);
     }
-    // D0 = v * M (and the cost tables)
-    for (int64_t i = tid; i < a.B * N; i += nthreads) {
-        const int64_t b = i / N, r = i % N;
-        const int h = (int)(r / a.W), w = (int)(r % a.W);
-        a.Dw[(b * a.H + h) * a.Wp + w] = __fmul_rn(a.v, a.mask[i]);
-    }
-    if (a.table) {
+    // D0 = v * M and the cost tables, one row (b, h) per block at a time; the
+    // padding columns of Dw, Dt, Ev and Eh are +inf
+    for (int64_t row = blockIdx.x; row < (int64_t)a.B * a.H; row += gridDim.x) {
+        const int b = (int)(row / a.H), h = (int)(row - (int64_t)b * a.H);
+        const float* m = a.mask + row * a.W;
+        float* dw = a.Dw + row * a.Wp;
+        for (int w = threadIdx.x; w < a.Wp; w += blockDim.x)
+            dw[w] = w < a.W ? __fmul_rn(a.v, m[w]) : kInf;
+        if (!a.table) continue;
         // Ev[k][h][w]: edge (h, w) - (h+1, w+k-1);  Eh[k][w][h]: edge (h, w) - (h+k-1, w+1)
-        for (int64_t i = tid; i < a.B * N; i += nthreads) {
-            const int64_t b = i / N, r = i % N;
-            const int h = (int)(r / a.W), w = (int)(r % a.W);
-            const float* img = a.image + b * a.C * N;
+        const float* img = a.image + (int64_t)b * a.C * N;
+        for (int w = threadIdx.x; w < a.Wp; w += blockDim.x) {
             const float* self = img + (int64_t)h * a.W + w;
             for (int k = 0; k < 3; ++k) {
                 float cv = kInf, ch = kInf;
                 const int wn = w + k - 1, hn = h + k - 1;
-                if (h + 1 < a.H && wn >= 0 && wn < a.W)
+                if (w < a.W && h + 1 < a.H && wn >= 0 && wn < a.W)
                     cv = edge_cost(img + (int64_t)(h + 1) * a.W + wn, self, a.C, N, a.tv[k], a.lambda);
                 if (w + 1 < a.W && hn >= 0 && hn < a.H)
                     ch = edge_cost(img + (int64_t)hn * a.W + w + 1, self, a.C, N, a.th[k], a.lambda);
-                a.Ev[((b * 3 + k) * a.H + h) * a.Wp + w] = cv;
-                a.Eh[((b * 3 + k) * a.W + w) * a.Hp + h] = ch;
+                a.Ev[(((int64_t)b * 3 + k) * a.H + h) * a.Wp + w] = cv;
+                if (w < a.W) a.Eh[(((int64_t)b * 3 + k) * a.W + w) * a.Hp + h] = ch;
+            }
+        }
+    }
+    if (a.Hp > a.H) {
+        for (int64_t row = blockIdx.x; row < (int64_t)a.B * a.W; row += gridDim.x) {
+            const int b = (int)(row / a.W), w = (int)(row - (int64_t)b * a.W);
+            for (int j = a.H + threadIdx.x; j < a.Hp; j += blockDim.x) {
+                a.Dt[row * a.Hp + j] = kInf;
+                if (a.table)
+                    for (int k = 0; k < 3; ++k)
+                        a.Eh[(((int64_t)b * 3 + k) * a.W + w) * a.Hp + j] = kInf;
             }
         }
     }
