@@ -343,7 +343,8 @@ def run_fgx(args):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     build.build()
-    case = workloads.large2d()
+    case = workloads.large2d(size=args.size)
+    workload = WORKLOAD if args.size == 2048 else WORKLOAD.replace("2048x2048", f"{args.size}x{args.size}")
     B, C, H, W = case.image.shape
     N = B * H * W
     its = case.iterations
@@ -427,7 +428,7 @@ def run_fgx(args):
         "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": t_max * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic",
-        "config": {"workload": WORKLOAD, "parallelism": f"replicas x{world}",
+        "config": {"workload": workload, "parallelism": f"replicas x{world}",
                    "l2": "flushed between steps (256 MB write outside the timed events)",
                    "device_status": fgx.status_string(status),
                    "wall_s_timed_loop": wall},
@@ -441,7 +442,7 @@ def run_fgx(args):
         "gpu_launches": args.steps,
         "clocks": clk.summary(),
     }
-    if not args.no_cpu_baseline:
+    if not args.no_cpu_baseline and args.size == 2048:
         line["cpu_baseline"] = cpu_baseline_sample(case)
     if extras is not None:
         line["extras"] = extras
@@ -456,6 +457,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="fgx", choices=["fgx", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--size", type=int, default=2048,
+                    help="side of the 2D image (2048 is the benchmark; smaller sides are for "
+                         "profiler captures)")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the other workloads (3D, batched, differentiable)")
     args = ap.parse_args()

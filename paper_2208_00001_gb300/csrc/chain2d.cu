@@ -569,6 +569,60 @@ __device__ bool chain_tile(const Chain2DArgs& a, const TileGeo& g, int t_app, in
     return true;
 }
 
+// Initial distances and cost tables, one 32 x 32 pixel tile per block
+// (32 x 8 threads, four rows each): Dw = v * M, Ev[k][h][w] = cost of the edge
+// (h, w) - (h+1, w+k-1), Eh[k][w][h] = cost of the edge (h, w) - (h+k-1, w+1)
+// (written through a shared-memory transpose so both tables are stored along
+// their contiguous dimension); padding columns and missing edges are +inf.
+constexpr int kInitTile = 32;
+__global__ void __launch_bounds__(256) chain2d_init_kernel(const Chain2DArgs a) {
+    __shared__ float eh[3][kInitTile][kInitTile + 1];
+    const int64_t N = (int64_t)a.H * a.W;
+    const int b = blockIdx.z;
+    const int w0 = blockIdx.x * kInitTile, h0 = blockIdx.y * kInitTile;
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const float* img = a.image + (int64_t)b * a.C * N;
+    const int w = w0 + tx;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const int hl = ty + 8 * i, h = h0 + hl;
+        if (h < a.H && w < a.Wp) {
+            const int64_t row = (int64_t)b * a.H + h;
+            a.Dw[row * a.Wp + w] = w < a.W ? __fmul_rn(a.v, a.mask[row * a.W + w]) : kInf;
+        }
+        if (!a.table) continue;
+        const float* self = img + (int64_t)h * a.W + w;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            float cv = kInf, ch = kInf;
+            const int wn = w + k - 1, hn = h + k - 1;
+            if (h < a.H && w < a.W) {
+                if (h + 1 < a.H && wn >= 0 && wn < a.W)
+                    cv = edge_cost(img + (int64_t)(h + 1) * a.W + wn, self, a.C, N, a.tv[k], a.lambda);
+                if (w + 1 < a.W && hn >= 0 && hn < a.H)
+                    ch = edge_cost(img + (int64_t)hn * a.W + w + 1, self, a.C, N, a.th[k], a.lambda);
+            }
+            if (h < a.H && w < a.Wp) a.Ev[(((int64_t)b * 3 + k) * a.H + h) * a.Wp + w] = cv;
+            eh[k][tx][hl] = ch;  // [w local][h local]
+        }
+    }
+    __syncthreads();
+    // transposed write-out: rows w of Eh (and the +inf padding rows of Dt)
+    const int h = h0 + tx;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const int wl = ty + 8 * i, ww = w0 + wl;
+        if (ww >= a.W || h >= a.Hp) continue;
+        const int64_t row = (int64_t)b * a.W + ww;
+        if (h >= a.H) a.Dt[row * a.Hp + h] = kInf;
+        if (a.table) {
+#pragma unroll
+            for (int k = 0; k < 3; ++k)
+                a.Eh[(((int64_t)b * 3 + k) * a.W + ww) * a.Hp + h] = h < a.H ? eh[k][wl][tx] : kInf;
+        }
+    }
+}
+
 template <bool fwd, bool table>
 __device__ bool run_tile(const Chain2DArgs& a, int t_app, int pass, int b, int tile,
                          TileSmem& sm, unsigned int cb) {
@@ -606,46 +660,11 @@ __global__ void __launch_bounds__(kBlockThreads, 1) chain2d_kernel(const Chain2D
         }
         for (int i = 0; i < kNo; ++i) mbar_init(&sm.out_empty[i], 1);
     }
-    // D0 = v * M and the cost tables, one row (b, h) per block at a time; the
-    // padding columns of Dw, Dt, Ev and Eh are +inf
-    for (int64_t row = blockIdx.x; row < (int64_t)a.B * a.H; row += gridDim.x) {
-        const int b = (int)(row / a.H), h = (int)(row - (int64_t)b * a.H);
-        const float* m = a.mask + row * a.W;
-        float* dw = a.Dw + row * a.Wp;
-        for (int w = threadIdx.x; w < a.Wp; w += blockDim.x)
-            dw[w] = w < a.W ? __fmul_rn(a.v, m[w]) : kInf;
-        if (!a.table) continue;
-        // Ev[k][h][w]: edge (h, w) - (h+1, w+k-1);  Eh[k][w][h]: edge (h, w) - (h+k-1, w+1)
-        const float* img = a.image + (int64_t)b * a.C * N;
-        for (int w = threadIdx.x; w < a.Wp; w += blockDim.x) {
-            const float* self = img + (int64_t)h * a.W + w;
-            for (int k = 0; k < 3; ++k) {
-                float cv = kInf, ch = kInf;
-                const int wn = w + k - 1, hn = h + k - 1;
-                if (w < a.W && h + 1 < a.H && wn >= 0 && wn < a.W)
-                    cv = edge_cost(img + (int64_t)(h + 1) * a.W + wn, self, a.C, N, a.tv[k], a.lambda);
-                if (w + 1 < a.W && hn >= 0 && hn < a.H)
-                    ch = edge_cost(img + (int64_t)hn * a.W + w + 1, self, a.C, N, a.th[k], a.lambda);
-                a.Ev[(((int64_t)b * 3 + k) * a.H + h) * a.Wp + w] = cv;
-                if (w < a.W) a.Eh[(((int64_t)b * 3 + k) * a.W + w) * a.Hp + h] = ch;
-            }
-        }
-    }
-    if (a.Hp > a.H) {
-        for (int64_t row = blockIdx.x; row < (int64_t)a.B * a.W; row += gridDim.x) {
-            const int b = (int)(row / a.W), w = (int)(row - (int64_t)b * a.W);
-            for (int j = a.H + threadIdx.x; j < a.Hp; j += blockDim.x) {
-                a.Dt[row * a.Hp + j] = kInf;
-                if (a.table)
-                    for (int k = 0; k < 3; ++k)
-                        a.Eh[(((int64_t)b * 3 + k) * a.W + w) * a.Hp + j] = kInf;
-            }
-        }
-    }
+    __syncthreads();
     unsigned long long* timeline = (unsigned long long*)((char*)a.status + 128);
-    if (blockIdx.x == 0 && threadIdx.x == 0) timeline[0] = (unsigned long long)gtimer();
-    bool alive = grid_barrier(a.barrier, epoch++, a.status, a.timeout_ns);
-    if (blockIdx.x == 0 && threadIdx.x == 0) timeline[1] = (unsigned long long)gtimer();
+    if (blockIdx.x == 0 && threadIdx.x == 0)
+        timeline[0] = timeline[1] = (unsigned long long)gtimer();
+    bool alive = true;
     unsigned int cb = 0;  // chunks handed over so far in this block
     const int napps = a.iterations * 4;
     for (int t_app = 0; t_app < napps && alive; ++t_app) {
@@ -769,14 +788,21 @@ int run_chain2d(const float* image, const float* mask, float* dist, int64_t B, i
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, chain2d_kernel, kBlockThreads,
                                                       smem) != cudaSuccess || per_sm < 1)
         return FGX_ERR_CUDA;
-    // one tile per block; blocks beyond the tiles of one wave of images only
-    // help with the cost tables
+    // one tile per block: as many blocks as the tiles of all images, or as
+    // many as fit (images then run in waves)
     int64_t grid = (int64_t)per_sm * sms;
     if (opt && opt->max_blocks) grid = std::min<int64_t>(grid, opt->max_blocks);
-    grid = std::max<int64_t>(1, std::min<int64_t>(grid, std::max<int64_t>(B * max_tiles, sms)));
+    grid = std::max<int64_t>(1, std::min<int64_t>(grid, B * max_tiles));
     if (grid < max_tiles) return FGX_ERR_UNSUPPORTED;
+    if (B > 65535 || (a.Hp + kInitTile - 1) / kInitTile > 65535) return FGX_ERR_UNSUPPORTED;
     cudaStream_t s = (cudaStream_t)stream;
     if (cudaMemsetAsync(workspace, 0, kHeaderBytes + xbytes, s) != cudaSuccess) return FGX_ERR_CUDA;
+    if (iterations > 0) {
+        const dim3 ig((unsigned)((a.Wp + kInitTile - 1) / kInitTile),
+                      (unsigned)((a.Hp + kInitTile - 1) / kInitTile), (unsigned)B);
+        chain2d_init_kernel<<<ig, dim3(32, 8), 0, s>>>(a);
+        if (cudaGetLastError() != cudaSuccess) return FGX_ERR_CUDA;
+    }
     cudaLaunchConfig_t cfg = {};
     cudaLaunchAttribute attr[1];
     cfg.gridDim = dim3((unsigned)grid);
