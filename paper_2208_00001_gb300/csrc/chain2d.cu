@@ -50,6 +50,7 @@ struct Chain2DArgs {
     const float* image;  // [B][C][H][W]
     const float* mask;   // [B][H][W]
     float* dist;         // [B][H][W]
+    uint8_t* codes;      // [iterations * 4][B][H][W] parent codes, or null
     int B, C, H, W, Wp, Hp;
     float v, lambda;
     int iterations;
@@ -109,6 +110,7 @@ struct TileSmem {
     unsigned long long pad_[16 - 2 * kNci - kNo];
     float in[kNci][kCh][4][kRow];   // per line: old values, edge rows E0, E1, E2
     float out[kNo][kCh][kOutLd];    // chain results per line
+    uint8_t outc[kNo][kCh][kRegion];  // parent codes per line (when recorded)
 };
 
 // Source of the +inf rows copied into the ring for lanes outside the array.
@@ -203,6 +205,8 @@ struct TileGeo {
     int64_t eplane;
     float* out;
     int out_ld;
+    uint8_t* codes;  // codes of this pass application and image (image order), or null
+    bool codes_rows; // the pass's lines are rows of the image (vertical pass)
 };
 
 __device__ __forceinline__ TileGeo tile_geo(const Chain2DArgs& a, int t_app, int pass, int b,
@@ -229,6 +233,8 @@ __device__ __forceinline__ TileGeo tile_geo(const Chain2DArgs& a, int t_app, int
     else if (pass == 2) { g.out = a.Dt + (int64_t)b * a.W * a.Hp; g.out_ld = a.Hp; }
     else if (last_rl) { g.out = a.dist + (int64_t)b * a.H * a.W; g.out_ld = a.W; }
     else { g.out = a.Dw + (int64_t)b * a.H * a.Wp; g.out_ld = a.Wp; }
+    g.codes = a.codes ? a.codes + ((int64_t)t_app * a.B + b) * a.H * a.W : nullptr;
+    g.codes_rows = vert;
     return g;
 }
 
@@ -274,7 +280,7 @@ __device__ bool producer_tile(const Chain2DArgs& a, const TileGeo& g, TileSmem& 
 }
 
 // Flusher warp: writes the owned columns of each finished chunk.
-template <bool fwd>
+template <bool fwd, bool codes>
 __device__ bool flusher_tile(const Chain2DArgs& a, const TileGeo& g, TileSmem& sm,
                              unsigned int cb) {
     const int lane = threadIdx.x & 31;
@@ -333,6 +339,27 @@ __device__ bool flusher_tile(const Chain2DArgs& a, const TileGeo& g, TileSmem& s
                 }
             }
         }
+        if (codes) {
+            if (g.codes_rows) {
+                // vertical pass: the lines are rows of the image
+#pragma unroll
+                for (int j = 0; j < kCh; ++j) {
+                    if (j >= nl) break;
+                    const int line = fwd ? s0 + j : L - 1 - (s0 + j);
+                    const uint8_t* cj = &sm.outc[slot][j][4 * lane];
+                    uint8_t* row = g.codes + (int64_t)line * g.Q + c0;
+#pragma unroll
+                    for (int i = 0; i < 4; ++i)
+                        if (owned[i]) row[i] = cj[i];
+                }
+            } else {
+                // horizontal pass: the lines are columns of the image
+                const int jj = lane & (kCh - 1);
+                const int line = fwd ? s0 + jj : L - 1 - (s0 + jj);
+                for (int col = lane >> 3; col < ncol; col += 4)
+                    if (jj < nl) g.codes[(int64_t)(g.q0 + col) * L + line] = sm.outc[slot][jj][off + col];
+            }
+        }
         __syncwarp();
         if (lane == 0) mbar_arrive(&sm.out_empty[slot]);
     }
@@ -386,27 +413,41 @@ __device__ __forceinline__ void load_line(const float (*p)[kRow], int lane, Line
 // lanes.  Columns outside the array stay at +inf: with cost tables their old
 // values and the costs of every edge into them are +inf already (table and
 // array padding, +inf ring rows), with constant costs they are masked.
-template <bool masked>
+template <bool masked, bool codes>
 __device__ __forceinline__ void chain_step(float (&dp)[4], const LineIn& c, const bool (&valid)[4],
-                                           int lane, float* out) {
+                                           int lane, float* out, uint8_t* outc) {
     float left = __shfl_up_sync(0xffffffffu, dp[3], 1);
     float right = __shfl_down_sync(0xffffffffu, dp[0], 1);
     if (lane == 0) left = kInf;
     if (lane == 31) right = kInf;
     float nd[4];
+    unsigned int packed = 0;
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
+        const float x0 = (i > 0) ? __fadd_rn(dp[i - 1], c.c0[i]) : 0.0f;
+        const float x1 = __fadd_rn(dp[i], c.c1[i]);
+        const float x2 = (i < 3) ? __fadd_rn(dp[i + 1], c.c2[i]) : 0.0f;
         float best = c.dold[i];
-        if (i > 0) best = fminf(best, __fadd_rn(dp[i - 1], c.c0[i]));
-        best = fminf(best, __fadd_rn(dp[i], c.c1[i]));
-        if (i < 3) best = fminf(best, __fadd_rn(dp[i + 1], c.c2[i]));
-        if (i == 0) best = fminf(best, __fadd_rn(left, c.c0[0]));
-        if (i == 3) best = fminf(best, __fadd_rn(right, c.c2[3]));
+        if (i > 0) best = fminf(best, x0);
+        best = fminf(best, x1);
+        if (i < 3) best = fminf(best, x2);
+        const float y0 = (i == 0) ? __fadd_rn(left, c.c0[0]) : x0;
+        const float y2 = (i == 3) ? __fadd_rn(right, c.c2[3]) : x2;
+        if (i == 0) best = fminf(best, y0);
+        if (i == 3) best = fminf(best, y2);
         nd[i] = (!masked || valid[i]) ? best : kInf;
+        if (codes) {
+            // 0: kept its value; else 1 + the lowest parent index reaching the
+            // (strictly smaller) minimum
+            const unsigned int code =
+                nd[i] < c.dold[i] ? (y0 == nd[i] ? 1u : (x1 == nd[i] ? 2u : 3u)) : 0u;
+            packed |= code << (8 * i);
+        }
     }
 #pragma unroll
     for (int i = 0; i < 4; ++i) dp[i] = nd[i];
     *reinterpret_cast<float4*>(out) = make_float4(nd[0], nd[1], nd[2], nd[3]);
+    if (codes) *reinterpret_cast<unsigned int*>(outc) = packed;
 }
 
 // Ring refresh of a multi-tile pass before step s (dp holds line s-1):
@@ -505,7 +546,7 @@ __device__ __forceinline__ bool exchange(const Chain2DArgs& a, const TileGeo& g,
 // first line of the sweep, which has no parents) runs with +inf parents and
 // so keeps the old values.  AHEAD lines of input are held in registers ahead
 // of the step that uses them.
-template <bool fwd, bool table, int AHEAD>
+template <bool fwd, bool table, bool codes, int AHEAD>
 __device__ bool chain_tile(const Chain2DArgs& a, const TileGeo& g, int t_app, int b, int tile,
                            TileSmem& sm, unsigned int cb, float k0, float k1, float k2) {
     constexpr int NB = AHEAD == 1 ? 2 : 4;  // register buffers (divides kCh)
@@ -561,7 +602,8 @@ __device__ bool chain_tile(const Chain2DArgs& a, const TileGeo& g, int t_app, in
             const int nj = j + AHEAD;
             load_line<fwd, table>(nj < kCh ? cur[nj] : nxt[nj - kCh], lane, buf[nj % NB], k0, k1,
                                   k2);
-            chain_step<!table>(dp, buf[j % NB], valid, lane, &sm.out[oslot][j][4 * lane]);
+            chain_step<!table, codes>(dp, buf[j % NB], valid, lane, &sm.out[oslot][j][4 * lane],
+                                      &sm.outc[oslot][j][4 * lane]);
         }
         __syncwarp();
         if (lane == 0) mbar_arrive(&sm.done[slot]);
@@ -623,7 +665,7 @@ __global__ void __launch_bounds__(256) chain2d_init_kernel(const Chain2DArgs a) 
     }
 }
 
-template <bool fwd, bool table>
+template <bool fwd, bool table, bool codes>
 __device__ bool run_tile(const Chain2DArgs& a, int t_app, int pass, int b, int tile,
                          TileSmem& sm, unsigned int cb) {
     const TileGeo g = tile_geo(a, t_app, pass, b, tile);
@@ -633,12 +675,25 @@ __device__ bool run_tile(const Chain2DArgs& a, int t_app, int pass, int b, int t
         const float k0 = vert ? a.cv[0] : a.chh[0];
         const float k1 = vert ? a.cv[1] : a.chh[1];
         const float k2 = vert ? a.cv[2] : a.chh[2];
-        return chain_tile<fwd, table, table ? 2 : 1>(a, g, t_app, b, tile, sm, cb, k0, k1, k2);
+        return chain_tile<fwd, table, codes, table ? 2 : 1>(a, g, t_app, b, tile, sm, cb, k0, k1,
+                                                            k2);
     }
     if (warp == 1) return producer_tile<fwd, table>(a, g, sm, cb);
-    return flusher_tile<fwd>(a, g, sm, cb);
+    return flusher_tile<fwd, codes>(a, g, sm, cb);
 }
 
+template <bool codes>
+__device__ __forceinline__ bool run_pass_tile(const Chain2DArgs& a, bool fwd, int t_app, int pass,
+                                              int b, int tile, TileSmem& sm, unsigned int cb) {
+    if (fwd && a.table) return run_tile<true, true, codes>(a, t_app, pass, b, tile, sm, cb);
+    if (fwd) return run_tile<true, false, codes>(a, t_app, pass, b, tile, sm, cb);
+    if (a.table) return run_tile<false, true, codes>(a, t_app, pass, b, tile, sm, cb);
+    return run_tile<false, false, codes>(a, t_app, pass, b, tile, sm, cb);
+}
+
+// One persistent launch for all passes; `codes` selects the variant that also
+// records the parent codes.
+template <bool codes>
 __global__ void __launch_bounds__(kBlockThreads, 1) chain2d_kernel(const Chain2DArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     TileSmem& sm = *reinterpret_cast<TileSmem*>(smem_raw);
@@ -680,10 +735,7 @@ __global__ void __launch_bounds__(kBlockThreads, 1) chain2d_kernel(const Chain2D
                 if (b < a.B) {
                     const int tile = blockIdx.x % ntiles;
                     const bool fwd = (pass == 0 || pass == 2);
-                    if (fwd && a.table) ok = run_tile<true, true>(a, t_app, pass, b, tile, sm, cb);
-                    else if (fwd) ok = run_tile<true, false>(a, t_app, pass, b, tile, sm, cb);
-                    else if (a.table) ok = run_tile<false, true>(a, t_app, pass, b, tile, sm, cb);
-                    else ok = run_tile<false, false>(a, t_app, pass, b, tile, sm, cb);
+                    ok = run_pass_tile<codes>(a, fwd, t_app, pass, b, tile, sm, cb);
                     cb += (unsigned int)((L + kCh - 1) / kCh);
                 }
             }
@@ -729,9 +781,9 @@ int chain2d_geometry(int64_t H, int64_t W, const fgx_options* opt, int* K, int* 
     return FGX_OK;
 }
 
-int run_chain2d(const float* image, const float* mask, float* dist, int64_t B, int64_t C,
-                int64_t H, int64_t W, float v, float lambda, int iterations, void* workspace,
-                size_t ws_bytes, const fgx_options* opt, int sms, void* stream) {
+int run_chain2d(const float* image, const float* mask, float* dist, uint8_t* codes, int64_t B,
+                int64_t C, int64_t H, int64_t W, float v, float lambda, int iterations,
+                void* workspace, size_t ws_bytes, const fgx_options* opt, int sms, void* stream) {
     Chain2DArgs a;
     std::memset(&a, 0, sizeof(a));
     int K, T, tv, th;
@@ -742,6 +794,7 @@ int run_chain2d(const float* image, const float* mask, float* dist, int64_t B, i
     a.image = image;
     a.mask = mask;
     a.dist = dist;
+    a.codes = codes;
     a.B = (int)B;
     a.C = (int)C;
     a.H = (int)H;
@@ -781,11 +834,12 @@ int run_chain2d(const float* image, const float* mask, float* dist, int64_t B, i
     a.Eh = (float*)(p + off);
 
     const size_t smem = sizeof(TileSmem);
-    if (cudaFuncSetAttribute(chain2d_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    auto kernel = codes ? chain2d_kernel<true> : chain2d_kernel<false>;
+    if (cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)smem) != cudaSuccess)
         return FGX_ERR_CUDA;
     int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, chain2d_kernel, kBlockThreads,
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kBlockThreads,
                                                       smem) != cudaSuccess || per_sm < 1)
         return FGX_ERR_CUDA;
     // one tile per block: as many blocks as the tiles of all images, or as
@@ -813,7 +867,7 @@ int run_chain2d(const float* image, const float* mask, float* dist, int64_t B, i
     attr[0].val.cooperative = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    if (cudaLaunchKernelEx(&cfg, chain2d_kernel, a) != cudaSuccess) return FGX_ERR_CUDA;
+    if (cudaLaunchKernelEx(&cfg, kernel, a) != cudaSuccess) return FGX_ERR_CUDA;
     return FGX_OK;
 }
 

@@ -227,19 +227,19 @@ int run_forward(int ndim, const float* image, const float* mask, float* dist, in
         return FGX_ERR_NOT_DEVICE_PTR;
     const size_t nb = (size_t)(B * N) * sizeof(float);
     if (overlaps(dist, nb, image, (size_t)(B * C * N) * sizeof(float))) return FGX_ERR_ARG;
-    if (use_chain2d && ndim == 2 && !codes) {
-        if (!workspace || ws_bytes < pl.chain_bytes) return FGX_ERR_WORKSPACE;
-        if (!is_device_ptr(workspace)) return FGX_ERR_NOT_DEVICE_PTR;
-        return run_chain2d(image, mask, dist, B, C, H, W, v, lambda, iterations, workspace,
-                           ws_bytes, opt, pl.sms, stream);
-    }
-    if (!workspace || ws_bytes < pl.ws_bytes) return FGX_ERR_WORKSPACE;
-    if (!is_device_ptr(workspace)) return FGX_ERR_NOT_DEVICE_PTR;
     const size_t need_codes = (size_t)iterations * pl.args.npass * (size_t)(B * N);
     if (codes) {
         if (codes_bytes < need_codes) return FGX_ERR_WORKSPACE;
         if (!is_device_ptr(codes)) return FGX_ERR_NOT_DEVICE_PTR;
     }
+    if (use_chain2d && ndim == 2) {
+        if (!workspace || ws_bytes < pl.chain_bytes) return FGX_ERR_WORKSPACE;
+        if (!is_device_ptr(workspace)) return FGX_ERR_NOT_DEVICE_PTR;
+        return run_chain2d(image, mask, dist, codes, B, C, H, W, v, lambda, iterations,
+                           workspace, ws_bytes, opt, pl.sms, stream);
+    }
+    if (!workspace || ws_bytes < pl.ws_bytes) return FGX_ERR_WORKSPACE;
+    if (!is_device_ptr(workspace)) return FGX_ERR_NOT_DEVICE_PTR;
     SweepArgs& a = pl.args;
     a.image = image;
     a.mask = mask;
@@ -344,7 +344,8 @@ int fgx_geodesic2d_fwd_train(const float* image, const float* mask, float* dist,
                              size_t workspace_bytes, const fgx_options* opt, void* stream) {
     if (!saved && (size_t)iterations * B * H * W > 0) return FGX_ERR_WORKSPACE;
     return run_forward(2, image, mask, dist, B, C, 1, H, W, nullptr, v, lambda, iterations,
-                       (uint8_t*)saved, saved_bytes, workspace, workspace_bytes, opt, stream);
+                       (uint8_t*)saved, saved_bytes, workspace, workspace_bytes, opt, stream,
+                       true);
 }
 
 int fgx_geodesic3d_fwd_train(const float* image, const float* mask, float* dist, int64_t B,

@@ -135,9 +135,9 @@ void pass_extents(int axis, const int64_t ext[3], PassGeom* g);
 size_t chain2d_workspace_bytes(int64_t B, int64_t C, int64_t H, int64_t W, int tiles);
 int chain2d_geometry(int64_t H, int64_t W, const fgx_options* opt, int* K, int* T, int* tv,
                      int* th);
-int run_chain2d(const float* image, const float* mask, float* dist, int64_t B, int64_t C,
-                int64_t H, int64_t W, float v, float lambda, int iterations, void* workspace,
-                size_t ws_bytes, const fgx_options* opt, int sms, void* stream);
+int run_chain2d(const float* image, const float* mask, float* dist, uint8_t* codes, int64_t B,
+                int64_t C, int64_t H, int64_t W, float v, float lambda, int iterations,
+                void* workspace, size_t ws_bytes, const fgx_options* opt, int sms, void* stream);
 
 // Adjoint launchers (adjoint_kernel.cu)
 int launch_adjoint(const AdjointArgs& a, int grid, size_t smem, void* stream);

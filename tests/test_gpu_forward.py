@@ -170,6 +170,30 @@ def test_fwd_train_codes_match_oracle(fgx):
         np.testing.assert_array_equal(saved.cpu().numpy(), want_codes)
 
 
+@pytest.mark.parametrize("lam,opts", [
+    (0.75, None),                                             # rows and columns of 3 tiles
+    (0.0, None),                                              # constant costs
+    (1.0, dict(tile_width=16, tile_lines=8)),                 # many narrow tiles
+    (0.5, dict(tile_width=24, tile_lines=16, max_blocks=14)),  # images in waves
+])
+def test_fwd_train_codes_2d_multi_tile(fgx, lam, opts):
+    """2D parent codes of every pass application equal the oracle's, also
+    with tiles, ring refreshes and several waves of images."""
+    rng = np.random.default_rng(17)
+    img = rng.uniform(0, 1, (3, 2, 150, 301)).astype(np.float32)
+    m = np.ones((3, 1, 150, 301), np.float32)
+    m[0, 0, 7, 9] = 0
+    m[1, 0, 140, 290] = 0
+    m[2, 0, 75, 150] = 0
+    m[2, 0, 0, 300] = 0.25
+    case = workloads.Case("codes2d", img, m, 3.0, lam, 2)
+    d, saved = fgx.forward_train(torch.from_numpy(img).cuda(), torch.from_numpy(m).cuda(),
+                                 case.v, lam, 2, options=opts, check=True)
+    want_d, want_codes = oracle.gdt(img, m, case.v, lam, 2, return_codes=True, threads=THREADS)
+    assert_bit_exact(d.cpu().numpy(), want_d)
+    np.testing.assert_array_equal(saved.cpu().numpy(), want_codes)
+
+
 # ----------------------------------------------------------------- errors
 
 def test_error_codes(fgx):
