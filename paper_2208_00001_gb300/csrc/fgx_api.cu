@@ -108,6 +108,7 @@ struct Plan {
     size_t smem = 0;
     size_t ws_bytes = 0;      // tiled sweep kernel
     size_t chain_bytes = 0;   // 2D warp-chain kernel (0 when not applicable)
+    size_t vol3d_bytes = 0;   // 3D plane-tile kernel (0 when not applicable)
     int sms = 0;
 };
 
@@ -194,6 +195,7 @@ int plan_forward(int ndim, int64_t B, int64_t C, int64_t D, int64_t H, int64_t W
         chain2d_geometry(H, W, opt, &K, &T, &tv, &th);
         pl->chain_bytes = chain2d_workspace_bytes(B, C, H, W, std::max(tv, th));
     }
+    if (ndim == 3) pl->vol3d_bytes = vol3d_workspace_bytes(a, opt, dev.sms);
     return FGX_OK;
 }
 
@@ -237,6 +239,13 @@ int run_forward(int ndim, const float* image, const float* mask, float* dist, in
         if (!is_device_ptr(workspace)) return FGX_ERR_NOT_DEVICE_PTR;
         return run_chain2d(image, mask, dist, codes, B, C, H, W, v, lambda, iterations,
                            workspace, ws_bytes, opt, pl.sms, stream);
+    }
+    if (ndim == 3 && !codes && pl.vol3d_bytes && workspace && ws_bytes >= pl.vol3d_bytes &&
+        vol3d_supports(pl.args, opt, pl.sms)) {
+        if (!is_device_ptr(workspace)) return FGX_ERR_NOT_DEVICE_PTR;
+        SweepArgs f = pl.args;
+        f.timeout_ns = pl.args.timeout_ns;
+        return run_vol3d(f, image, mask, dist, v, workspace, ws_bytes, opt, pl.sms, stream);
     }
     if (!workspace || ws_bytes < pl.ws_bytes) return FGX_ERR_WORKSPACE;
     if (!is_device_ptr(workspace)) return FGX_ERR_NOT_DEVICE_PTR;
@@ -299,7 +308,7 @@ int fgx_geodesic_workspace_size(int ndim, int64_t B, int64_t C, int64_t D, int64
     Plan pl;
     int st = plan_forward(ndim, B, C, D, H, W, unit, 0.5f, 1, opt, &pl);
     if (st != FGX_OK) return st;
-    *bytes = std::max(pl.ws_bytes, pl.chain_bytes);
+    *bytes = std::max(std::max(pl.ws_bytes, pl.chain_bytes), pl.vol3d_bytes);
     return FGX_OK;
 }
 

@@ -135,6 +135,13 @@ void pass_extents(int axis, const int64_t ext[3], PassGeom* g);
 size_t chain2d_workspace_bytes(int64_t B, int64_t C, int64_t H, int64_t W, int tiles);
 int chain2d_geometry(int64_t H, int64_t W, const fgx_options* opt, int* K, int* T, int* tv,
                      int* th);
+// 3D forward on register-blocked plane tiles (vol3d.cu): workspace bytes, 0
+// when the call does not fit that kernel (the tiled engine runs it instead).
+size_t vol3d_workspace_bytes(const SweepArgs& f, const fgx_options* opt, int sms);
+bool vol3d_supports(const SweepArgs& f, const fgx_options* opt, int sms);
+int run_vol3d(const SweepArgs& f, const float* image, const float* mask, float* dist, float v,
+              void* workspace, size_t ws_bytes, const fgx_options* opt, int sms, void* stream);
+
 int run_chain2d(const float* image, const float* mask, float* dist, uint8_t* codes, int64_t B,
                 int64_t C, int64_t H, int64_t W, float v, float lambda, int iterations,
                 void* workspace, size_t ws_bytes, const fgx_options* opt, int sms, void* stream);

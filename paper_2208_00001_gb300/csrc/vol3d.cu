@@ -1,0 +1,629 @@
+// 3D forward on register-blocked plane tiles (FastGeodis, Implementation
+// section: six passes per iteration, every voxel of a plane updated from the
+// nine voxels of the already-updated previous plane).
+//
+// Decomposition.  One cooperative persistent launch runs all passes.  For a
+// pass along one axis the plane (P x Q voxels) is cut into tiles of
+// kTP x kTQ owned voxels; one thread block per tile computes a region of
+// kRP x kRQ = 32 x 32 voxels: the tile plus a ring of kRing voxels on every
+// side.  Eight compute warps each hold four region rows: lane q owns column q
+// of the region and keeps the four distances of its rows in registers.  A
+// plane step needs the 3 x 3 parents of every voxel: the own column's rows
+// come from registers plus the two boundary rows of the warps above and below
+// (shared memory, one named barrier of the compute warps per step), the
+// neighbouring columns by warp shuffles.  Old distances and intensities of
+// upcoming planes are staged in shared memory by four producer warps with
+// cp.async (chunks of kChunk planes, one mbarrier per chunk).  The dependency
+// cone shrinks the exact part of the region by one voxel per side and step,
+// so the owned voxels stay exact for kRing steps; then every block publishes
+// its owned voxels as 64-bit (value, tag) words and refreshes its ring from
+// the owners' words (bounded polling, no fences: every word carries its own
+// tag).  Passes are separated by a grid barrier.  Ring voxels are recomputed
+// with exactly the operations of their owners, so results stay bit-exact.
+//
+// Edge costs are evaluated on the fly in the fixed order of the method:
+//  constant (lambda = 0): sqrt(t_k), one constant per stencil offset;
+//  absolute (lambda = 1, one channel): |I(x) - I(y)|, which equals
+//    sqrt_rn(fl(d*d)) for d = 0 and 2^-63 <= |d| <= 2^63; a first kernel
+//    checks that every intensity is 0 or has magnitude in [2^-40, 2^62],
+//    which bounds every difference to that range; otherwise each candidate
+//    is checked and falls back to the square root;
+//  general: sqrt_rn(t_k + lambda * sum_ch (I(x)-I(y))^2).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+
+#include "device_sync.cuh"
+#include "fgx_internal.h"
+
+namespace fgx {
+namespace {
+
+using namespace dev;
+
+constexpr int kRows = 4;                  // region rows per compute thread
+constexpr int kCW = 8;                    // compute warps
+constexpr int kPW = 4;                    // producer warps
+constexpr int kRP = kRows * kCW;          // region rows
+constexpr int kRQ = 32;                   // region columns (one per lane)
+constexpr int kRing = 4;                  // ring width = steps between refreshes
+constexpr int kTP = kRP - 2 * kRing;      // owned rows of a tile
+constexpr int kTQ = kRQ - 2 * kRing;      // owned columns of a tile
+constexpr int kPlane = kRP * kRQ;         // region voxels
+constexpr int kChunk = kRing;             // planes per staging chunk
+constexpr int kNst = 3;                   // chunks in the staging ring
+constexpr int kMaxCI = 3;                 // intensity channels the stage holds
+constexpr int kBlock3 = (kCW + kPW) * 32;
+constexpr int kXWords = kTP * kTQ;        // published words per tile and parity
+constexpr int kRangeFlagOffset = 32;      // workspace header: intensity range flag
+#define kInf3 __int_as_float(0x7f800000)
+
+enum { kModeConst = 0, kModeAbs = 1, kModeGeneral = 2 };
+
+struct Vol3DArgs {
+    const float* image;  // [B][C][N]
+    const float* mask;   // [B][N]
+    float* dist;         // [B][N]
+    int64_t B, C, N;
+    float v, lambda;
+    int iterations;
+    int mode;
+    PassGeom pass[kMaxPasses];
+    int ntp[kMaxPasses], ntq[kMaxPasses];
+    int max_tiles;
+    unsigned long long* xbuf;  // [B][max_tiles][2 parities][kXWords]
+    unsigned int* barrier;
+    int* status;
+    const int* range_flag;     // nonzero: some intensity outside the |d| range
+    long long timeout_ns;
+};
+
+struct Head3 {
+    unsigned long long full[kNst], empty[kNst];
+    float rowtop[2][kCW][kRQ];  // first row of each warp, per step parity
+    float rowbot[2][kCW][kRQ];  // last row of each warp
+};
+static_assert(sizeof(Head3) % 16 == 0, "stage must stay 16-byte aligned");
+
+__device__ __align__(16) unsigned int g_inf4[4] = {0x7f800000u, 0x7f800000u, 0x7f800000u,
+                                                  0x7f800000u};
+
+__device__ __forceinline__ unsigned int saddr3(const void* p) {
+    return (unsigned int)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void cp_async4(void* smem, const void* gmem) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(saddr3(smem)), "l"(gmem)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_arrive_noinc(unsigned long long* b) {
+    asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(saddr3(b))
+                 : "memory");
+}
+__device__ __forceinline__ void cp_wait_all3() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+__device__ __forceinline__ void mbar_init3(unsigned long long* b, unsigned int count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(saddr3(b)), "r"(count)
+                 : "memory");
+}
+__device__ __forceinline__ void mbar_arrive3(unsigned long long* b) {
+    asm volatile("mbarrier.arrive.release.cta.shared::cta.b64 _, [%0];" ::"r"(saddr3(b))
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_try3(unsigned long long* b, unsigned int parity) {
+    unsigned int ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.acquire.cta.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(saddr3(b)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// Bounded wait for the phase of parity `parity` of *b (false on timeout or
+// an earlier failure recorded in the status word).
+__device__ __noinline__ bool mbar_wait3(unsigned long long* b, unsigned int parity, int* status,
+                                        long long timeout_ns) {
+    if (mbar_try3(b, parity)) return true;
+    const long long t0 = gtimer();
+    for (;;) {
+        if (mbar_try3(b, parity)) return true;
+        if (status_of(status) != 0) return false;
+        if (gtimer() - t0 > timeout_ns) {
+            record_timeout(status);
+            return false;
+        }
+    }
+}
+// Compute-warp barrier (the producer warps never join it).
+__device__ __forceinline__ void compute_sync() {
+    asm volatile("bar.sync 1, %0;" ::"n"(kCW * 32) : "memory");
+}
+
+// Position of one tile of one pass application.
+struct Tile3 {
+    const PassGeom* g;
+    int jp, jq, ntq, tile;
+    int64_t b;
+    int L, nch;
+    int64_t p0, q0;  // plane coordinates of region row 0 and column 0
+};
+
+__device__ __forceinline__ float* stage_plane(float* stage, int slot, int j, int arr, int CI) {
+    return stage + ((size_t)(slot * kChunk + j) * (1 + CI) + arr) * kPlane;
+}
+
+// Producer warps: planes of old distances and intensities into the staging
+// ring, chunk after chunk, once the compute warps have released the slot.
+// Voxels outside the volume are staged as +inf.
+template <int CI>
+__device__ bool producer3(const Vol3DArgs& a, const Tile3& t, Head3& h, float* stage,
+                          unsigned int cb) {
+    const PassGeom& g = *t.g;
+    const int lane = threadIdx.x & 31, pw = (threadIdx.x >> 5) - kCW;
+    const int64_t q = t.q0 + lane;
+    const bool qin = q >= 0 && q < g.Q;
+    const float* img = a.image + t.b * a.C * a.N;
+    const float* dist = a.dist + t.b * a.N;
+    for (int c = 0; c < t.nch; ++c) {
+        const unsigned int gc = cb + c;
+        const int slot = (int)(gc % kNst);
+        if (gc >= (unsigned)kNst &&
+            !__all_sync(0xffffffffu, mbar_wait3(&h.empty[slot], ((gc / kNst) & 1u) ^ 1u,
+                                                a.status, a.timeout_ns))) {
+            cp_wait_all3();
+            return false;
+        }
+        const int jn = min(kChunk, t.L - c * kChunk);
+        for (int j = 0; j < jn; ++j) {
+            const int s = c * kChunk + j;
+            const int64_t line = g.dir > 0 ? s : (t.L - 1 - s);
+#pragma unroll
+            for (int rr = 0; rr < kRP / kPW; ++rr) {
+                const int r = pw + kPW * rr;
+                const int64_t p = t.p0 + r;
+                const bool in = qin && p >= 0 && p < g.P;
+                const int64_t off = line * g.sl + p * g.sp + q * g.sq;
+                float* dst = stage_plane(stage, slot, j, 0, CI) + r * kRQ + lane;
+                cp_async4(dst, in ? (const void*)(dist + off) : (const void*)g_inf4);
+#pragma unroll
+                for (int ch = 0; ch < CI; ++ch)
+                    cp_async4(dst + (ch + 1) * kPlane,
+                              in ? (const void*)(img + ch * a.N + off) : (const void*)g_inf4);
+            }
+        }
+        cp_arrive_noinc(&h.full[slot]);
+    }
+    return true;
+}
+
+// Ring refresh after step s: publish the owned voxels of plane s, then take
+// every ring voxel inside the volume from the tile that owns it.
+__device__ bool exchange3(const Vol3DArgs& a, const Tile3& t, int w, unsigned int tg, int par,
+                          float (&d)[kRows]) {
+    const PassGeom& g = *t.g;
+    const int lane = threadIdx.x & 31;
+    unsigned long long* base = a.xbuf + (size_t)t.b * a.max_tiles * 2 * kXWords;
+    unsigned long long* mine = base + ((size_t)t.tile * 2 + par) * kXWords;
+    const bool qown = lane >= kRing && lane < kRing + kTQ;
+    const int64_t q = t.q0 + lane;
+    const bool qin = q >= 0 && q < g.Q;
+    const unsigned long long* src[kRows];
+    bool need[kRows];
+#pragma unroll
+    for (int i = 0; i < kRows; ++i) {
+        const int r = w * kRows + i;
+        const bool pown = r >= kRing && r < kRing + kTP;
+        const unsigned long long word =
+            ((unsigned long long)tg << 32) | (unsigned int)__float_as_uint(d[i]);
+        if (pown && qown) st_relaxed_u64(mine + (r - kRing) * kTQ + (lane - kRing), word);
+        const int64_t p = t.p0 + r;
+        need[i] = !(pown && qown) && qin && p >= 0 && p < g.P;
+        src[i] = nullptr;
+        if (need[i]) {
+            const int op = (int)(p / kTP), oq = (int)(q / kTQ);
+            const int lr = (int)(p - (int64_t)op * kTP), lq = (int)(q - (int64_t)oq * kTQ);
+            src[i] = base + ((size_t)(op * t.ntq + oq) * 2 + par) * kXWords + lr * kTQ + lq;
+        }
+    }
+    long long t0 = 0;
+    for (unsigned int it = 0;; ++it) {
+        bool done = true;
+#pragma unroll
+        for (int i = 0; i < kRows; ++i) {
+            if (!need[i]) continue;
+            const unsigned long long wv = ld_relaxed_u64(src[i]);
+            if ((unsigned int)(wv >> 32) == tg) {
+                d[i] = __uint_as_float((unsigned int)wv);
+                need[i] = false;
+            } else {
+                done = false;
+            }
+        }
+        if (__all_sync(0xffffffffu, done)) return true;
+        // the status word and the clock are read every 16th poll only
+        if ((it & 15u) == 15u) {
+            int fail = 0;
+            if (lane == 0) {
+                const long long now = gtimer();
+                if (t0 == 0) t0 = now;
+                if (status_of(a.status) != 0) fail = 1;
+                else if (now - t0 > a.timeout_ns) {
+                    record_timeout(a.status);
+                    fail = 1;
+                }
+            }
+            if (__shfl_sync(0xffffffffu, fail, 0)) return false;
+        }
+    }
+}
+
+// Edge cost of one parent, in the fixed arithmetic order of the method.
+template <int MODE, int CI, bool CHECKED>
+__device__ __forceinline__ float cost3(const float (&ix)[CI > 0 ? CI : 1],
+                                       const float (&iy)[CI > 0 ? CI : 1], float t, float c0,
+                                       float lam) {
+    if (MODE == kModeConst) return c0;
+    if (MODE == kModeAbs) {
+        const float d = __fsub_rn(ix[0], iy[0]);
+        const float ad = fabsf(d);
+        if (!CHECKED) return ad;
+        const unsigned int ub = __float_as_uint(ad);
+        if ((ub - 0x20000000u) <= 0x3F000000u || ub == 0u) return ad;
+        return __fsqrt_rn(__fmul_rn(d, d));
+    }
+    float di2 = 0.0f;
+#pragma unroll
+    for (int ch = 0; ch < CI; ++ch) {
+        const float d = __fsub_rn(ix[ch], iy[ch]);
+        di2 = ch == 0 ? __fmul_rn(d, d) : __fadd_rn(di2, __fmul_rn(d, d));
+    }
+    return __fsqrt_rn(__fadd_rn(t, __fmul_rn(lam, di2)));
+}
+
+// Compute warps of one tile: plane steps 1 .. L-1, ring refresh every kRing
+// steps, owned voxels written to the distance map.
+template <int MODE, int CI, bool CHECKED>
+__device__ bool compute3(const Vol3DArgs& a, const Tile3& t, int t_app, Head3& h, float* stage,
+                         unsigned int cb) {
+    constexpr int NI = CI > 0 ? CI : 1;
+    const PassGeom& g = *t.g;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int64_t q = t.q0 + lane;
+    const bool qin = q >= 0 && q < g.Q;
+    const bool qown = lane >= kRing && lane < kRing + kTQ;
+    bool valid[kRows], own[kRows];
+    int64_t goff[kRows];
+#pragma unroll
+    for (int i = 0; i < kRows; ++i) {
+        const int r = w * kRows + i;
+        const int64_t p = t.p0 + r;
+        valid[i] = qin && p >= 0 && p < g.P;
+        own[i] = valid[i] && qown && r >= kRing && r < kRing + kTP;
+        goff[i] = p * g.sp + q * g.sq;
+    }
+    float* dist = a.dist + t.b * a.N;
+    const float lam = a.lambda;
+    float tk[9], ck[9];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+        tk[k] = g.t[k];
+        ck[k] = g.c[k];
+    }
+    // clamped stage columns of the left and right neighbours (their parent
+    // distances are +inf where the clamp applies)
+    const int cl = max(lane - 1, 0), cr = min(lane + 1, kRQ - 1);
+    const int rows0 = w * kRows;
+
+    // After a failure (timeout, or one reported by another block) the warps
+    // keep stepping through the named barriers with every wait skipped, so
+    // that no compute warp is left waiting for one that gave up.
+    bool failed = !__all_sync(0xffffffffu, mbar_wait3(&h.full[cb % kNst], (cb / kNst) & 1u,
+                                                      a.status, a.timeout_ns));
+    float d[kRows];
+    {
+        const float* S0 = stage_plane(stage, (int)(cb % kNst), 0, 0, CI);
+#pragma unroll
+        for (int i = 0; i < kRows; ++i) d[i] = S0[(rows0 + i) * kRQ + lane];
+    }
+    const unsigned int tag_base = ((unsigned int)(t_app + 1)) << 16;
+    int xi = 0;
+    for (int s = 1; s < t.L; ++s) {
+        const unsigned int gc = cb + s / kChunk;
+        const int j = s % kChunk;
+        const int slot = (int)(gc % kNst);
+        if (j == 0 && !failed &&
+            !__all_sync(0xffffffffu, mbar_wait3(&h.full[slot], (gc / kNst) & 1u, a.status,
+                                                a.timeout_ns)))
+            failed = true;
+        // boundary rows of plane s-1 for the warps above and below
+        const int rb = s & 1;
+        h.rowtop[rb][w][lane] = d[0];
+        h.rowbot[rb][w][lane] = d[kRows - 1];
+        compute_sync();
+        // plane s-2 is no longer read by any compute warp: free its chunk if
+        // it was the chunk's last plane
+        if (threadIdx.x == 0 && s >= 2 && (s - 2) % kChunk == kChunk - 1)
+            mbar_arrive3(&h.empty[(cb + (s - 2) / kChunk) % kNst]);
+        float col[kRows + 2], lft[kRows + 2], rgt[kRows + 2];
+        col[0] = w > 0 ? h.rowbot[rb][w - 1][lane] : kInf3;
+#pragma unroll
+        for (int i = 0; i < kRows; ++i) col[i + 1] = d[i];
+        col[kRows + 1] = w < kCW - 1 ? h.rowtop[rb][w + 1][lane] : kInf3;
+#pragma unroll
+        for (int k = 0; k < kRows + 2; ++k) {
+            lft[k] = __shfl_up_sync(0xffffffffu, col[k], 1);
+            rgt[k] = __shfl_down_sync(0xffffffffu, col[k], 1);
+            if (lane == 0) lft[k] = kInf3;
+            if (lane == 31) rgt[k] = kInf3;
+        }
+        // old distances and intensities of plane s, intensities of plane s-1
+        const float* Sd = stage_plane(stage, slot, j, 0, CI);
+        const unsigned int gcp = cb + (s - 1) / kChunk;
+        const int slotp = (int)(gcp % kNst), jp = (s - 1) % kChunk;
+        float ip[kRows + 2][3][NI], ix[kRows][NI];
+        if (CI > 0) {
+#pragma unroll
+            for (int k = 0; k < kRows + 2; ++k) {
+                const int rr = min(max(rows0 + k - 1, 0), kRP - 1);
+#pragma unroll
+                for (int ch = 0; ch < CI; ++ch) {
+                    const float* Pi = stage_plane(stage, slotp, jp, 1 + ch, CI) + rr * kRQ;
+                    ip[k][0][ch] = Pi[cl];
+                    ip[k][1][ch] = Pi[lane];
+                    ip[k][2][ch] = Pi[cr];
+                }
+            }
+#pragma unroll
+            for (int i = 0; i < kRows; ++i)
+#pragma unroll
+                for (int ch = 0; ch < CI; ++ch)
+                    ix[i][ch] = stage_plane(stage, slot, j, 1 + ch, CI)[(rows0 + i) * kRQ + lane];
+        }
+        const int64_t lo = (int64_t)(g.dir > 0 ? s : (t.L - 1 - s)) * g.sl;
+#pragma unroll
+        for (int i = 0; i < kRows; ++i) {
+            float best = Sd[(rows0 + i) * kRQ + lane];
+#pragma unroll
+            for (int dp = -1; dp <= 1; ++dp) {
+#pragma unroll
+                for (int dq = -1; dq <= 1; ++dq) {
+                    const int k = (dp + 1) * 3 + (dq + 1);
+                    const int rk = i + 1 + dp;
+                    const float pd = dq < 0 ? lft[rk] : (dq == 0 ? col[rk] : rgt[rk]);
+                    const float c = cost3<MODE, CI, CHECKED>(ix[i], ip[rk][dq + 1], tk[k], ck[k],
+                                                             lam);
+                    best = fminf(best, __fadd_rn(pd, c));
+                }
+            }
+            d[i] = (MODE == kModeConst && !valid[i]) ? kInf3 : best;
+            if (own[i]) dist[lo + goff[i]] = d[i];
+        }
+        if (s % kRing == 0 && s + 1 < t.L) {
+            if (!failed && !exchange3(a, t, w, tag_base | (unsigned int)(xi + 1), xi & 1, d))
+                failed = true;
+            ++xi;
+        }
+    }
+    // free the chunks still held (those whose last plane is one of the last two)
+    compute_sync();
+    if (threadIdx.x == 0) {
+        const int nch = t.nch;
+        for (int c = max(0, nch - 2); c < nch; ++c) {
+            const int last = min(c * kChunk + kChunk - 1, t.L - 1);
+            if (last >= t.L - 2) mbar_arrive3(&h.empty[(cb + c) % kNst]);
+        }
+    }
+    return !failed;
+}
+
+// D0 = v * M, and the intensity range test that allows |d| as the cost.
+__global__ void __launch_bounds__(256) init3d_kernel(const float* mask, float* dist, float v,
+                                                     int64_t n, const float* image, int64_t ni,
+                                                     int* range_flag) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
+        dist[i] = __fmul_rn(v, mask[i]);
+    if (!range_flag) return;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < ni; i += stride) {
+        const float x = fabsf(image[i]);
+        // 0, or a magnitude in [2^-40, 2^62] (false for NaN and infinity)
+        const bool ok = x == 0.0f || (x >= 0x1p-40f && x <= 0x1p62f);
+        if (!ok && *(volatile int*)range_flag == 0) atomicOr(range_flag, 1);
+    }
+}
+
+template <int MODE, int CI>
+__device__ __forceinline__ bool run_tile3(const Vol3DArgs& a, const Tile3& t, int t_app, Head3& h,
+                                          float* stage, unsigned int cb, bool checked) {
+    if ((int)(threadIdx.x >> 5) >= kCW) return producer3<CI>(a, t, h, stage, cb);
+    if (MODE == kModeAbs && checked) return compute3<MODE, CI, true>(a, t, t_app, h, stage, cb);
+    return compute3<MODE, CI, false>(a, t, t_app, h, stage, cb);
+}
+
+template <int MODE, int CI>
+__global__ void __launch_bounds__(kBlock3, 1) vol3d_kernel(const Vol3DArgs a) {
+    extern __shared__ __align__(16) unsigned char smem3[];
+    Head3& h = *reinterpret_cast<Head3*>(smem3);
+    float* stage = reinterpret_cast<float*>(smem3 + sizeof(Head3));
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < kNst; ++i) {
+            mbar_init3(&h.full[i], kPW * 32);  // one asynchronous arrival per producer lane
+            mbar_init3(&h.empty[i], 1);
+        }
+    }
+    __syncthreads();
+    const bool checked = MODE == kModeAbs && *a.range_flag != 0;
+    unsigned long long* timeline = (unsigned long long*)((char*)a.status + 128);
+    if (blockIdx.x == 0 && threadIdx.x == 0) timeline[0] = (unsigned long long)gtimer();
+    unsigned int epoch = 1;
+    unsigned int cb = 0;  // staging chunks handed over so far in this block
+    const int napps = a.iterations * kMaxPasses;
+    bool alive = true;
+    for (int t_app = 0; t_app < napps && alive; ++t_app) {
+        const int pass = t_app % kMaxPasses;
+        const PassGeom& g = a.pass[pass];
+        const int ntiles = a.ntp[pass] * a.ntq[pass];
+        const int per_wave = gridDim.x / ntiles;
+        const int64_t nwaves = (a.B + per_wave - 1) / per_wave;
+        const int L = (int)g.L;
+        const int nch = L > 1 ? (L + kChunk - 1) / kChunk : 0;
+        for (int64_t wv = 0; wv < nwaves; ++wv) {
+            if ((int)blockIdx.x >= per_wave * ntiles) continue;
+            const int64_t b = wv * per_wave + blockIdx.x / ntiles;
+            if (b >= a.B) continue;
+            Tile3 t;
+            t.g = &g;
+            t.tile = blockIdx.x % ntiles;
+            t.jp = t.tile / a.ntq[pass];
+            t.jq = t.tile % a.ntq[pass];
+            t.ntq = a.ntq[pass];
+            t.b = b;
+            t.L = L;
+            t.nch = nch;
+            t.p0 = (int64_t)t.jp * kTP - kRing;
+            t.q0 = (int64_t)t.jq * kTQ - kRing;
+            if (nch > 0) run_tile3<MODE, CI>(a, t, t_app, h, stage, cb, checked);
+            cb += (unsigned int)nch;
+        }
+        alive = grid_barrier(a.barrier, epoch++, a.status, a.timeout_ns);
+        if (blockIdx.x == 0 && threadIdx.x == 0 && t_app + 1 < 16)
+            timeline[t_app + 1] = (unsigned long long)gtimer();
+    }
+}
+
+size_t stage_bytes(int CI) {
+    return sizeof(Head3) + (size_t)kNst * kChunk * (1 + CI) * kPlane * sizeof(float);
+}
+
+using Vol3DKernel = void (*)(Vol3DArgs);
+
+Vol3DKernel pick_kernel(int mode, int CI) {
+    if (mode == kModeConst) return vol3d_kernel<kModeConst, 0>;
+    if (mode == kModeAbs) return vol3d_kernel<kModeAbs, 1>;
+    if (CI == 1) return vol3d_kernel<kModeGeneral, 1>;
+    if (CI == 2) return vol3d_kernel<kModeGeneral, 2>;
+    return vol3d_kernel<kModeGeneral, 3>;
+}
+
+struct Vol3DPlan {
+    int mode = 0, CI = 0, grid = 0, max_tiles = 0;
+    int ntp[kMaxPasses] = {}, ntq[kMaxPasses] = {};
+    size_t smem = 0, ws_bytes = 0;
+};
+
+// Whether the 3D call fits this kernel (at most kMaxCI channels in the
+// general cost, every tile of a pass co-resident, no tile-shape options),
+// and its launch geometry.
+bool plan_vol3d(const SweepArgs& f, const fgx_options* opt, int sms, Vol3DPlan* vp,
+                bool any_mode = false) {
+    if (f.ndim != 3) return false;
+    if (opt && (opt->tile_lines || opt->tile_width || opt->tile_height)) return false;
+    vp->mode = f.cost_mode == kCostConst ? kModeConst
+               : f.cost_mode == kCostAbs ? kModeAbs : kModeGeneral;
+    vp->CI = vp->mode == kModeConst ? 0 : (int)f.C;
+    // a workspace-size query covers every cost mode: plan the cheapest one
+    if (any_mode) {
+        vp->mode = kModeConst;
+        vp->CI = 0;
+    }
+    // the general cost takes one IEEE square root per candidate; at 36
+    // candidates per thread and step that is slower here than in the tiled
+    // engine, which runs those calls
+    if (vp->mode == kModeGeneral) return false;
+    if (vp->CI > kMaxCI) return false;
+    int max_tiles = 1;
+    for (int i = 0; i < kMaxPasses; ++i) {
+        const PassGeom& g = f.pass[i];
+        vp->ntp[i] = (int)std::max<int64_t>(1, (g.P + kTP - 1) / kTP);
+        vp->ntq[i] = (int)std::max<int64_t>(1, (g.Q + kTQ - 1) / kTQ);
+        if ((int64_t)vp->ntp[i] * vp->ntq[i] > (1 << 20)) return false;
+        max_tiles = std::max(max_tiles, vp->ntp[i] * vp->ntq[i]);
+    }
+    vp->max_tiles = max_tiles;
+    vp->smem = stage_bytes(vp->CI);
+    Vol3DKernel k = pick_kernel(vp->mode, vp->CI);
+    if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)vp->smem) !=
+        cudaSuccess)
+        return false;
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kBlock3, vp->smem) !=
+            cudaSuccess ||
+        per_sm < 1)
+        return false;
+    int64_t grid = (int64_t)per_sm * sms;
+    if (opt && opt->max_blocks) grid = std::min<int64_t>(grid, opt->max_blocks);
+    grid = std::min<int64_t>(grid, std::max<int64_t>(1, f.B * max_tiles));
+    if (grid < max_tiles) return false;
+    vp->grid = (int)grid;
+    vp->ws_bytes = kHeaderBytes + (size_t)std::max<int64_t>(f.B, 1) * max_tiles * 2 * kXWords * 8;
+    return true;
+}
+
+}  // namespace
+
+bool vol3d_supports(const SweepArgs& f, const fgx_options* opt, int sms) {
+    Vol3DPlan vp;
+    return plan_vol3d(f, opt, sms, &vp);
+}
+
+size_t vol3d_workspace_bytes(const SweepArgs& f, const fgx_options* opt, int sms) {
+    Vol3DPlan vp;
+    return plan_vol3d(f, opt, sms, &vp, true) ? vp.ws_bytes : 0;
+}
+
+int run_vol3d(const SweepArgs& f, const float* image, const float* mask, float* dist, float v,
+              void* workspace, size_t ws_bytes, const fgx_options* opt, int sms, void* stream) {
+    Vol3DPlan vp;
+    if (!plan_vol3d(f, opt, sms, &vp)) return FGX_ERR_UNSUPPORTED;
+    if (ws_bytes < vp.ws_bytes) return FGX_ERR_WORKSPACE;
+    Vol3DArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.image = image;
+    a.mask = mask;
+    a.dist = dist;
+    a.B = f.B;
+    a.C = f.C;
+    a.N = f.N;
+    a.v = v;
+    a.lambda = f.lambda;
+    a.iterations = f.iterations;
+    a.mode = vp.mode;
+    for (int i = 0; i < kMaxPasses; ++i) {
+        a.pass[i] = f.pass[i];
+        a.ntp[i] = vp.ntp[i];
+        a.ntq[i] = vp.ntq[i];
+    }
+    a.max_tiles = vp.max_tiles;
+    char* w = (char*)workspace;
+    a.status = (int*)w;
+    a.barrier = (unsigned int*)(w + 64);
+    int* range_flag = (int*)(w + kRangeFlagOffset);
+    a.range_flag = range_flag;
+    a.xbuf = (unsigned long long*)(w + kHeaderBytes);
+    a.timeout_ns = f.timeout_ns;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (cudaMemsetAsync(workspace, 0, vp.ws_bytes, s) != cudaSuccess) return FGX_ERR_CUDA;
+    const int64_t n = f.B * f.N;
+    const int ig = (int)std::min<int64_t>((n + 255) / 256, (int64_t)sms * 16);
+    init3d_kernel<<<std::max(ig, 1), 256, 0, s>>>(mask, dist, v, n, image, f.B * f.C * f.N,
+                                                 vp.mode == kModeAbs ? range_flag : nullptr);
+    if (cudaGetLastError() != cudaSuccess) return FGX_ERR_CUDA;
+    if (f.iterations == 0) return FGX_OK;
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    cfg.gridDim = dim3((unsigned)vp.grid);
+    cfg.blockDim = dim3(kBlock3);
+    cfg.dynamicSmemBytes = vp.smem;
+    cfg.stream = s;
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    if (cudaLaunchKernelEx(&cfg, pick_kernel(vp.mode, vp.CI), a) != cudaSuccess)
+        return FGX_ERR_CUDA;
+    return FGX_OK;
+}
+
+}  // namespace fgx

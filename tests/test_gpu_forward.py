@@ -114,6 +114,27 @@ def test_edge_shapes_3d(fgx, shape):
                                                           tile_lines=2)), want)
 
 
+@pytest.mark.parametrize("lam,tiny", [(1.0, False), (1.0, True), (0.0, False)])
+def test_plane_tiles_3d_bit_exact(fgx, lam, tiny):
+    """3D passes over planes of several 24 x 24 tiles in both directions,
+    three volumes (also in waves of blocks), anisotropic spacing; with tiny
+    intensities the |d| cost takes its checked path."""
+    rng = np.random.default_rng(31)
+    shape = (30, 75, 53)
+    img = rng.uniform(-50, 50, (3, 1) + shape).astype(np.float32)
+    if tiny:
+        img[1, 0, ::3] *= np.float32(1e-30)  # differences below 2^-63 occur
+    m = np.ones((3, 1) + shape, np.float32)
+    m[0, 0, 3, 4, 5] = 0
+    m[1, 0, 29, 74, 52] = 0
+    m[2, 0, 15, 37, 26] = 0
+    m[2, 0, 0, 0, 0] = 0.5
+    case = workloads.Case("tiles3d", img, m, 1e5, lam, 2, (2.0, 0.75, 1.25))
+    want = oracle_run(case)
+    assert_bit_exact(gpu_run(fgx, case), want)
+    assert_bit_exact(gpu_run(fgx, case, options=dict(max_blocks=20)), want)
+
+
 def test_batch_of_images_bit_exact(fgx):
     rng = np.random.default_rng(7)
     img = rng.uniform(0, 1, (5, 2, 70, 90)).astype(np.float32)
