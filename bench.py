@@ -242,12 +242,19 @@ def _roof(bytes_, t, peak):
     return {"achieved_gbs": gbs, "frac": gbs / peak, "algorithmic_bytes": bytes_}
 
 
-def measure_extras(fgx, dev, flush, stream, peak, steps=5):
+EXTRAS = ("2d_plain_256", "2d_large_lambda0", "2d_large_lambda1", "2d_large_lambda0.5_it4",
+          "3d_volume_128x256x256", "batched_64x2d_16x3d", "diff_2d_8x512x512",
+          "diff_3d_96x160x160")
+
+
+def measure_extras(fgx, dev, flush, stream, peak, steps=5, only=None):
     """The other workloads of the method on this GPU, each timed like the
-    headline (warm-up, L2 flush between steps, CUDA events)."""
+    headline (warm-up, L2 flush between steps, CUDA events); `only` names a
+    single one of them."""
     import torch
     import workloads
     out = {}
+    want = lambda name: only is None or only == name  # noqa: E731
 
     def fwd_bytes(c):
         npass = 6 if c.ndim == 3 else 4
@@ -268,17 +275,34 @@ def measure_extras(fgx, dev, flush, stream, peak, steps=5):
         st = fgx.workspace_status(ws)
         return t, st
 
-    for name, c in [("2d_plain_256", workloads.plain2d()),
-                    ("2d_large_lambda0", workloads.large2d(lam=0.0)),
-                    ("2d_large_lambda1", workloads.large2d(lam=1.0)),
-                    ("2d_large_lambda0.5_it4", workloads.large2d(iterations=4)),
-                    ("3d_volume_128x256x256", workloads.volume3d())]:
+    for name, make in [("2d_plain_256", lambda: workloads.plain2d()),
+                       ("2d_large_lambda0", lambda: workloads.large2d(lam=0.0)),
+                       ("2d_large_lambda1", lambda: workloads.large2d(lam=1.0)),
+                       ("2d_large_lambda0.5_it4", lambda: workloads.large2d(iterations=4)),
+                       ("3d_volume_128x256x256", lambda: workloads.volume3d())]:
+        if not want(name):
+            continue
+        c = make()
         t, st = run_case(c)
         out[name] = {"ms": t * 1e3, "mvox_per_s_per_iter": c.voxels * c.iterations / t / 1e6,
                      "roofline": _roof(fwd_bytes(c), t, peak),
                      "device_status": fgx.status_string(st)}
 
-    # batched: one persistent launch vs the same instances as sequential calls
+    if want("batched_64x2d_16x3d"):
+        out.update(_batched_extra(fgx, dev, flush, stream, peak, steps, fwd_bytes))
+    for name, make in [("diff_2d_8x512x512", lambda: workloads.diff2d()),
+                       ("diff_3d_96x160x160", lambda: workloads.diff3d())]:
+        if want(name):
+            out.update(_diff_extra(fgx, dev, flush, stream, peak, steps, name, make()))
+    return out
+
+
+def _batched_extra(fgx, dev, flush, stream, peak, steps, fwd_bytes):
+    """Batched workload: one persistent launch vs the same instances as
+    sequential calls."""
+    import torch
+    import workloads
+    out = {}
     cases = workloads.batched()
     gpu = [(torch.from_numpy(c.image).to(dev), torch.from_numpy(c.mask).to(dev), c.v, c.lam,
             c.iterations, c.spacing or (1.0, 1.0, 1.0)) for c in cases]
@@ -302,34 +326,35 @@ def measure_extras(fgx, dev, flush, stream, peak, steps=5):
         "sequential_mvox_per_s_per_iter": units / t_s / 1e6,
         "roofline_one_launch": _roof(bbytes, t_b, peak),
         "device_status": fgx.status_string(st_b)}
-
-    # differentiable: forward, forward with codes, backward
-    for name, c in [("diff_2d_8x512x512", workloads.diff2d()),
-                    ("diff_3d_96x160x160", workloads.diff3d())]:
-        img = torch.from_numpy(c.image).to(dev)
-        m = torch.from_numpy(c.mask).to(dev)
-        w = torch.from_numpy(c.extra["w"]).to(dev)
-        f_plain = lambda: fgx.geodesic(img, m, c.v, c.lam, c.iterations, spacing=c.spacing)  # noqa
-        f_train = lambda: fgx.forward_train(img, m, c.v, c.lam, c.iterations,  # noqa
-                                            spacing=c.spacing)
-        d, saved = f_train()
-        f_bwd = lambda: fgx.backward(w, img, saved, c.v, c.lam, c.iterations,  # noqa
-                                     spacing=c.spacing)
-        for f in (f_plain, f_train, f_bwd):
-            f()
-        tp = _device_time(f_plain, steps, flush, stream)
-        tt = _device_time(f_train, steps, flush, stream)
-        tb = _device_time(f_bwd, steps, flush, stream)
-        units = c.voxels * c.iterations
-        C = c.image.shape[1]
-        npass = 6 if c.ndim == 3 else 4
-        bwd_bytes = c.voxels * c.iterations * npass * (8 + 2 + 4 * C + 8 * C)
-        out[name] = {"fwd_ms": tp * 1e3, "fwd_train_ms": tt * 1e3, "bwd_ms": tb * 1e3,
-                     "fwd_plus_bwd_ms": (tt + tb) * 1e3,
-                     "fwd_mvox_per_s_per_iter": units / tp / 1e6,
-                     "fwd_plus_bwd_mvox_per_s_per_iter": units / (tt + tb) / 1e6,
-                     "bwd_roofline": _roof(bwd_bytes, tb, peak)}
     return out
+
+
+def _diff_extra(fgx, dev, flush, stream, peak, steps, name, c):
+    """Differentiable workload: forward, forward with codes, backward."""
+    import torch
+    img = torch.from_numpy(c.image).to(dev)
+    m = torch.from_numpy(c.mask).to(dev)
+    w = torch.from_numpy(c.extra["w"]).to(dev)
+    f_plain = lambda: fgx.geodesic(img, m, c.v, c.lam, c.iterations, spacing=c.spacing)  # noqa
+    f_train = lambda: fgx.forward_train(img, m, c.v, c.lam, c.iterations,  # noqa
+                                        spacing=c.spacing)
+    d, saved = f_train()
+    f_bwd = lambda: fgx.backward(w, img, saved, c.v, c.lam, c.iterations,  # noqa
+                                 spacing=c.spacing)
+    for f in (f_plain, f_train, f_bwd):
+        f()
+    tp = _device_time(f_plain, steps, flush, stream)
+    tt = _device_time(f_train, steps, flush, stream)
+    tb = _device_time(f_bwd, steps, flush, stream)
+    units = c.voxels * c.iterations
+    C = c.image.shape[1]
+    npass = 6 if c.ndim == 3 else 4
+    bwd_bytes = c.voxels * c.iterations * npass * (8 + 2 + 4 * C + 8 * C)
+    return {name: {"fwd_ms": tp * 1e3, "fwd_train_ms": tt * 1e3, "bwd_ms": tb * 1e3,
+                   "fwd_plus_bwd_ms": (tt + tb) * 1e3,
+                   "fwd_mvox_per_s_per_iter": units / tp / 1e6,
+                   "fwd_plus_bwd_mvox_per_s_per_iter": units / (tt + tb) / 1e6,
+                   "bwd_roofline": _roof(bwd_bytes, tb, peak)}}
 
 
 def run_fgx(args):
@@ -343,6 +368,14 @@ def run_fgx(args):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     build.build()
+    if args.extra:
+        # one of the other workloads alone (profiler captures of its kernels)
+        flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+        res = measure_extras(fgx, dev, flush, torch.cuda.current_stream(), _peaks()[0],
+                             steps=args.steps, only=args.extra)
+        if rank == 0:
+            print(json.dumps({"extra": args.extra, **res}))
+        return 0
     case = workloads.large2d(size=args.size)
     workload = WORKLOAD if args.size == 2048 else WORKLOAD.replace("2048x2048", f"{args.size}x{args.size}")
     B, C, H, W = case.image.shape
@@ -457,6 +490,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="fgx", choices=["fgx", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--extra", choices=EXTRAS, default=None,
+                    help="time only this one of the other workloads (for profiler captures)")
     ap.add_argument("--size", type=int, default=2048,
                     help="side of the 2D image (2048 is the benchmark; smaller sides are for "
                          "profiler captures)")

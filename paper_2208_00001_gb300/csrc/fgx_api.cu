@@ -203,7 +203,7 @@ int run_forward(int ndim, const float* image, const float* mask, float* dist, in
                 int64_t D, int64_t H, int64_t W, const float spacing[3], float v, float lambda,
                 int iterations, uint8_t* codes, size_t codes_bytes, void* workspace,
                 size_t ws_bytes, const fgx_options* opt, void* stream,
-                bool use_chain2d = false) {
+                bool fast_kernels = false) {
     if (!(std::isfinite(v) && v > 0.f)) return FGX_ERR_ARG;
     if (!(lambda >= 0.f && lambda <= 1.f)) return FGX_ERR_ARG;
     if (iterations < 0) return FGX_ERR_ARG;
@@ -234,14 +234,16 @@ int run_forward(int ndim, const float* image, const float* mask, float* dist, in
         if (codes_bytes < need_codes) return FGX_ERR_WORKSPACE;
         if (!is_device_ptr(codes)) return FGX_ERR_NOT_DEVICE_PTR;
     }
-    if (use_chain2d && ndim == 2) {
+    // the 2D chain kernel and the 3D plane-tile kernel serve the public
+    // calls; the allocation-free entry keeps to the tiled engine
+    if (fast_kernels && ndim == 2) {
         if (!workspace || ws_bytes < pl.chain_bytes) return FGX_ERR_WORKSPACE;
         if (!is_device_ptr(workspace)) return FGX_ERR_NOT_DEVICE_PTR;
         return run_chain2d(image, mask, dist, codes, B, C, H, W, v, lambda, iterations,
                            workspace, ws_bytes, opt, pl.sms, stream);
     }
-    if (ndim == 3 && !codes && pl.vol3d_bytes && workspace && ws_bytes >= pl.vol3d_bytes &&
-        vol3d_supports(pl.args, opt, pl.sms)) {
+    if (fast_kernels && ndim == 3 && !codes && pl.vol3d_bytes && workspace &&
+        ws_bytes >= pl.vol3d_bytes && vol3d_supports(pl.args, opt, pl.sms)) {
         if (!is_device_ptr(workspace)) return FGX_ERR_NOT_DEVICE_PTR;
         SweepArgs f = pl.args;
         f.timeout_ns = pl.args.timeout_ns;
@@ -324,7 +326,7 @@ int fgx_geodesic3d(const float* image, const float* mask, float* dist, int64_t B
                    float lambda, int iterations, void* workspace, size_t workspace_bytes,
                    const fgx_options* opt, void* stream) {
     return run_forward(3, image, mask, dist, B, C, D, H, W, spacing, v, lambda, iterations,
-                       nullptr, 0, workspace, workspace_bytes, opt, stream);
+                       nullptr, 0, workspace, workspace_bytes, opt, stream, true);
 }
 
 int fgx_workspace_status(const void* workspace, void* stream) {
