@@ -47,13 +47,16 @@ def _peaks():
         return 6800.0, "fallback"
 
 
+# Sources that define the headline kernel (chain2d_kernel and its helpers).
+KERNEL_SOURCES = ("chain2d.cu", "device_sync.cuh")
+
+
 def _kernel_hash():
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2208_00001_gb300", "csrc")
-    for fn in sorted(os.listdir(csrc)):
-        if fn.endswith((".cu", ".h")):
-            with open(os.path.join(csrc, fn), "rb") as fh:
-                h.update(fh.read())
+    for fn in KERNEL_SOURCES:
+        with open(os.path.join(csrc, fn), "rb") as fh:
+            h.update(fh.read())
     return h.hexdigest()[:16]
 
 
