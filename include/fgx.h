@@ -207,9 +207,11 @@ int fgx_geodesic3d_fwd_train(const float* image, const float* mask, float* dist,
                              void* saved, size_t saved_bytes, void* workspace,
                              size_t workspace_bytes, const fgx_options* opt, void* stream);
 
-/* Scratch bytes for the backward (adjoint G buffer and status). */
+/* Scratch bytes for the backward of `iterations` iterations: status, the
+ * adjoint buffers, the codes in the line layout of each pass application and
+ * (2D) the adjoint of every pass application for the image gradient. */
 int fgx_backward_workspace_size(int ndim, int64_t B, int64_t C, int64_t D, int64_t H, int64_t W,
-                                const fgx_options* opt, size_t* bytes);
+                                int iterations, const fgx_options* opt, size_t* bytes);
 
 /* Reverse sweep through the recorded codes: pass applications in reverse,
  * lines in reverse sweep order; each element with a parent pushes its

@@ -93,7 +93,7 @@ _SIGS = {
                                   _sz, _vp, _sz, _vp, _vp], _i32),
     "fgx_geodesic3d_fwd_train": ([_vp, _vp, _vp, _i64, _i64, _i64, _i64, _i64, _vp, _f32, _f32,
                                   _i32, _vp, _sz, _vp, _sz, _vp, _vp], _i32),
-    "fgx_backward_workspace_size": ([_i32, _i64, _i64, _i64, _i64, _i64, _vp,
+    "fgx_backward_workspace_size": ([_i32, _i64, _i64, _i64, _i64, _i64, _i32, _vp,
                                      ctypes.POINTER(_sz)], _i32),
     "fgx_geodesic2d_bwd": ([_vp, _vp, _vp, _sz, _vp, _vp, _i64, _i64, _i64, _i64, _f32, _f32,
                             _i32, _vp, _sz, _vp, _vp], _i32),
@@ -283,9 +283,9 @@ def workspace_timeline(ws):
     return [int(x) for x in hdr.tolist()]
 
 
-def backward_workspace_size(ndim, B, C, D, H, W, options=None):
+def backward_workspace_size(ndim, B, C, D, H, W, iterations, options=None):
     n = ctypes.c_size_t(0)
-    _check(lib().fgx_backward_workspace_size(ndim, B, C, D, H, W, _opt(options),
+    _check(lib().fgx_backward_workspace_size(ndim, B, C, D, H, W, int(iterations), _opt(options),
                                              ctypes.byref(n)), "backward workspace size")
     return n.value
 
@@ -303,7 +303,7 @@ def backward(grad_dist, image, saved, v, lam, iterations, spacing=None, need_ima
         gm = torch.empty_like(grad_dist) if need_mask else None
         if gi is None and gm is None:
             return None, None
-        ws = _workspace(backward_workspace_size(ndim, B, C, D, H, W, options), dev)
+        ws = _workspace(backward_workspace_size(ndim, B, C, D, H, W, iterations, options), dev)
         if ndim == 2:
             st = lib().fgx_geodesic2d_bwd(_ptr(grad_dist), _ptr(image), _ptr(saved),
                                           saved.numel(), _ptr(gi), _ptr(gm), B, C, H, W,

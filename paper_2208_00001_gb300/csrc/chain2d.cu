@@ -34,6 +34,7 @@
 #include <cmath>
 #include <cstring>
 
+#include "chain_common.cuh"
 #include "device_sync.cuh"
 #include "fgx_internal.h"
 
@@ -43,7 +44,6 @@ namespace {
 
 constexpr int kRegion = 128;           // columns per tile region (4 per lane)
 constexpr int kBlockThreads = 96;      // chain, producer and flusher warps
-constexpr int kMaxRing = 48;           // words per exchanged strip
 #define kInf __int_as_float(0x7f800000)
 
 struct Chain2DArgs {
@@ -71,11 +71,7 @@ struct Chain2DArgs {
 };
 
 using namespace dev;
-
-__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
-    const unsigned int sa = (unsigned int)__cvta_generic_to_shared(smem);
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sa), "l"(gmem) : "memory");
-}
+using namespace chain;
 // Cost of the undirected edge between a and b (same channel stride n), in the
 // fixed arithmetic order: di2 = sum_ch (I(a)-I(b))^2, c = sqrt(t + lambda*di2).
 __device__ __forceinline__ float edge_cost(const float* ia, const float* ib, int C, int64_t n,
@@ -117,83 +113,9 @@ struct TileSmem {
 __device__ __align__(16) unsigned int g_inf_row[4] = {0x7f800000u, 0x7f800000u, 0x7f800000u,
                                                       0x7f800000u};
 
-__device__ __forceinline__ unsigned int saddr(const void* p) {
-    return (unsigned int)__cvta_generic_to_shared(p);
-}
-__device__ __forceinline__ void mbar_init(unsigned long long* b, unsigned int count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(saddr(b)), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_arrive(unsigned long long* b) {
-    asm volatile("mbarrier.arrive.release.cta.shared::cta.b64 _, [%0];" ::"r"(saddr(b)) : "memory");
-}
-// One arrival on *b once every cp.async this thread issued so far has landed.
-__device__ __forceinline__ void cp_async_arrive_noinc(unsigned long long* b) {
-    asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(saddr(b)) : "memory");
-}
-__device__ __forceinline__ void cp_async_wait_all() {
-    asm volatile("cp.async.wait_all;" ::: "memory");
-}
-__device__ __forceinline__ bool mbar_test(unsigned long long* b, unsigned int parity) {
-    unsigned int ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.acquire.cta.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(ok)
-        : "r"(saddr(b)), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-// Non-blocking test of the same phase.
-__device__ __forceinline__ bool mbar_peek(unsigned long long* b, unsigned int parity) {
-    unsigned int ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.test_wait.parity.acquire.cta.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(ok)
-        : "r"(saddr(b)), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-// Waits (bounded) for the completion of the phase of parity `parity` of *b;
-// false on timeout or an earlier failure recorded in the status word.
-__device__ __noinline__ bool mbar_wait_slow(unsigned long long* b, unsigned int parity,
-                                            int* status, long long timeout_ns) {
-    const long long t0 = gtimer();
-    for (;;) {
-        if (mbar_test(b, parity)) return true;
-        if (status_of(status) != 0) return false;
-        if (gtimer() - t0 > timeout_ns) {
-            record_timeout(status);
-            return false;
-        }
-    }
-}
 __device__ __forceinline__ bool mbar_wait(unsigned long long* b, unsigned int parity,
                                           const Chain2DArgs& a) {
-    if (mbar_test(b, parity)) return true;
-    return mbar_wait_slow(b, parity, a.status, a.timeout_ns);
-}
-// Position of chunk gc in a ring of n slots: the slot and the parity of the
-// slot's phase that the chunk fills.
-struct RingPos {
-    int slot;
-    unsigned int par;
-    __device__ RingPos(unsigned int gc, int n) : slot((int)(gc % (unsigned)n)), par((gc / (unsigned)n) & 1u) {}
-    __device__ RingPos(int s, unsigned int p) : slot(s), par(p) {}
-    __device__ __forceinline__ RingPos next(int n) const {
-        return slot + 1 == n ? RingPos(0, par ^ 1u) : RingPos(slot + 1, par);
-    }
-};
-// Chunk gc of a ring of n slots: slot, parity of its "full" phase, and parity
-// of the "empty" phase that frees the slot (the release of chunk gc - n).
-__device__ __forceinline__ int slot_of(unsigned int gc, int n) { return (int)(gc % (unsigned)n); }
-__device__ __forceinline__ unsigned int full_parity(unsigned int gc, int n) {
-    return (gc / (unsigned)n) & 1u;
-}
-__device__ __forceinline__ unsigned int empty_parity(unsigned int gc, int n) {
-    return ((gc / (unsigned)n) & 1u) ^ 1u;
+    return chain::mbar_wait(b, parity, a.status, a.timeout_ns);
 }
 
 // Geometry of one tile of one pass, identical in the three warps.
@@ -450,96 +372,13 @@ __device__ __forceinline__ void chain_step(float (&dp)[4], const LineIn& c, cons
     if (codes) *reinterpret_cast<unsigned int*>(outc) = packed;
 }
 
-// Ring refresh of a multi-tile pass before step s (dp holds line s-1):
-// publish the owned columns the neighbours' rings cover, then take the ring
-// columns from the neighbours (bounded wait on the tags).
+// Ring refresh of a multi-tile pass before step s (dp holds line s-1).
 __device__ __forceinline__ bool exchange(const Chain2DArgs& a, const TileGeo& g, int b, int tile,
                                          unsigned int tg, int par, float (&dp)[4],
                                          const bool (&valid)[4]) {
-    const int lane = threadIdx.x & 31;
-    const int c0 = g.r0 + 4 * lane;
-    const int q0 = g.q0, K = g.K, T = g.T;
-    unsigned long long* mine =
-        a.xbuf + ((int64_t)b * a.max_tiles + tile) * (4 * kMaxRing) + par * (2 * kMaxRing);
-    const int rq = q0 + T - K;
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        const int c = c0 + i;
-        const unsigned long long w =
-            ((unsigned long long)tg << 32) | (unsigned int)__float_as_uint(dp[i]);
-        if (c >= q0 && c < q0 + K) st_relaxed_u64(mine + (c - q0), w);
-        if (c >= rq && c < q0 + T) st_relaxed_u64(mine + kMaxRing + (c - rq), w);
-    }
-    // ring lanes [q0-K, q0) and [q0+T, q0+T+K); lanes beyond the right ring
-    // hold columns outside the cone and are never refreshed
-    const bool left_ring = c0 < q0 && tile > 0;
-    const bool right_ring = c0 >= q0 + T && c0 < q0 + T + K && tile + 1 < g.ntiles;
-    const unsigned long long* nb = nullptr;
-    int base = 0;
-    if (left_ring) {
-        nb = a.xbuf + ((int64_t)b * a.max_tiles + tile - 1) * (4 * kMaxRing) +
-             par * (2 * kMaxRing) + kMaxRing;
-        base = c0 - (q0 - K);
-    } else if (right_ring) {
-        nb = a.xbuf + ((int64_t)b * a.max_tiles + tile + 1) * (4 * kMaxRing) +
-             par * (2 * kMaxRing);
-        base = c0 - (q0 + T);
-    }
-    // Two polls stay in flight, the second issued ~100 ns after the first,
-    // so one of them tends to reach the cache just after the neighbour's
-    // store instead of a full round trip later.
-    float got[4] = {dp[0], dp[1], dp[2], dp[3]};
-    bool done = (nb == nullptr);
-    unsigned long long wa[4], wb[4];
-    auto issue = [&](unsigned long long (&w)[4]) {
-#pragma unroll
-        for (int i = 0; i < 4; ++i) w[i] = ld_relaxed_u64(nb + base + i);
-    };
-    auto take = [&](const unsigned long long (&w)[4]) {
-        bool all = true;
-#pragma unroll
-        for (int i = 0; i < 4; ++i) all = all && (unsigned int)(w[i] >> 32) == tg;
-        if (all) {
-#pragma unroll
-            for (int i = 0; i < 4; ++i) got[i] = __uint_as_float((unsigned int)w[i]);
-        }
-        return all;
-    };
-    if (!done) issue(wa);
-    __nanosleep(50);
-    if (!done) issue(wb);
-    long long t0 = 0;
-    for (unsigned int it = 0;; ++it) {
-        if (!done) {
-            done = take(wa);
-            if (!done) issue(wa);
-        }
-        if (__all_sync(0xffffffffu, done)) break;
-        if (!done) {
-            done = take(wb);
-            if (!done) issue(wb);
-        }
-        if (__all_sync(0xffffffffu, done)) break;
-        // the status word and the clock are read every 8th round only
-        if ((it & 7u) == 7u) {
-            int fail = 0;
-            if (lane == 0) {
-                const long long now = gtimer();
-                if (t0 == 0) t0 = now;
-                if (status_of(a.status) != 0) fail = 1;
-                else if (now - t0 > a.timeout_ns) {
-                    record_timeout(a.status);
-                    fail = 1;
-                }
-            }
-            if (__shfl_sync(0xffffffffu, fail, 0)) return false;
-        }
-    }
-    if (nb) {
-#pragma unroll
-        for (int i = 0; i < 4; ++i) dp[i] = valid[i] ? got[i] : kInf;
-    }
-    return true;
+    const RingLink x{a.xbuf + (size_t)b * a.max_tiles * (4 * kMaxRing), a.status, a.timeout_ns};
+    return ring_exchange(x, tile, g.ntiles, g.q0, g.K, g.T, g.r0 + 4 * (int)(threadIdx.x & 31),
+                         tg, par, dp, valid, kInf);
 }
 
 // Chain warp.  Line j of chunk c is step s = kCh*c + j; the first step (the

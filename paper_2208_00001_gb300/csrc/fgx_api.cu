@@ -456,6 +456,16 @@ int run_backward(int ndim, const float* grad_dist, const float* image, const voi
         if (!saved || saved_bytes < need_codes) return FGX_ERR_WORKSPACE;
         if (!is_device_ptr(saved)) return FGX_ERR_NOT_DEVICE_PTR;
     }
+    if (ndim == 2 && iterations > 0 && workspace &&
+        ws_bytes >= adj2d_workspace_bytes(B, H, W, iterations, opt)) {
+        if (!is_device_ptr(workspace)) return FGX_ERR_NOT_DEVICE_PTR;
+        DeviceInfo dev;
+        st = current_device(&dev);
+        if (st != FGX_OK) return st;
+        st = run_adj2d(grad_dist, image, (const uint8_t*)saved, grad_image, grad_mask, B, C, H,
+                       W, v, lambda, iterations, workspace, ws_bytes, opt, dev.sms, stream);
+        if (st != FGX_ERR_UNSUPPORTED) return st;
+    }
     if (!workspace || ws_bytes < bp.ws_bytes) return FGX_ERR_WORKSPACE;
     if (!is_device_ptr(workspace)) return FGX_ERR_NOT_DEVICE_PTR;
     AdjointArgs& a = bp.args;
@@ -482,13 +492,16 @@ int run_backward(int ndim, const float* grad_dist, const float* image, const voi
 extern "C" {
 
 int fgx_backward_workspace_size(int ndim, int64_t B, int64_t C, int64_t D, int64_t H, int64_t W,
-                                const fgx_options* opt, size_t* bytes) {
+                                int iterations, const fgx_options* opt, size_t* bytes) {
     if (!bytes) return FGX_ERR_ARG;
+    if (iterations < 0) return FGX_ERR_ARG;
     const float unit[3] = {1.f, 1.f, 1.f};
     BwdPlan bp;
     int st = plan_backward(ndim, B, C, D, H, W, unit, 0.5f, 1, opt, &bp);
     if (st != FGX_OK) return st;
     *bytes = bp.ws_bytes;
+    if (ndim == 2 && iterations > 0)
+        *bytes = std::max(*bytes, adj2d_workspace_bytes(B, H, W, iterations, opt));
     return FGX_OK;
 }
 

@@ -142,6 +142,14 @@ bool vol3d_supports(const SweepArgs& f, const fgx_options* opt, int sms);
 int run_vol3d(const SweepArgs& f, const float* image, const float* mask, float* dist, float v,
               void* workspace, size_t ws_bytes, const fgx_options* opt, int sms, void* stream);
 
+// 2D reverse sweep on warp chains (adj2d.cu).
+size_t adj2d_workspace_bytes(int64_t B, int64_t H, int64_t W, int iterations,
+                             const fgx_options* opt);
+int run_adj2d(const float* grad_dist, const float* image, const uint8_t* codes,
+              float* grad_image, float* grad_mask, int64_t B, int64_t C, int64_t H, int64_t W,
+              float v, float lambda, int iterations, void* workspace, size_t ws_bytes,
+              const fgx_options* opt, int sms, void* stream);
+
 int run_chain2d(const float* image, const float* mask, float* dist, uint8_t* codes, int64_t B,
                 int64_t C, int64_t H, int64_t W, float v, float lambda, int iterations,
                 void* workspace, size_t ws_bytes, const fgx_options* opt, int sms, void* stream);

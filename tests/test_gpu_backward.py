@@ -85,6 +85,27 @@ def test_backward_2d_many_tiles_and_channels(fgx):
         _bits_equal(gm, wm, f"grad_mask {opts}")
 
 
+@pytest.mark.parametrize("C,lam", [(3, 0.6), (5, 0.3), (1, 0.0)])
+def test_backward_2d_multi_tile_bit_exact(fgx, C, lam):
+    """Reverse sweep over rows and columns of several line tiles (default
+    geometry, ring refreshes), three or five channels, constant costs; also
+    the call that asks for dL/dM only."""
+    rng = np.random.default_rng(40 + C)
+    img = rng.uniform(0, 1, (2, C, 140, 290)).astype(np.float32)
+    m = rng.uniform(0, 1, (2, 1, 140, 290)).astype(np.float32)
+    m[0, 0, 5:9, 200:204] = 0
+    m[1, 0, 120, 7] = 0
+    case = workloads.Case("bwd2d", img, m, 7.0, lam, 2)
+    w = rng.uniform(-1, 1, m.shape).astype(np.float32)
+    d, codes, gi, gm = _run(fgx, case, w)
+    wi, wm = _oracle(case, w, codes)
+    _bits_equal(gi, wi, "grad_image")
+    _bits_equal(gm, wm, "grad_mask")
+    _, _, gi2, gm2 = _run(fgx, case, w, need_image=False)
+    assert gi2 is None
+    _bits_equal(gm2, wm, "grad_mask alone")
+
+
 def test_backward_3d_bit_exact(fgx):
     case = workloads.diff3d(shape=(14, 19, 23), v=10.0)
     w = case.extra["w"]
