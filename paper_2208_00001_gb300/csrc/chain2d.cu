@@ -455,14 +455,31 @@ __device__ bool chain_tile(const Chain2DArgs& a, const TileGeo& g, int t_app, in
 // (h, w) - (h+1, w+k-1), Eh[k][w][h] = cost of the edge (h, w) - (h+k-1, w+1)
 // (written through a shared-memory transpose so both tables are stored along
 // their contiguous dimension); padding columns and missing edges are +inf.
+// CC > 0: the CC channels of the tile and a one-pixel halo are staged in
+// shared memory once; CC == 0: any channel count, read from global memory.
 constexpr int kInitTile = 32;
+constexpr int kHalo = kInitTile + 2;
+template <int CC>
 __global__ void __launch_bounds__(256) chain2d_init_kernel(const Chain2DArgs a) {
     __shared__ float eh[3][kInitTile][kInitTile + 1];
+    __shared__ float tile[CC > 0 ? CC : 1][kHalo][kHalo + 1];
     const int64_t N = (int64_t)a.H * a.W;
     const int b = blockIdx.z;
     const int w0 = blockIdx.x * kInitTile, h0 = blockIdx.y * kInitTile;
     const int tx = threadIdx.x, ty = threadIdx.y;
     const float* img = a.image + (int64_t)b * a.C * N;
+    if (CC > 0 && a.table) {
+        // rows h0-1 .. h0+32, columns w0-1 .. w0+32 (0 outside the image)
+        for (int idx = ty * 32 + tx; idx < kHalo * kHalo; idx += 256) {
+            const int r = idx / kHalo, c = idx - r * kHalo;
+            const int h = h0 - 1 + r, w = w0 - 1 + c;
+            const bool in = h >= 0 && h < a.H && w >= 0 && w < a.W;
+#pragma unroll
+            for (int ch = 0; ch < (CC > 0 ? CC : 1); ++ch)
+                tile[ch][r][c] = in ? img[ch * N + (int64_t)h * a.W + w] : 0.0f;
+        }
+        __syncthreads();
+    }
     const int w = w0 + tx;
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
@@ -472,15 +489,30 @@ __global__ void __launch_bounds__(256) chain2d_init_kernel(const Chain2DArgs a) 
             a.Dw[row * a.Wp + w] = w < a.W ? __fmul_rn(a.v, a.mask[row * a.W + w]) : kInf;
         }
         if (!a.table) continue;
-        const float* self = img + (int64_t)h * a.W + w;
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
             float cv = kInf, ch = kInf;
             const int wn = w + k - 1, hn = h + k - 1;
-            if (h < a.H && w < a.W) {
-                if (h + 1 < a.H && wn >= 0 && wn < a.W)
+            const bool has_v = h < a.H && w < a.W && h + 1 < a.H && wn >= 0 && wn < a.W;
+            const bool has_h = h < a.H && w < a.W && w + 1 < a.W && hn >= 0 && hn < a.H;
+            if (CC > 0) {
+                // fixed arithmetic order: di2 = sum_ch (I(a)-I(b))^2, c = sqrt(t + lambda*di2)
+                float dv = 0.0f, dh = 0.0f;
+#pragma unroll
+                for (int c = 0; c < (CC > 0 ? CC : 1); ++c) {
+                    const float self = tile[c][hl + 1][tx + 1];
+                    const float x = __fsub_rn(tile[c][hl + 2][tx + k], self);
+                    const float y = __fsub_rn(tile[c][hl + k][tx + 2], self);
+                    dv = __fadd_rn(dv, __fmul_rn(x, x));
+                    dh = __fadd_rn(dh, __fmul_rn(y, y));
+                }
+                if (has_v) cv = __fsqrt_rn(__fadd_rn(a.tv[k], __fmul_rn(a.lambda, dv)));
+                if (has_h) ch = __fsqrt_rn(__fadd_rn(a.th[k], __fmul_rn(a.lambda, dh)));
+            } else {
+                const float* self = img + (int64_t)h * a.W + w;
+                if (has_v)
                     cv = edge_cost(img + (int64_t)(h + 1) * a.W + wn, self, a.C, N, a.tv[k], a.lambda);
-                if (w + 1 < a.W && hn >= 0 && hn < a.H)
+                if (has_h)
                     ch = edge_cost(img + (int64_t)hn * a.W + w + 1, self, a.C, N, a.th[k], a.lambda);
             }
             if (h < a.H && w < a.Wp) a.Ev[(((int64_t)b * 3 + k) * a.H + h) * a.Wp + w] = cv;
@@ -693,7 +725,11 @@ int run_chain2d(const float* image, const float* mask, float* dist, uint8_t* cod
     if (iterations > 0) {
         const dim3 ig((unsigned)((a.Wp + kInitTile - 1) / kInitTile),
                       (unsigned)((a.Hp + kInitTile - 1) / kInitTile), (unsigned)B);
-        chain2d_init_kernel<<<ig, dim3(32, 8), 0, s>>>(a);
+        if (C == 1) chain2d_init_kernel<1><<<ig, dim3(32, 8), 0, s>>>(a);
+        else if (C == 2) chain2d_init_kernel<2><<<ig, dim3(32, 8), 0, s>>>(a);
+        else if (C == 3) chain2d_init_kernel<3><<<ig, dim3(32, 8), 0, s>>>(a);
+        else if (C == 4) chain2d_init_kernel<4><<<ig, dim3(32, 8), 0, s>>>(a);
+        else chain2d_init_kernel<0><<<ig, dim3(32, 8), 0, s>>>(a);
         if (cudaGetLastError() != cudaSuccess) return FGX_ERR_CUDA;
     }
     cudaLaunchConfig_t cfg = {};
