@@ -335,13 +335,21 @@ __device__ __forceinline__ void load_line(const float (*p)[kRow], int lane, Line
 // lanes.  Columns outside the array stay at +inf: with cost tables their old
 // values and the costs of every edge into them are +inf already (table and
 // array padding, +inf ring rows), with constant costs they are masked.
-template <bool masked, bool codes>
-__device__ __forceinline__ void chain_step(float (&dp)[4], const LineIn& c, const bool (&valid)[4],
-                                           int lane, float* out, uint8_t* outc) {
-    float left = __shfl_up_sync(0xffffffffu, dp[3], 1);
-    float right = __shfl_down_sync(0xffffffffu, dp[0], 1);
+// The neighbouring lanes' edge columns of the previous line; issued before
+// the next line's shared-memory loads so that the shuffles, which sit on the
+// line-to-line chain, do not queue behind them.
+__device__ __forceinline__ void chain_shuffle(const float (&dp)[4], int lane, float& left,
+                                              float& right) {
+    left = __shfl_up_sync(0xffffffffu, dp[3], 1);
+    right = __shfl_down_sync(0xffffffffu, dp[0], 1);
     if (lane == 0) left = kInf;
     if (lane == 31) right = kInf;
+}
+
+template <bool masked, bool codes>
+__device__ __forceinline__ void chain_step(float (&dp)[4], float left, float right,
+                                           const LineIn& c, const bool (&valid)[4], float* out,
+                                           uint8_t* outc) {
     float nd[4];
     unsigned int packed = 0;
 #pragma unroll
@@ -439,10 +447,12 @@ __device__ bool chain_tile(const Chain2DArgs& a, const TileGeo& g, int t_app, in
 #pragma unroll
         for (int j = 0; j < kCh; ++j) {
             const int nj = j + AHEAD;
+            float left, right;
+            chain_shuffle(dp, lane, left, right);
             load_line<fwd, table>(nj < kCh ? cur[nj] : nxt[nj - kCh], lane, buf[nj % NB], k0, k1,
                                   k2);
-            chain_step<!table, codes>(dp, buf[j % NB], valid, lane, &sm.out[oslot][j][4 * lane],
-                                      &sm.outc[oslot][j][4 * lane]);
+            chain_step<!table, codes>(dp, left, right, buf[j % NB], valid,
+                                      &sm.out[oslot][j][4 * lane], &sm.outc[oslot][j][4 * lane]);
         }
         __syncwarp();
         if (lane == 0) mbar_arrive(&sm.done[slot]);
