@@ -79,7 +79,7 @@ struct Adj2DArgs {
 
 struct AdjSmem {
     unsigned long long in_full[kNciA], done[kNciA], out_empty[kNoA];
-    unsigned long long pad_[16 - 2 * kNciA - kNoA];
+    unsigned long long pad_[2 - (2 * kNciA + kNoA) % 2];  // keeps the rings 16-byte aligned
     float g[kNciA][kChA][kRegionA];      // incoming adjoint per line
     unsigned int c[kNciA][kChA][32];     // code bytes per line, four per lane
     float outg[kNoA][kChA][kOutLdA];     // masked adjoint per line (next application)

@@ -103,7 +103,7 @@ struct TileSmem {
     // has finished a chunk (its input slot is free, its output is ready);
     // out_empty: the flusher has written an output slot out
     unsigned long long in_full[kNci], done[kNci], out_empty[kNo];
-    unsigned long long pad_[16 - 2 * kNci - kNo];
+    unsigned long long pad_[2 - (2 * kNci + kNo) % 2];  // keeps the rings 16-byte aligned
     float in[kNci][kCh][4][kRow];   // per line: old values, edge rows E0, E1, E2
     float out[kNo][kCh][kOutLd];    // chain results per line
     uint8_t outc[kNo][kCh][kRegion];  // parent codes per line (when recorded)
