@@ -150,8 +150,8 @@ typedef struct fgx_instance {
  * instances' buffers stay valid. */
 typedef struct fgx_batched_plan {
     uint32_t size;          /* sizeof(fgx_batched_plan)                      */
-    int32_t n;              /* instances scheduled                           */
-    int32_t grid;           /* thread blocks of the persistent launch        */
+    int32_t n;              /* instances on the tiled engine (3D, and 2D with 0 iterations) */
+    int32_t grid;           /* thread blocks of that persistent launch       */
     int32_t smem_bytes;     /* dynamic shared memory per block               */
     int32_t rounds;         /* pass-application rounds                       */
     int32_t region, kmax;   /* tile buffer geometry                          */
@@ -160,6 +160,11 @@ typedef struct fgx_batched_plan {
     uint64_t desc_off, waves_off, items_off;  /* table offsets in workspace  */
     void* workspace;
     uint64_t workspace_bytes;
+    /* 2D instances with at least one iteration: the line-chain launch      */
+    int32_t n2d, grid2d, rounds2d;
+    int32_t channels2d;     /* common channel count of the 2D instances (0: mixed) */
+    int32_t max_wp2d, max_hp2d;  /* largest padded extents (table init grid) */
+    uint64_t desc2d_off, waves2d_off, items2d_off;
 } fgx_batched_plan;
 
 /* Workspace bytes for a batched launch of these instances. */

@@ -69,7 +69,11 @@ class BatchedPlanC(ctypes.Structure):
                 ("timeout_ms", ctypes.c_int32), ("clear_bytes", ctypes.c_uint64),
                 ("desc_off", ctypes.c_uint64), ("waves_off", ctypes.c_uint64),
                 ("items_off", ctypes.c_uint64), ("workspace", ctypes.c_void_p),
-                ("workspace_bytes", ctypes.c_uint64)]
+                ("workspace_bytes", ctypes.c_uint64), ("n2d", ctypes.c_int32),
+                ("grid2d", ctypes.c_int32), ("rounds2d", ctypes.c_int32),
+                ("channels2d", ctypes.c_int32), ("max_wp2d", ctypes.c_int32),
+                ("max_hp2d", ctypes.c_int32), ("desc2d_off", ctypes.c_uint64),
+                ("waves2d_off", ctypes.c_uint64), ("items2d_off", ctypes.c_uint64)]
 
 
 _i64, _i32, _f32, _vp, _sz = (ctypes.c_int64, ctypes.c_int, ctypes.c_float, ctypes.c_void_p,

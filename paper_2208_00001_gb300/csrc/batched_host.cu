@@ -1,12 +1,14 @@
 // Batched launch of instances of uneven shapes (2D and 3D mixed): host-side
-// planning of the work list and the C ABI entry points.
+// planning of the work lists and the C ABI entry points.
 //
 // Every instance runs the same raster-scan schedule as a single call (4 or 6
-// passes per iteration, FastGeodis Implementation section) on the tiled
-// engine.  Instances advance one pass application per round; a round packs
-// whole instances into waves of co-resident thread blocks (first fit), so
-// the tiles of an instance that wait on one another always run together; the
-// rounds are separated by a grid barrier inside the one persistent launch.
+// passes per iteration, FastGeodis Implementation section).  2D instances
+// run on the line-chain kernel, the others on the tiled engine: two
+// persistent launches on the caller's stream.  In each, instances advance one
+// pass application per round; a round packs whole instances into waves of
+// co-resident thread blocks (first fit), so the tiles of an instance that
+// wait on one another always run together; rounds are separated by a grid
+// barrier inside the launch.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -22,6 +24,7 @@ namespace {
 size_t al256(size_t x) { return (x + 255) & ~size_t(255); }
 
 struct Schedule {
+    // tiled engine (3D instances, and 2D instances with no iteration)
     std::vector<InstDesc> desc;
     std::vector<int> round_waves;
     std::vector<int> wave_items;
@@ -29,7 +32,49 @@ struct Schedule {
     size_t smem = 0, flags_bytes = 0;
     size_t desc_off = 0, waves_off = 0, items_off = 0, total = 0;
     long long timeout_ns = 0;
+    // line-chain kernel (2D instances)
+    std::vector<int> c_index;                 // instance index of each chain instance
+    std::vector<int> c_tiles_v, c_tiles_h;
+    std::vector<size_t> c_xoff, c_soff;       // exchange words / buffers, relative
+    std::vector<int> c_round_waves, c_wave_items;
+    int c_grid = 0, c_rounds = 0, c_channels = 0, c_max_wp = 0, c_max_hp = 0;
+    size_t c_smem = 0, c_xbuf_bytes = 0, c_sec_bytes = 0;
+    size_t c_xbuf_off = 0, c_desc_off = 0, c_waves_off = 0, c_items_off = 0, c_sec_off = 0;
 };
+
+// First-fit packing of whole instances into waves of `grid` blocks, one
+// round per pass application; tiles(i, r) is instance i's tile count in
+// round r (0 once the instance is done).
+template <class Tiles>
+void pack_rounds(int n, int rounds, int grid, Tiles tiles, std::vector<int>* round_waves,
+                 std::vector<int>* wave_items) {
+    round_waves->assign(1, 0);
+    wave_items->clear();
+    for (int r = 0; r < rounds; ++r) {
+        std::vector<int> used;                                   // blocks used per wave
+        std::vector<std::vector<std::pair<int, int>>> members;  // (instance, first block)
+        for (int i = 0; i < n; ++i) {
+            const int nt = tiles(i, r);
+            if (nt == 0) continue;
+            size_t w = 0;
+            while (w < used.size() && used[w] + nt > grid) ++w;
+            if (w == used.size()) {
+                used.push_back(0);
+                members.emplace_back();
+            }
+            members[w].push_back({i, used[w]});
+            used[w] += nt;
+        }
+        for (size_t w = 0; w < used.size(); ++w) {
+            const size_t base = wave_items->size();
+            wave_items->resize(base + grid, -1);
+            for (auto& m : members[w])
+                for (int t = 0; t < tiles(m.first, r); ++t)
+                    (*wave_items)[base + m.second + t] = (m.first << 16) | t;
+        }
+        round_waves->push_back(round_waves->back() + (int)used.size());
+    }
+}
 
 int check_instance(const fgx_instance& it) {
     if (it.ndim != 2 && it.ndim != 3) return FGX_ERR_ARG;
@@ -61,6 +106,36 @@ int build_schedule(const fgx_instance* items, int n, const fgx_options* opt, boo
         if (st != FGX_OK) return st;
         const int64_t N = it.D * it.H * it.W;
         if (N == 0) continue;
+        if (it.ndim == 2 && it.iterations > 0) {
+            // line-chain kernel; pointers are checked below
+            if (check_ptrs) {
+                if (!it.image || !it.mask || !it.dist) return FGX_ERR_ARG;
+                if (!device_pointer(it.image) || !device_pointer(it.mask) ||
+                    !device_pointer(it.dist))
+                    return FGX_ERR_NOT_DEVICE_PTR;
+                const char* d = (const char*)it.dist;
+                const char* im = (const char*)it.image;
+                if (d < im + N * it.channels * 4 && im < d + N * 4) return FGX_ERR_ARG;
+            }
+            int tv = 0, th = 0;
+            size_t xb = 0;
+            const size_t sb = chain2d_instance_desc(nullptr, it, opt, nullptr, nullptr, nullptr,
+                                                    &xb, &tv, &th);
+            if (std::max(tv, th) > 65535) return FGX_ERR_UNSUPPORTED;
+            S->c_index.push_back(i);
+            S->c_tiles_v.push_back(tv);
+            S->c_tiles_h.push_back(th);
+            S->c_xoff.push_back(S->c_xbuf_bytes);
+            S->c_soff.push_back(S->c_sec_bytes);
+            S->c_xbuf_bytes += xb;
+            S->c_sec_bytes += sb;
+            S->c_rounds = std::max(S->c_rounds, it.iterations * 4);
+            S->c_max_wp = std::max<int>(S->c_max_wp, (int)((it.W + 3) & ~int64_t(3)));
+            S->c_max_hp = std::max<int>(S->c_max_hp, (int)((it.H + 3) & ~int64_t(3)));
+            S->c_channels = S->c_index.size() == 1 ? (int)it.channels
+                            : (S->c_channels == it.channels ? S->c_channels : 0);
+            continue;
+        }
         if (check_ptrs) {
             if (!it.image || !it.mask || !it.dist) return FGX_ERR_ARG;
             if (!device_pointer(it.image) || !device_pointer(it.mask) ||
@@ -117,46 +192,54 @@ int build_schedule(const fgx_instance* items, int n, const fgx_options* opt, boo
     }
     if (S->timeout_ns == 0)
         S->timeout_ns = (long long)((opt && opt->timeout_ms) ? opt->timeout_ms : 2000) * 1000000LL;
-    // rounds and waves
+    // rounds and waves of the engine
     int rounds = 0;
     for (const InstDesc& d : S->desc) rounds = std::max(rounds, d.napps);
     S->rounds = rounds;
-    S->round_waves.assign(1, 0);
-    S->wave_items.clear();
-    for (int r = 0; r < rounds; ++r) {
-        std::vector<int> used;  // blocks used per wave of this round
-        std::vector<std::vector<std::pair<int, int>>> members;  // (instance, first block)
-        for (int i = 0; i < (int)S->desc.size(); ++i) {
-            const InstDesc& d = S->desc[i];
-            if (r >= d.napps) continue;
-            const PassGeom& g = d.pass[r % d.npass];
-            const int tiles = g.ntp * g.ntq;
-            size_t w = 0;
-            while (w < used.size() && used[w] + tiles > S->grid) ++w;
-            if (w == used.size()) {
-                used.push_back(0);
-                members.emplace_back();
-            }
-            members[w].push_back({i, used[w]});
-            used[w] += tiles;
+    pack_rounds((int)S->desc.size(), rounds, std::max(S->grid, 1),
+                [&](int i, int r) {
+                    const InstDesc& d = S->desc[i];
+                    if (r >= d.napps) return 0;
+                    const PassGeom& g = d.pass[r % d.npass];
+                    return g.ntp * g.ntq;
+                },
+                &S->round_waves, &S->wave_items);
+    // the line-chain launch for the 2D instances
+    if (S->c_channels > 4) S->c_channels = 0;
+    if (!S->c_index.empty()) {
+        if (sms == 0) {
+            const float unit[3] = {1.f, 1.f, 1.f};
+            SweepArgs tmp;
+            const int st = plan_instance(2, 1, 1, 8, 8, unit, 0.5f, opt, &tmp, &sms);
+            if (st != FGX_OK) return st;
         }
-        for (size_t w = 0; w < used.size(); ++w) {
-            const size_t base = S->wave_items.size();
-            S->wave_items.resize(base + S->grid, -1);
-            for (auto& m : members[w]) {
-                const InstDesc& d = S->desc[m.first];
-                const PassGeom& g = d.pass[r % d.npass];
-                for (int t = 0; t < g.ntp * g.ntq; ++t)
-                    S->wave_items[base + m.second + t] = (m.first << 16) | t;
-            }
-        }
-        S->round_waves.push_back(S->round_waves.back() + (int)used.size());
+        const int st = chain2d_batched_geometry(sms, opt, &S->c_grid, &S->c_smem);
+        if (st != FGX_OK) return st;
+        for (size_t k = 0; k < S->c_index.size(); ++k)
+            if (std::max(S->c_tiles_v[k], S->c_tiles_h[k]) > S->c_grid) return FGX_ERR_UNSUPPORTED;
+        const int nc = (int)S->c_index.size();
+        pack_rounds(nc, S->c_rounds, S->c_grid,
+                    [&](int k, int r) {
+                        if (r >= items[S->c_index[k]].iterations * 4) return 0;
+                        return (r & 3) < 2 ? S->c_tiles_v[k] : S->c_tiles_h[k];
+                    },
+                    &S->c_round_waves, &S->c_wave_items);
+        if (S->timeout_ns == 0)
+            S->timeout_ns = (long long)((opt && opt->timeout_ms) ? opt->timeout_ms : 2000) *
+                            1000000LL;
     }
     S->flags_bytes = al256((size_t)std::max(flags_total, 1) * 8);
-    S->desc_off = kHeaderBytes + S->flags_bytes;
+    // layout: header | engine tags | chain exchange words (the cleared prefix)
+    // | engine tables | chain tables | chain buffers
+    S->c_xbuf_off = kHeaderBytes + S->flags_bytes;
+    S->desc_off = S->c_xbuf_off + al256(S->c_xbuf_bytes);
     S->waves_off = S->desc_off + al256(S->desc.size() * sizeof(InstDesc) + 1);
     S->items_off = S->waves_off + al256(S->round_waves.size() * sizeof(int));
-    S->total = S->items_off + al256(S->wave_items.size() * sizeof(int) + 1);
+    S->c_desc_off = S->items_off + al256(S->wave_items.size() * sizeof(int) + 1);
+    S->c_waves_off = S->c_desc_off + al256(S->c_index.size() * chain2d_desc_size() + 1);
+    S->c_items_off = S->c_waves_off + al256(S->c_round_waves.size() * sizeof(int) + 1);
+    S->c_sec_off = S->c_items_off + al256(S->c_wave_items.size() * sizeof(int) + 1);
+    S->total = S->c_sec_off + al256(S->c_sec_bytes);
     return FGX_OK;
 }
 
@@ -190,20 +273,28 @@ int fgx_batched_prepare(const fgx_instance* items, int n, void* workspace,
     if (!device_pointer(workspace)) return FGX_ERR_NOT_DEVICE_PTR;
     cudaStream_t s = (cudaStream_t)stream;
     char* w = (char*)workspace;
-    if (!S.desc.empty()) {
-        if (cudaMemcpyAsync(w + S.desc_off, S.desc.data(), S.desc.size() * sizeof(InstDesc),
-                            cudaMemcpyHostToDevice, s) != cudaSuccess ||
-            cudaMemcpyAsync(w + S.waves_off, S.round_waves.data(),
-                            S.round_waves.size() * sizeof(int), cudaMemcpyHostToDevice,
-                            s) != cudaSuccess ||
-            (!S.wave_items.empty() &&
-             cudaMemcpyAsync(w + S.items_off, S.wave_items.data(),
-                             S.wave_items.size() * sizeof(int), cudaMemcpyHostToDevice,
-                             s) != cudaSuccess))
-            return FGX_ERR_CUDA;
-        // the host vectors are freed on return: finish the copies first
-        if (cudaStreamSynchronize(s) != cudaSuccess) return FGX_ERR_CUDA;
+    auto put = [&](size_t off, const void* src, size_t bytes) {
+        return bytes == 0 ||
+               cudaMemcpyAsync(w + off, src, bytes, cudaMemcpyHostToDevice, s) == cudaSuccess;
+    };
+    // chain arguments carry device pointers into this workspace
+    std::vector<unsigned char> cdesc(S.c_index.size() * chain2d_desc_size());
+    for (size_t k = 0; k < S.c_index.size(); ++k) {
+        size_t xb = 0;
+        int tv = 0, th = 0;
+        chain2d_instance_desc(cdesc.data() + k * chain2d_desc_size(), items[S.c_index[k]], opt, w,
+                              w + S.c_xbuf_off + S.c_xoff[k], w + S.c_sec_off + S.c_soff[k], &xb,
+                              &tv, &th);
     }
+    if (!put(S.desc_off, S.desc.data(), S.desc.size() * sizeof(InstDesc)) ||
+        !put(S.waves_off, S.round_waves.data(), S.round_waves.size() * sizeof(int)) ||
+        !put(S.items_off, S.wave_items.data(), S.wave_items.size() * sizeof(int)) ||
+        !put(S.c_desc_off, cdesc.data(), cdesc.size()) ||
+        !put(S.c_waves_off, S.c_round_waves.data(), S.c_round_waves.size() * sizeof(int)) ||
+        !put(S.c_items_off, S.c_wave_items.data(), S.c_wave_items.size() * sizeof(int)))
+        return FGX_ERR_CUDA;
+    // the host vectors are freed on return: finish the copies first
+    if (cudaStreamSynchronize(s) != cudaSuccess) return FGX_ERR_CUDA;
     std::memset(plan, 0, sizeof(*plan));
     plan->size = sizeof(fgx_batched_plan);
     plan->n = (int)S.desc.size();
@@ -213,12 +304,21 @@ int fgx_batched_prepare(const fgx_instance* items, int n, void* workspace,
     plan->region = S.region;
     plan->kmax = S.kmax;
     plan->timeout_ms = (int)(S.timeout_ns / 1000000LL);
-    plan->clear_bytes = kHeaderBytes + S.flags_bytes;
+    plan->clear_bytes = S.desc_off;  // header, engine tags and chain exchange words
     plan->desc_off = S.desc_off;
     plan->waves_off = S.waves_off;
     plan->items_off = S.items_off;
     plan->workspace = workspace;
     plan->workspace_bytes = S.total;
+    plan->n2d = (int)S.c_index.size();
+    plan->grid2d = S.c_grid;
+    plan->rounds2d = S.c_rounds;
+    plan->channels2d = S.c_channels;
+    plan->max_wp2d = S.c_max_wp;
+    plan->max_hp2d = S.c_max_hp;
+    plan->desc2d_off = S.c_desc_off;
+    plan->waves2d_off = S.c_waves_off;
+    plan->items2d_off = S.c_items_off;
     return FGX_OK;
 }
 
@@ -227,7 +327,17 @@ int fgx_batched_run(const fgx_batched_plan* plan, void* stream) {
     cudaStream_t s = (cudaStream_t)stream;
     char* w = (char*)plan->workspace;
     if (cudaMemsetAsync(w, 0, plan->clear_bytes, s) != cudaSuccess) return FGX_ERR_CUDA;
+    const long long timeout_ns = (long long)plan->timeout_ms * 1000000LL;
+    if (plan->n2d > 0) {
+        const int st = launch_chain2d_batched(
+            w + plan->desc2d_off, plan->n2d, plan->channels2d, plan->max_wp2d, plan->max_hp2d,
+            plan->rounds2d, (const int*)(w + plan->waves2d_off),
+            (const int*)(w + plan->items2d_off), plan->grid2d, w, timeout_ns, stream);
+        if (st != FGX_OK) return st;
+    }
     if (plan->n == 0) return FGX_OK;
+    if (plan->n2d > 0 && cudaMemsetAsync(w + 64, 0, 4, s) != cudaSuccess)
+        return FGX_ERR_CUDA;  // fresh grid-barrier counter for the second launch
     BatchedArgs a;
     std::memset(&a, 0, sizeof(a));
     a.desc = (const InstDesc*)(w + plan->desc_off);
@@ -238,7 +348,7 @@ int fgx_batched_run(const fgx_batched_plan* plan, void* stream) {
     a.flags = (unsigned long long*)(w + kHeaderBytes);
     a.barrier = (unsigned int*)(w + 64);
     a.status = (int*)w;
-    a.timeout_ns = (long long)plan->timeout_ms * 1000000LL;
+    a.timeout_ns = timeout_ns;
     int per_sm = 0;
     int st = batched_max_blocks_per_sm((size_t)plan->smem_bytes, &per_sm);
     if (st != FGX_OK) return st;

@@ -470,11 +470,10 @@ __device__ bool chain_tile(const Chain2DArgs& a, const TileGeo& g, int t_app, in
 constexpr int kInitTile = 32;
 constexpr int kHalo = kInitTile + 2;
 template <int CC>
-__global__ void __launch_bounds__(256) chain2d_init_kernel(const Chain2DArgs a) {
+__device__ __forceinline__ void init_tile(const Chain2DArgs& a, int b) {
     __shared__ float eh[3][kInitTile][kInitTile + 1];
     __shared__ float tile[CC > 0 ? CC : 1][kHalo][kHalo + 1];
     const int64_t N = (int64_t)a.H * a.W;
-    const int b = blockIdx.z;
     const int w0 = blockIdx.x * kInitTile, h0 = blockIdx.y * kInitTile;
     const int tx = threadIdx.x, ty = threadIdx.y;
     const float* img = a.image + (int64_t)b * a.C * N;
@@ -544,6 +543,19 @@ __global__ void __launch_bounds__(256) chain2d_init_kernel(const Chain2DArgs a) 
                 a.Eh[(((int64_t)b * 3 + k) * a.W + ww) * a.Hp + h] = h < a.H ? eh[k][wl][tx] : kInf;
         }
     }
+}
+
+template <int CC>
+__global__ void __launch_bounds__(256) chain2d_init_kernel(const Chain2DArgs a) {
+    init_tile<CC>(a, blockIdx.z);
+}
+
+// Batched launch: instance blockIdx.z of an array of single-image arguments.
+template <int CC>
+__global__ void __launch_bounds__(256) chain2d_init_batched_kernel(const Chain2DArgs* desc) {
+    const Chain2DArgs& a = desc[blockIdx.z];
+    if ((int)blockIdx.x * kInitTile >= a.Wp || (int)blockIdx.y * kInitTile >= a.Hp) return;
+    init_tile<CC>(a, 0);
 }
 
 template <bool fwd, bool table, bool codes>
@@ -627,6 +639,52 @@ __global__ void __launch_bounds__(kBlockThreads, 1) chain2d_kernel(const Chain2D
     }
 }
 
+// Work list of a batched launch of single images of uneven shapes: round r
+// applies pass r % 4 of every instance that has r < 4 * iterations; the
+// round's (instance, tile) items are packed into waves of at most one item
+// per block, so that all tiles of an instance's pass run together.
+struct Chain2DBatch {
+    const Chain2DArgs* desc;   // [n] single-image arguments
+    int rounds;
+    const int* round_waves;    // [rounds + 1] first wave of each round
+    const int* wave_items;     // [waves][gridDim.x]: (instance << 16) | tile, or -1
+    unsigned int* barrier;
+    int* status;
+    long long timeout_ns;
+};
+
+__global__ void __launch_bounds__(kBlockThreads, 1) chain2d_batched_kernel(const Chain2DBatch bt) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    TileSmem& sm = *reinterpret_cast<TileSmem*>(smem_raw);
+    for (int i = threadIdx.x; i < kNci * kCh * 4 * kRow; i += blockDim.x)
+        (&sm.in[0][0][0][0])[i] = kInf;
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < kNci; ++i) {
+            mbar_init(&sm.in_full[i], 32);
+            mbar_init(&sm.done[i], 1);
+        }
+        for (int i = 0; i < kNo; ++i) mbar_init(&sm.out_empty[i], 1);
+    }
+    __syncthreads();
+    unsigned int epoch = 1;
+    unsigned int cb = 0;
+    bool alive = true;
+    for (int r = 0; r < bt.rounds && alive; ++r) {
+        const int pass = r & 3;
+        const bool fwd = pass == 0 || pass == 2;
+        bool ok = true;
+        for (int wv = bt.round_waves[r]; wv < bt.round_waves[r + 1] && ok; ++wv) {
+            const int item = bt.wave_items[(int64_t)wv * gridDim.x + blockIdx.x];
+            if (item < 0) continue;
+            const Chain2DArgs& a = bt.desc[item >> 16];
+            ok = run_pass_tile<false>(a, fwd, r, pass, 0, item & 0xffff, sm, cb);
+            const int L = pass < 2 ? a.H : a.W;
+            cb += (unsigned int)((L + kCh - 1) / kCh);
+        }
+        alive = grid_barrier(bt.barrier, epoch++, bt.status, bt.timeout_ns);
+    }
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------- host ----
@@ -662,57 +720,79 @@ int chain2d_geometry(int64_t H, int64_t W, const fgx_options* opt, int* K, int* 
     return FGX_OK;
 }
 
+namespace {
+
+// Fills the arguments of B images of one shape: the status word and barrier
+// counter are `hdr`'s, the exchange words start at `xb`, the other buffers
+// (Dw, Dt, Ev, Eh) are laid out from `sec` (any of them null for a size
+// query).  Returns the bytes from `sec`; *xbytes receives the exchange bytes.
+size_t fill_chain_args(Chain2DArgs* a, const float* image, const float* mask, float* dist,
+                       uint8_t* codes, int64_t B, int64_t C, int64_t H, int64_t W, float v,
+                       float lambda, int iterations, const fgx_options* opt, char* hdr, char* xb,
+                       char* sec, size_t* xbytes) {
+    std::memset(a, 0, sizeof(*a));
+    int K, T, tv, th;
+    chain2d_geometry(H, W, opt, &K, &T, &tv, &th);
+    const int max_tiles = std::max(tv, th);
+    a->image = image;
+    a->mask = mask;
+    a->dist = dist;
+    a->codes = codes;
+    a->B = (int)B;
+    a->C = (int)C;
+    a->H = (int)H;
+    a->W = (int)W;
+    a->Wp = (int)((W + 3) & ~int64_t(3));
+    a->Hp = (int)((H + 3) & ~int64_t(3));
+    a->v = v;
+    a->lambda = lambda;
+    a->iterations = iterations;
+    a->table = lambda != 0.0f;
+    const float unit[3] = {1.f, 1.f, 1.f};
+    float t9[9];
+    pass_offsets_t(2, 1, unit, lambda, t9);  // pass along H: offsets along W
+    for (int k = 0; k < 3; ++k) { a->tv[k] = t9[k]; a->cv[k] = std::sqrt(t9[k]); }
+    pass_offsets_t(2, 2, unit, lambda, t9);  // pass along W: offsets along H
+    for (int k = 0; k < 3; ++k) { a->th[k] = t9[k]; a->chh[k] = std::sqrt(t9[k]); }
+    a->K = K;
+    a->T = T;
+    a->tiles_v = tv;
+    a->tiles_h = th;
+    a->max_tiles = max_tiles;
+    a->timeout_ns = (long long)((opt && opt->timeout_ms) ? opt->timeout_ms : 2000) * 1000000LL;
+    auto al = [](size_t x) { return (x + 255) & ~size_t(255); };
+    a->status = (int*)hdr;
+    a->barrier = (unsigned int*)(hdr ? hdr + 64 : nullptr);
+    a->xbuf = (unsigned long long*)xb;
+    *xbytes = al((size_t)B * max_tiles * 4 * kMaxRing * 8);
+    size_t off = 0;
+    a->Dw = (float*)(sec ? sec + off : nullptr);
+    off += al((size_t)B * H * a->Wp * 4);
+    a->Dt = (float*)(sec ? sec + off : nullptr);
+    off += al((size_t)B * W * a->Hp * 4);
+    a->Ev = (float*)(sec ? sec + off : nullptr);
+    off += al((size_t)B * 3 * H * a->Wp * 4);
+    a->Eh = (float*)(sec ? sec + off : nullptr);
+    off += al((size_t)B * 3 * W * a->Hp * 4);
+    return off;
+}
+
+}  // namespace
+
 int run_chain2d(const float* image, const float* mask, float* dist, uint8_t* codes, int64_t B,
                 int64_t C, int64_t H, int64_t W, float v, float lambda, int iterations,
                 void* workspace, size_t ws_bytes, const fgx_options* opt, int sms, void* stream) {
     Chain2DArgs a;
-    std::memset(&a, 0, sizeof(a));
-    int K, T, tv, th;
-    chain2d_geometry(H, W, opt, &K, &T, &tv, &th);
-    const int max_tiles = std::max(tv, th);
-    const size_t need = chain2d_workspace_bytes(B, C, H, W, max_tiles);
-    if (ws_bytes < need) return FGX_ERR_WORKSPACE;
-    a.image = image;
-    a.mask = mask;
-    a.dist = dist;
-    a.codes = codes;
-    a.B = (int)B;
-    a.C = (int)C;
-    a.H = (int)H;
-    a.W = (int)W;
-    a.Wp = (int)((W + 3) & ~int64_t(3));
-    a.Hp = (int)((H + 3) & ~int64_t(3));
-    a.v = v;
-    a.lambda = lambda;
-    a.iterations = iterations;
-    a.table = lambda != 0.0f;
-    const float unit[3] = {1.f, 1.f, 1.f};
-    float t9[9];
-    pass_offsets_t(2, 1, unit, lambda, t9);  // pass along H: offsets along W
-    for (int k = 0; k < 3; ++k) { a.tv[k] = t9[k]; a.cv[k] = std::sqrt(t9[k]); }
-    pass_offsets_t(2, 2, unit, lambda, t9);  // pass along W: offsets along H
-    for (int k = 0; k < 3; ++k) { a.th[k] = t9[k]; a.chh[k] = std::sqrt(t9[k]); }
-    a.K = K;
-    a.T = T;
-    a.tiles_v = tv;
-    a.tiles_h = th;
-    a.max_tiles = max_tiles;
-    a.timeout_ns = (long long)((opt && opt->timeout_ms) ? opt->timeout_ms : 2000) * 1000000LL;
-    auto al = [](size_t x) { return (x + 255) & ~size_t(255); };
     char* p = (char*)workspace;
-    a.status = (int*)p;
-    a.barrier = (unsigned int*)(p + 64);
-    size_t off = kHeaderBytes;
-    a.xbuf = (unsigned long long*)(p + off);
-    const size_t xbytes = al((size_t)B * max_tiles * 4 * kMaxRing * 8);
-    off += xbytes;
-    a.Dw = (float*)(p + off);
-    off += al((size_t)B * H * a.Wp * 4);
-    a.Dt = (float*)(p + off);
-    off += al((size_t)B * W * a.Hp * 4);
-    a.Ev = (float*)(p + off);
-    off += al((size_t)B * 3 * H * a.Wp * 4);
-    a.Eh = (float*)(p + off);
+    size_t xbytes = 0;
+    fill_chain_args(&a, image, mask, dist, codes, B, C, H, W, v, lambda, iterations, opt, nullptr,
+                    nullptr, nullptr, &xbytes);
+    const size_t need = kHeaderBytes + xbytes +
+                        fill_chain_args(&a, image, mask, dist, codes, B, C, H, W, v, lambda,
+                                        iterations, opt, p, p + kHeaderBytes,
+                                        p + kHeaderBytes + xbytes, &xbytes);
+    if (ws_bytes < need) return FGX_ERR_WORKSPACE;
+    const int max_tiles = a.max_tiles;
 
     const size_t smem = sizeof(TileSmem);
     auto kernel = codes ? chain2d_kernel<true> : chain2d_kernel<false>;
@@ -753,6 +833,76 @@ int run_chain2d(const float* image, const float* mask, float* dist, uint8_t* cod
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     if (cudaLaunchKernelEx(&cfg, kernel, a) != cudaSuccess) return FGX_ERR_CUDA;
+    return FGX_OK;
+}
+
+// ---------------------------------------------------- batched 2D instances ----
+
+size_t chain2d_desc_size() { return sizeof(Chain2DArgs); }
+
+size_t chain2d_instance_desc(void* desc, const fgx_instance& it, const fgx_options* opt,
+                             char* hdr, char* xb, char* sec, size_t* xbytes, int* tiles_v,
+                             int* tiles_h) {
+    Chain2DArgs a;
+    const size_t n = fill_chain_args(&a, it.image, it.mask, it.dist, nullptr, 1, it.channels,
+                                     it.H, it.W, it.v, it.lambda, it.iterations, opt, hdr, xb,
+                                     sec, xbytes);
+    if (desc) std::memcpy(desc, &a, sizeof(a));
+    *tiles_v = a.tiles_v;
+    *tiles_h = a.tiles_h;
+    return n;
+}
+
+int chain2d_batched_geometry(int sms, const fgx_options* opt, int* grid, size_t* smem) {
+    *smem = sizeof(TileSmem);
+    if (cudaFuncSetAttribute(chain2d_batched_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)*smem) != cudaSuccess)
+        return FGX_ERR_CUDA;
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, chain2d_batched_kernel,
+                                                      kBlockThreads, *smem) != cudaSuccess ||
+        per_sm < 1)
+        return FGX_ERR_CUDA;
+    int64_t g = (int64_t)per_sm * sms;
+    if (opt && opt->max_blocks) g = std::min<int64_t>(g, opt->max_blocks);
+    *grid = (int)std::max<int64_t>(1, g);
+    return FGX_OK;
+}
+
+int launch_chain2d_batched(const void* desc, int n, int init_channels, int max_wp, int max_hp,
+                           int rounds, const int* round_waves, const int* wave_items, int grid,
+                           char* hdr, long long timeout_ns, void* stream) {
+    cudaStream_t s = (cudaStream_t)stream;
+    const Chain2DArgs* d = (const Chain2DArgs*)desc;
+    const dim3 ig((unsigned)((max_wp + kInitTile - 1) / kInitTile),
+                  (unsigned)((max_hp + kInitTile - 1) / kInitTile), (unsigned)n);
+    switch (init_channels) {
+        case 1: chain2d_init_batched_kernel<1><<<ig, dim3(32, 8), 0, s>>>(d); break;
+        case 2: chain2d_init_batched_kernel<2><<<ig, dim3(32, 8), 0, s>>>(d); break;
+        case 3: chain2d_init_batched_kernel<3><<<ig, dim3(32, 8), 0, s>>>(d); break;
+        case 4: chain2d_init_batched_kernel<4><<<ig, dim3(32, 8), 0, s>>>(d); break;
+        default: chain2d_init_batched_kernel<0><<<ig, dim3(32, 8), 0, s>>>(d); break;
+    }
+    if (cudaGetLastError() != cudaSuccess) return FGX_ERR_CUDA;
+    Chain2DBatch bt;
+    bt.desc = d;
+    bt.rounds = rounds;
+    bt.round_waves = round_waves;
+    bt.wave_items = wave_items;
+    bt.barrier = (unsigned int*)(hdr + 64);
+    bt.status = (int*)hdr;
+    bt.timeout_ns = timeout_ns;
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3(kBlockThreads);
+    cfg.dynamicSmemBytes = sizeof(TileSmem);
+    cfg.stream = s;
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    if (cudaLaunchKernelEx(&cfg, chain2d_batched_kernel, bt) != cudaSuccess) return FGX_ERR_CUDA;
     return FGX_OK;
 }
 

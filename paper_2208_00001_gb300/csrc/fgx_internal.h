@@ -142,6 +142,19 @@ bool vol3d_supports(const SweepArgs& f, const fgx_options* opt, int sms);
 int run_vol3d(const SweepArgs& f, const float* image, const float* mask, float* dist, float v,
               void* workspace, size_t ws_bytes, const fgx_options* opt, int sms, void* stream);
 
+// Batched 2D instances on the line-chain kernel (chain2d.cu): the size of
+// one instance's argument block, filling it (buffers: exchange words at xb,
+// Dw/Dt/Ev/Eh from sec; returns the bytes from sec), the launch geometry and
+// the launch (table init of every instance, then the rounds).
+size_t chain2d_desc_size();
+size_t chain2d_instance_desc(void* desc, const fgx_instance& it, const fgx_options* opt,
+                             char* hdr, char* xb, char* sec, size_t* xbytes, int* tiles_v,
+                             int* tiles_h);
+int chain2d_batched_geometry(int sms, const fgx_options* opt, int* grid, size_t* smem);
+int launch_chain2d_batched(const void* desc, int n, int init_channels, int max_wp, int max_hp,
+                           int rounds, const int* round_waves, const int* wave_items, int grid,
+                           char* hdr, long long timeout_ns, void* stream);
+
 // 2D reverse sweep on warp chains (adj2d.cu).
 size_t adj2d_workspace_bytes(int64_t B, int64_t H, int64_t W, int iterations,
                              const fgx_options* opt);

@@ -89,6 +89,7 @@ static_assert(sizeof(Head3) % 16 == 0, "stage must stay 16-byte aligned");
 
 __device__ __align__(16) unsigned int g_inf4[4] = {0x7f800000u, 0x7f800000u, 0x7f800000u,
                                                   0x7f800000u};
+__device__ __align__(16) unsigned int g_zero4v[4] = {0u, 0u, 0u, 0u};
 
 __device__ __forceinline__ unsigned int saddr3(const void* p) {
     return (unsigned int)__cvta_generic_to_shared(p);
@@ -156,7 +157,8 @@ __device__ __forceinline__ float* stage_plane(float* stage, int slot, int j, int
 
 // Producer warps: planes of old distances and intensities into the staging
 // ring, chunk after chunk, once the compute warps have released the slot.
-// Voxels outside the volume are staged as +inf.
+// Voxels outside the volume are staged with distance +inf and intensity 0
+// (finite costs: a square root never sees an infinite argument).
 template <int CI>
 __device__ bool producer3(const Vol3DArgs& a, const Tile3& t, Head3& h, float* stage,
                           unsigned int cb) {
@@ -190,7 +192,7 @@ __device__ bool producer3(const Vol3DArgs& a, const Tile3& t, Head3& h, float* s
 #pragma unroll
                 for (int ch = 0; ch < CI; ++ch)
                     cp_async4(dst + (ch + 1) * kPlane,
-                              in ? (const void*)(img + ch * a.N + off) : (const void*)g_inf4);
+                              in ? (const void*)(img + ch * a.N + off) : (const void*)g_zero4v);
             }
         }
         cp_arrive_noinc(&h.full[slot]);
@@ -397,7 +399,7 @@ __device__ bool compute3(const Vol3DArgs& a, const Tile3& t, int t_app, Head3& h
                     best = fminf(best, __fadd_rn(pd, c));
                 }
             }
-            d[i] = (MODE == kModeConst && !valid[i]) ? kInf3 : best;
+            d[i] = valid[i] ? best : kInf3;
             if (own[i]) dist[lo + goff[i]] = d[i];
         }
         if (s % kRing == 0 && s + 1 < t.L) {
@@ -528,10 +530,6 @@ bool plan_vol3d(const SweepArgs& f, const fgx_options* opt, int sms, Vol3DPlan* 
         vp->mode = kModeConst;
         vp->CI = 0;
     }
-    // the general cost takes one IEEE square root per candidate; at 36
-    // candidates per thread and step that is slower here than in the tiled
-    // engine, which runs those calls
-    if (vp->mode == kModeGeneral) return false;
     if (vp->CI > kMaxCI) return false;
     int max_tiles = 1;
     for (int i = 0; i < kMaxPasses; ++i) {
