@@ -165,6 +165,9 @@ typedef struct fgx_batched_plan {
     int32_t channels2d;     /* common channel count of the 2D instances (0: mixed) */
     int32_t max_wp2d, max_hp2d;  /* largest padded extents (table init grid) */
     uint64_t desc2d_off, waves2d_off, items2d_off;
+    /* 3D instances the plane-tile kernel takes: the plane-tile launch        */
+    int32_t n3d, grid3d, rounds3d, smem3d;
+    uint64_t desc3d_off, waves3d_off, items3d_off;
 } fgx_batched_plan;
 
 /* Workspace bytes for a batched launch of these instances. */

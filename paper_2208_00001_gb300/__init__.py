@@ -73,7 +73,10 @@ class BatchedPlanC(ctypes.Structure):
                 ("grid2d", ctypes.c_int32), ("rounds2d", ctypes.c_int32),
                 ("channels2d", ctypes.c_int32), ("max_wp2d", ctypes.c_int32),
                 ("max_hp2d", ctypes.c_int32), ("desc2d_off", ctypes.c_uint64),
-                ("waves2d_off", ctypes.c_uint64), ("items2d_off", ctypes.c_uint64)]
+                ("waves2d_off", ctypes.c_uint64), ("items2d_off", ctypes.c_uint64),
+                ("n3d", ctypes.c_int32), ("grid3d", ctypes.c_int32), ("rounds3d", ctypes.c_int32),
+                ("smem3d", ctypes.c_int32), ("desc3d_off", ctypes.c_uint64),
+                ("waves3d_off", ctypes.c_uint64), ("items3d_off", ctypes.c_uint64)]
 
 
 _i64, _i32, _f32, _vp, _sz = (ctypes.c_int64, ctypes.c_int, ctypes.c_float, ctypes.c_void_p,

@@ -3,8 +3,9 @@
 //
 // Every instance runs the same raster-scan schedule as a single call (4 or 6
 // passes per iteration, FastGeodis Implementation section).  2D instances
-// run on the line-chain kernel, the others on the tiled engine: two
-// persistent launches on the caller's stream.  In each, instances advance one
+// run on the line-chain kernel, 3D instances on the plane-tile kernel, the
+// rest (tile options, more channels than it stages) on the tiled engine: up
+// to three persistent launches on the caller's stream.  In each, instances advance one
 // pass application per round; a round packs whole instances into waves of
 // co-resident thread blocks (first fit), so the tiles of an instance that
 // wait on one another always run together; rounds are separated by a grid
@@ -40,6 +41,16 @@ struct Schedule {
     int c_grid = 0, c_rounds = 0, c_channels = 0, c_max_wp = 0, c_max_hp = 0;
     size_t c_smem = 0, c_xbuf_bytes = 0, c_sec_bytes = 0;
     size_t c_xbuf_off = 0, c_desc_off = 0, c_waves_off = 0, c_items_off = 0, c_sec_off = 0;
+    // plane-tile kernel (3D instances)
+    std::vector<int> v_index;
+    std::vector<std::vector<int>> v_tiles;
+    std::vector<SweepArgs> v_args;
+    std::vector<size_t> v_xoff;
+    std::vector<int> v_round_waves, v_wave_items;
+    int v_grid = 0, v_rounds = 0, v_ci = 0, v_max_tiles = 0;
+    int sms = 0;
+    size_t v_smem = 0, v_xbuf_bytes = 0;
+    size_t v_flag_off = 0, v_xbuf_off = 0, v_desc_off = 0, v_waves_off = 0, v_items_off = 0;
 };
 
 // First-fit packing of whole instances into waves of `grid` blocks, one
@@ -149,6 +160,33 @@ int build_schedule(const fgx_instance* items, int n, const fgx_options* opt, boo
         st = plan_instance(it.ndim, it.channels, it.D, it.H, it.W, it.spacing, it.lambda, opt, &a,
                            &sms);
         if (st != FGX_OK) return st;
+        if (it.ndim == 3) {
+            size_t xb = 0;
+            int ci = 0, mt = 0, tiles[kMaxPasses];
+            if (vol3d_instance_desc(nullptr, it, a, opt, sms, nullptr, nullptr, nullptr, &xb, &ci,
+                                    &mt, tiles)) {
+                if (check_ptrs) {
+                    if (!it.image || !it.mask || !it.dist) return FGX_ERR_ARG;
+                    if (!device_pointer(it.image) || !device_pointer(it.mask) ||
+                        !device_pointer(it.dist))
+                        return FGX_ERR_NOT_DEVICE_PTR;
+                    const char* d = (const char*)it.dist;
+                    const char* im = (const char*)it.image;
+                    if (d < im + N * it.channels * 4 && im < d + N * 4) return FGX_ERR_ARG;
+                }
+                a.timeout_ns = (long long)((opt && opt->timeout_ms) ? opt->timeout_ms : 2000) *
+                               1000000LL;
+                S->v_index.push_back(i);
+                S->v_tiles.emplace_back(tiles, tiles + kMaxPasses);
+                S->v_args.push_back(a);
+                S->v_xoff.push_back(S->v_xbuf_bytes);
+                S->v_xbuf_bytes += al256(xb);
+                S->v_ci = std::max(S->v_ci, ci);
+                S->v_max_tiles = std::max(S->v_max_tiles, mt);
+                S->v_rounds = std::max(S->v_rounds, it.iterations * kMaxPasses);
+                continue;
+            }
+        }
         InstDesc d;
         std::memset(&d, 0, sizeof(d));
         d.image = it.image;
@@ -204,6 +242,21 @@ int build_schedule(const fgx_instance* items, int n, const fgx_options* opt, boo
                     return g.ntp * g.ntq;
                 },
                 &S->round_waves, &S->wave_items);
+    // the plane-tile launch for the 3D instances
+    if (!S->v_index.empty()) {
+        const int st = vol3d_batched_geometry(sms, S->v_ci, opt, &S->v_grid, &S->v_smem);
+        if (st != FGX_OK) return st;
+        if (S->v_max_tiles > S->v_grid) return FGX_ERR_UNSUPPORTED;
+        pack_rounds((int)S->v_index.size(), S->v_rounds, S->v_grid,
+                    [&](int k, int r) {
+                        if (r >= items[S->v_index[k]].iterations * kMaxPasses) return 0;
+                        return S->v_tiles[k][r % kMaxPasses];
+                    },
+                    &S->v_round_waves, &S->v_wave_items);
+        if (S->timeout_ns == 0)
+            S->timeout_ns = (long long)((opt && opt->timeout_ms) ? opt->timeout_ms : 2000) *
+                            1000000LL;
+    }
     // the line-chain launch for the 2D instances
     if (S->c_channels > 4) S->c_channels = 0;
     if (!S->c_index.empty()) {
@@ -228,17 +281,24 @@ int build_schedule(const fgx_instance* items, int n, const fgx_options* opt, boo
             S->timeout_ns = (long long)((opt && opt->timeout_ms) ? opt->timeout_ms : 2000) *
                             1000000LL;
     }
+    S->sms = sms;
     S->flags_bytes = al256((size_t)std::max(flags_total, 1) * 8);
-    // layout: header | engine tags | chain exchange words (the cleared prefix)
-    // | engine tables | chain tables | chain buffers
+    // layout: header | engine tags | chain exchange words | plane-tile range
+    // flags and exchange words (the cleared prefix) | engine tables | chain
+    // tables | plane-tile tables | chain buffers
     S->c_xbuf_off = kHeaderBytes + S->flags_bytes;
-    S->desc_off = S->c_xbuf_off + al256(S->c_xbuf_bytes);
+    S->v_flag_off = S->c_xbuf_off + al256(S->c_xbuf_bytes);
+    S->v_xbuf_off = S->v_flag_off + al256(S->v_index.size() * sizeof(int));
+    S->desc_off = S->v_xbuf_off + al256(S->v_xbuf_bytes);
     S->waves_off = S->desc_off + al256(S->desc.size() * sizeof(InstDesc) + 1);
     S->items_off = S->waves_off + al256(S->round_waves.size() * sizeof(int));
     S->c_desc_off = S->items_off + al256(S->wave_items.size() * sizeof(int) + 1);
     S->c_waves_off = S->c_desc_off + al256(S->c_index.size() * chain2d_desc_size() + 1);
     S->c_items_off = S->c_waves_off + al256(S->c_round_waves.size() * sizeof(int) + 1);
-    S->c_sec_off = S->c_items_off + al256(S->c_wave_items.size() * sizeof(int) + 1);
+    S->v_desc_off = S->c_items_off + al256(S->c_wave_items.size() * sizeof(int) + 1);
+    S->v_waves_off = S->v_desc_off + al256(S->v_index.size() * vol3d_desc_size() + 1);
+    S->v_items_off = S->v_waves_off + al256(S->v_round_waves.size() * sizeof(int) + 1);
+    S->c_sec_off = S->v_items_off + al256(S->v_wave_items.size() * sizeof(int) + 1);
     S->total = S->c_sec_off + al256(S->c_sec_bytes);
     return FGX_OK;
 }
@@ -286,7 +346,19 @@ int fgx_batched_prepare(const fgx_instance* items, int n, void* workspace,
                               w + S.c_xbuf_off + S.c_xoff[k], w + S.c_sec_off + S.c_soff[k], &xb,
                               &tv, &th);
     }
+    std::vector<unsigned char> vdesc(S.v_index.size() * vol3d_desc_size());
+    for (size_t k = 0; k < S.v_index.size(); ++k) {
+        size_t xb = 0;
+        int ci = 0, mt = 0, tiles[kMaxPasses];
+        if (!vol3d_instance_desc(vdesc.data() + k * vol3d_desc_size(), items[S.v_index[k]],
+                                 S.v_args[k], opt, S.sms, w, (int*)(w + S.v_flag_off) + k,
+                                 w + S.v_xbuf_off + S.v_xoff[k], &xb, &ci, &mt, tiles))
+            return FGX_ERR_UNSUPPORTED;
+    }
     if (!put(S.desc_off, S.desc.data(), S.desc.size() * sizeof(InstDesc)) ||
+        !put(S.v_desc_off, vdesc.data(), vdesc.size()) ||
+        !put(S.v_waves_off, S.v_round_waves.data(), S.v_round_waves.size() * sizeof(int)) ||
+        !put(S.v_items_off, S.v_wave_items.data(), S.v_wave_items.size() * sizeof(int)) ||
         !put(S.waves_off, S.round_waves.data(), S.round_waves.size() * sizeof(int)) ||
         !put(S.items_off, S.wave_items.data(), S.wave_items.size() * sizeof(int)) ||
         !put(S.c_desc_off, cdesc.data(), cdesc.size()) ||
@@ -319,6 +391,13 @@ int fgx_batched_prepare(const fgx_instance* items, int n, void* workspace,
     plan->desc2d_off = S.c_desc_off;
     plan->waves2d_off = S.c_waves_off;
     plan->items2d_off = S.c_items_off;
+    plan->n3d = (int)S.v_index.size();
+    plan->grid3d = S.v_grid;
+    plan->rounds3d = S.v_rounds;
+    plan->smem3d = (int)S.v_smem;
+    plan->desc3d_off = S.v_desc_off;
+    plan->waves3d_off = S.v_waves_off;
+    plan->items3d_off = S.v_items_off;
     return FGX_OK;
 }
 
@@ -335,9 +414,21 @@ int fgx_batched_run(const fgx_batched_plan* plan, void* stream) {
             (const int*)(w + plan->items2d_off), plan->grid2d, w, timeout_ns, stream);
         if (st != FGX_OK) return st;
     }
+    if (plan->n3d > 0) {
+        if (plan->n2d > 0 && cudaMemsetAsync(w + 64, 0, 4, s) != cudaSuccess)
+            return FGX_ERR_CUDA;  // fresh grid-barrier counter for this launch
+        int sms = 0;
+        if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, 0) != cudaSuccess)
+            return FGX_ERR_CUDA;
+        const int st = launch_vol3d_batched(
+            w + plan->desc3d_off, plan->n3d, plan->rounds3d, (const int*)(w + plan->waves3d_off),
+            (const int*)(w + plan->items3d_off), plan->grid3d, (size_t)plan->smem3d, w,
+            timeout_ns, sms, stream);
+        if (st != FGX_OK) return st;
+    }
     if (plan->n == 0) return FGX_OK;
-    if (plan->n2d > 0 && cudaMemsetAsync(w + 64, 0, 4, s) != cudaSuccess)
-        return FGX_ERR_CUDA;  // fresh grid-barrier counter for the second launch
+    if ((plan->n2d > 0 || plan->n3d > 0) && cudaMemsetAsync(w + 64, 0, 4, s) != cudaSuccess)
+        return FGX_ERR_CUDA;  // fresh grid-barrier counter for this launch
     BatchedArgs a;
     std::memset(&a, 0, sizeof(a));
     a.desc = (const InstDesc*)(w + plan->desc_off);

@@ -155,6 +155,19 @@ int launch_chain2d_batched(const void* desc, int n, int init_channels, int max_w
                            int rounds, const int* round_waves, const int* wave_items, int grid,
                            char* hdr, long long timeout_ns, void* stream);
 
+// Batched 3D instances on the plane-tile kernel (vol3d.cu): argument block
+// size, filling one (false when the instance does not fit the kernel; with
+// desc null only the sizes), launch geometry and the launch (D0 and range
+// tests of every instance, then the rounds).
+size_t vol3d_desc_size();
+bool vol3d_instance_desc(void* desc, const fgx_instance& it, const SweepArgs& f,
+                         const fgx_options* opt, int sms, char* hdr, int* range_flag, char* xb,
+                         size_t* xbytes, int* ci, int* max_tiles, int tiles[kMaxPasses]);
+int vol3d_batched_geometry(int sms, int max_ci, const fgx_options* opt, int* grid, size_t* smem);
+int launch_vol3d_batched(const void* desc, int n, int rounds, const int* round_waves,
+                         const int* wave_items, int grid, size_t smem, char* hdr,
+                         long long timeout_ns, int sms, void* stream);
+
 // 2D reverse sweep on warp chains (adj2d.cu).
 size_t adj2d_workspace_bytes(int64_t B, int64_t H, int64_t W, int iterations,
                              const fgx_options* opt);

@@ -495,6 +495,83 @@ __global__ void __launch_bounds__(kBlock3, 1) vol3d_kernel(const Vol3DArgs a) {
     }
 }
 
+// Batched launch: work list of (instance, tile) items per round, one round
+// per pass application, grid barrier between rounds; every instance has its
+// own arguments (cost mode, planes, exchange words, range flag).
+struct Vol3DBatch {
+    const Vol3DArgs* desc;
+    int rounds;
+    const int* round_waves;   // [rounds + 1]
+    const int* wave_items;    // [waves][gridDim.x]: (instance << 16) | tile, or -1
+    unsigned int* barrier;
+    int* status;
+    long long timeout_ns;
+};
+
+// D0 = v * M and the intensity range test of instance blockIdx.y.
+__global__ void __launch_bounds__(256) init3d_batched_kernel(const Vol3DArgs* desc) {
+    const Vol3DArgs& a = desc[blockIdx.y];
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.N; i += stride)
+        a.dist[i] = __fmul_rn(a.v, a.mask[i]);
+    if (a.mode != kModeAbs) return;
+    int* flag = const_cast<int*>(a.range_flag);
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.C * a.N; i += stride) {
+        const float x = fabsf(a.image[i]);
+        const bool ok = x == 0.0f || (x >= 0x1p-40f && x <= 0x1p62f);
+        if (!ok && *(volatile int*)flag == 0) atomicOr(flag, 1);
+    }
+}
+
+__device__ bool run_item3(const Vol3DArgs& a, const Tile3& t, int t_app, Head3& h, float* stage,
+                          unsigned int cb) {
+    if (a.mode == kModeConst) return run_tile3<kModeConst, 0>(a, t, t_app, h, stage, cb, false);
+    if (a.mode == kModeAbs)
+        return run_tile3<kModeAbs, 1>(a, t, t_app, h, stage, cb, *a.range_flag != 0);
+    if (a.C == 1) return run_tile3<kModeGeneral, 1>(a, t, t_app, h, stage, cb, false);
+    if (a.C == 2) return run_tile3<kModeGeneral, 2>(a, t, t_app, h, stage, cb, false);
+    return run_tile3<kModeGeneral, 3>(a, t, t_app, h, stage, cb, false);
+}
+
+__global__ void __launch_bounds__(kBlock3, 1) vol3d_batched_kernel(const Vol3DBatch bt) {
+    extern __shared__ __align__(16) unsigned char smem3[];
+    Head3& h = *reinterpret_cast<Head3*>(smem3);
+    float* stage = reinterpret_cast<float*>(smem3 + sizeof(Head3));
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < kNst; ++i) {
+            mbar_init3(&h.full[i], kPW * 32);
+            mbar_init3(&h.empty[i], 1);
+        }
+    }
+    __syncthreads();
+    unsigned int epoch = 1;
+    unsigned int cb = 0;
+    bool alive = true;
+    for (int r = 0; r < bt.rounds && alive; ++r) {
+        for (int wv = bt.round_waves[r]; wv < bt.round_waves[r + 1]; ++wv) {
+            const int item = bt.wave_items[(int64_t)wv * gridDim.x + blockIdx.x];
+            if (item < 0) continue;
+            const Vol3DArgs& a = bt.desc[item >> 16];
+            const int pass = r % kMaxPasses;
+            const PassGeom& g = a.pass[pass];
+            Tile3 t;
+            t.g = &g;
+            t.tile = item & 0xffff;
+            t.jp = t.tile / a.ntq[pass];
+            t.jq = t.tile % a.ntq[pass];
+            t.ntq = a.ntq[pass];
+            t.b = 0;
+            t.L = (int)g.L;
+            t.nch = t.L > 1 ? (t.L + kChunk - 1) / kChunk : 0;
+            t.p0 = (int64_t)t.jp * kTP - kRing;
+            t.q0 = (int64_t)t.jq * kTQ - kRing;
+            if (t.nch > 0) run_item3(a, t, r, h, stage, cb);
+            cb += (unsigned int)t.nch;
+        }
+        alive = grid_barrier(bt.barrier, epoch++, bt.status, bt.timeout_ns);
+    }
+}
+
 size_t stage_bytes(int CI) {
     return sizeof(Head3) + (size_t)kNst * kChunk * (1 + CI) * kPlane * sizeof(float);
 }
@@ -621,6 +698,93 @@ int run_vol3d(const SweepArgs& f, const float* image, const float* mask, float* 
     cfg.numAttrs = 1;
     if (cudaLaunchKernelEx(&cfg, pick_kernel(vp.mode, vp.CI), a) != cudaSuccess)
         return FGX_ERR_CUDA;
+    return FGX_OK;
+}
+
+// ---------------------------------------------------- batched 3D instances ----
+
+size_t vol3d_desc_size() { return sizeof(Vol3DArgs); }
+
+bool vol3d_instance_desc(void* desc, const fgx_instance& it, const SweepArgs& f,
+                         const fgx_options* opt, int sms, char* hdr, int* range_flag, char* xb,
+                         size_t* xbytes, int* ci, int* max_tiles, int tiles[kMaxPasses]) {
+    Vol3DPlan vp;
+    if (!plan_vol3d(f, opt, sms, &vp)) return false;
+    *xbytes = (size_t)vp.max_tiles * 2 * kXWords * 8;
+    *ci = vp.CI;
+    *max_tiles = vp.max_tiles;
+    for (int i = 0; i < kMaxPasses; ++i) tiles[i] = vp.ntp[i] * vp.ntq[i];
+    if (!desc) return true;
+    Vol3DArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.image = it.image;
+    a.mask = it.mask;
+    a.dist = it.dist;
+    a.B = 1;
+    a.C = f.C;
+    a.N = f.N;
+    a.v = it.v;
+    a.lambda = f.lambda;
+    a.iterations = it.iterations;
+    a.mode = vp.mode;
+    for (int i = 0; i < kMaxPasses; ++i) {
+        a.pass[i] = f.pass[i];
+        a.ntp[i] = vp.ntp[i];
+        a.ntq[i] = vp.ntq[i];
+    }
+    a.max_tiles = vp.max_tiles;
+    a.xbuf = (unsigned long long*)xb;
+    a.barrier = (unsigned int*)(hdr + 64);
+    a.status = (int*)hdr;
+    a.range_flag = range_flag;
+    a.timeout_ns = f.timeout_ns;
+    std::memcpy(desc, &a, sizeof(a));
+    return true;
+}
+
+int vol3d_batched_geometry(int sms, int max_ci, const fgx_options* opt, int* grid, size_t* smem) {
+    *smem = stage_bytes(max_ci);
+    if (cudaFuncSetAttribute(vol3d_batched_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)*smem) != cudaSuccess)
+        return FGX_ERR_CUDA;
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, vol3d_batched_kernel, kBlock3,
+                                                      *smem) != cudaSuccess ||
+        per_sm < 1)
+        return FGX_ERR_CUDA;
+    int64_t g = (int64_t)per_sm * sms;
+    if (opt && opt->max_blocks) g = std::min<int64_t>(g, opt->max_blocks);
+    *grid = (int)std::max<int64_t>(1, g);
+    return FGX_OK;
+}
+
+int launch_vol3d_batched(const void* desc, int n, int rounds, const int* round_waves,
+                         const int* wave_items, int grid, size_t smem, char* hdr,
+                         long long timeout_ns, int sms, void* stream) {
+    cudaStream_t s = (cudaStream_t)stream;
+    const Vol3DArgs* d = (const Vol3DArgs*)desc;
+    init3d_batched_kernel<<<dim3((unsigned)std::max(1, sms * 4), (unsigned)n), 256, 0, s>>>(d);
+    if (cudaGetLastError() != cudaSuccess) return FGX_ERR_CUDA;
+    if (rounds == 0) return FGX_OK;
+    Vol3DBatch bt;
+    bt.desc = d;
+    bt.rounds = rounds;
+    bt.round_waves = round_waves;
+    bt.wave_items = wave_items;
+    bt.barrier = (unsigned int*)(hdr + 64);
+    bt.status = (int*)hdr;
+    bt.timeout_ns = timeout_ns;
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3(kBlock3);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    if (cudaLaunchKernelEx(&cfg, vol3d_batched_kernel, bt) != cudaSuccess) return FGX_ERR_CUDA;
     return FGX_OK;
 }
 
