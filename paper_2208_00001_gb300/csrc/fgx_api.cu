@@ -242,12 +242,11 @@ int run_forward(int ndim, const float* image, const float* mask, float* dist, in
         return run_chain2d(image, mask, dist, codes, B, C, H, W, v, lambda, iterations,
                            workspace, ws_bytes, opt, pl.sms, stream);
     }
-    if (fast_kernels && ndim == 3 && !codes && pl.vol3d_bytes && workspace &&
+    if (fast_kernels && ndim == 3 && pl.vol3d_bytes && workspace &&
         ws_bytes >= pl.vol3d_bytes && vol3d_supports(pl.args, opt, pl.sms)) {
         if (!is_device_ptr(workspace)) return FGX_ERR_NOT_DEVICE_PTR;
-        SweepArgs f = pl.args;
-        f.timeout_ns = pl.args.timeout_ns;
-        return run_vol3d(f, image, mask, dist, v, workspace, ws_bytes, opt, pl.sms, stream);
+        return run_vol3d(pl.args, image, mask, dist, codes, v, workspace, ws_bytes, opt, pl.sms,
+                         stream);
     }
     if (!workspace || ws_bytes < pl.ws_bytes) return FGX_ERR_WORKSPACE;
     if (!is_device_ptr(workspace)) return FGX_ERR_NOT_DEVICE_PTR;
@@ -366,7 +365,8 @@ int fgx_geodesic3d_fwd_train(const float* image, const float* mask, float* dist,
                              size_t workspace_bytes, const fgx_options* opt, void* stream) {
     if (!saved && (size_t)iterations * B * D * H * W > 0) return FGX_ERR_WORKSPACE;
     return run_forward(3, image, mask, dist, B, C, D, H, W, spacing, v, lambda, iterations,
-                       (uint8_t*)saved, saved_bytes, workspace, workspace_bytes, opt, stream);
+                       (uint8_t*)saved, saved_bytes, workspace, workspace_bytes, opt, stream,
+                       true);
 }
 
 }  // extern "C"

@@ -139,8 +139,9 @@ int chain2d_geometry(int64_t H, int64_t W, const fgx_options* opt, int* K, int* 
 // when the call does not fit that kernel (the tiled engine runs it instead).
 size_t vol3d_workspace_bytes(const SweepArgs& f, const fgx_options* opt, int sms);
 bool vol3d_supports(const SweepArgs& f, const fgx_options* opt, int sms);
-int run_vol3d(const SweepArgs& f, const float* image, const float* mask, float* dist, float v,
-              void* workspace, size_t ws_bytes, const fgx_options* opt, int sms, void* stream);
+int run_vol3d(const SweepArgs& f, const float* image, const float* mask, float* dist,
+              uint8_t* codes, float v, void* workspace, size_t ws_bytes, const fgx_options* opt,
+              int sms, void* stream);
 
 // Batched 2D instances on the line-chain kernel (chain2d.cu): the size of
 // one instance's argument block, filling it (buffers: exchange words at xb,

@@ -66,6 +66,7 @@ struct Vol3DArgs {
     const float* image;  // [B][C][N]
     const float* mask;   // [B][N]
     float* dist;         // [B][N]
+    uint8_t* codes;      // [iterations * 6][B][N] parent codes, or null
     int64_t B, C, N;
     float v, lambda;
     int iterations;
@@ -285,8 +286,10 @@ __device__ __forceinline__ float cost3(const float (&ix)[CI > 0 ? CI : 1],
 }
 
 // Compute warps of one tile: plane steps 1 .. L-1, ring refresh every kRing
-// steps, owned voxels written to the distance map.
-template <int MODE, int CI, bool CHECKED>
+// steps, owned voxels written to the distance map (and with CODES their
+// parent codes: 0 if the voxel kept its value, else 1 + the lowest stencil
+// offset whose candidate is the strictly smaller minimum).
+template <int MODE, int CI, bool CHECKED, bool CODES>
 __device__ bool compute3(const Vol3DArgs& a, const Tile3& t, int t_app, Head3& h, float* stage,
                          unsigned int cb) {
     constexpr int NI = CI > 0 ? CI : 1;
@@ -306,6 +309,7 @@ __device__ bool compute3(const Vol3DArgs& a, const Tile3& t, int t_app, Head3& h
         goff[i] = p * g.sp + q * g.sq;
     }
     float* dist = a.dist + t.b * a.N;
+    uint8_t* codes = CODES ? a.codes + ((int64_t)t_app * a.B + t.b) * a.N : nullptr;
     const float lam = a.lambda;
     float tk[9], ck[9];
 #pragma unroll
@@ -387,6 +391,7 @@ __device__ bool compute3(const Vol3DArgs& a, const Tile3& t, int t_app, Head3& h
 #pragma unroll
         for (int i = 0; i < kRows; ++i) {
             float best = Sd[(rows0 + i) * kRQ + lane];
+            unsigned int code = 0;
 #pragma unroll
             for (int dp = -1; dp <= 1; ++dp) {
 #pragma unroll
@@ -396,11 +401,16 @@ __device__ bool compute3(const Vol3DArgs& a, const Tile3& t, int t_app, Head3& h
                     const float pd = dq < 0 ? lft[rk] : (dq == 0 ? col[rk] : rgt[rk]);
                     const float c = cost3<MODE, CI, CHECKED>(ix[i], ip[rk][dq + 1], tk[k], ck[k],
                                                              lam);
-                    best = fminf(best, __fadd_rn(pd, c));
+                    const float cand = __fadd_rn(pd, c);
+                    if (CODES && cand < best) code = (unsigned int)(k + 1);
+                    best = fminf(best, cand);
                 }
             }
             d[i] = valid[i] ? best : kInf3;
-            if (own[i]) dist[lo + goff[i]] = d[i];
+            if (own[i]) {
+                dist[lo + goff[i]] = d[i];
+                if (CODES) codes[lo + goff[i]] = (uint8_t)code;
+            }
         }
         if (s % kRing == 0 && s + 1 < t.L) {
             if (!failed && !exchange3(a, t, w, tag_base | (unsigned int)(xi + 1), xi & 1, d))
@@ -436,15 +446,16 @@ __global__ void __launch_bounds__(256) init3d_kernel(const float* mask, float* d
     }
 }
 
-template <int MODE, int CI>
+template <int MODE, int CI, bool CODES = false>
 __device__ __forceinline__ bool run_tile3(const Vol3DArgs& a, const Tile3& t, int t_app, Head3& h,
                                           float* stage, unsigned int cb, bool checked) {
     if ((int)(threadIdx.x >> 5) >= kCW) return producer3<CI>(a, t, h, stage, cb);
-    if (MODE == kModeAbs && checked) return compute3<MODE, CI, true>(a, t, t_app, h, stage, cb);
-    return compute3<MODE, CI, false>(a, t, t_app, h, stage, cb);
+    if (MODE == kModeAbs && checked)
+        return compute3<MODE, CI, true, CODES>(a, t, t_app, h, stage, cb);
+    return compute3<MODE, CI, false, CODES>(a, t, t_app, h, stage, cb);
 }
 
-template <int MODE, int CI>
+template <int MODE, int CI, bool CODES>
 __global__ void __launch_bounds__(kBlock3, 1) vol3d_kernel(const Vol3DArgs a) {
     extern __shared__ __align__(16) unsigned char smem3[];
     Head3& h = *reinterpret_cast<Head3*>(smem3);
@@ -486,7 +497,7 @@ __global__ void __launch_bounds__(kBlock3, 1) vol3d_kernel(const Vol3DArgs a) {
             t.nch = nch;
             t.p0 = (int64_t)t.jp * kTP - kRing;
             t.q0 = (int64_t)t.jq * kTQ - kRing;
-            if (nch > 0) run_tile3<MODE, CI>(a, t, t_app, h, stage, cb, checked);
+            if (nch > 0) run_tile3<MODE, CI, CODES>(a, t, t_app, h, stage, cb, checked);
             cb += (unsigned int)nch;
         }
         alive = grid_barrier(a.barrier, epoch++, a.status, a.timeout_ns);
@@ -578,12 +589,16 @@ size_t stage_bytes(int CI) {
 
 using Vol3DKernel = void (*)(Vol3DArgs);
 
-Vol3DKernel pick_kernel(int mode, int CI) {
-    if (mode == kModeConst) return vol3d_kernel<kModeConst, 0>;
-    if (mode == kModeAbs) return vol3d_kernel<kModeAbs, 1>;
-    if (CI == 1) return vol3d_kernel<kModeGeneral, 1>;
-    if (CI == 2) return vol3d_kernel<kModeGeneral, 2>;
-    return vol3d_kernel<kModeGeneral, 3>;
+template <bool CODES>
+Vol3DKernel pick_kernel_t(int mode, int CI) {
+    if (mode == kModeConst) return vol3d_kernel<kModeConst, 0, CODES>;
+    if (mode == kModeAbs) return vol3d_kernel<kModeAbs, 1, CODES>;
+    if (CI == 1) return vol3d_kernel<kModeGeneral, 1, CODES>;
+    if (CI == 2) return vol3d_kernel<kModeGeneral, 2, CODES>;
+    return vol3d_kernel<kModeGeneral, 3, CODES>;
+}
+Vol3DKernel pick_kernel(int mode, int CI, bool codes = false) {
+    return codes ? pick_kernel_t<true>(mode, CI) : pick_kernel_t<false>(mode, CI);
 }
 
 struct Vol3DPlan {
@@ -648,8 +663,9 @@ size_t vol3d_workspace_bytes(const SweepArgs& f, const fgx_options* opt, int sms
     return plan_vol3d(f, opt, sms, &vp, true) ? vp.ws_bytes : 0;
 }
 
-int run_vol3d(const SweepArgs& f, const float* image, const float* mask, float* dist, float v,
-              void* workspace, size_t ws_bytes, const fgx_options* opt, int sms, void* stream) {
+int run_vol3d(const SweepArgs& f, const float* image, const float* mask, float* dist,
+              uint8_t* codes, float v, void* workspace, size_t ws_bytes, const fgx_options* opt,
+              int sms, void* stream) {
     Vol3DPlan vp;
     if (!plan_vol3d(f, opt, sms, &vp)) return FGX_ERR_UNSUPPORTED;
     if (ws_bytes < vp.ws_bytes) return FGX_ERR_WORKSPACE;
@@ -658,6 +674,7 @@ int run_vol3d(const SweepArgs& f, const float* image, const float* mask, float* 
     a.image = image;
     a.mask = mask;
     a.dist = dist;
+    a.codes = codes;
     a.B = f.B;
     a.C = f.C;
     a.N = f.N;
@@ -680,6 +697,10 @@ int run_vol3d(const SweepArgs& f, const float* image, const float* mask, float* 
     a.timeout_ns = f.timeout_ns;
     cudaStream_t s = (cudaStream_t)stream;
     if (cudaMemsetAsync(workspace, 0, vp.ws_bytes, s) != cudaSuccess) return FGX_ERR_CUDA;
+    // codes of the first plane of every sweep stay 0 (it keeps its values)
+    const size_t ncodes = (size_t)f.iterations * kMaxPasses * (size_t)(f.B * f.N);
+    if (codes && ncodes && cudaMemsetAsync(codes, 0, ncodes, s) != cudaSuccess)
+        return FGX_ERR_CUDA;
     const int64_t n = f.B * f.N;
     const int ig = (int)std::min<int64_t>((n + 255) / 256, (int64_t)sms * 16);
     init3d_kernel<<<std::max(ig, 1), 256, 0, s>>>(mask, dist, v, n, image, f.B * f.C * f.N,
@@ -696,7 +717,11 @@ int run_vol3d(const SweepArgs& f, const float* image, const float* mask, float* 
     attr[0].val.cooperative = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    if (cudaLaunchKernelEx(&cfg, pick_kernel(vp.mode, vp.CI), a) != cudaSuccess)
+    Vol3DKernel k = pick_kernel(vp.mode, vp.CI, codes != nullptr);
+    if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)vp.smem) !=
+        cudaSuccess)
+        return FGX_ERR_CUDA;
+    if (cudaLaunchKernelEx(&cfg, k, a) != cudaSuccess)
         return FGX_ERR_CUDA;
     return FGX_OK;
 }
