@@ -48,7 +48,7 @@ def _peaks():
 
 
 # Sources that define the headline kernel (chain2d_kernel and its helpers).
-KERNEL_SOURCES = ("chain2d.cu", "device_sync.cuh")
+KERNEL_SOURCES = ("chain2d.cu", "chain_common.cuh", "device_sync.cuh")
 
 
 def _kernel_hash():
