@@ -382,6 +382,8 @@ struct BwdPlan {
     size_t smem = 0;
     size_t ws_bytes = 0;
     size_t flags_bytes = 0;
+    SweepArgs fwd;  // geometry of the forward sweep (3D plane-tile reverse sweep)
+    int sms = 0;
 };
 
 size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
@@ -395,6 +397,8 @@ int plan_backward(int ndim, int64_t B, int64_t C, int64_t D, int64_t H, int64_t 
     AdjointArgs& a = bp->args;
     std::memset(&a, 0, sizeof(a));
     const SweepArgs& f = pl.args;
+    bp->fwd = f;
+    bp->sms = pl.sms;
     a.B = B;
     a.C = C;
     a.N = f.N;
@@ -466,6 +470,15 @@ int run_backward(int ndim, const float* grad_dist, const float* image, const voi
                        W, v, lambda, iterations, workspace, ws_bytes, opt, dev.sms, stream);
         if (st != FGX_ERR_UNSUPPORTED) return st;
     }
+    if (ndim == 3 && iterations > 0 && workspace) {
+        const size_t need = adj3d_workspace_bytes(bp.fwd, iterations, opt, bp.sms);
+        if (need && ws_bytes >= need) {
+            if (!is_device_ptr(workspace)) return FGX_ERR_NOT_DEVICE_PTR;
+            st = run_adj3d(bp.fwd, grad_dist, image, (const uint8_t*)saved, grad_image,
+                           grad_mask, v, iterations, workspace, ws_bytes, opt, bp.sms, stream);
+            if (st != FGX_ERR_UNSUPPORTED) return st;
+        }
+    }
     if (!workspace || ws_bytes < bp.ws_bytes) return FGX_ERR_WORKSPACE;
     if (!is_device_ptr(workspace)) return FGX_ERR_NOT_DEVICE_PTR;
     AdjointArgs& a = bp.args;
@@ -497,11 +510,13 @@ int fgx_backward_workspace_size(int ndim, int64_t B, int64_t C, int64_t D, int64
     if (iterations < 0) return FGX_ERR_ARG;
     const float unit[3] = {1.f, 1.f, 1.f};
     BwdPlan bp;
-    int st = plan_backward(ndim, B, C, D, H, W, unit, 0.5f, 1, opt, &bp);
+    int st = plan_backward(ndim, B, C, D, H, W, unit, 0.5f, std::max(iterations, 1), opt, &bp);
     if (st != FGX_OK) return st;
     *bytes = bp.ws_bytes;
     if (ndim == 2 && iterations > 0)
         *bytes = std::max(*bytes, adj2d_workspace_bytes(B, H, W, iterations, opt));
+    if (ndim == 3 && iterations > 0)
+        *bytes = std::max(*bytes, adj3d_workspace_bytes(bp.fwd, iterations, opt, bp.sms));
     return FGX_OK;
 }
 

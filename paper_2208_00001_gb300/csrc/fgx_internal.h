@@ -177,6 +177,15 @@ int run_adj2d(const float* grad_dist, const float* image, const uint8_t* codes,
               float v, float lambda, int iterations, void* workspace, size_t ws_bytes,
               const fgx_options* opt, int sms, void* stream);
 
+// 3D reverse sweep on plane tiles (vol3d.cu): workspace bytes (0 when the
+// geometry does not fit the kernel) and the run (adjoint kernel, then the
+// per-voxel image gradient when grad_image is wanted).
+size_t adj3d_workspace_bytes(const SweepArgs& f, int iterations, const fgx_options* opt,
+                             int sms);
+int run_adj3d(const SweepArgs& f, const float* grad_dist, const float* image,
+              const uint8_t* codes, float* grad_image, float* grad_mask, float v, int iterations,
+              void* workspace, size_t ws_bytes, const fgx_options* opt, int sms, void* stream);
+
 int run_chain2d(const float* image, const float* mask, float* dist, uint8_t* codes, int64_t B,
                 int64_t C, int64_t H, int64_t W, float v, float lambda, int iterations,
                 void* workspace, size_t ws_bytes, const fgx_options* opt, int sms, void* stream);

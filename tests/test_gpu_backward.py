@@ -129,6 +129,33 @@ def test_backward_3d_anisotropic_multichannel(fgx):
     _bits_equal(gm, wm, "grad_mask")
 
 
+@pytest.mark.parametrize("C,lam,spacing,opts", [
+    (1, 1.0, (1.0, 1.0, 1.0), None),
+    (2, 0.4, (2.5, 1.0, 0.75), None),
+    (3, 0.0, (1.0, 2.0, 1.0), dict(max_blocks=18)),
+    (1, 0.7, (1.5, 1.0, 1.0), dict(max_blocks=16)),
+])
+def test_backward_3d_multi_tile_bit_exact(fgx, C, lam, spacing, opts):
+    """Reverse sweep over planes of several plane tiles along both in-plane
+    axes (ring refreshes), three instances, waves of instances when the grid
+    is capped; also the call that asks for dL/dM only."""
+    rng = np.random.default_rng(60 + C)
+    img = rng.uniform(0, 1, (3, C, 30, 50, 61)).astype(np.float32)
+    m = rng.uniform(0, 1, (3, 1, 30, 50, 61)).astype(np.float32)
+    m[0, 0, 3:6, 40:44, 10:12] = 0
+    m[1, 0, 29, 0, 60] = 0
+    m[2, 0, 15, 25, 30] = 0
+    case = workloads.Case("bwd3d", img, m, 6.0, lam, 2, spacing)
+    w = rng.uniform(-1, 1, m.shape).astype(np.float32)
+    d, codes, gi, gm = _run(fgx, case, w, options=opts)
+    wi, wm = _oracle(case, w, codes)
+    _bits_equal(gi, wi, "grad_image")
+    _bits_equal(gm, wm, "grad_mask")
+    _, _, gi2, gm2 = _run(fgx, case, w, options=opts, need_image=False)
+    assert gi2 is None
+    _bits_equal(gm2, wm, "grad_mask alone")
+
+
 @pytest.mark.parametrize("which", ["image", "mask"])
 def test_backward_single_output(fgx, which):
     case = workloads.diff2d(batch=1, size=40, v=10.0)
