@@ -68,6 +68,10 @@ typedef struct fgx_options {
     int32_t tile_height;  /* 3D: elements per tile along the outer in-line axis; 0 = auto */
     int32_t max_blocks;   /* cap on resident thread blocks; 0 = all that fit */
     int32_t timeout_ms;   /* inter-block wait limit; 0 = 2000 ms */
+    int32_t segments;     /* 2D single-call forward: line segments per pass run at once
+                           * speculatively (exact results; a segment whose start line
+                           * changes runs again); 0 = as many as one block per SM
+                           * allows, 1 = off, n = at most n (up to 8) */
 } fgx_options;
 
 /* Human-readable name of a status code (static string). */

@@ -43,6 +43,9 @@ namespace fgx {
 namespace {
 
 constexpr int kRegion = 128;           // columns per tile region (4 per lane)
+constexpr int kMaxSeg = 8;             // speculative segments per pass at most
+constexpr int kMinSegLines = 64;       // shortest segment worth a separate chain
+constexpr int kMaxSegImages = 128;     // images of one call that segments are used for
 constexpr int kBlockThreads = 96;      // chain, producer and flusher warps
 #define kInf __int_as_float(0x7f800000)
 
@@ -68,6 +71,13 @@ struct Chain2DArgs {
     int K, T;            // ring and owned widths of multi-tile passes
     int tiles_v, tiles_h;
     int max_tiles;
+    // speculative line segments (1: a pass runs as one chain)
+    int nseg_v, nseg_h;      // segments of a vertical / horizontal pass
+    int seglen_v, seglen_h;  // lines per segment (whole chunks)
+    int max_seg;             // exchange areas per image (kMaxSeg, or 1)
+    int bnd_ld;              // floats per boundary line (max(H, W) rounded up)
+    float* bnd;              // [B][kMaxSeg - 1][bnd_ld] boundary lines the segments started from
+    unsigned int* segflag;   // [B][kMaxSeg][2]: boundary changed (phase A, re-run), tag t_app + 1
 };
 
 using namespace dev;
@@ -118,9 +128,11 @@ __device__ __forceinline__ bool mbar_wait(unsigned long long* b, unsigned int pa
     return chain::mbar_wait(b, parity, a.status, a.timeout_ns);
 }
 
-// Geometry of one tile of one pass, identical in the three warps.
+// Geometry of one tile of one pass (or of one line segment of it), identical
+// in the three warps.
 struct TileGeo {
     int L, Q, ld, ntiles, K, T, q0, q1, r0, nch;
+    int s0, ns;      // first step and number of steps of the segment
     bool multi;
     const float* src;
     const float* E;
@@ -129,10 +141,23 @@ struct TileGeo {
     int out_ld;
     uint8_t* codes;  // codes of this pass application and image (image order), or null
     bool codes_rows; // the pass's lines are rows of the image (vertical pass)
+    unsigned long long* xb;  // exchange area of this image and segment
+    unsigned int tag_base;
+    const float* bline;      // values of the line before step s0 (element q at q * bstride), or null
+    int bstride;
+    const float* cmp;        // line the next segment started from (element q at q), or null
+    unsigned int* flag;      // set to flag_tag when the last line differs from it
+    unsigned int flag_tag;
 };
 
+// Line of step s of a pass in sweep order.
+__device__ __forceinline__ int line_of(bool fwd, int L, int s) { return fwd ? s : L - 1 - s; }
+
+// Segment `seg` of the pass (seg = 0 with one segment: the whole pass);
+// rerun: the segment runs again from the exact line before it.
 __device__ __forceinline__ TileGeo tile_geo(const Chain2DArgs& a, int t_app, int pass, int b,
-                                            int tile) {
+                                            int tile, int seg = 0, bool rerun = false,
+                                            int nseg = 1) {
     TileGeo g;
     const bool vert = pass < 2;  // rows of Dw (TB/BT) or rows of Dt (LR/RL)
     g.L = vert ? a.H : a.W;
@@ -145,7 +170,6 @@ __device__ __forceinline__ TileGeo tile_geo(const Chain2DArgs& a, int t_app, int
     g.q0 = g.multi ? tile * g.T : 0;
     g.q1 = min(g.Q, g.q0 + g.T);
     g.r0 = g.q0 - g.K;
-    g.nch = (g.L + kCh - 1) / kCh;
     g.src = vert ? a.Dw + (int64_t)b * a.H * a.Wp : a.Dt + (int64_t)b * a.W * a.Hp;
     g.E = vert ? a.Ev + (int64_t)b * 3 * a.H * a.Wp : a.Eh + (int64_t)b * 3 * a.W * a.Hp;
     g.eplane = (int64_t)g.L * g.ld;
@@ -157,6 +181,34 @@ __device__ __forceinline__ TileGeo tile_geo(const Chain2DArgs& a, int t_app, int
     else { g.out = a.Dw + (int64_t)b * a.H * a.Wp; g.out_ld = a.Wp; }
     g.codes = a.codes ? a.codes + ((int64_t)t_app * a.B + b) * a.H * a.W : nullptr;
     g.codes_rows = vert;
+    const int seglen = nseg > 1 ? (vert ? a.seglen_v : a.seglen_h) : g.L;
+    g.s0 = seg * seglen;
+    g.ns = min(seglen, g.L - g.s0);
+    g.nch = (g.ns + kCh - 1) / kCh;
+    g.xb = a.xbuf + ((size_t)b * a.max_seg + seg) * a.max_tiles * (4 * kMaxRing);
+    // tags differ between pass applications and between a segment's first
+    // run and its re-run (both use the same exchange area)
+    g.tag_base = ((unsigned int)(2 * t_app + (rerun ? 2 : 1))) << 16;
+    g.bline = nullptr;
+    g.bstride = 1;
+    g.cmp = nullptr;
+    g.flag = nullptr;
+    g.flag_tag = (unsigned int)(t_app + 1);
+    if (seg > 0) {
+        if (rerun) {
+            // the exact line before the segment, as the pass wrote it
+            const int line = line_of(pass == 0 || pass == 2, g.L, g.s0 - 1);
+            const bool fwd = pass == 0 || pass == 2;
+            g.bline = fwd ? g.out + (int64_t)line * g.out_ld : g.out + line;
+            g.bstride = fwd ? 1 : g.out_ld;
+        } else {
+            g.bline = a.bnd + ((int64_t)b * (kMaxSeg - 1) + seg - 1) * a.bnd_ld;
+        }
+    }
+    if (seg + 1 < nseg) {
+        g.cmp = a.bnd + ((int64_t)b * (kMaxSeg - 1) + seg) * a.bnd_ld;
+        g.flag = a.segflag + ((int64_t)b * kMaxSeg + seg + 1) * 2 + (rerun ? 1 : 0);
+    }
     return g;
 }
 
@@ -179,9 +231,9 @@ __device__ bool producer_tile(const Chain2DArgs& a, const TileGeo& g, TileSmem& 
             cp_async_wait_all();
             return false;
         }
-        const int jn = min(kCh, L - c * kCh);
+        const int jn = min(kCh, g.ns - c * kCh);
         for (int j = 0; j < jn; ++j) {
-            const int s = c * kCh + j;
+            const int s = g.s0 + c * kCh + j;
             const int line = fwd ? s : (L - 1 - s);
             float(*row)[kRow] = sm.in[slot][j];
             // lanes outside the array get +inf rows: their columns stay at
@@ -220,8 +272,8 @@ __device__ bool flusher_tile(const Chain2DArgs& a, const TileGeo& g, TileSmem& s
         if (!__all_sync(0xffffffffu,
                         mbar_wait(&sm.done[slot_of(gc, kNci)], full_parity(gc, kNci), a)))
             return false;
-        const int s0 = c * kCh;
-        const int nl = min(kCh, L - s0);
+        const int s0 = g.s0 + c * kCh;
+        const int nl = min(kCh, g.ns - c * kCh);
         if (fwd) {
             // rows of the output array: each lane writes its own four columns
             float4 v[kCh];
@@ -384,7 +436,8 @@ __device__ __forceinline__ void chain_step(float (&dp)[4], float left, float rig
 __device__ __forceinline__ bool exchange(const Chain2DArgs& a, const TileGeo& g, int b, int tile,
                                          unsigned int tg, int par, float (&dp)[4],
                                          const bool (&valid)[4]) {
-    const RingLink x{a.xbuf + (size_t)b * a.max_tiles * (4 * kMaxRing), a.status, a.timeout_ns};
+    (void)b;
+    const RingLink x{g.xb, a.status, a.timeout_ns};
     return ring_exchange(x, tile, g.ntiles, g.q0, g.K, g.T, g.r0 + 4 * (int)(threadIdx.x & 31),
                          tg, par, dp, valid, kInf);
 }
@@ -402,8 +455,16 @@ __device__ bool chain_tile(const Chain2DArgs& a, const TileGeo& g, int t_app, in
     bool valid[4];
 #pragma unroll
     for (int i = 0; i < 4; ++i) valid[i] = (c0 + i >= 0) && (c0 + i < g.Q);
-    const unsigned int tag_base = ((unsigned int)(t_app + 1)) << 16;
+    (void)t_app;
+    const unsigned int tag_base = g.tag_base;
+    // the line before the first step: none at the start of a pass (+inf
+    // parents), else the line the segment starts from
     float dp[4] = {kInf, kInf, kInf, kInf};
+    if (g.bline) {
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+            if (valid[i]) dp[i] = __ldcg(g.bline + (int64_t)(c0 + i) * g.bstride);
+    }
     LineIn buf[NB];
     // ring positions (slot, phase parity) of chunks gc, gc+1, gc+2 of the
     // input ring and gc, gc+1 of the output ring, advanced without divisions
@@ -456,6 +517,18 @@ __device__ bool chain_tile(const Chain2DArgs& a, const TileGeo& g, int t_app, in
         }
         __syncwarp();
         if (lane == 0) mbar_arrive(&sm.done[slot]);
+    }
+    if (g.cmp) {
+        // the segment's last line against the line the next segment started from
+        bool diff = false;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int c = c0 + i;
+            if (c >= g.q0 && c < g.q1 &&
+                __float_as_uint(dp[i]) != __float_as_uint(__ldcg(g.cmp + c)))
+                diff = true;
+        }
+        if (__any_sync(0xffffffffu, diff) && lane == 0) atomicMax(g.flag, g.flag_tag);
     }
     return true;
 }
@@ -558,10 +631,12 @@ __global__ void __launch_bounds__(256) chain2d_init_batched_kernel(const Chain2D
     init_tile<CC>(a, 0);
 }
 
+// Not inlined: the pass driver calls it from two places, and each variant's
+// chain loop keeps its own register allocation.
 template <bool fwd, bool table, bool codes>
-__device__ bool run_tile(const Chain2DArgs& a, int t_app, int pass, int b, int tile,
-                         TileSmem& sm, unsigned int cb) {
-    const TileGeo g = tile_geo(a, t_app, pass, b, tile);
+__device__ __noinline__ bool run_tile(const Chain2DArgs& a, int t_app, int pass, int b, int tile,
+                         TileSmem& sm, unsigned int cb, int seg, bool rerun, int nseg) {
+    const TileGeo g = tile_geo(a, t_app, pass, b, tile, seg, rerun, nseg);
     const int warp = threadIdx.x >> 5;
     if (warp == 0) {
         const bool vert = pass < 2;
@@ -577,11 +652,86 @@ __device__ bool run_tile(const Chain2DArgs& a, int t_app, int pass, int b, int t
 
 template <bool codes>
 __device__ __forceinline__ bool run_pass_tile(const Chain2DArgs& a, bool fwd, int t_app, int pass,
-                                              int b, int tile, TileSmem& sm, unsigned int cb) {
-    if (fwd && a.table) return run_tile<true, true, codes>(a, t_app, pass, b, tile, sm, cb);
-    if (fwd) return run_tile<true, false, codes>(a, t_app, pass, b, tile, sm, cb);
-    if (a.table) return run_tile<false, true, codes>(a, t_app, pass, b, tile, sm, cb);
-    return run_tile<false, false, codes>(a, t_app, pass, b, tile, sm, cb);
+                                              int b, int tile, TileSmem& sm, unsigned int cb,
+                                              int seg = 0, bool rerun = false, int nseg = 1) {
+    if (fwd && a.table)
+        return run_tile<true, true, codes>(a, t_app, pass, b, tile, sm, cb, seg, rerun, nseg);
+    if (fwd)
+        return run_tile<true, false, codes>(a, t_app, pass, b, tile, sm, cb, seg, rerun, nseg);
+    if (a.table)
+        return run_tile<false, true, codes>(a, t_app, pass, b, tile, sm, cb, seg, rerun, nseg);
+    return run_tile<false, false, codes>(a, t_app, pass, b, tile, sm, cb, seg, rerun, nseg);
+}
+
+// Speculative segments of one pass application (all images in one wave: the
+// host sizes the grid for B * S * ntiles blocks).  Phase A: the tiles of
+// segments 1 .. S-1 save the line before their segment (the values the pass
+// starts from), then every segment runs at once from its saved line.  A pass
+// only lowers values, so a segment that started from a line whose exact value
+// differs from the saved one holds values >= the exact ones; running it again
+// from the exact line over those values gives the exact result (a min-plus
+// line step is monotone and min(old, spec, exact chain) = min(old, exact
+// chain)).  Phase B visits the segments in order: segment j runs again when
+// the exact last line of segment j-1 differs from the line j started from
+// (each segment's chain compares its last line and sets the boundary's
+// flag).  Every block takes the same decisions from the same flags, so all
+// blocks meet the same grid barriers.
+template <bool codes>
+__device__ bool run_pass_segments(const Chain2DArgs& a, int t_app, int pass, int S, int ntiles,
+                                  TileSmem& sm, unsigned int& cb, unsigned int& epoch,
+                                  uint8_t* rr) {
+    const bool fwd = (pass == 0 || pass == 2);
+    const bool vert = pass < 2;
+    const int L = vert ? a.H : a.W;
+    const int u = blockIdx.x;
+    const bool active = u < a.B * S * ntiles;
+    const int b = active ? u / (S * ntiles) : 0;
+    const int seg = active ? (u / ntiles) % S : 0;
+    const int tile = u % ntiles;
+    // phase A.1: save the owned columns of the line before each segment
+    if (active && seg > 0) {
+        const TileGeo g = tile_geo(a, t_app, pass, b, tile, seg, false, S);
+        const int line = line_of(fwd, L, g.s0 - 1);
+        const float* srow = g.src + (int64_t)line * g.ld;
+        float* dst = a.bnd + ((int64_t)b * (kMaxSeg - 1) + seg - 1) * a.bnd_ld;
+        for (int q = g.q0 + (int)threadIdx.x; q < g.q1; q += blockDim.x) dst[q] = __ldcg(srow + q);
+    }
+    if (!grid_barrier(a.barrier, epoch++, a.status, a.timeout_ns)) return false;
+    // phase A.2: all segments at once
+    bool ok = true;
+    if (active) {
+        ok = run_pass_tile<codes>(a, fwd, t_app, pass, b, tile, sm, cb, seg, false, S);
+        const TileGeo g = tile_geo(a, t_app, pass, b, tile, seg, false, S);
+        cb += (unsigned int)g.nch;
+    }
+    if (!grid_barrier(a.barrier, epoch++, a.status, a.timeout_ns) || !ok) return false;
+    // phase B: segments in order, again where their start line changed
+    __shared__ int any;
+    if (threadIdx.x == 0)
+        for (int i = 0; i < a.B; ++i) rr[i] = 0;
+    const unsigned int tag = (unsigned int)(t_app + 1);
+    for (int j = 1; j < S; ++j) {
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            any = 0;
+            for (int i = 0; i < a.B; ++i) {
+                const unsigned int* f = a.segflag + ((int64_t)i * kMaxSeg + j) * 2;
+                const unsigned int fv = ld_relaxed_u32(f + (rr[i] ? 1 : 0));
+                rr[i] = fv == tag;
+                any |= rr[i];
+            }
+        }
+        __syncthreads();
+        if (!any) continue;
+        const int bb = u / ntiles;
+        if (u < a.B * ntiles && rr[bb]) {
+            ok = run_pass_tile<codes>(a, fwd, t_app, pass, bb, tile, sm, cb, j, true, S);
+            const TileGeo g = tile_geo(a, t_app, pass, bb, tile, j, true, S);
+            cb += (unsigned int)g.nch;
+        }
+        if (!grid_barrier(a.barrier, epoch++, a.status, a.timeout_ns) || !ok) return false;
+    }
+    return true;
 }
 
 // One persistent launch for all passes; `codes` selects the variant that also
@@ -615,10 +765,18 @@ __global__ void __launch_bounds__(kBlockThreads, 1) chain2d_kernel(const Chain2D
     bool alive = true;
     unsigned int cb = 0;  // chunks handed over so far in this block
     const int napps = a.iterations * 4;
+    __shared__ uint8_t rerun[kMaxSegImages];
     for (int t_app = 0; t_app < napps && alive; ++t_app) {
         const int pass = t_app % 4;
         const int ntiles = pass < 2 ? a.tiles_v : a.tiles_h;
         const int L = pass < 2 ? a.H : a.W;
+        const int S = pass < 2 ? a.nseg_v : a.nseg_h;
+        if (S > 1 && a.B <= kMaxSegImages && a.B * S * ntiles <= (int)gridDim.x) {
+            alive = run_pass_segments<codes>(a, t_app, pass, S, ntiles, sm, cb, epoch, rerun);
+            if (blockIdx.x == 0 && threadIdx.x == 0 && t_app + 2 < 16)
+                timeline[t_app + 2] = (unsigned long long)gtimer();
+            continue;
+        }
         const int per_wave = gridDim.x / ntiles;
         const int nwaves = (a.B + per_wave - 1) / per_wave;
         bool ok = true;
@@ -689,18 +847,6 @@ __global__ void __launch_bounds__(kBlockThreads, 1) chain2d_batched_kernel(const
 
 // ---------------------------------------------------------------- host ----
 
-size_t chain2d_workspace_bytes(int64_t B, int64_t C, int64_t H, int64_t W, int tiles) {
-    (void)C;
-    auto al = [](size_t x) { return (x + 255) & ~size_t(255); };
-    const int64_t Wp = (W + 3) & ~int64_t(3), Hp = (H + 3) & ~int64_t(3);
-    size_t n = kHeaderBytes;
-    n += al((size_t)B * tiles * 4 * kMaxRing * 8);
-    n += al((size_t)B * H * Wp * 4);
-    n += al((size_t)B * W * Hp * 4);
-    n += al((size_t)B * 3 * H * Wp * 4);
-    n += al((size_t)B * 3 * W * Hp * 4);
-    return n;
-}
 
 int chain2d_geometry(int64_t H, int64_t W, const fgx_options* opt, int* K, int* T, int* tv,
                      int* th) {
@@ -726,10 +872,12 @@ namespace {
 // counter are `hdr`'s, the exchange words start at `xb`, the other buffers
 // (Dw, Dt, Ev, Eh) are laid out from `sec` (any of them null for a size
 // query).  Returns the bytes from `sec`; *xbytes receives the exchange bytes.
+// max_seg: exchange areas per image (kMaxSeg for speculative segments, 1
+// without); the segment counts themselves are set by the caller (1 here).
 size_t fill_chain_args(Chain2DArgs* a, const float* image, const float* mask, float* dist,
                        uint8_t* codes, int64_t B, int64_t C, int64_t H, int64_t W, float v,
                        float lambda, int iterations, const fgx_options* opt, char* hdr, char* xb,
-                       char* sec, size_t* xbytes) {
+                       char* sec, size_t* xbytes, int max_seg) {
     std::memset(a, 0, sizeof(*a));
     int K, T, tv, th;
     chain2d_geometry(H, W, opt, &K, &T, &tv, &th);
@@ -763,8 +911,19 @@ size_t fill_chain_args(Chain2DArgs* a, const float* image, const float* mask, fl
     auto al = [](size_t x) { return (x + 255) & ~size_t(255); };
     a->status = (int*)hdr;
     a->barrier = (unsigned int*)(hdr ? hdr + 64 : nullptr);
+    // no segment areas where no pass can be split
+    if (std::max(H, W) < 2 * kMinSegLines || B > kMaxSegImages || (opt && opt->segments == 1))
+        max_seg = 1;
+    a->nseg_v = a->nseg_h = 1;
+    a->seglen_v = (int)H;
+    a->seglen_h = (int)W;
+    a->max_seg = max_seg;
+    a->bnd_ld = (int)((std::max(H, W) + 3) & ~int64_t(3));
     a->xbuf = (unsigned long long*)xb;
-    *xbytes = al((size_t)B * max_tiles * 4 * kMaxRing * 8);
+    *xbytes = al((size_t)B * max_seg * max_tiles * 4 * kMaxRing * 8);
+    // segment flags live in the zeroed exchange area
+    a->segflag = (unsigned int*)(xb && max_seg > 1 ? xb + *xbytes : nullptr);
+    if (max_seg > 1) *xbytes += al((size_t)B * kMaxSeg * 2 * 4);
     size_t off = 0;
     a->Dw = (float*)(sec ? sec + off : nullptr);
     off += al((size_t)B * H * a->Wp * 4);
@@ -774,10 +933,42 @@ size_t fill_chain_args(Chain2DArgs* a, const float* image, const float* mask, fl
     off += al((size_t)B * 3 * H * a->Wp * 4);
     a->Eh = (float*)(sec ? sec + off : nullptr);
     off += al((size_t)B * 3 * W * a->Hp * 4);
+    a->bnd = (float*)(sec && max_seg > 1 ? sec + off : nullptr);
+    if (max_seg > 1) off += al((size_t)B * (kMaxSeg - 1) * a->bnd_ld * 4);
     return off;
 }
 
+// Segments per pass for a grid of `blocks` resident blocks: as many as fit
+// (all images' tiles of every segment at once), at least kMinSegLines lines
+// each, at most `want` (0: kMaxSeg).
+void choose_segments(Chain2DArgs* a, int64_t blocks, int want) {
+    const int cap = want > 0 ? std::min(want, kMaxSeg) : kMaxSeg;
+    auto pick = [&](int L, int tiles, int* nseg, int* seglen) {
+        *nseg = 1;
+        *seglen = L;
+        if (a->max_seg <= 1 || a->B > kMaxSegImages) return;
+        int S = (int)std::min<int64_t>(cap, blocks / ((int64_t)a->B * tiles));
+        S = std::min(S, L / kMinSegLines);
+        if (S < 2) return;
+        const int len = ((L + S - 1) / S + kCh - 1) / kCh * kCh;
+        *seglen = len;
+        *nseg = (L + len - 1) / len;
+        if (*nseg < 2) { *nseg = 1; *seglen = L; }
+    };
+    pick(a->H, a->tiles_v, &a->nseg_v, &a->seglen_v);
+    pick(a->W, a->tiles_h, &a->nseg_h, &a->seglen_h);
+}
+
 }  // namespace
+
+size_t chain2d_workspace_bytes(int64_t B, int64_t C, int64_t H, int64_t W,
+                               const fgx_options* opt) {
+    Chain2DArgs a;
+    size_t xbytes = 0;
+    const size_t sec = fill_chain_args(&a, nullptr, nullptr, nullptr, nullptr, B, C, H, W, 1.0f,
+                                       0.5f, 1, opt, nullptr, nullptr, nullptr, &xbytes, kMaxSeg);
+    return kHeaderBytes + xbytes + sec;
+}
 
 int run_chain2d(const float* image, const float* mask, float* dist, uint8_t* codes, int64_t B,
                 int64_t C, int64_t H, int64_t W, float v, float lambda, int iterations,
@@ -786,11 +977,11 @@ int run_chain2d(const float* image, const float* mask, float* dist, uint8_t* cod
     char* p = (char*)workspace;
     size_t xbytes = 0;
     fill_chain_args(&a, image, mask, dist, codes, B, C, H, W, v, lambda, iterations, opt, nullptr,
-                    nullptr, nullptr, &xbytes);
+                    nullptr, nullptr, &xbytes, kMaxSeg);
     const size_t need = kHeaderBytes + xbytes +
                         fill_chain_args(&a, image, mask, dist, codes, B, C, H, W, v, lambda,
                                         iterations, opt, p, p + kHeaderBytes,
-                                        p + kHeaderBytes + xbytes, &xbytes);
+                                        p + kHeaderBytes + xbytes, &xbytes, kMaxSeg);
     if (ws_bytes < need) return FGX_ERR_WORKSPACE;
     const int max_tiles = a.max_tiles;
 
@@ -807,7 +998,16 @@ int run_chain2d(const float* image, const float* mask, float* dist, uint8_t* cod
     // many as fit (images then run in waves)
     int64_t grid = (int64_t)per_sm * sms;
     if (opt && opt->max_blocks) grid = std::min<int64_t>(grid, opt->max_blocks);
-    grid = std::max<int64_t>(1, std::min<int64_t>(grid, B * max_tiles));
+    // speculative segments: by default one block per SM; a forced count may
+    // use every resident block.  Not with codes: a re-run over speculative
+    // values would take a value already reached for one kept, so the codes
+    // variant runs each pass as one chain.
+    const int want = opt ? opt->segments : 0;
+    if (!codes) choose_segments(&a, want > 0 ? grid : std::min<int64_t>(grid, sms), want);
+    const int64_t seg_blocks = std::max<int64_t>((int64_t)a.nseg_v * a.tiles_v,
+                                                 (int64_t)a.nseg_h * a.tiles_h);
+    grid = std::max<int64_t>(1, std::min<int64_t>(grid, B * std::max<int64_t>(max_tiles,
+                                                                               seg_blocks)));
     if (grid < max_tiles) return FGX_ERR_UNSUPPORTED;
     if (B > 65535 || (a.Hp + kInitTile - 1) / kInitTile > 65535) return FGX_ERR_UNSUPPORTED;
     cudaStream_t s = (cudaStream_t)stream;
@@ -846,7 +1046,7 @@ size_t chain2d_instance_desc(void* desc, const fgx_instance& it, const fgx_optio
     Chain2DArgs a;
     const size_t n = fill_chain_args(&a, it.image, it.mask, it.dist, nullptr, 1, it.channels,
                                      it.H, it.W, it.v, it.lambda, it.iterations, opt, hdr, xb,
-                                     sec, xbytes);
+                                     sec, xbytes, 1);
     if (desc) std::memcpy(desc, &a, sizeof(a));
     *tiles_v = a.tiles_v;
     *tiles_h = a.tiles_h;

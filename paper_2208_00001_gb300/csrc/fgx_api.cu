@@ -117,7 +117,7 @@ int plan_forward(int ndim, int64_t B, int64_t C, int64_t D, int64_t H, int64_t W
                  Plan* pl) {
     if (opt && opt->size != sizeof(fgx_options)) return FGX_ERR_ARG;
     if (opt && (opt->tile_lines < 0 || opt->tile_width < 0 || opt->tile_height < 0 ||
-                opt->max_blocks < 0 || opt->timeout_ms < 0))
+                opt->max_blocks < 0 || opt->timeout_ms < 0 || opt->segments < 0))
         return FGX_ERR_ARG;
     if (ndim != 2 && ndim != 3) return FGX_ERR_ARG;
     if (B < 0 || C < 1 || D < 0 || H < 0 || W < 0) return FGX_ERR_SHAPE;
@@ -190,11 +190,7 @@ int plan_forward(int ndim, int64_t B, int64_t C, int64_t D, int64_t H, int64_t W
     pl->sms = dev.sms;
     pl->ws_bytes = kHeaderBytes + (size_t)std::max<int64_t>(B, 1) * max_tiles * 8;
     pl->chain_bytes = 0;
-    if (ndim == 2) {
-        int K, T, tv, th;
-        chain2d_geometry(H, W, opt, &K, &T, &tv, &th);
-        pl->chain_bytes = chain2d_workspace_bytes(B, C, H, W, std::max(tv, th));
-    }
+    if (ndim == 2) pl->chain_bytes = chain2d_workspace_bytes(B, C, H, W, opt);
     if (ndim == 3) pl->vol3d_bytes = vol3d_workspace_bytes(a, opt, dev.sms);
     return FGX_OK;
 }

@@ -132,7 +132,8 @@ void pass_offsets_t(int ndim, int axis, const float sp[3], float lambda, float t
 void pass_extents(int axis, const int64_t ext[3], PassGeom* g);
 
 // 2D warp-chain forward (chain2d.cu)
-size_t chain2d_workspace_bytes(int64_t B, int64_t C, int64_t H, int64_t W, int tiles);
+size_t chain2d_workspace_bytes(int64_t B, int64_t C, int64_t H, int64_t W,
+                               const fgx_options* opt);
 int chain2d_geometry(int64_t H, int64_t W, const fgx_options* opt, int* K, int* T, int* tv,
                      int* th);
 // 3D forward on register-blocked plane tiles (vol3d.cu): workspace bytes, 0

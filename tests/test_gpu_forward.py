@@ -215,6 +215,31 @@ def test_fwd_train_codes_2d_multi_tile(fgx, lam, opts):
     np.testing.assert_array_equal(saved.cpu().numpy(), want_codes)
 
 
+@pytest.mark.parametrize("B,C,H,W,lam,its,segs,soft", [
+    (1, 3, 700, 900, 0.5, 2, 3, False),   # converged second iteration: no re-runs
+    (1, 1, 1000, 300, 1.0, 3, 5, False),  # five row segments, four column segments
+    (2, 1, 512, 640, 0.0, 2, 4, False),   # two images, constant costs
+    (1, 2, 400, 400, 0.3, 1, 6, True),    # soft mask: start lines change, re-runs
+    (1, 1, 300, 2000, 0.8, 2, 8, True),   # short columns: fewer column segments
+])
+def test_speculative_segments_2d(fgx, B, C, H, W, lam, its, segs, soft):
+    """Passes split into line segments that run at once from the old start
+    lines, re-run in order where a start line changed: bit-exact to the
+    oracle, and equal to the unsegmented kernel."""
+    rng = np.random.default_rng(B * 1000 + H + W)
+    img = np.stack([np.stack([workloads.blurred_noise(rng, (H, W)) for _ in range(C)])
+                    for _ in range(B)])
+    if soft:
+        m = rng.uniform(0, 1, (B, 1, H, W)).astype(np.float32)
+    else:
+        m = np.stack([workloads.seed_block_mask(rng, (H, W), 5, 3)[None] for _ in range(B)])
+    case = workloads.Case("segments", img.astype(np.float32), m.astype(np.float32),
+                          10.0 if soft else 1e10, lam, its)
+    want = oracle_run(case)
+    assert_bit_exact(gpu_run(fgx, case, options=dict(segments=segs)), want)
+    assert_bit_exact(gpu_run(fgx, case, options=dict(segments=1)), want)
+
+
 # ----------------------------------------------------------------- errors
 
 def test_error_codes(fgx):
