@@ -427,6 +427,7 @@ def run_fgx(args):
     peak, peak_kind = _peaks()
     achieved = bytes_per_launch / t_step / 1e9
     traffic = _profile_traffic("chain2d_kernel_2d_large")
+    serial_steps = its * 2 * ((H - 1) + (W - 1))
 
     # end-to-end through the public API with host buffers
     h_img = torch.from_numpy(case.image).pin_memory()
@@ -475,7 +476,14 @@ def run_fgx(args):
         "e2e": {"value": world * N * its / t_e2e / 1e6, "unit": "Mvoxel/s",
                 "h2d_bytes_per_step": int(h_img.numel() * 4 + h_m.numel() * 4),
                 "d2h_bytes_per_step": int(h_out.numel() * 4)},
-        "gpu_launches": args.steps,
+        # per step: the table/initialisation kernel and the persistent sweep kernel
+        "gpu_launches": 2 * args.steps,
+        # the serial chain of line steps (a pass updates line l from line l-1)
+        # against the HBM bound: the former binds
+        "critical_path": {"serial_line_steps": serial_steps,
+                          "ns_per_serial_step": t_step * 1e9 / serial_steps,
+                          "hbm_bound_ms": bytes_per_launch / (peak * 1e9) * 1e3,
+                          "binds": "line-step latency"},
         "clocks": clk.summary(),
     }
     if not args.no_cpu_baseline and args.size == 2048:

@@ -44,8 +44,9 @@ namespace {
 
 constexpr int kRegion = 128;           // columns per tile region (4 per lane)
 constexpr int kMaxSeg = 8;             // speculative segments per pass at most
-constexpr int kMinSegLines = 64;       // shortest segment worth a separate chain
+constexpr int kMinSegLines = 256;      // shortest segment worth a separate chain
 constexpr int kMaxSegImages = 128;     // images of one call that segments are used for
+constexpr int kMaxCk = 64;             // checkpoints of one re-run at most
 constexpr int kBlockThreads = 96;      // chain, producer and flusher warps
 #define kInf __int_as_float(0x7f800000)
 
@@ -78,6 +79,7 @@ struct Chain2DArgs {
     int bnd_ld;              // floats per boundary line (max(H, W) rounded up)
     float* bnd;              // [B][kMaxSeg - 1][bnd_ld] boundary lines the segments started from
     unsigned int* segflag;   // [B][kMaxSeg][2]: boundary changed (phase A, re-run), tag t_app + 1
+    unsigned int* ckpt;      // [B][kMaxSeg][kMaxCk]: re-run checkpoints (arrivals | changed << 16)
 };
 
 using namespace dev;
@@ -114,6 +116,8 @@ struct TileSmem {
     // out_empty: the flusher has written an output slot out
     unsigned long long in_full[kNci], done[kNci], out_empty[kNo];
     unsigned long long pad_[2 - (2 * kNci + kNo) % 2];  // keeps the rings 16-byte aligned
+    int stop_chunk;                 // a re-run stopped early: chunks from here are skipped
+    int pad2_[3];
     float in[kNci][kCh][4][kRow];   // per line: old values, edge rows E0, E1, E2
     float out[kNo][kCh][kOutLd];    // chain results per line
     uint8_t outc[kNo][kCh][kRegion];  // parent codes per line (when recorded)
@@ -147,7 +151,11 @@ struct TileGeo {
     int bstride;
     const float* cmp;        // line the next segment started from (element q at q), or null
     unsigned int* flag;      // set to flag_tag when the last line differs from it
+    const unsigned int* flag_first;  // the flag the first run set (a re-run that stops early
+                                     // keeps the first run's last line)
     unsigned int flag_tag;
+    unsigned int* ck;        // re-run checkpoints of this image and segment, or null
+    int ck_every;            // chunks between checkpoints
 };
 
 // Line of step s of a pass in sweep order.
@@ -193,7 +201,10 @@ __device__ __forceinline__ TileGeo tile_geo(const Chain2DArgs& a, int t_app, int
     g.bstride = 1;
     g.cmp = nullptr;
     g.flag = nullptr;
+    g.flag_first = nullptr;
     g.flag_tag = (unsigned int)(t_app + 1);
+    g.ck = nullptr;
+    g.ck_every = 1;
     if (seg > 0) {
         if (rerun) {
             // the exact line before the segment, as the pass wrote it
@@ -207,7 +218,18 @@ __device__ __forceinline__ TileGeo tile_geo(const Chain2DArgs& a, int t_app, int
     }
     if (seg + 1 < nseg) {
         g.cmp = a.bnd + ((int64_t)b * (kMaxSeg - 1) + seg) * a.bnd_ld;
-        g.flag = a.segflag + ((int64_t)b * kMaxSeg + seg + 1) * 2 + (rerun ? 1 : 0);
+        unsigned int* f = a.segflag + ((int64_t)b * kMaxSeg + seg + 1) * 2;
+        g.flag = f + (rerun ? 1 : 0);
+        g.flag_first = f;
+    }
+    // a re-run can stop early where the first run's values are its old
+    // values: in the passes that update their lines in place
+    const bool fwd = pass == 0 || pass == 2;
+    if (seg > 0 && rerun && fwd) {
+        g.ck = a.ckpt + ((int64_t)b * kMaxSeg + seg) * kMaxCk;
+        const int base = g.multi ? g.K / kCh : 5;
+        const int npts = (g.nch + base - 1) / base;
+        g.ck_every = base * ((npts + kMaxCk - 2) / (kMaxCk - 1));
     }
     return g;
 }
@@ -230,6 +252,11 @@ __device__ bool producer_tile(const Chain2DArgs& a, const TileGeo& g, TileSmem& 
             !__all_sync(0xffffffffu, mbar_wait(&sm.done[slot], empty_parity(gc, kNci), a))) {
             cp_async_wait_all();
             return false;
+        }
+        if (c >= *(volatile int*)&sm.stop_chunk) {
+            // a re-run that stopped early: the chunk is only handed over
+            mbar_arrive(&sm.in_full[slot]);
+            continue;
         }
         const int jn = min(kCh, g.ns - c * kCh);
         for (int j = 0; j < jn; ++j) {
@@ -274,6 +301,12 @@ __device__ bool flusher_tile(const Chain2DArgs& a, const TileGeo& g, TileSmem& s
             return false;
         const int s0 = g.s0 + c * kCh;
         const int nl = min(kCh, g.ns - c * kCh);
+        if (c >= *(volatile int*)&sm.stop_chunk) {
+            // a re-run that stopped early: these lines already hold their values
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&sm.out_empty[slot]);
+            continue;
+        }
         if (fwd) {
             // rows of the output array: each lane writes its own four columns
             float4 v[kCh];
@@ -442,11 +475,61 @@ __device__ __forceinline__ bool exchange(const Chain2DArgs& a, const TileGeo& g,
                          tg, par, dp, valid, kInf);
 }
 
+// Checkpoint k >= 1 of a re-run (at a chunk boundary; dp holds the last
+// line of the previous chunk, dl that line's old values, i.e. the first
+// run's).  Each tile adds one arrival to the checkpoint's word, plus 1 << 16
+// if its owned columns of that line changed (a single reduction: no fence).
+// The decision at checkpoint k concerns checkpoint k - kCkLag, whose word
+// was read one checkpoint earlier (pv) and is complete by then unless a tile
+// lags that far behind (then it is read again until complete): a line in
+// which no column changed means every later line equals the first run's (the
+// same line step from the same line), so all tiles stop at this chunk.
+// Returns false on a failed wait.
+constexpr int kCkLag = 2;
+__device__ __forceinline__ bool checkpoint(const Chain2DArgs& a, const TileGeo& g, int k,
+                                           const float (&dp)[4], const float (&dl)[4], int c0,
+                                           unsigned int& pv, bool& stop) {
+    const int lane = threadIdx.x & 31;
+    bool ch = false;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const int c = c0 + i;
+        if (c >= g.q0 && c < g.q1 && __float_as_uint(dp[i]) != __float_as_uint(dl[i])) ch = true;
+    }
+    ch = __any_sync(0xffffffffu, ch);
+    int verdict = 0;  // 0: go on, 1: stop, -1: failed
+    if (lane == 0) {
+        atomicAdd(g.ck + k, ch ? 0x10001u : 1u);
+        if (k > kCkLag) {
+            const unsigned int want = (unsigned int)g.ntiles;
+            long long t0 = 0;
+            for (unsigned int it = 0; (pv & 0xffffu) < want; ++it) {
+                pv = ld_relaxed_u32(g.ck + k - kCkLag);
+                if ((it & 15u) == 15u) {
+                    const long long now = gtimer();
+                    if (t0 == 0) t0 = now;
+                    if (status_of(a.status) != 0) { verdict = -1; break; }
+                    if (now - t0 > a.timeout_ns) {
+                        record_timeout(a.status);
+                        verdict = -1;
+                        break;
+                    }
+                }
+            }
+            if (verdict == 0 && (pv >> 16) == 0u) verdict = 1;
+        }
+        if (k + 1 > kCkLag) pv = ld_relaxed_u32(g.ck + k + 1 - kCkLag);  // for the next checkpoint
+    }
+    verdict = __shfl_sync(0xffffffffu, verdict, 0);
+    stop = verdict == 1;
+    return verdict >= 0;
+}
+
 // Chain warp.  Line j of chunk c is step s = kCh*c + j; the first step (the
 // first line of the sweep, which has no parents) runs with +inf parents and
 // so keeps the old values.  AHEAD lines of input are held in registers ahead
 // of the step that uses them.
-template <bool fwd, bool table, bool codes, int AHEAD>
+template <bool fwd, bool table, bool codes, int AHEAD, bool CK>
 __device__ bool chain_tile(const Chain2DArgs& a, const TileGeo& g, int t_app, int b, int tile,
                            TileSmem& sm, unsigned int cb, float k0, float k1, float k2) {
     constexpr int NB = AHEAD == 1 ? 2 : 4;  // register buffers (divides kCh)
@@ -481,6 +564,8 @@ __device__ bool chain_tile(const Chain2DArgs& a, const TileGeo& g, int t_app, in
     // test found the chunk not ready yet.
     bool in_ready = g.nch < 2 || mbar_peek(&sm.in_full[i1.slot], i1.par);
     bool out_ready = cb < (unsigned)kNo || mbar_peek(&sm.out_empty[o0.slot], o0.par ^ 1u);
+    bool skip = false;  // a re-run found its values equal to the first run's
+    unsigned int ck_prev = 0;  // checkpoint word read one checkpoint earlier
     for (int c = 0; c < g.nch; ++c) {
         const unsigned int gc = cb + c;
         const int slot = i0.slot, nslot = i1.slot, oslot = o0.slot;
@@ -497,11 +582,24 @@ __device__ bool chain_tile(const Chain2DArgs& a, const TileGeo& g, int t_app, in
         i2 = i2.next(kNci);
         o0 = o1;
         o1 = o1.next(kNo);
-        if (c * kCh == next_refresh) {
+        if (!skip && c * kCh == next_refresh) {
             if (!exchange(a, g, b, tile, tag_base | (unsigned int)(blk + 1), blk & 1, dp, valid))
                 return false;
             next_refresh += g.K;
             ++blk;
+        }
+        if (CK && !skip && c > 0 && c % g.ck_every == 0) {
+            if (!checkpoint(a, g, c / g.ck_every, dp, buf[(kCh - 1) % NB].dold, c0, ck_prev,
+                            skip))
+                return false;
+            if (skip && lane == 0) *(volatile int*)&sm.stop_chunk = c;
+        }
+        if (CK && skip) {
+            // the rest of the segment keeps the first run's values: chunks
+            // are only handed over
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&sm.done[slot]);
+            continue;
         }
         const float(*cur)[4][kRow] = sm.in[slot];
         const float(*nxt)[4][kRow] = sm.in[nslot];
@@ -518,7 +616,11 @@ __device__ bool chain_tile(const Chain2DArgs& a, const TileGeo& g, int t_app, in
         __syncwarp();
         if (lane == 0) mbar_arrive(&sm.done[slot]);
     }
-    if (g.cmp) {
+    if (CK && skip) {
+        // the last line is the first run's: so is its comparison
+        if (g.flag && lane == 0 && ld_relaxed_u32(g.flag_first) == g.flag_tag)
+            atomicMax(g.flag, g.flag_tag);
+    } else if (g.cmp) {
         // the segment's last line against the line the next segment started from
         bool diff = false;
 #pragma unroll
@@ -633,7 +735,7 @@ __global__ void __launch_bounds__(256) chain2d_init_batched_kernel(const Chain2D
 
 // Not inlined: the pass driver calls it from two places, and each variant's
 // chain loop keeps its own register allocation.
-template <bool fwd, bool table, bool codes>
+template <bool fwd, bool table, bool codes, bool CK = false>
 __device__ __noinline__ bool run_tile(const Chain2DArgs& a, int t_app, int pass, int b, int tile,
                          TileSmem& sm, unsigned int cb, int seg, bool rerun, int nseg) {
     const TileGeo g = tile_geo(a, t_app, pass, b, tile, seg, rerun, nseg);
@@ -643,7 +745,7 @@ __device__ __noinline__ bool run_tile(const Chain2DArgs& a, int t_app, int pass,
         const float k0 = vert ? a.cv[0] : a.chh[0];
         const float k1 = vert ? a.cv[1] : a.chh[1];
         const float k2 = vert ? a.cv[2] : a.chh[2];
-        return chain_tile<fwd, table, codes, table ? 2 : 1>(a, g, t_app, b, tile, sm, cb, k0, k1,
+        return chain_tile<fwd, table, codes, table ? 2 : 1, CK>(a, g, t_app, b, tile, sm, cb, k0, k1,
                                                             k2);
     }
     if (warp == 1) return producer_tile<fwd, table>(a, g, sm, cb);
@@ -654,6 +756,12 @@ template <bool codes>
 __device__ __forceinline__ bool run_pass_tile(const Chain2DArgs& a, bool fwd, int t_app, int pass,
                                               int b, int tile, TileSmem& sm, unsigned int cb,
                                               int seg = 0, bool rerun = false, int nseg = 1) {
+    // re-runs of in-place passes carry the early-stop checkpoints
+    const bool ck = rerun && seg > 0 && !codes;
+    if (fwd && a.table && ck)
+        return run_tile<true, true, false, true>(a, t_app, pass, b, tile, sm, cb, seg, rerun, nseg);
+    if (fwd && ck)
+        return run_tile<true, false, false, true>(a, t_app, pass, b, tile, sm, cb, seg, rerun, nseg);
     if (fwd && a.table)
         return run_tile<true, true, codes>(a, t_app, pass, b, tile, sm, cb, seg, rerun, nseg);
     if (fwd)
@@ -674,8 +782,10 @@ __device__ __forceinline__ bool run_pass_tile(const Chain2DArgs& a, bool fwd, in
 // chain)).  Phase B visits the segments in order: segment j runs again when
 // the exact last line of segment j-1 differs from the line j started from
 // (each segment's chain compares its last line and sets the boundary's
-// flag).  Every block takes the same decisions from the same flags, so all
-// blocks meet the same grid barriers.
+// flag).  In the passes that update their lines in place a re-run reads the
+// first run's values as old values and stops as soon as a whole line equals
+// them (checkpoints every ring refresh).  Every block takes the same decisions
+// from the same flags, so all blocks meet the same grid barriers.
 template <bool codes>
 __device__ bool run_pass_segments(const Chain2DArgs& a, int t_app, int pass, int S, int ntiles,
                                   TileSmem& sm, unsigned int& cb, unsigned int& epoch,
@@ -689,6 +799,10 @@ __device__ bool run_pass_segments(const Chain2DArgs& a, int t_app, int pass, int
     const int seg = active ? (u / ntiles) % S : 0;
     const int tile = u % ntiles;
     // phase A.1: save the owned columns of the line before each segment
+    if (active && seg > 0 && tile == 0) {
+        unsigned int* ck = a.ckpt + ((int64_t)b * kMaxSeg + seg) * kMaxCk;
+        for (int i = threadIdx.x; i < kMaxCk; i += blockDim.x) ck[i] = 0u;
+    }
     if (active && seg > 0) {
         const TileGeo g = tile_geo(a, t_app, pass, b, tile, seg, false, S);
         const int line = line_of(fwd, L, g.s0 - 1);
@@ -711,6 +825,7 @@ __device__ bool run_pass_segments(const Chain2DArgs& a, int t_app, int pass, int
         for (int i = 0; i < a.B; ++i) rr[i] = 0;
     const unsigned int tag = (unsigned int)(t_app + 1);
     for (int j = 1; j < S; ++j) {
+        if (threadIdx.x == 0) sm.stop_chunk = 0x7fffffff;
         __syncthreads();
         if (threadIdx.x == 0) {
             any = 0;
@@ -731,6 +846,8 @@ __device__ bool run_pass_segments(const Chain2DArgs& a, int t_app, int pass, int
         }
         if (!grid_barrier(a.barrier, epoch++, a.status, a.timeout_ns) || !ok) return false;
     }
+    if (threadIdx.x == 0) sm.stop_chunk = 0x7fffffff;
+    __syncthreads();
     return true;
 }
 
@@ -757,6 +874,7 @@ __global__ void __launch_bounds__(kBlockThreads, 1) chain2d_kernel(const Chain2D
             mbar_init(&sm.done[i], 1);
         }
         for (int i = 0; i < kNo; ++i) mbar_init(&sm.out_empty[i], 1);
+        sm.stop_chunk = 0x7fffffff;
     }
     __syncthreads();
     unsigned long long* timeline = (unsigned long long*)((char*)a.status + 128);
@@ -822,6 +940,7 @@ __global__ void __launch_bounds__(kBlockThreads, 1) chain2d_batched_kernel(const
             mbar_init(&sm.done[i], 1);
         }
         for (int i = 0; i < kNo; ++i) mbar_init(&sm.out_empty[i], 1);
+        sm.stop_chunk = 0x7fffffff;  // no early stops in batched runs
     }
     __syncthreads();
     unsigned int epoch = 1;
@@ -935,6 +1054,8 @@ size_t fill_chain_args(Chain2DArgs* a, const float* image, const float* mask, fl
     off += al((size_t)B * 3 * W * a->Hp * 4);
     a->bnd = (float*)(sec && max_seg > 1 ? sec + off : nullptr);
     if (max_seg > 1) off += al((size_t)B * (kMaxSeg - 1) * a->bnd_ld * 4);
+    a->ckpt = (unsigned int*)(sec && max_seg > 1 ? sec + off : nullptr);
+    if (max_seg > 1) off += al((size_t)B * kMaxSeg * kMaxCk * 4);
     return off;
 }
 

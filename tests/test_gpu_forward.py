@@ -221,6 +221,7 @@ def test_fwd_train_codes_2d_multi_tile(fgx, lam, opts):
     (2, 1, 512, 640, 0.0, 2, 4, False),   # two images, constant costs
     (1, 2, 400, 400, 0.3, 1, 6, True),    # soft mask: start lines change, re-runs
     (1, 1, 300, 2000, 0.8, 2, 8, True),   # short columns: fewer column segments
+    (1, 1, 1500, 500, 0.5, 2, 3, True),   # long segments: re-runs that stop early
 ])
 def test_speculative_segments_2d(fgx, B, C, H, W, lam, its, segs, soft):
     """Passes split into line segments that run at once from the old start
