@@ -58,6 +58,7 @@ constexpr int kMaxCI = 3;                 // intensity channels the stage holds
 constexpr int kBlock3 = (kCW + kPW) * 32;
 constexpr int kXWords = kTP * kTQ;        // published words per tile and parity
 constexpr int kRangeFlagOffset = 32;      // workspace header: intensity range flag
+constexpr int kTransposeWarps = 8;        // warps of a block that transpose (8 shared tiles)
 #define kInf3 __int_as_float(0x7f800000)
 
 enum { kModeConst = 0, kModeAbs = 1, kModeGeneral = 2 };
@@ -79,6 +80,11 @@ struct Vol3DArgs {
     int* status;
     const int* range_flag;     // nonzero: some intensity outside the |d| range
     long long timeout_ns;
+    // W passes on transposed copies (planes of those passes have H as their
+    // contiguous axis, so staging loads and result stores are coalesced):
+    float* distT;              // [B][W][D][H], or null (W passes on dist itself)
+    float* imageT;             // [B][C][W][D][H] (cost modes that read intensities)
+    int64_t D, H, W;
 };
 
 struct Head3 {
@@ -146,6 +152,8 @@ __device__ __forceinline__ void compute_sync() {
 // Position of one tile of one pass application.
 struct Tile3 {
     const PassGeom* g;
+    float* dist;       // distances of this instance in the pass's layout
+    const float* img;  // intensities of this instance in the pass's layout
     int jp, jq, ntq, tile;
     int64_t b;
     int L, nch;
@@ -167,8 +175,8 @@ __device__ bool producer3(const Vol3DArgs& a, const Tile3& t, Head3& h, float* s
     const int lane = threadIdx.x & 31, pw = (threadIdx.x >> 5) - kCW;
     const int64_t q = t.q0 + lane;
     const bool qin = q >= 0 && q < g.Q;
-    const float* img = a.image + t.b * a.C * a.N;
-    const float* dist = a.dist + t.b * a.N;
+    const float* img = t.img;
+    const float* dist = t.dist;
     for (int c = 0; c < t.nch; ++c) {
         const unsigned int gc = cb + c;
         const int slot = (int)(gc % kNst);
@@ -316,7 +324,7 @@ __device__ bool compute3(const Vol3DArgs& a, const Tile3& t, int t_app, Head3& h
         own[i] = valid[i] && qown && r >= kRing && r < kRing + kTP;
         goff[i] = p * g.sp + q * g.sq;
     }
-    float* dist = a.dist + t.b * a.N;
+    float* dist = t.dist;
     uint8_t* codes = CODES ? a.codes + ((int64_t)t_app * a.B + t.b) * a.N : nullptr;
     const float lam = a.lambda;
     float tk[9], ck[9];
@@ -455,6 +463,54 @@ __global__ void __launch_bounds__(256) init3d_kernel(const float* mask, float* d
     }
 }
 
+// Transposes `count` arrays of R x W floats (R = D*H) into W x R (back:
+// W x R into R x W).  Each of `nwarps` warps of a block moves whole 32 x 32
+// tiles through its own 32 x 33 shared tile (32 loads in flight per lane);
+// tiles are spread over all warps of the grid.  The sources may have been
+// written by other blocks of the same launch: read through L2.
+__device__ void transpose_rw(const float* src, float* dst, int64_t count, int64_t R, int64_t W,
+                             bool back, float* smem, int nwarps) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (warp < nwarps) {
+        float* tile = smem + warp * (32 * 33);
+        const int64_t rows = back ? W : R, cols = back ? R : W;  // of the source
+        const int64_t tr = (rows + 31) / 32, tc = (cols + 31) / 32;
+        const int64_t ntile = count * tr * tc;
+        for (int64_t ti = (int64_t)blockIdx.x * nwarps + warp; ti < ntile;
+             ti += (int64_t)gridDim.x * nwarps) {
+            const int64_t c = ti / (tr * tc), rem = ti - c * (tr * tc);
+            const int64_t r0 = (rem / tc) * 32, c0 = (rem % tc) * 32;
+            const float* S = src + c * R * W;
+            float* Dd = dst + c * R * W;
+            float v[32];
+#pragma unroll
+            for (int y = 0; y < 32; ++y) {
+                const int64_t r = r0 + y, cc = c0 + lane;
+                v[y] = (r < rows && cc < cols) ? __ldcg(S + r * cols + cc) : 0.0f;
+            }
+            __syncwarp();
+#pragma unroll
+            for (int y = 0; y < 32; ++y) tile[y * 33 + lane] = v[y];
+            __syncwarp();
+#pragma unroll
+            for (int y = 0; y < 32; ++y) {
+                const int64_t cc = c0 + y, r = r0 + lane;
+                if (cc < cols && r < rows) Dd[cc * rows + r] = tile[lane * 33 + y];
+            }
+        }
+    }
+    __syncthreads();
+}
+
+// The image in the W passes' layout, once per call (all SMs, before the
+// persistent launch).
+__global__ void __launch_bounds__(256) transpose_image3d_kernel(const float* image, float* imageT,
+                                                                int64_t count, int64_t R,
+                                                                int64_t W) {
+    __shared__ float smem[8 * 32 * 33];
+    transpose_rw(image, imageT, count, R, W, false, smem, 8);
+}
+
 template <int MODE, int CI, bool CODES = false>
 __device__ __forceinline__ bool run_tile3(const Vol3DArgs& a, const Tile3& t, int t_app, Head3& h,
                                           float* stage, unsigned int cb, bool checked) {
@@ -483,9 +539,17 @@ __global__ void __launch_bounds__(kBlock3, 1) vol3d_kernel(const Vol3DArgs a) {
     unsigned int cb = 0;  // staging chunks handed over so far in this block
     const int napps = a.iterations * kMaxPasses;
     bool alive = true;
+    const bool tw = a.distT != nullptr;
+    const int64_t R = a.D * a.H;
+
     for (int t_app = 0; t_app < napps && alive; ++t_app) {
         const int pass = t_app % kMaxPasses;
         const PassGeom& g = a.pass[pass];
+        const bool on_t = tw && pass >= 4;  // this pass runs on the transposed copies
+        if (tw && pass == 4) {
+            transpose_rw(a.dist, a.distT, a.B, R, a.W, false, stage, kTransposeWarps);
+            if (!(alive = grid_barrier(a.barrier, epoch++, a.status, a.timeout_ns))) break;
+        }
         const int ntiles = a.ntp[pass] * a.ntq[pass];
         const int per_wave = gridDim.x / ntiles;
         const int64_t nwaves = (a.B + per_wave - 1) / per_wave;
@@ -502,6 +566,8 @@ __global__ void __launch_bounds__(kBlock3, 1) vol3d_kernel(const Vol3DArgs a) {
             t.jq = t.tile % a.ntq[pass];
             t.ntq = a.ntq[pass];
             t.b = b;
+            t.dist = (on_t ? a.distT : a.dist) + b * a.N;
+            t.img = (on_t ? a.imageT : a.image) + b * a.C * a.N;
             t.L = L;
             t.nch = nch;
             t.p0 = (int64_t)t.jp * kTP - kRing;
@@ -510,6 +576,10 @@ __global__ void __launch_bounds__(kBlock3, 1) vol3d_kernel(const Vol3DArgs a) {
             cb += (unsigned int)nch;
         }
         alive = grid_barrier(a.barrier, epoch++, a.status, a.timeout_ns);
+        if (alive && tw && pass == 5) {
+            transpose_rw(a.distT, a.dist, a.B, R, a.W, true, stage, kTransposeWarps);
+            alive = grid_barrier(a.barrier, epoch++, a.status, a.timeout_ns);
+        }
         if (blockIdx.x == 0 && threadIdx.x == 0 && t_app + 1 < 16)
             timeline[t_app + 1] = (unsigned long long)gtimer();
     }
@@ -581,6 +651,8 @@ __global__ void __launch_bounds__(kBlock3, 1) vol3d_batched_kernel(const Vol3DBa
             t.jq = t.tile % a.ntq[pass];
             t.ntq = a.ntq[pass];
             t.b = 0;
+            t.dist = a.dist;
+            t.img = a.image;
             t.L = (int)g.L;
             t.nch = t.L > 1 ? (t.L + kChunk - 1) / kChunk : 0;
             t.p0 = (int64_t)t.jp * kTP - kRing;
@@ -614,6 +686,8 @@ struct Vol3DPlan {
     int mode = 0, CI = 0, grid = 0, max_tiles = 0;
     int ntp[kMaxPasses] = {}, ntq[kMaxPasses] = {};
     size_t smem = 0, ws_bytes = 0;
+    size_t zero_bytes = 0;             // header and exchange words (cleared per call)
+    size_t distT_off = 0, imageT_off = 0;  // transposed copies for the W passes
 };
 
 // Whether the 3D call fits this kernel (at most kMaxCI channels in the
@@ -656,7 +730,11 @@ bool plan_vol3d(const SweepArgs& f, const fgx_options* opt, int sms, Vol3DPlan* 
     grid = std::min<int64_t>(grid, std::max<int64_t>(1, f.B * max_tiles));
     if (grid < max_tiles) return false;
     vp->grid = (int)grid;
-    vp->ws_bytes = kHeaderBytes + (size_t)std::max<int64_t>(f.B, 1) * max_tiles * 2 * kXWords * 8;
+    auto al = [](size_t x) { return (x + 255) & ~size_t(255); };
+    vp->zero_bytes = kHeaderBytes + (size_t)std::max<int64_t>(f.B, 1) * max_tiles * 2 * kXWords * 8;
+    vp->distT_off = al(vp->zero_bytes);
+    vp->imageT_off = vp->distT_off + al((size_t)f.B * f.N * 4);
+    vp->ws_bytes = vp->imageT_off + al((size_t)f.B * f.C * f.N * 4);
     return true;
 }
 
@@ -704,8 +782,21 @@ int run_vol3d(const SweepArgs& f, const float* image, const float* mask, float* 
     a.range_flag = range_flag;
     a.xbuf = (unsigned long long*)(w + kHeaderBytes);
     a.timeout_ns = f.timeout_ns;
+    a.D = f.pass[0].L;
+    a.H = f.pass[2].L;
+    a.W = f.pass[4].L;
+    if (!codes && a.W > 1) {
+        // the W passes run on [W][D][H] copies: their planes' rows are contiguous
+        a.distT = (float*)(w + vp.distT_off);
+        a.imageT = vp.mode == kModeConst ? nullptr : (float*)(w + vp.imageT_off);
+        for (int i = 4; i < 6; ++i) {
+            a.pass[i].sl = a.D * a.H;
+            a.pass[i].sp = a.H;
+            a.pass[i].sq = 1;
+        }
+    }
     cudaStream_t s = (cudaStream_t)stream;
-    if (cudaMemsetAsync(workspace, 0, vp.ws_bytes, s) != cudaSuccess) return FGX_ERR_CUDA;
+    if (cudaMemsetAsync(workspace, 0, vp.zero_bytes, s) != cudaSuccess) return FGX_ERR_CUDA;
     // codes of the first plane of every sweep stay 0 (it keeps its values)
     const size_t ncodes = (size_t)f.iterations * kMaxPasses * (size_t)(f.B * f.N);
     if (codes && ncodes && cudaMemsetAsync(codes, 0, ncodes, s) != cudaSuccess)
@@ -715,6 +806,11 @@ int run_vol3d(const SweepArgs& f, const float* image, const float* mask, float* 
     init3d_kernel<<<std::max(ig, 1), 256, 0, s>>>(mask, dist, v, n, image, f.B * f.C * f.N,
                                                  vp.mode == kModeAbs ? range_flag : nullptr);
     if (cudaGetLastError() != cudaSuccess) return FGX_ERR_CUDA;
+    if (a.imageT && f.iterations > 0) {
+        transpose_image3d_kernel<<<sms * 8, 256, 0, s>>>(image, a.imageT, f.B * f.C,
+                                                          a.D * a.H, a.W);
+        if (cudaGetLastError() != cudaSuccess) return FGX_ERR_CUDA;
+    }
     if (f.iterations == 0) return FGX_OK;
     cudaLaunchConfig_t cfg = {};
     cudaLaunchAttribute attr[1];
