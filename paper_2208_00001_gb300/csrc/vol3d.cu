@@ -154,6 +154,7 @@ struct Tile3 {
     const PassGeom* g;
     float* dist;       // distances of this instance in the pass's layout
     const float* img;  // intensities of this instance in the pass's layout
+    int64_t csl, csp, csq;  // strides of line, p and q in the image order of the codes
     int jp, jq, ntq, tile;
     int64_t b;
     int L, nch;
@@ -315,7 +316,7 @@ __device__ bool compute3(const Vol3DArgs& a, const Tile3& t, int t_app, Head3& h
     const bool qin = q >= 0 && q < g.Q;
     const bool qown = lane >= kRing && lane < kRing + kTQ;
     bool valid[kRows], own[kRows];
-    int64_t goff[kRows];
+    int64_t goff[kRows], goffc[CODES ? kRows : 1];
 #pragma unroll
     for (int i = 0; i < kRows; ++i) {
         const int r = w * kRows + i;
@@ -323,6 +324,7 @@ __device__ bool compute3(const Vol3DArgs& a, const Tile3& t, int t_app, Head3& h
         valid[i] = qin && p >= 0 && p < g.P;
         own[i] = valid[i] && qown && r >= kRing && r < kRing + kTP;
         goff[i] = p * g.sp + q * g.sq;
+        if (CODES) goffc[i] = p * t.csp + q * t.csq;
     }
     float* dist = t.dist;
     uint8_t* codes = CODES ? a.codes + ((int64_t)t_app * a.B + t.b) * a.N : nullptr;
@@ -403,7 +405,8 @@ __device__ bool compute3(const Vol3DArgs& a, const Tile3& t, int t_app, Head3& h
                 for (int ch = 0; ch < CI; ++ch)
                     ix[i][ch] = stage_plane(stage, slot, j, 1 + ch, CI)[(rows0 + i) * kRQ + lane];
         }
-        const int64_t lo = (int64_t)(g.dir > 0 ? s : (t.L - 1 - s)) * g.sl;
+        const int64_t line = g.dir > 0 ? s : (t.L - 1 - s);
+        const int64_t lo = line * g.sl;
 #pragma unroll
         for (int i = 0; i < kRows; ++i) {
             float best = Sd[(rows0 + i) * kRQ + lane];
@@ -425,7 +428,7 @@ __device__ bool compute3(const Vol3DArgs& a, const Tile3& t, int t_app, Head3& h
             d[i] = valid[i] ? best : kInf3;
             if (own[i]) {
                 dist[lo + goff[i]] = d[i];
-                if (CODES) codes[lo + goff[i]] = (uint8_t)code;
+                if (CODES) codes[line * t.csl + goffc[i]] = (uint8_t)code;
             }
         }
         if (s % kRing == 0 && s + 1 < t.L) {
@@ -568,6 +571,9 @@ __global__ void __launch_bounds__(kBlock3, 1) vol3d_kernel(const Vol3DArgs a) {
             t.b = b;
             t.dist = (on_t ? a.distT : a.dist) + b * a.N;
             t.img = (on_t ? a.imageT : a.image) + b * a.C * a.N;
+            t.csl = on_t ? 1 : g.sl;
+            t.csp = on_t ? a.H * a.W : g.sp;
+            t.csq = on_t ? a.W : g.sq;
             t.L = L;
             t.nch = nch;
             t.p0 = (int64_t)t.jp * kTP - kRing;
@@ -653,6 +659,9 @@ __global__ void __launch_bounds__(kBlock3, 1) vol3d_batched_kernel(const Vol3DBa
             t.b = 0;
             t.dist = a.dist;
             t.img = a.image;
+            t.csl = g.sl;
+            t.csp = g.sp;
+            t.csq = g.sq;
             t.L = (int)g.L;
             t.nch = t.L > 1 ? (t.L + kChunk - 1) / kChunk : 0;
             t.p0 = (int64_t)t.jp * kTP - kRing;
@@ -785,7 +794,7 @@ int run_vol3d(const SweepArgs& f, const float* image, const float* mask, float* 
     a.D = f.pass[0].L;
     a.H = f.pass[2].L;
     a.W = f.pass[4].L;
-    if (!codes && a.W > 1) {
+    if (a.W > 1) {
         // the W passes run on [W][D][H] copies: their planes' rows are contiguous
         a.distT = (float*)(w + vp.distT_off);
         a.imageT = vp.mode == kModeConst ? nullptr : (float*)(w + vp.imageT_off);
