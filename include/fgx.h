@@ -132,6 +132,45 @@ int fgx_geodesic_noalloc(int ndim, const float* image, const float* mask, float*
  * (FGX_ERR_TIMEOUT).  Returns FGX_ERR_CUDA if the copy fails. */
 int fgx_workspace_status(const void* workspace, void* stream);
 
+/* ------------------------------------------------ derived transforms ---- */
+
+/* Euclidean-only transform (lambda = 0): the cost of a step is its
+ * spacing-weighted length sqrt(s2), no image is read (Summary section: the
+ * generalised transform reduces to the Euclidean one when the image term has
+ * no weight).  Same mask, dist, workspace and error behaviour as
+ * fgx_geodesic2d / fgx_geodesic3d with C = 1 (the workspace size query takes
+ * C = 1); results equal those calls with lambda = 0 and any image, bit for
+ * bit. */
+int fgx_euclidean2d(const float* mask, float* dist, int64_t B, int64_t H, int64_t W, float v,
+                    int iterations, void* workspace, size_t workspace_bytes,
+                    const fgx_options* opt, void* stream);
+int fgx_euclidean3d(const float* mask, float* dist, int64_t B, int64_t D, int64_t H, int64_t W,
+                    const float spacing[3], float v, int iterations, void* workspace,
+                    size_t workspace_bytes, const fgx_options* opt, void* stream);
+
+/* Scratch bytes of fgx_signed_geodesic2d / 3d: the forward's workspace plus
+ * one distance map of B * D * H * W floats. */
+int fgx_signed_workspace_size(int ndim, int64_t B, int64_t C, int64_t D, int64_t H, int64_t W,
+                              const fgx_options* opt, size_t* bytes);
+
+/* Signed generalised geodesic distance (the paper names it among the
+ * applications, without a definition; reading used here): with M the mask in
+ * [0, 1], dist = GDT(M) - GDT(1 - M), each term the forward transform of the
+ * same image (1 - M and the difference rounded to float32).  Negative inside
+ * the region where M = 0, positive where M = 1; swapping M and 1 - M negates
+ * the result exactly.  Arguments as fgx_geodesic2d / 3d; dist may alias mask
+ * but not image.  The two transforms run one after the other on `stream`
+ * with the single-call kernels; a device wait timeout in either is reported
+ * by fgx_workspace_status. */
+int fgx_signed_geodesic2d(const float* image, const float* mask, float* dist, int64_t B,
+                          int64_t C, int64_t H, int64_t W, float v, float lambda, int iterations,
+                          void* workspace, size_t workspace_bytes, const fgx_options* opt,
+                          void* stream);
+int fgx_signed_geodesic3d(const float* image, const float* mask, float* dist, int64_t B,
+                          int64_t C, int64_t D, int64_t H, int64_t W, const float spacing[3],
+                          float v, float lambda, int iterations, void* workspace,
+                          size_t workspace_bytes, const fgx_options* opt, void* stream);
+
 /* ------------------------------------------------------------ batched ---- */
 
 /* One instance of a batched call (B = 1 per instance).  Pointers are device

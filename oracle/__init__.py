@@ -15,10 +15,15 @@ Functions here are ctypes wrappers taking and returning numpy arrays:
 * :func:`gdt_schedule` - float64 forward with any pass schedule, optionally
   iterated to its fixed point.
 * :func:`backward` - reverse sweep through recorded codes (dL/dI, dL/dM).
+* :func:`euclidean` - the transform at lambda = 0 (no image term).
+* :func:`signed_gdt` - signed transform GDT(M) - GDT(1 - M) (the paper names
+  signed geodesic distance among the applications without defining it; this
+  is the reading the library implements).
 
 Parity status: forward pinned (Dijkstra at the fixed point, chamfer and
 total-variation closed forms, 1D brute force, invariants); backward pinned by
-float64 central differences.  The paper itself prints no numeric example, so
+float64 central differences; the signed transform pinned by its half-plane
+closed form and its antisymmetry.  The paper itself prints no numeric example, so
 no value of the paper's own is pinned.
 """
 from __future__ import annotations
@@ -192,3 +197,23 @@ def backward(grad_dist, image, codes, v, lam, iterations, spacing=None, dtype=np
     if r != 0:
         raise ValueError(f"oracle_backward failed ({r})")
     return gi, gm
+
+
+def euclidean(mask, v, iterations, spacing=None, threads=1):
+    """The transform at lambda = 0: every step costs its spacing-weighted
+    length; the image term has no weight, so a zero image stands in."""
+    mask = np.ascontiguousarray(mask, np.float32)
+    image = np.zeros(mask.shape, np.float32)
+    return gdt(image, mask, v, 0.0, iterations, spacing=spacing, threads=threads)
+
+
+def signed_gdt(image, mask, v, lam, iterations, spacing=None, threads=1):
+    """Signed transform GDT(M) - GDT(1 - M) in float32: the transform seeded
+    by the region M = 0 minus the one seeded by M = 1, so negative inside the
+    region M = 0 and positive where M = 1.  The complement and the difference
+    are rounded to float32."""
+    m = np.ascontiguousarray(mask, np.float32)
+    comp = (np.float32(1.0) - m).astype(np.float32)
+    a = gdt(image, m, v, lam, iterations, spacing=spacing, threads=threads)
+    b = gdt(image, comp, v, lam, iterations, spacing=spacing, threads=threads)
+    return (a - b).astype(np.float32)

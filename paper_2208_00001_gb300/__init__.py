@@ -93,6 +93,15 @@ _SIGS = {
     "fgx_geodesic3d": ([_vp, _vp, _vp, _i64, _i64, _i64, _i64, _i64, _vp, _f32, _f32, _i32, _vp,
                         _sz, _vp, _vp], _i32),
     "fgx_workspace_status": ([_vp, _vp], _i32),
+    "fgx_euclidean2d": ([_vp, _vp, _i64, _i64, _i64, _f32, _i32, _vp, _sz, _vp, _vp], _i32),
+    "fgx_euclidean3d": ([_vp, _vp, _i64, _i64, _i64, _i64, _vp, _f32, _i32, _vp, _sz, _vp, _vp],
+                        _i32),
+    "fgx_signed_workspace_size": ([_i32, _i64, _i64, _i64, _i64, _i64, _vp,
+                                   ctypes.POINTER(_sz)], _i32),
+    "fgx_signed_geodesic2d": ([_vp, _vp, _vp, _i64, _i64, _i64, _i64, _f32, _f32, _i32, _vp,
+                               _sz, _vp, _vp], _i32),
+    "fgx_signed_geodesic3d": ([_vp, _vp, _vp, _i64, _i64, _i64, _i64, _i64, _vp, _f32, _f32,
+                               _i32, _vp, _sz, _vp, _vp], _i32),
     "fgx_batched_workspace_size": ([_vp, _i32, _vp, ctypes.POINTER(_sz)], _i32),
     "fgx_geodesic_batched": ([_vp, _i32, _vp, _sz, _vp, _vp], _i32),
     "fgx_batched_prepare": ([_vp, _i32, _vp, _sz, _vp, _vp, _vp], _i32),
@@ -239,6 +248,69 @@ def geodesic3d(image, mask, spacing, v, lam, iterations, out=None, options=None,
                "fgx_geodesic3d")
         if check:
             _check(workspace_status(ws), "fgx_geodesic3d (device)")
+    return out
+
+
+def euclidean(mask, v, iterations, spacing=None, out=None, options=None, workspace=None,
+              check=False):
+    """Euclidean-only transform (lambda = 0, no image): mask (B,1,H,W) or
+    (B,1,D,H,W); spacing (sD,sH,sW) in 3D."""
+    _check_tensor(mask, "mask")
+    ndim = mask.dim() - 2
+    if ndim not in (2, 3) or mask.shape[1] != 1:
+        raise ValueError("expected a (B,1,H,W) or (B,1,D,H,W) mask")
+    B = mask.shape[0]
+    D, H, W = (1,) + tuple(mask.shape[2:]) if ndim == 2 else tuple(mask.shape[2:])
+    dev = mask.device
+    with torch.cuda.device(dev):
+        if out is None:
+            out = torch.empty_like(mask)
+        ws = workspace if workspace is not None else _workspace(
+            workspace_size(ndim, B, 1, D, H, W, options), dev)
+        if ndim == 2:
+            st = lib().fgx_euclidean2d(_ptr(mask), _ptr(out), B, H, W, float(v), int(iterations),
+                                       _ptr(ws), ws.numel(), _opt(options), _stream())
+        else:
+            st = lib().fgx_euclidean3d(_ptr(mask), _ptr(out), B, D, H, W, _spacing(spacing),
+                                       float(v), int(iterations), _ptr(ws), ws.numel(),
+                                       _opt(options), _stream())
+        _check(st, "fgx_euclidean")
+        if check:
+            _check(workspace_status(ws), "fgx_euclidean (device)")
+    return out
+
+
+def signed_workspace_size(ndim, B, C, D, H, W, options=None):
+    n = ctypes.c_size_t(0)
+    _check(lib().fgx_signed_workspace_size(ndim, B, C, D, H, W, _opt(options), ctypes.byref(n)),
+           "signed workspace size")
+    return n.value
+
+
+def signed_geodesic(image, mask, v, lam, iterations, spacing=None, out=None, options=None,
+                    workspace=None, check=False):
+    """Signed transform GDT(mask) - GDT(1 - mask): negative inside the region
+    mask = 0, positive where mask = 1.  2D or 3D by the image rank."""
+    ndim = image.dim() - 2
+    B, C, D, H, W = _shape(image, mask, ndim)
+    dev = image.device
+    with torch.cuda.device(dev):
+        if out is None:
+            out = torch.empty_like(mask)
+        ws = workspace if workspace is not None else _workspace(
+            signed_workspace_size(ndim, B, C, D, H, W, options), dev)
+        if ndim == 2:
+            st = lib().fgx_signed_geodesic2d(_ptr(image), _ptr(mask), _ptr(out), B, C, H, W,
+                                             float(v), float(lam), int(iterations), _ptr(ws),
+                                             ws.numel(), _opt(options), _stream())
+        else:
+            st = lib().fgx_signed_geodesic3d(_ptr(image), _ptr(mask), _ptr(out), B, C, D, H, W,
+                                             _spacing(spacing), float(v), float(lam),
+                                             int(iterations), _ptr(ws), ws.numel(),
+                                             _opt(options), _stream())
+        _check(st, "fgx_signed_geodesic")
+        if check:
+            _check(workspace_status(ws), "fgx_signed_geodesic (device)")
     return out
 
 

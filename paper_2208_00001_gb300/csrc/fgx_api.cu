@@ -220,11 +220,13 @@ int run_forward(int ndim, const float* image, const float* mask, float* dist, in
             return FGX_ERR_CUDA;
         return FGX_OK;
     }
-    if (!image || !mask || !dist) return FGX_ERR_ARG;
-    if (!is_device_ptr(image) || !is_device_ptr(mask) || !is_device_ptr(dist))
+    // no image is read when lambda = 0 (the Euclidean entry passes none)
+    if (!mask || !dist || (!image && lambda != 0.f)) return FGX_ERR_ARG;
+    if ((image && !is_device_ptr(image)) || !is_device_ptr(mask) || !is_device_ptr(dist))
         return FGX_ERR_NOT_DEVICE_PTR;
     const size_t nb = (size_t)(B * N) * sizeof(float);
-    if (overlaps(dist, nb, image, (size_t)(B * C * N) * sizeof(float))) return FGX_ERR_ARG;
+    if (image && overlaps(dist, nb, image, (size_t)(B * C * N) * sizeof(float)))
+        return FGX_ERR_ARG;
     const size_t need_codes = (size_t)iterations * pl.args.npass * (size_t)(B * N);
     if (codes) {
         if (codes_bytes < need_codes) return FGX_ERR_WORKSPACE;
@@ -322,6 +324,45 @@ int fgx_geodesic3d(const float* image, const float* mask, float* dist, int64_t B
                    const fgx_options* opt, void* stream) {
     return run_forward(3, image, mask, dist, B, C, D, H, W, spacing, v, lambda, iterations,
                        nullptr, 0, workspace, workspace_bytes, opt, stream, true);
+}
+
+int fgx_euclidean2d(const float* mask, float* dist, int64_t B, int64_t H, int64_t W, float v,
+                    int iterations, void* workspace, size_t workspace_bytes,
+                    const fgx_options* opt, void* stream) {
+    return run_forward(2, nullptr, mask, dist, B, 1, 1, H, W, nullptr, v, 0.0f, iterations,
+                       nullptr, 0, workspace, workspace_bytes, opt, stream, true);
+}
+
+int fgx_euclidean3d(const float* mask, float* dist, int64_t B, int64_t D, int64_t H, int64_t W,
+                    const float spacing[3], float v, int iterations, void* workspace,
+                    size_t workspace_bytes, const fgx_options* opt, void* stream) {
+    return run_forward(3, nullptr, mask, dist, B, 1, D, H, W, spacing, v, 0.0f, iterations,
+                       nullptr, 0, workspace, workspace_bytes, opt, stream, true);
+}
+
+int fgx_signed_workspace_size(int ndim, int64_t B, int64_t C, int64_t D, int64_t H, int64_t W,
+                              const fgx_options* opt, size_t* bytes) {
+    size_t fwd = 0;
+    const int st = fgx_geodesic_workspace_size(ndim, B, C, D, H, W, opt, &fwd);
+    if (st != FGX_OK) return st;
+    *bytes = signed_workspace_bytes(fwd, B * D * H * W);
+    return FGX_OK;
+}
+
+int fgx_signed_geodesic2d(const float* image, const float* mask, float* dist, int64_t B,
+                          int64_t C, int64_t H, int64_t W, float v, float lambda, int iterations,
+                          void* workspace, size_t workspace_bytes, const fgx_options* opt,
+                          void* stream) {
+    return run_signed(2, image, mask, dist, B, C, 1, H, W, nullptr, v, lambda, iterations,
+                      workspace, workspace_bytes, opt, stream);
+}
+
+int fgx_signed_geodesic3d(const float* image, const float* mask, float* dist, int64_t B,
+                          int64_t C, int64_t D, int64_t H, int64_t W, const float spacing[3],
+                          float v, float lambda, int iterations, void* workspace,
+                          size_t workspace_bytes, const fgx_options* opt, void* stream) {
+    return run_signed(3, image, mask, dist, B, C, D, H, W, spacing, v, lambda, iterations,
+                      workspace, workspace_bytes, opt, stream);
 }
 
 int fgx_workspace_status(const void* workspace, void* stream) {

@@ -187,6 +187,14 @@ int run_adj3d(const SweepArgs& f, const float* grad_dist, const float* image,
               const uint8_t* codes, float* grad_image, float* grad_mask, float v, int iterations,
               void* workspace, size_t ws_bytes, const fgx_options* opt, int sms, void* stream);
 
+// Signed transform GDT(M) - GDT(1 - M) (signed.cu): workspace bytes for a
+// forward workspace of `forward_bytes` and n elements, and the run.
+size_t signed_workspace_bytes(size_t forward_bytes, int64_t n);
+int run_signed(int ndim, const float* image, const float* mask, float* dist, int64_t B,
+               int64_t C, int64_t D, int64_t H, int64_t W, const float spacing[3], float v,
+               float lambda, int iterations, void* workspace, size_t ws_bytes,
+               const fgx_options* opt, void* stream);
+
 int run_chain2d(const float* image, const float* mask, float* dist, uint8_t* codes, int64_t B,
                 int64_t C, int64_t H, int64_t W, float v, float lambda, int iterations,
                 void* workspace, size_t ws_bytes, const fgx_options* opt, int sms, void* stream);
