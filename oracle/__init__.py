@@ -15,6 +15,8 @@ Functions here are ctypes wrappers taking and returning numpy arrays:
 * :func:`gdt_schedule` - float64 forward with any pass schedule, optionally
   iterated to its fixed point.
 * :func:`backward` - reverse sweep through recorded codes (dL/dI, dL/dM).
+* :func:`param_terms` / :func:`param_grads` - the gradients with respect to
+  lambda and v through recorded codes.
 * :func:`euclidean` - the transform at lambda = 0 (no image term).
 * :func:`signed_gdt` - signed transform GDT(M) - GDT(1 - M) (the paper names
   signed geodesic distance among the applications without defining it; this
@@ -76,9 +78,11 @@ def _load():
                                                  ctypes.c_double, ctypes.c_double, vp, i32, i32,
                                                  vp]
             lib.oracle_backward_f32.argtypes = [vp, vp, vp, vp, vp, i32, i64, i64, i64, i64, i64,
-                                                vp, ctypes.c_float, ctypes.c_float, i32]
+                                                vp, ctypes.c_float, ctypes.c_float, i32, vp, vp,
+                                                vp]
             lib.oracle_backward_f64.argtypes = [vp, vp, vp, vp, vp, i32, i64, i64, i64, i64, i64,
-                                                vp, ctypes.c_double, ctypes.c_double, i32]
+                                                vp, ctypes.c_double, ctypes.c_double, i32, vp, vp,
+                                                vp]
             for f in (lib.oracle_gdt_f32, lib.oracle_gdt_f64, lib.oracle_gdt_sched_f64,
                       lib.oracle_backward_f32, lib.oracle_backward_f64):
                 f.restype = ctypes.c_int
@@ -193,10 +197,52 @@ def backward(grad_dist, image, codes, v, lam, iterations, spacing=None, dtype=np
     gm = np.empty_like(grad_dist) if need_mask else None
     f = lib.oracle_backward_f32 if dt == np.float32 else lib.oracle_backward_f64
     r = f(_ptr(grad_dist), _ptr(image), _ptr(codes), _ptr(gi), _ptr(gm), ndim, B, C, D, H, W,
-          _ptr(sp), dt.type(v).item(), dt.type(lam).item(), int(iterations))
+          _ptr(sp), dt.type(v).item(), dt.type(lam).item(), int(iterations), None, None, None)
     if r != 0:
         raise ValueError(f"oracle_backward failed ({r})")
     return gi, gm
+
+
+def param_terms(grad_dist, image, mask, codes, v, lam, iterations, spacing=None,
+                dtype=np.float32):
+    """Per-element terms of the parameter gradients through recorded codes:
+    (lambda_terms, v_terms), each shaped like mask.  lambda_terms holds, per
+    element and over the pass applications in reverse order, the element's
+    adjoint times d c / d lambda = (di2 - s2) / (2c) of its own parent edge
+    (c^2 = (1 - lambda) s2 + lambda di2; 0 where c = 0); v_terms = M * G0 with
+    G0 the adjoint of D0 = v M.  dL/dlambda and dL/dv are their sums
+    (:func:`param_grads`)."""
+    lib = _load()
+    dt = np.dtype(dtype)
+    image = np.ascontiguousarray(image, dtype=dt)
+    grad_dist = np.ascontiguousarray(grad_dist, dtype=dt)
+    mask = np.ascontiguousarray(mask, dtype=dt)
+    ndim, B, C, D, H, W = _shape(image, grad_dist)
+    if spacing is None:
+        spacing = (1.0, 1.0, 1.0)
+    elif ndim == 2:
+        spacing = (1.0, *spacing)
+    sp = np.ascontiguousarray(spacing, dtype=dt)
+    codes = np.ascontiguousarray(codes, dtype=np.uint8)
+    if codes.shape != (iterations * num_passes(ndim), B, D * H * W):
+        raise ValueError("codes shape mismatch")
+    lt = np.empty_like(grad_dist)
+    vt = np.empty_like(grad_dist)
+    f = lib.oracle_backward_f32 if dt == np.float32 else lib.oracle_backward_f64
+    r = f(_ptr(grad_dist), _ptr(image), _ptr(codes), None, None, ndim, B, C, D, H, W,
+          _ptr(sp), dt.type(v).item(), dt.type(lam).item(), int(iterations), _ptr(mask),
+          _ptr(lt), _ptr(vt))
+    if r != 0:
+        raise ValueError(f"oracle_backward failed ({r})")
+    return lt, vt
+
+
+def param_grads(grad_dist, image, mask, codes, v, lam, iterations, spacing=None):
+    """(dL/dlambda, dL/dv): the float32 per-element terms of
+    :func:`param_terms` summed in float64 (numpy's pairwise order)."""
+    lt, vt = param_terms(grad_dist, image, mask, codes, v, lam, iterations, spacing)
+    return (float(np.sum(lt.astype(np.float64).ravel(), dtype=np.float64)),
+            float(np.sum(vt.astype(np.float64).ravel(), dtype=np.float64)))
 
 
 def euclidean(mask, v, iterations, spacing=None, threads=1):

@@ -105,11 +105,14 @@ int oracle_gdt_sched_f64(const double* image, const double* mask, double* dist, 
 }
 
 /* Backward through recorded codes (see gdt_core.inc).  grad_dist is read
- * only; grad_image (nullable) and grad_mask (nullable) are written. */
+ * only; grad_image, grad_mask, lambda_terms and v_terms (all nullable; v_terms
+ * needs mask) are written. */
 int oracle_backward_f32(const float* grad_dist, const float* image, const uint8_t* codes,
                         float* grad_image, float* grad_mask, int ndim, int64_t B, int64_t C,
                         int64_t D, int64_t H, int64_t W, const float* spacing, float v,
-                        float lambda, int iterations) {
+                        float lambda, int iterations, const float* mask, float* lambda_terms,
+                        float* v_terms) {
+    if (v_terms && !mask) return -1;
     if (check_common(ndim, B, C, D, H, W) || iterations < 0) return -1;
     const int64_t ext[3] = {D, H, W};
     const int64_t N = D * H * W;
@@ -118,7 +121,7 @@ int oracle_backward_f32(const float* grad_dist, const float* image, const uint8_
     memcpy(G, grad_dist, (size_t)(B * N) * sizeof(float));
     int r = backward_f32(ndim, image, codes, G, grad_image, grad_mask, B, C, ext, spacing, v,
                          lambda, ndim == 3 ? SCHED_3D : SCHED_2D, oracle_num_passes(ndim),
-                         iterations);
+                         iterations, mask, lambda_terms, v_terms);
     free(G);
     return r;
 }
@@ -126,7 +129,9 @@ int oracle_backward_f32(const float* grad_dist, const float* image, const uint8_
 int oracle_backward_f64(const double* grad_dist, const double* image, const uint8_t* codes,
                         double* grad_image, double* grad_mask, int ndim, int64_t B, int64_t C,
                         int64_t D, int64_t H, int64_t W, const double* spacing, double v,
-                        double lambda, int iterations) {
+                        double lambda, int iterations, const double* mask, double* lambda_terms,
+                        double* v_terms) {
+    if (v_terms && !mask) return -1;
     if (check_common(ndim, B, C, D, H, W) || iterations < 0) return -1;
     const int64_t ext[3] = {D, H, W};
     const int64_t N = D * H * W;
@@ -135,7 +140,7 @@ int oracle_backward_f64(const double* grad_dist, const double* image, const uint
     memcpy(G, grad_dist, (size_t)(B * N) * sizeof(double));
     int r = backward_f64(ndim, image, codes, G, grad_image, grad_mask, B, C, ext, spacing, v,
                          lambda, ndim == 3 ? SCHED_3D : SCHED_2D, oracle_num_passes(ndim),
-                         iterations);
+                         iterations, mask, lambda_terms, v_terms);
     free(G);
     return r;
 }

@@ -119,3 +119,58 @@ def test_backward_lambda0_has_no_image_gradient_and_mask_gradient_is_v_times_cou
     # every element is reached from the single seed
     assert gm[0, 0, 2, 3] == pytest.approx(1e10 * m.size)
     assert np.count_nonzero(gm) == 1
+
+
+# ------------------------------------------------ lambda and v gradients
+
+def _param_fd(img, m, v, lam, its, sp, w, which):
+    """Central difference of sum(w * D) in lambda or v (float64), and whether
+    the perturbation left every code unchanged."""
+    def run(vv, ll):
+        return oracle.gdt(img, m, vv, ll, its, spacing=sp, dtype=np.float64, return_codes=True)
+    _, base = run(v, lam)
+    if which == "lambda":
+        (dp, cp), (dm, cm) = run(v, lam + H_FD), run(v, lam - H_FD)
+    else:
+        (dp, cp), (dm, cm) = run(v + H_FD * v, lam), run(v - H_FD * v, lam)
+    stable = np.array_equal(cp, base) and np.array_equal(cm, base)
+    h = H_FD if which == "lambda" else H_FD * v
+    return float(np.sum(w * (dp - dm))) / (2 * h), stable, base
+
+
+@pytest.mark.parametrize("shape,C,lam,sp", [
+    ((1, 1, 24, 29), 1, 0.75, None),
+    ((2, 3, 13, 17), 3, 0.4, None),
+    ((1, 2, 9, 11, 10), 2, 0.6, (2.5, 1.0, 0.75)),
+])
+def test_param_grads_match_central_differences(shape, C, lam, sp):
+    """dL/dlambda (each used edge's cost derivative (di2 - s2) / (2c) times
+    the element's adjoint) and dL/dv (sum of M * G0) against float64 central
+    differences of the forward."""
+    rng = np.random.default_rng(sum(shape))
+    img = rng.uniform(0, 1, shape)
+    m = rng.uniform(0, 1, (shape[0], 1) + shape[2:])
+    m.reshape(shape[0], -1)[:, 3] = 0.0
+    w = rng.uniform(0, 1, m.shape)
+    v = 4.0
+    for which in ("lambda", "v"):
+        fd, stable, codes = _param_fd(img, m, v, lam, 2, sp, w, which)
+        assert stable
+        lt, vt = oracle.param_terms(w, img, m, codes, v, lam, 2, spacing=sp, dtype=np.float64)
+        an = float(np.sum(lt if which == "lambda" else vt))
+        assert abs(an - fd) <= 1e-6 * max(abs(fd), 1e-12), (which, an, fd)
+        assert abs(an) > 0
+
+
+def test_param_grads_float32_terms_track_float64():
+    """The float32 terms (the GPU's reference) stay close to the float64 ones."""
+    case = workloads.diff2d(batch=1, size=40, v=10.0)
+    d, codes = oracle.gdt(case.image, case.mask, case.v, case.lam, case.iterations,
+                          return_codes=True)
+    g32 = oracle.param_grads(case.extra["w"], case.image, case.mask, codes, case.v, case.lam,
+                             case.iterations)
+    lt, vt = oracle.param_terms(case.extra["w"], case.image, case.mask, codes, case.v, case.lam,
+                                case.iterations, dtype=np.float64)
+    g64 = (float(np.sum(lt)), float(np.sum(vt)))
+    for a, b in zip(g32, g64):
+        assert abs(a - b) <= 1e-4 * abs(b), (a, b)
