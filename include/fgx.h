@@ -283,6 +283,36 @@ int fgx_geodesic3d_bwd(const float* grad_dist, const float* image, const void* s
                        float v, float lambda, int iterations, void* workspace,
                        size_t workspace_bytes, const fgx_options* opt, void* stream);
 
+/* Scratch bytes of fgx_geodesic_bwd_params: the reverse sweep's workspace
+ * (fgx_backward_workspace_size) plus three arrays of B*D*H*W floats. */
+int fgx_params_workspace_size(int ndim, int64_t B, int64_t C, int64_t D, int64_t H, int64_t W,
+                              int iterations, const fgx_options* opt, size_t* bytes);
+
+/* Gradients with respect to the scalar parameters lambda and v (extension
+ * of the differentiable transform), through the codes of
+ * fgx_geodesic*_fwd_train.  Since D = D(y) + c for an element whose value
+ * came from parent y and c^2 = (1 - lambda) s2 + lambda di2 (s2 the
+ * spacing-weighted squared offset, di2 the squared intensity difference),
+ * dL/dlambda = sum over pass applications and such elements of
+ * A(x) (di2 - s2) / (2c) (0 where c = 0), A the element's adjoint; and since
+ * D0 = v M, dL/dv = sum of M(x) G0(x), G0 the adjoint of D0.  lambda_terms
+ * and v_terms ([B][D][H][W] float32, nullable) receive the per-element terms
+ * (over the applications in reverse order, in float32 with the fixed
+ * operation order of the method); grad_lambda and grad_v (device memory, one
+ * double each, nullable) receive their sums over the call in float64, by a
+ * fixed-shape tree (the same bits on every run).  grad_image and grad_mask
+ * (nullable) are the outputs of fgx_geodesic*_bwd.  mask is the forward's
+ * mask.  2D: ndim = 2, D = 1, spacing NULL.  Only the warp-chain (2D) and
+ * plane-tile (3D) reverse sweeps carry the terms: 3D tile-shape options give
+ * FGX_ERR_UNSUPPORTED. */
+int fgx_geodesic_bwd_params(int ndim, const float* grad_dist, const float* image,
+                            const float* mask, const void* saved, size_t saved_bytes,
+                            float* grad_image, float* grad_mask, float* lambda_terms,
+                            float* v_terms, double* grad_lambda, double* grad_v, int64_t B,
+                            int64_t C, int64_t D, int64_t H, int64_t W, const float spacing[3],
+                            float v, float lambda, int iterations, void* workspace,
+                            size_t workspace_bytes, const fgx_options* opt, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -93,6 +93,11 @@ _SIGS = {
     "fgx_geodesic3d": ([_vp, _vp, _vp, _i64, _i64, _i64, _i64, _i64, _vp, _f32, _f32, _i32, _vp,
                         _sz, _vp, _vp], _i32),
     "fgx_workspace_status": ([_vp, _vp], _i32),
+    "fgx_params_workspace_size": ([_i32, _i64, _i64, _i64, _i64, _i64, _i32, _vp,
+                                   ctypes.POINTER(_sz)], _i32),
+    "fgx_geodesic_bwd_params": ([_i32, _vp, _vp, _vp, _vp, _sz, _vp, _vp, _vp, _vp, _vp, _vp,
+                                 _i64, _i64, _i64, _i64, _i64, _vp, _f32, _f32, _i32, _vp, _sz,
+                                 _vp, _vp], _i32),
     "fgx_euclidean2d": ([_vp, _vp, _i64, _i64, _i64, _f32, _i32, _vp, _sz, _vp, _vp], _i32),
     "fgx_euclidean3d": ([_vp, _vp, _i64, _i64, _i64, _i64, _vp, _f32, _i32, _vp, _sz, _vp, _vp],
                         _i32),
@@ -249,6 +254,40 @@ def geodesic3d(image, mask, spacing, v, lam, iterations, out=None, options=None,
         if check:
             _check(workspace_status(ws), "fgx_geodesic3d (device)")
     return out
+
+
+def backward_params(grad_dist, image, mask, saved, v, lam, iterations, spacing=None,
+                    need_image=False, need_mask=False, options=None, check=False):
+    """Gradients with respect to lambda and v through the saved codes:
+    returns (grad_lambda, grad_v, lambda_terms, v_terms, grad_image,
+    grad_mask).  The two scalars are float64 0-d tensors on the device (sums
+    of the per-element float32 terms by a fixed tree); grad_image and
+    grad_mask are None unless asked for."""
+    ndim = image.dim() - 2
+    B, C, D, H, W = _shape(image, mask, ndim)
+    _check_tensor(grad_dist, "grad_dist")
+    dev = image.device
+    with torch.cuda.device(dev):
+        n = ctypes.c_size_t(0)
+        _check(lib().fgx_params_workspace_size(ndim, B, C, D, H, W, int(iterations),
+                                               _opt(options), ctypes.byref(n)),
+               "params workspace size")
+        ws = _workspace(n.value, dev)
+        lt = torch.empty_like(mask)
+        vt = torch.empty_like(mask)
+        sums = torch.zeros(2, dtype=torch.float64, device=dev)
+        gi = torch.empty_like(image) if need_image else None
+        gm = torch.empty_like(mask) if need_mask else None
+        _check(lib().fgx_geodesic_bwd_params(
+            ndim, _ptr(grad_dist), _ptr(image), _ptr(mask), _ptr(saved), saved.numel(),
+            _ptr(gi) if gi is not None else None, _ptr(gm) if gm is not None else None,
+            _ptr(lt), _ptr(vt), ctypes.c_void_p(sums.data_ptr()),
+            ctypes.c_void_p(sums.data_ptr() + 8), B, C, D, H, W,
+            _spacing(spacing) if ndim == 3 else None, float(v), float(lam), int(iterations),
+            _ptr(ws), ws.numel(), _opt(options), _stream()), "fgx_geodesic_bwd_params")
+        if check:
+            _check(workspace_status(ws), "fgx_geodesic_bwd_params (device)")
+    return sums[0], sums[1], lt, vt, gi, gm
 
 
 def euclidean(mask, v, iterations, spacing=None, out=None, options=None, workspace=None,

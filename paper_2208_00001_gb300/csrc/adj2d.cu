@@ -61,6 +61,7 @@ struct Adj2DArgs {
     const float* grad_dist;   // [B][H][W]
     const uint8_t* codes;     // [T][B][H][W], image order
     float* grad_mask;         // [B][H][W] or null
+    float* g0;                // [B][H][W] adjoint of D0 (image order), or null
     int B, H, W, Wp, Hp, T;
     float v;
     float* Gw[2];             // [B][H][Wp] adjoint in row layout (two buffers)
@@ -148,6 +149,7 @@ struct AdjGeo {
     bool gdst_transposed;
     float* gmask;              // first application: dL/dM = v * adjoint of this image
                                // (image order), else null
+    float* g0;                 // first application: the adjoint itself (image order), or null
     float* adst;               // A of this application (pass layout), or null
 };
 
@@ -219,16 +221,15 @@ __device__ bool adj_flusher(const Adj2DArgs& a, const AdjGeo& g, AdjSmem& sm, un
                     if (owned[3]) p[3] = v.w;
                 }
             }
-            if (g.gmask || (g.gdst && !g.gdst_transposed)) {
+            if (g.gmask || g.g0 || (g.gdst && !g.gdst_transposed)) {
                 const float4 v = *reinterpret_cast<const float4*>(&sm.outg[slot][j][4 * lane]);
                 const float vv[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
                 for (int i = 0; i < 4; ++i) {
                     if (!owned[i]) continue;
-                    if (g.gmask)
-                        g.gmask[row * a.W + c0 + i] = __fmul_rn(a.v, vv[i]);
-                    else
-                        g.gdst[row * g.gdst_ld + c0 + i] = vv[i];
+                    if (g.gmask) g.gmask[row * a.W + c0 + i] = __fmul_rn(a.v, vv[i]);
+                    if (g.g0) g.g0[row * a.W + c0 + i] = vv[i];
+                    if (g.gdst && !g.gdst_transposed) g.gdst[row * g.gdst_ld + c0 + i] = vv[i];
                 }
             }
         }
@@ -398,6 +399,7 @@ __global__ void __launch_bounds__(kBlockA, 1) adj2d_kernel(const Adj2DArgs a) {
             g.gsrc = (in_vert ? a.Gw[in_idx] : a.Gt[in_idx]) + (int64_t)b * plane;
             g.csrc = (vert ? a.Cv : a.Ch) + ((int64_t)t * a.B + b) * plane;
             g.gmask = (t == 0 && a.grad_mask) ? a.grad_mask + (int64_t)b * a.H * a.W : nullptr;
+            g.g0 = (t == 0 && a.g0) ? a.g0 + (int64_t)b * a.H * a.W : nullptr;
             g.gdst = nullptr;
             g.gdst_ld = 0;
             g.gdst_transposed = false;
@@ -425,29 +427,38 @@ struct Grad2DArgs {
     const float* image;       // [B][C][H][W]
     const uint8_t* codes;     // [T][B][H][W]
     const float* Astore;      // [T][B][slab], pass layout
-    float* grad_image;        // [B][C][H][W]
+    float* grad_image;        // [B][C][H][W], or null
+    float* lambda_terms;      // [B][H][W] per-element terms of dL/dlambda, or null
     int64_t slab;
     int B, C, H, W, Wp, Hp, T;
     float lambda;
     float tv[3], th[3];       // (1 - lambda) |offset|^2 of vertical / horizontal passes
+    float sv[3], sh[3];       // |offset|^2 of vertical / horizontal passes
 };
 
 // Edge cost between image elements x and y, channel stride n, in the fixed
 // order of the method: di2 = sum_ch (I(x)-I(y))^2, c = sqrt(t + lambda*di2).
 __device__ __forceinline__ float grad_cost(const float* img, int64_t x, int64_t y, int C,
-                                           int64_t n, float t, float lam) {
+                                           int64_t n, float t, float lam, float* di2_out = nullptr) {
     float di2 = 0.0f;
     for (int ch = 0; ch < C; ++ch) {
         const float d = __fsub_rn(img[ch * n + x], img[ch * n + y]);
         di2 = __fadd_rn(di2, __fmul_rn(d, d));
     }
+    if (di2_out) *di2_out = di2;
     return __fsqrt_rn(__fadd_rn(t, __fmul_rn(lam, di2)));
+}
+
+// d c / d lambda of an edge (c^2 = (1 - lambda) s2 + lambda di2) times the
+// child's adjoint, in the fixed order (di2 - s2) / (c + c), then the product.
+__device__ __forceinline__ float lambda_term(float A, float di2, float s2, float c) {
+    return __fmul_rn(A, __fdiv_rn(__fsub_rn(di2, s2), __fadd_rn(c, c)));
 }
 
 // Image gradient, one thread per element, pass applications in reverse
 // order; CC > 0 keeps CC channels in registers, CC == 0 accumulates in the
 // output array (each element is touched by its own thread only).
-template <int CC>
+template <int CC, bool IMG>
 __global__ void __launch_bounds__(256) grad2d_kernel(const Grad2DArgs a) {
     const int64_t N = (int64_t)a.H * a.W;
     const int C = CC > 0 ? CC : a.C;
@@ -458,12 +469,13 @@ __global__ void __launch_bounds__(256) grad2d_kernel(const Grad2DArgs a) {
         const int64_t e = i - (int64_t)b * N;
         const int h = (int)(e / a.W), w = (int)(e - (int64_t)h * a.W);
         const float* img = a.image + (int64_t)b * a.C * N;
-        float* gout = a.grad_image + (int64_t)b * a.C * N + e;
+        float* gout = IMG ? a.grad_image + (int64_t)b * a.C * N + e : nullptr;
+        float lt = 0.0f;  // this element's terms of dL/dlambda
         float gi[CC > 0 ? CC : 1];
         if (CC > 0) {
 #pragma unroll
             for (int ch = 0; ch < (CC > 0 ? CC : 1); ++ch) gi[ch] = 0.0f;
-        } else {
+        } else if (IMG) {
             for (int ch = 0; ch < C; ++ch) gout[ch * N] = 0.0f;
         }
         auto add_term = [&](float wgt, int64_t x, int64_t y, bool minus) {
@@ -497,7 +509,7 @@ __global__ void __launch_bounds__(256) grad2d_kernel(const Grad2DArgs a) {
             };
             // children on the next line of the forward sweep, offset order
             const int cl = line + dir;
-            if (cl >= 0 && cl < L) {
+            if (IMG && cl >= 0 && cl < L) {
 #pragma unroll
                 for (int k = 0; k < 3; ++k) {
                     const int cq = q + 1 - k;
@@ -518,17 +530,21 @@ __global__ void __launch_bounds__(256) grad2d_kernel(const Grad2DArgs a) {
             // (codes outside 1..3 or pointing outside the line are ignored)
             if (code >= 1 && code <= 3 && pl >= 0 && pl < L && pq >= 0 && pq < Q) {
                 const int64_t p = at(pl, pq);
-                const float c = grad_cost(img, e, p, C, N, tk[code - 1], lam);
+                float di2;
+                const float c = grad_cost(img, e, p, C, N, tk[code - 1], lam, &di2);
                 if (c > 0.0f) {
-                    const float wgt = __fdiv_rn(__fmul_rn(A[(int64_t)line * ld + q], lam), c);
-                    add_term(wgt, e, p, false);
+                    const float Ae = A[(int64_t)line * ld + q];
+                    if (a.lambda_terms)
+                        lt = __fadd_rn(lt, lambda_term(Ae, di2, (vert ? a.sv : a.sh)[code - 1], c));
+                    if (IMG) add_term(__fdiv_rn(__fmul_rn(Ae, lam), c), e, p, false);
                 }
             }
         }
-        if (CC > 0) {
+        if (CC > 0 && IMG) {
 #pragma unroll
             for (int ch = 0; ch < (CC > 0 ? CC : 1); ++ch) gout[ch * N] = gi[ch];
         }
+        if (a.lambda_terms) a.lambda_terms[i] = lt;
     }
 }
 
@@ -578,7 +594,7 @@ size_t adj2d_workspace_bytes(int64_t B, int64_t H, int64_t W, int iterations,
 int run_adj2d(const float* grad_dist, const float* image, const uint8_t* codes,
               float* grad_image, float* grad_mask, int64_t B, int64_t C, int64_t H, int64_t W,
               float v, float lambda, int iterations, void* workspace, size_t ws_bytes,
-              const fgx_options* opt, int sms, void* stream) {
+              const fgx_options* opt, int sms, void* stream, float* g0, float* lambda_terms) {
     const int T = iterations * 4;
     if (T <= 0 || B * (T + 1) > 65535) return FGX_ERR_UNSUPPORTED;
     const Adj2DLayout l = adj2d_layout(B, H, W, T, opt);
@@ -589,6 +605,7 @@ int run_adj2d(const float* grad_dist, const float* image, const uint8_t* codes,
     a.grad_dist = grad_dist;
     a.codes = codes;
     a.grad_mask = grad_mask;
+    a.g0 = g0;
     a.B = (int)B;
     a.H = (int)H;
     a.W = (int)W;
@@ -602,7 +619,8 @@ int run_adj2d(const float* grad_dist, const float* image, const uint8_t* codes,
     }
     a.Cv = (uint8_t*)(w + l.cv_off);
     a.Ch = (uint8_t*)(w + l.ch_off);
-    a.Astore = grad_image ? (float*)(w + l.a_off) : nullptr;
+    const bool need_a = grad_image || lambda_terms;  // the per-element pass needs every A
+    a.Astore = need_a ? (float*)(w + l.a_off) : nullptr;
     a.slab = l.slab;
     a.xbuf = (unsigned long long*)(w + l.xbuf_off);
     a.barrier = (unsigned int*)(w + 64);
@@ -614,7 +632,7 @@ int run_adj2d(const float* grad_dist, const float* image, const uint8_t* codes,
     a.tiles_h = l.th;
     a.max_tiles = l.max_tiles;
 
-    auto kernel = grad_image ? adj2d_kernel<true> : adj2d_kernel<false>;
+    auto kernel = need_a ? adj2d_kernel<true> : adj2d_kernel<false>;
     const size_t smem = sizeof(AdjSmem);
     if (cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
         cudaSuccess)
@@ -646,13 +664,14 @@ int run_adj2d(const float* grad_dist, const float* image, const uint8_t* codes,
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     if (cudaLaunchKernelEx(&cfg, kernel, a) != cudaSuccess) return FGX_ERR_CUDA;
-    if (grad_image) {
+    if (need_a) {
         Grad2DArgs g;
         std::memset(&g, 0, sizeof(g));
         g.image = image;
         g.codes = codes;
         g.Astore = a.Astore;
         g.grad_image = grad_image;
+        g.lambda_terms = lambda_terms;
         g.slab = l.slab;
         g.B = (int)B;
         g.C = (int)C;
@@ -668,13 +687,21 @@ int run_adj2d(const float* grad_dist, const float* image, const uint8_t* codes,
         for (int k = 0; k < 3; ++k) g.tv[k] = t9[k];
         pass_offsets_t(2, 2, unit, lambda, t9);  // pass along W: offsets along H
         for (int k = 0; k < 3; ++k) g.th[k] = t9[k];
+        pass_offsets_t(2, 1, unit, 0.0f, t9);    // (1 - 0) |offset|^2
+        for (int k = 0; k < 3; ++k) g.sv[k] = t9[k];
+        pass_offsets_t(2, 2, unit, 0.0f, t9);
+        for (int k = 0; k < 3; ++k) g.sh[k] = t9[k];
         const int64_t n = B * H * W;
         const int gg = (int)std::min<int64_t>((n + 255) / 256, (int64_t)sms * 8);
-        if (C == 1) grad2d_kernel<1><<<gg, 256, 0, s>>>(g);
-        else if (C == 2) grad2d_kernel<2><<<gg, 256, 0, s>>>(g);
-        else if (C == 3) grad2d_kernel<3><<<gg, 256, 0, s>>>(g);
-        else if (C == 4) grad2d_kernel<4><<<gg, 256, 0, s>>>(g);
-        else grad2d_kernel<0><<<gg, 256, 0, s>>>(g);
+        if (grad_image) {
+            if (C == 1) grad2d_kernel<1, true><<<gg, 256, 0, s>>>(g);
+            else if (C == 2) grad2d_kernel<2, true><<<gg, 256, 0, s>>>(g);
+            else if (C == 3) grad2d_kernel<3, true><<<gg, 256, 0, s>>>(g);
+            else if (C == 4) grad2d_kernel<4, true><<<gg, 256, 0, s>>>(g);
+            else grad2d_kernel<0, true><<<gg, 256, 0, s>>>(g);
+        } else {
+            grad2d_kernel<0, false><<<gg, 256, 0, s>>>(g);
+        }
         if (cudaGetLastError() != cudaSuccess) return FGX_ERR_CUDA;
     }
     return FGX_OK;

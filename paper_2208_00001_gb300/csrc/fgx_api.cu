@@ -463,11 +463,14 @@ int plan_backward(int ndim, int64_t B, int64_t C, int64_t D, int64_t H, int64_t 
     return FGX_OK;
 }
 
+// g0 / lambda_terms (nullable): the adjoint of D0 and the per-element terms of
+// dL/dlambda, which only the warp-chain (2D) and plane-tile (3D) reverse
+// sweeps produce.
 int run_backward(int ndim, const float* grad_dist, const float* image, const void* saved,
                  size_t saved_bytes, float* grad_image, float* grad_mask, int64_t B, int64_t C,
                  int64_t D, int64_t H, int64_t W, const float spacing[3], float v, float lambda,
                  int iterations, void* workspace, size_t ws_bytes, const fgx_options* opt,
-                 void* stream) {
+                 void* stream, float* g0 = nullptr, float* lambda_terms = nullptr) {
     if (!(std::isfinite(v) && v > 0.f)) return FGX_ERR_ARG;
     if (!(lambda >= 0.f && lambda <= 1.f)) return FGX_ERR_ARG;
     if (iterations < 0) return FGX_ERR_ARG;
@@ -488,7 +491,8 @@ int run_backward(int ndim, const float* grad_dist, const float* image, const voi
         return FGX_OK;
     }
     if (!grad_dist || !image) return FGX_ERR_ARG;
-    if (!grad_image && !grad_mask) return FGX_ERR_ARG;
+    const bool params = g0 || lambda_terms;
+    if (!grad_image && !grad_mask && !params) return FGX_ERR_ARG;
     if (!is_device_ptr(grad_dist) || !is_device_ptr(image)) return FGX_ERR_NOT_DEVICE_PTR;
     if (grad_image && !is_device_ptr(grad_image)) return FGX_ERR_NOT_DEVICE_PTR;
     if (grad_mask && !is_device_ptr(grad_mask)) return FGX_ERR_NOT_DEVICE_PTR;
@@ -497,6 +501,22 @@ int run_backward(int ndim, const float* grad_dist, const float* image, const voi
         if (!saved || saved_bytes < need_codes) return FGX_ERR_WORKSPACE;
         if (!is_device_ptr(saved)) return FGX_ERR_NOT_DEVICE_PTR;
     }
+    if (params && iterations == 0) {
+        // D = v M: the adjoint of D0 is dL/dD, and no edge cost is used
+        const size_t nb = (size_t)(B * N) * sizeof(float);
+        if (g0 && cudaMemcpyAsync(g0, grad_dist, nb, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+            return FGX_ERR_CUDA;
+        if (lambda_terms && cudaMemsetAsync(lambda_terms, 0, nb, s) != cudaSuccess)
+            return FGX_ERR_CUDA;
+        if (!grad_image && !grad_mask) {
+            if (workspace && ws_bytes >= kHeaderBytes &&
+                cudaMemsetAsync(workspace, 0, kHeaderBytes, s) != cudaSuccess)
+                return FGX_ERR_CUDA;
+            return FGX_OK;
+        }
+        g0 = lambda_terms = nullptr;
+    }
+
     if (ndim == 2 && iterations > 0 && workspace &&
         ws_bytes >= adj2d_workspace_bytes(B, H, W, iterations, opt)) {
         if (!is_device_ptr(workspace)) return FGX_ERR_NOT_DEVICE_PTR;
@@ -504,18 +524,26 @@ int run_backward(int ndim, const float* grad_dist, const float* image, const voi
         st = current_device(&dev);
         if (st != FGX_OK) return st;
         st = run_adj2d(grad_dist, image, (const uint8_t*)saved, grad_image, grad_mask, B, C, H,
-                       W, v, lambda, iterations, workspace, ws_bytes, opt, dev.sms, stream);
+                       W, v, lambda, iterations, workspace, ws_bytes, opt, dev.sms, stream, g0,
+                       lambda_terms);
         if (st != FGX_ERR_UNSUPPORTED) return st;
     }
     if (ndim == 3 && iterations > 0 && workspace) {
         const size_t need = adj3d_workspace_bytes(bp.fwd, iterations, opt, bp.sms);
         if (need && ws_bytes >= need) {
             if (!is_device_ptr(workspace)) return FGX_ERR_NOT_DEVICE_PTR;
+            // |offset|^2 per pass and stencil offset: the offsets with lambda = 0
+            float s2[kMaxPasses * 9];
+            for (int i = 0; i < kMaxPasses; ++i)
+                pass_offsets_t(3, kSched3D[i][0], spacing, 0.0f, s2 + 9 * i);
             st = run_adj3d(bp.fwd, grad_dist, image, (const uint8_t*)saved, grad_image,
-                           grad_mask, v, iterations, workspace, ws_bytes, opt, bp.sms, stream);
+                           grad_mask, v, iterations, workspace, ws_bytes, opt, bp.sms, stream,
+                           g0, lambda_terms, s2);
             if (st != FGX_ERR_UNSUPPORTED) return st;
         }
     }
+    // the tiled engine's reverse sweep has no parameter terms
+    if (g0 || lambda_terms) return FGX_ERR_UNSUPPORTED;
     if (!workspace || ws_bytes < bp.ws_bytes) return FGX_ERR_WORKSPACE;
     if (!is_device_ptr(workspace)) return FGX_ERR_NOT_DEVICE_PTR;
     AdjointArgs& a = bp.args;
@@ -534,6 +562,22 @@ int run_backward(int ndim, const float* grad_dist, const float* image, const voi
     if (cudaMemsetAsync(workspace, 0, kHeaderBytes + bp.flags_bytes, s) != cudaSuccess)
         return FGX_ERR_CUDA;
     return launch_adjoint(a, bp.grid, bp.smem, stream);
+}
+
+struct ParamsLayout {
+    size_t g0_off, lt_off, vt_off, total;
+};
+
+// Workspace of the parameter gradients: the reverse sweep's workspace, then
+// G0 and scratch for the two per-element term arrays.
+ParamsLayout params_layout(size_t bwd, int64_t n) {
+    ParamsLayout l;
+    const size_t arr = align256((size_t)std::max<int64_t>(n, 1) * sizeof(float));
+    l.g0_off = align256(bwd);
+    l.lt_off = l.g0_off + arr;
+    l.vt_off = l.lt_off + arr;
+    l.total = l.vt_off + arr;
+    return l;
 }
 
 }  // namespace
@@ -575,6 +619,47 @@ int fgx_geodesic3d_bwd(const float* grad_dist, const float* image, const void* s
     return run_backward(3, grad_dist, image, saved, saved_bytes, grad_image, grad_mask, B, C, D,
                         H, W, spacing, v, lambda, iterations, workspace, workspace_bytes, opt,
                         stream);
+}
+
+int fgx_params_workspace_size(int ndim, int64_t B, int64_t C, int64_t D, int64_t H, int64_t W,
+                              int iterations, const fgx_options* opt, size_t* bytes) {
+    size_t bwd = 0;
+    const int st = fgx_backward_workspace_size(ndim, B, C, D, H, W, iterations, opt, &bwd);
+    if (st != FGX_OK) return st;
+    *bytes = params_layout(bwd, B * D * H * W).total;
+    return FGX_OK;
+}
+
+int fgx_geodesic_bwd_params(int ndim, const float* grad_dist, const float* image,
+                            const float* mask, const void* saved, size_t saved_bytes,
+                            float* grad_image, float* grad_mask, float* lambda_terms,
+                            float* v_terms, double* grad_lambda, double* grad_v, int64_t B,
+                            int64_t C, int64_t D, int64_t H, int64_t W, const float spacing[3],
+                            float v, float lambda, int iterations, void* workspace,
+                            size_t workspace_bytes, const fgx_options* opt, void* stream) {
+    if (ndim != 2 && ndim != 3) return FGX_ERR_ARG;
+    if (ndim == 2) D = 1;
+    size_t bwd = 0;
+    int st = fgx_backward_workspace_size(ndim, B, C, D, H, W, iterations, opt, &bwd);
+    if (st != FGX_OK) return st;
+    const int64_t n = B * D * H * W;
+    const ParamsLayout l = params_layout(bwd, n);
+    if (!workspace || workspace_bytes < l.total) return FGX_ERR_WORKSPACE;
+    if (!mask) return FGX_ERR_ARG;
+    if (!is_device_ptr(workspace) || (n > 0 && !is_device_ptr(mask)))
+        return FGX_ERR_NOT_DEVICE_PTR;
+    for (void* p : {(void*)lambda_terms, (void*)v_terms, (void*)grad_lambda, (void*)grad_v})
+        if (p && !is_device_ptr(p)) return FGX_ERR_NOT_DEVICE_PTR;
+    char* w = (char*)workspace;
+    float* g0 = (float*)(w + l.g0_off);
+    float* lt = lambda_terms ? lambda_terms : (float*)(w + l.lt_off);
+    float* vt = v_terms ? v_terms : (float*)(w + l.vt_off);
+    st = run_backward(ndim, grad_dist, image, saved, saved_bytes, grad_image, grad_mask, B, C, D,
+                      H, W, spacing, v, lambda, iterations, workspace, bwd, opt, stream, g0, lt);
+    if (st != FGX_OK) return st;
+    DeviceInfo dev;
+    if ((st = current_device(&dev)) != FGX_OK) return st;
+    return run_param_sums(mask, g0, vt, lt, grad_lambda, grad_v, n, dev.sms, stream);
 }
 
 

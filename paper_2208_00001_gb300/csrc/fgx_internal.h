@@ -173,10 +173,13 @@ int launch_vol3d_batched(const void* desc, int n, int rounds, const int* round_w
 // 2D reverse sweep on warp chains (adj2d.cu).
 size_t adj2d_workspace_bytes(int64_t B, int64_t H, int64_t W, int iterations,
                              const fgx_options* opt);
+// Optional outputs: g0 (the adjoint of D0, [B][H][W]) and lambda_terms (per
+// element terms of dL/dlambda, [B][H][W]).
 int run_adj2d(const float* grad_dist, const float* image, const uint8_t* codes,
               float* grad_image, float* grad_mask, int64_t B, int64_t C, int64_t H, int64_t W,
               float v, float lambda, int iterations, void* workspace, size_t ws_bytes,
-              const fgx_options* opt, int sms, void* stream);
+              const fgx_options* opt, int sms, void* stream, float* g0 = nullptr,
+              float* lambda_terms = nullptr);
 
 // 3D reverse sweep on plane tiles (vol3d.cu): workspace bytes (0 when the
 // geometry does not fit the kernel) and the run (adjoint kernel, then the
@@ -185,7 +188,14 @@ size_t adj3d_workspace_bytes(const SweepArgs& f, int iterations, const fgx_optio
                              int sms);
 int run_adj3d(const SweepArgs& f, const float* grad_dist, const float* image,
               const uint8_t* codes, float* grad_image, float* grad_mask, float v, int iterations,
-              void* workspace, size_t ws_bytes, const fgx_options* opt, int sms, void* stream);
+              void* workspace, size_t ws_bytes, const fgx_options* opt, int sms, void* stream,
+              float* g0 = nullptr, float* lambda_terms = nullptr, const float* s2 = nullptr);
+
+// Parameter gradients (param_grads.cu): v_terms = mask * g0 per element, then
+// grad_lambda / grad_v (device doubles, nullable) = float64 sums of
+// lambda_terms / v_terms by a fixed-shape tree.
+int run_param_sums(const float* mask, const float* g0, float* v_terms, const float* lambda_terms,
+                   double* grad_lambda, double* grad_v, int64_t n, int sms, void* stream);
 
 // Signed transform GDT(M) - GDT(1 - M) (signed.cu): workspace bytes for a
 // forward workspace of `forward_bytes` and n elements, and the run.

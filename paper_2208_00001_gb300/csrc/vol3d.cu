@@ -952,6 +952,7 @@ struct Adj3DArgs {
     const float* grad_dist;   // [B][N]
     const uint8_t* codes;     // [T][B][N]
     float* grad_mask;         // [B][N] or null
+    float* g0;                // [B][N] adjoint of D0, or null
     float* G[2];              // [B][N] adjoint buffers
     float* Astore;            // [T][B][N] adjoint of every application, or null
     int64_t B, N;
@@ -1027,7 +1028,7 @@ __device__ bool adj_producer3(const Adj3DArgs& a, const Tile3& t, const float* g
 // Compute warps: planes 0 .. L-1 of the reverse sweep.
 __device__ bool adj_compute3(const Adj3DArgs& a, const Tile3& t, int t_app, AdjHead3& h,
                              const float* stg, const uint8_t* stc, unsigned int cb, float* gdst,
-                             float* gmask, float* adst) {
+                             float* gmask, float* adst, float* g0) {
     const PassGeom& g = *t.g;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int64_t q = t.q0 + lane;
@@ -1114,6 +1115,7 @@ __device__ bool adj_compute3(const Adj3DArgs& a, const Tile3& t, int t_app, AdjH
             if (own[i]) {
                 const float gout = Sc[(rows0 + i) * kRQ + lane] != 0 ? 0.0f : acc;
                 if (gmask) gmask[lo + goff[i]] = __fmul_rn(a.v, gout);
+                if (g0) g0[lo + goff[i]] = gout;
                 if (gdst) gdst[lo + goff[i]] = gout;
                 if (adst) adst[lo + goff[i]] = acc;
             }
@@ -1186,7 +1188,8 @@ __global__ void __launch_bounds__(kBlock3, 1) adj3d_kernel(const Adj3DArgs a) {
                 float* gdst = t_app > 0 ? a.G[out_idx] + b * a.N : nullptr;
                 float* gmask = (t_app == 0 && a.grad_mask) ? a.grad_mask + b * a.N : nullptr;
                 float* adst = STORE_A ? a.Astore + ((int64_t)t_app * a.B + b) * a.N : nullptr;
-                adj_compute3(a, t, a.T - 1 - t_app, h, stg, stc, cb, gdst, gmask, adst);
+                float* g0 = (t_app == 0 && a.g0) ? a.g0 + b * a.N : nullptr;
+                adj_compute3(a, t, a.T - 1 - t_app, h, stg, stc, cb, gdst, gmask, adst, g0);
             }
             cb += (unsigned int)nch;
         }
@@ -1199,21 +1202,25 @@ struct Grad3DArgs {
     const float* image;       // [B][C][N]
     const uint8_t* codes;     // [T][B][N]
     const float* Astore;      // [T][B][N]
-    float* grad_image;        // [B][C][N]
+    float* grad_image;        // [B][C][N], or null
+    float* lambda_terms;      // [B][N] per-voxel terms of dL/dlambda, or null
     int64_t B, C, N;
     int64_t D, H, W;
     float lambda;
     int T;
     PassGeom pass[kMaxPasses];
+    float s2[kMaxPasses][9];  // |offset|^2 of every pass and stencil offset
 };
 
 __device__ __forceinline__ float grad_cost3(const float* img, int64_t x, int64_t y, int C,
-                                            int64_t n, float t, float lam) {
+                                            int64_t n, float t, float lam,
+                                            float* di2_out = nullptr) {
     float di2 = 0.0f;
     for (int ch = 0; ch < C; ++ch) {
         const float d = __fsub_rn(img[ch * n + x], img[ch * n + y]);
         di2 = __fadd_rn(di2, __fmul_rn(d, d));
     }
+    if (di2_out) *di2_out = di2;
     return __fsqrt_rn(__fadd_rn(t, __fmul_rn(lam, di2)));
 }
 
@@ -1221,7 +1228,10 @@ __device__ __forceinline__ float grad_cost3(const float* img, int64_t x, int64_t
 // applications in reverse order: per application the terms of the children
 // that chose the voxel (offset order), then the term of its own parent.
 // The gradient accumulates in the output array (each voxel is touched by its
-// own thread only).
+// own thread only).  With lambda_terms, each voxel also sums, over the
+// applications in the same order, its adjoint times d c / d lambda of its own
+// parent edge, (di2 - s2) / (c + c).
+template <bool IMG>
 __global__ void __launch_bounds__(256) grad3d_kernel(const Grad3DArgs a) {
     const float lam = a.lambda;
     const int C = (int)a.C;
@@ -1231,8 +1241,10 @@ __global__ void __launch_bounds__(256) grad3d_kernel(const Grad3DArgs a) {
         const int64_t dd = e / (a.H * a.W), rem = e - dd * a.H * a.W;
         const int64_t hh = rem / a.W, ww = rem - hh * a.W;
         const float* img = a.image + b * a.C * a.N;
-        float* gout = a.grad_image + b * a.C * a.N + e;
-        for (int ch = 0; ch < C; ++ch) gout[ch * a.N] = 0.0f;
+        float* gout = IMG ? a.grad_image + b * a.C * a.N + e : nullptr;
+        float lt = 0.0f;
+        if (IMG)
+            for (int ch = 0; ch < C; ++ch) gout[ch * a.N] = 0.0f;
         for (int t = a.T - 1; t >= 0; --t) {
             const PassGeom& g = a.pass[t % kMaxPasses];
             const int64_t line = g.axis == 0 ? dd : (g.axis == 1 ? hh : ww);
@@ -1242,7 +1254,7 @@ __global__ void __launch_bounds__(256) grad3d_kernel(const Grad3DArgs a) {
             const uint8_t* cd = a.codes + ((int64_t)t * a.B + b) * a.N;
             // children on the next plane of the forward sweep, offset order
             const int64_t cl = line + g.dir;
-            if (cl >= 0 && cl < g.L) {
+            if (IMG && cl >= 0 && cl < g.L) {
                 for (int k = 0; k < 9; ++k) {
                     const int64_t cp = p - (k / 3 - 1), cq = q - (k % 3 - 1);
                     if (cp < 0 || cp >= g.P || cq < 0 || cq >= g.Q) continue;
@@ -1266,17 +1278,26 @@ __global__ void __launch_bounds__(256) grad3d_kernel(const Grad3DArgs a) {
                 const int64_t pp = p + (k / 3 - 1), pq = q + (k % 3 - 1);
                 if (pp >= 0 && pp < g.P && pq >= 0 && pq < g.Q) {
                     const int64_t y = pl * g.sl + pp * g.sp + pq * g.sq;
-                    const float c = grad_cost3(img, e, y, C, a.N, g.t[k], lam);
+                    float di2;
+                    const float c = grad_cost3(img, e, y, C, a.N, g.t[k], lam, &di2);
                     if (c > 0.0f) {
-                        const float wgt = __fdiv_rn(__fmul_rn(A[e], lam), c);
-                        for (int ch = 0; ch < C; ++ch)
-                            gout[ch * a.N] = __fadd_rn(
-                                gout[ch * a.N],
-                                __fmul_rn(wgt, __fsub_rn(img[ch * a.N + e], img[ch * a.N + y])));
+                        if (a.lambda_terms) {
+                            const float s2 = a.s2[t % kMaxPasses][k];
+                            lt = __fadd_rn(lt, __fmul_rn(A[e], __fdiv_rn(__fsub_rn(di2, s2),
+                                                                         __fadd_rn(c, c))));
+                        }
+                        if (IMG) {
+                            const float wgt = __fdiv_rn(__fmul_rn(A[e], lam), c);
+                            for (int ch = 0; ch < C; ++ch)
+                                gout[ch * a.N] = __fadd_rn(
+                                    gout[ch * a.N],
+                                    __fmul_rn(wgt, __fsub_rn(img[ch * a.N + e], img[ch * a.N + y])));
+                        }
                     }
                 }
             }
         }
+        if (a.lambda_terms) a.lambda_terms[i] = lt;
     }
 }
 
@@ -1339,7 +1360,9 @@ size_t adj3d_workspace_bytes(const SweepArgs& f, int iterations, const fgx_optio
 
 int run_adj3d(const SweepArgs& f, const float* grad_dist, const float* image,
               const uint8_t* codes, float* grad_image, float* grad_mask, float v, int iterations,
-              void* workspace, size_t ws_bytes, const fgx_options* opt, int sms, void* stream) {
+              void* workspace, size_t ws_bytes, const fgx_options* opt, int sms, void* stream,
+              float* g0, float* lambda_terms, const float* s2) {
+    if (lambda_terms && !s2) return FGX_ERR_ARG;
     Adj3DPlan p;
     if (!plan_adj3d(f, iterations, opt, sms, &p)) return FGX_ERR_UNSUPPORTED;
     if (ws_bytes < p.total) return FGX_ERR_WORKSPACE;
@@ -1349,9 +1372,11 @@ int run_adj3d(const SweepArgs& f, const float* grad_dist, const float* image,
     a.grad_dist = grad_dist;
     a.codes = codes;
     a.grad_mask = grad_mask;
+    a.g0 = g0;
     a.G[0] = (float*)(w + p.g_off[0]);
     a.G[1] = (float*)(w + p.g_off[1]);
-    a.Astore = grad_image ? (float*)(w + p.a_off) : nullptr;
+    const bool need_a = grad_image || lambda_terms;  // the per-voxel pass needs every A
+    a.Astore = need_a ? (float*)(w + p.a_off) : nullptr;
     a.B = f.B;
     a.N = f.N;
     a.v = v;
@@ -1378,16 +1403,20 @@ int run_adj3d(const SweepArgs& f, const float* grad_dist, const float* image,
     attr[0].val.cooperative = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    if (cudaLaunchKernelEx(&cfg, grad_image ? adj3d_kernel<true> : adj3d_kernel<false>, a) !=
+    if (cudaLaunchKernelEx(&cfg, need_a ? adj3d_kernel<true> : adj3d_kernel<false>, a) !=
         cudaSuccess)
         return FGX_ERR_CUDA;
-    if (grad_image) {
+    if (need_a) {
         Grad3DArgs g;
         std::memset(&g, 0, sizeof(g));
         g.image = image;
         g.codes = codes;
         g.Astore = a.Astore;
         g.grad_image = grad_image;
+        g.lambda_terms = lambda_terms;
+        if (s2)
+            for (int i = 0; i < kMaxPasses; ++i)
+                for (int k = 0; k < 9; ++k) g.s2[i][k] = s2[i * 9 + k];
         g.B = f.B;
         g.C = f.C;
         g.N = f.N;
@@ -1399,7 +1428,8 @@ int run_adj3d(const SweepArgs& f, const float* grad_dist, const float* image,
         for (int i = 0; i < kMaxPasses; ++i) g.pass[i] = f.pass[i];
         const int64_t n = f.B * f.N;
         const int gg = (int)std::min<int64_t>((n + 255) / 256, (int64_t)sms * 8);
-        grad3d_kernel<<<std::max(gg, 1), 256, 0, s>>>(g);
+        if (grad_image) grad3d_kernel<true><<<std::max(gg, 1), 256, 0, s>>>(g);
+        else grad3d_kernel<false><<<std::max(gg, 1), 256, 0, s>>>(g);
         if (cudaGetLastError() != cudaSuccess) return FGX_ERR_CUDA;
     }
     return FGX_OK;
