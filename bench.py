@@ -246,8 +246,8 @@ def _roof(bytes_, t, peak):
 
 
 EXTRAS = ("2d_plain_256", "2d_large_lambda0", "2d_large_lambda1", "2d_large_lambda0.5_it4",
-          "3d_volume_128x256x256", "batched_64x2d_16x3d", "diff_2d_8x512x512",
-          "diff_3d_96x160x160")
+          "3d_volume_128x256x256", "signed_2d_large", "batched_64x2d_16x3d",
+          "diff_2d_8x512x512", "diff_3d_96x160x160")
 
 
 def measure_extras(fgx, dev, flush, stream, peak, steps=5, only=None):
@@ -291,6 +291,23 @@ def measure_extras(fgx, dev, flush, stream, peak, steps=5, only=None):
                      "roofline": _roof(fwd_bytes(c), t, peak),
                      "device_status": fgx.status_string(st)}
 
+    if want("signed_2d_large"):
+        c = workloads.large2d()
+        img = torch.from_numpy(c.image).to(dev)
+        m = torch.from_numpy(c.mask).to(dev)
+        o = torch.empty_like(m)
+        B, C, H, W = c.image.shape
+        ws = torch.empty(fgx.signed_workspace_size(2, B, C, 1, H, W), dtype=torch.uint8,
+                         device=dev)
+        fn = lambda: fgx.signed_geodesic(img, m, c.v, c.lam, c.iterations, out=o,  # noqa
+                                         workspace=ws)
+        fn()
+        t = _device_time(fn, steps, flush, stream)
+        out["signed_2d_large"] = {
+            "ms": t * 1e3, "mvox_per_s_per_iter": 2 * c.voxels * c.iterations / t / 1e6,
+            "note": "two transforms (M and 1 - M) per call, counted as 2 x voxels",
+            "roofline": _roof(2 * fwd_bytes(c), t, peak),
+            "device_status": fgx.status_string(fgx.workspace_status(ws))}
     if want("batched_64x2d_16x3d"):
         out.update(_batched_extra(fgx, dev, flush, stream, peak, steps, fwd_bytes))
     for name, make in [("diff_2d_8x512x512", lambda: workloads.diff2d()),
@@ -349,12 +366,17 @@ def _diff_extra(fgx, dev, flush, stream, peak, steps, name, c):
     tp = _device_time(f_plain, steps, flush, stream)
     tt = _device_time(f_train, steps, flush, stream)
     tb = _device_time(f_bwd, steps, flush, stream)
+    f_par = lambda: fgx.backward_params(w, img, m, saved, c.v, c.lam, c.iterations,  # noqa
+                                        spacing=c.spacing, need_image=True, need_mask=True)
+    f_par()
+    tq = _device_time(f_par, steps, flush, stream)
     units = c.voxels * c.iterations
     C = c.image.shape[1]
     npass = 6 if c.ndim == 3 else 4
     bwd_bytes = c.voxels * c.iterations * npass * (8 + 2 + 4 * C + 8 * C)
     return {name: {"fwd_ms": tp * 1e3, "fwd_train_ms": tt * 1e3, "bwd_ms": tb * 1e3,
                    "fwd_plus_bwd_ms": (tt + tb) * 1e3,
+                   "bwd_with_lambda_v_grads_ms": tq * 1e3,
                    "fwd_mvox_per_s_per_iter": units / tp / 1e6,
                    "fwd_plus_bwd_mvox_per_s_per_iter": units / (tt + tb) / 1e6,
                    "bwd_roofline": _roof(bwd_bytes, tb, peak)}}
