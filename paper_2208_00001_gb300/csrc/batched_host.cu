@@ -53,20 +53,31 @@ struct Schedule {
     size_t v_flag_off = 0, v_xbuf_off = 0, v_desc_off = 0, v_waves_off = 0, v_items_off = 0;
 };
 
-// First-fit packing of whole instances into waves of `grid` blocks, one
-// round per pass application; tiles(i, r) is instance i's tile count in
-// round r (0 once the instance is done).
-template <class Tiles>
-void pack_rounds(int n, int rounds, int grid, Tiles tiles, std::vector<int>* round_waves,
-                 std::vector<int>* wave_items) {
+// Packing of whole instances into waves of `grid` blocks, one round per pass
+// application; tiles(i, r) is instance i's tile count in round r (0 once the
+// instance is done) and lines(i, r) its number of line steps.  A wave lasts
+// about as long as its longest instance, so the instances go in order of
+// decreasing line count (then tile count) into the first wave with room:
+// long instances share waves and short ones fill the gaps.
+template <class Tiles, class Lines>
+void pack_rounds(int n, int rounds, int grid, Tiles tiles, Lines lines,
+                 std::vector<int>* round_waves, std::vector<int>* wave_items) {
     round_waves->assign(1, 0);
     wave_items->clear();
+    std::vector<int> order;
     for (int r = 0; r < rounds; ++r) {
+        order.clear();
+        for (int i = 0; i < n; ++i)
+            if (tiles(i, r) > 0) order.push_back(i);
+        std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
+            const int64_t lx = lines(x, r), ly = lines(y, r);
+            if (lx != ly) return lx > ly;
+            return tiles(x, r) > tiles(y, r);
+        });
         std::vector<int> used;                                   // blocks used per wave
         std::vector<std::vector<std::pair<int, int>>> members;  // (instance, first block)
-        for (int i = 0; i < n; ++i) {
+        for (int i : order) {
             const int nt = tiles(i, r);
-            if (nt == 0) continue;
             size_t w = 0;
             while (w < used.size() && used[w] + nt > grid) ++w;
             if (w == used.size()) {
@@ -241,6 +252,10 @@ int build_schedule(const fgx_instance* items, int n, const fgx_options* opt, boo
                     const PassGeom& g = d.pass[r % d.npass];
                     return g.ntp * g.ntq;
                 },
+                [&](int i, int r) -> int64_t {
+                    const InstDesc& d = S->desc[i];
+                    return d.pass[r % d.npass].L;
+                },
                 &S->round_waves, &S->wave_items);
     // the plane-tile launch for the 3D instances
     if (!S->v_index.empty()) {
@@ -251,6 +266,9 @@ int build_schedule(const fgx_instance* items, int n, const fgx_options* opt, boo
                     [&](int k, int r) {
                         if (r >= items[S->v_index[k]].iterations * kMaxPasses) return 0;
                         return S->v_tiles[k][r % kMaxPasses];
+                    },
+                    [&](int k, int r) -> int64_t {
+                        return S->v_args[k].pass[r % kMaxPasses].L;
                     },
                     &S->v_round_waves, &S->v_wave_items);
         if (S->timeout_ns == 0)
@@ -275,6 +293,10 @@ int build_schedule(const fgx_instance* items, int n, const fgx_options* opt, boo
                     [&](int k, int r) {
                         if (r >= items[S->c_index[k]].iterations * 4) return 0;
                         return (r & 3) < 2 ? S->c_tiles_v[k] : S->c_tiles_h[k];
+                    },
+                    [&](int k, int r) -> int64_t {
+                        const fgx_instance& it = items[S->c_index[k]];
+                        return (r & 3) < 2 ? it.H : it.W;
                     },
                     &S->c_round_waves, &S->c_wave_items);
         if (S->timeout_ns == 0)
