@@ -78,7 +78,8 @@ struct Chain2DArgs {
     int max_seg;             // exchange areas per image (kMaxSeg, or 1)
     int bnd_ld;              // floats per boundary line (max(H, W) rounded up)
     float* bnd;              // [B][kMaxSeg - 1][bnd_ld] boundary lines the segments started from
-    unsigned int* segflag;   // [B][kMaxSeg][2]: boundary changed (phase A, re-run), tag t_app + 1
+    unsigned int* segflag;   // [B][kMaxSeg][2]: boundary changed (phase A, re-run), tag t_app + 1;
+                             // then [4]: 1 + the last application of each pass with re-runs
     unsigned int* ckpt;      // [B][kMaxSeg][kMaxCk]: re-run checkpoints (arrivals | changed << 16)
 };
 
@@ -838,6 +839,8 @@ __device__ bool run_pass_segments(const Chain2DArgs& a, int t_app, int pass, int
         }
         __syncthreads();
         if (!any) continue;
+        if (blockIdx.x == 0 && threadIdx.x == 0)  // remembered for this pass's next application
+            *(a.segflag + (int64_t)a.B * kMaxSeg * 2 + pass) = (unsigned int)(t_app + 1);
         const int bb = u / ntiles;
         if (u < a.B * ntiles && rr[bb]) {
             ok = run_pass_tile<codes>(a, fwd, t_app, pass, bb, tile, sm, cb, j, true, S);
@@ -889,7 +892,13 @@ __global__ void __launch_bounds__(kBlockThreads, 1) chain2d_kernel(const Chain2D
         const int ntiles = pass < 2 ? a.tiles_v : a.tiles_h;
         const int L = pass < 2 ? a.H : a.W;
         const int S = pass < 2 ? a.nseg_v : a.nseg_h;
-        if (S > 1 && a.B <= kMaxSegImages && a.B * S * ntiles <= (int)gridDim.x) {
+        // Segments from the second iteration on (the first one changes nearly
+        // every line: its start lines always move), and not in a pass whose
+        // segments ran again in the previous iteration.
+        const bool speculate = S > 1 && t_app >= 4 &&
+                               ld_relaxed_u32(a.segflag + (int64_t)a.B * kMaxSeg * 2 + pass) !=
+                                   (unsigned int)(t_app - 4 + 1);
+        if (speculate && a.B <= kMaxSegImages && a.B * S * ntiles <= (int)gridDim.x) {
             alive = run_pass_segments<codes>(a, t_app, pass, S, ntiles, sm, cb, epoch, rerun);
             if (blockIdx.x == 0 && threadIdx.x == 0 && t_app + 2 < 16)
                 timeline[t_app + 2] = (unsigned long long)gtimer();
@@ -1042,7 +1051,8 @@ size_t fill_chain_args(Chain2DArgs* a, const float* image, const float* mask, fl
     *xbytes = al((size_t)B * max_seg * max_tiles * 4 * kMaxRing * 8);
     // segment flags live in the zeroed exchange area
     a->segflag = (unsigned int*)(xb && max_seg > 1 ? xb + *xbytes : nullptr);
-    if (max_seg > 1) *xbytes += al((size_t)B * kMaxSeg * 2 * 4);
+    // (then one word per pass: 1 + the last application whose segments ran again)
+    if (max_seg > 1) *xbytes += al((size_t)B * kMaxSeg * 2 * 4 + 4 * 4);
     size_t off = 0;
     a->Dw = (float*)(sec ? sec + off : nullptr);
     off += al((size_t)B * H * a->Wp * 4);
