@@ -443,28 +443,45 @@ def backward(grad_dist, image, saved, v, lam, iterations, spacing=None, need_ima
 
 class GeodesicFn(torch.autograd.Function):
     """Differentiable transform: the forward records argmin parent codes, the
-    backward runs the reverse sweep through them (dL/dimage, dL/dmask)."""
+    backward runs the reverse sweep through them (dL/dimage, dL/dmask, and
+    dL/dv, dL/dlambda when v or lam is a tensor that requires grad)."""
 
     @staticmethod
     def forward(ctx, image, mask, v, lam, iterations, spacing=None, options=None):
-        dist, saved = forward_train(image.detach().contiguous(), mask.detach().contiguous(), v,
-                                    lam, iterations, spacing=spacing, options=options)
-        ctx.save_for_backward(image.detach(), saved)
-        ctx.params = (v, lam, iterations, spacing, options)
+        vf, lf = float(v), float(lam)
+        dist, saved = forward_train(image.detach().contiguous(), mask.detach().contiguous(), vf,
+                                    lf, iterations, spacing=spacing, options=options)
+        ctx.save_for_backward(image.detach(), mask.detach(), saved)
+        ctx.params = (vf, lf, iterations, spacing, options)
+        ctx.scalar_like = (v, lam)
         return dist
 
     @staticmethod
     def backward(ctx, grad_dist):
-        image, saved = ctx.saved_tensors
+        image, mask, saved = ctx.saved_tensors
         v, lam, iterations, spacing, options = ctx.params
-        gi, gm = backward(grad_dist.contiguous(), image, saved, v, lam, iterations,
-                          spacing=spacing, need_image=ctx.needs_input_grad[0],
-                          need_mask=ctx.needs_input_grad[1], options=options)
-        return gi, gm, None, None, None, None, None
+        need_i, need_m, need_v, need_l = ctx.needs_input_grad[:4]
+        gv = gl = None
+        if need_v or need_l:
+            dl, dv, _, _, gi, gm = backward_params(grad_dist.contiguous(), image, mask, saved, v,
+                                                   lam, iterations, spacing=spacing,
+                                                   need_image=need_i, need_mask=need_m,
+                                                   options=options)
+            tv, tl = ctx.scalar_like
+            if need_v:
+                gv = dv.to(tv.dtype).reshape(tv.shape)
+            if need_l:
+                gl = dl.to(tl.dtype).reshape(tl.shape)
+        else:
+            gi, gm = backward(grad_dist.contiguous(), image, saved, v, lam, iterations,
+                              spacing=spacing, need_image=need_i, need_mask=need_m,
+                              options=options)
+        return gi, gm, gv, gl, None, None, None
 
 
 def geodesic_autograd(image, mask, v, lam, iterations, spacing=None, options=None):
-    """Autograd entry point: dist = GeodesicFn(image, mask, ...)."""
+    """Autograd entry point: dist = GeodesicFn(image, mask, ...); v and lam
+    may be floats or 0-d tensors (then their gradients are returned too)."""
     return GeodesicFn.apply(image, mask, v, lam, iterations, spacing, options)
 
 

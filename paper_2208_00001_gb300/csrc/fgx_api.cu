@@ -645,7 +645,7 @@ int fgx_geodesic_bwd_params(int ndim, const float* grad_dist, const float* image
     const int64_t n = B * D * H * W;
     const ParamsLayout l = params_layout(bwd, n);
     if (!workspace || workspace_bytes < l.total) return FGX_ERR_WORKSPACE;
-    if (!mask) return FGX_ERR_ARG;
+    if (!mask && n > 0) return FGX_ERR_ARG;
     if (!is_device_ptr(workspace) || (n > 0 && !is_device_ptr(mask)))
         return FGX_ERR_NOT_DEVICE_PTR;
     for (void* p : {(void*)lambda_terms, (void*)v_terms, (void*)grad_lambda, (void*)grad_v})

@@ -113,3 +113,36 @@ def test_param_grads_2d_tile_options(fgx):
     want_lt, want_vt = oracle.param_terms(w, img, m, saved.cpu().numpy(), 2.0, 0.5, 2)
     _bits(lt.cpu().numpy(), want_lt, "lambda terms")
     _bits(vt.cpu().numpy(), want_vt, "v terms")
+
+
+def test_autograd_lambda_and_v(fgx):
+    """GeodesicFn returns dL/dv and dL/dlambda for tensor parameters (float64
+    sums cast to the parameters' dtype) next to the image and mask gradients."""
+    rng = np.random.default_rng(9)
+    img = rng.uniform(0, 1, (1, 1, 48, 60)).astype(np.float32)
+    m = rng.uniform(0, 1, (1, 1, 48, 60)).astype(np.float32)
+    m[0, 0, 10, 10] = 0
+    w = rng.uniform(0, 1, m.shape).astype(np.float32)
+    ti = torch.from_numpy(img).cuda().requires_grad_(True)
+    tm = torch.from_numpy(m).cuda().requires_grad_(True)
+    tv = torch.tensor(5.0, dtype=torch.float64, device="cuda", requires_grad=True)
+    tl = torch.tensor(0.6, dtype=torch.float64, device="cuda", requires_grad=True)
+    d = fgx.geodesic_autograd(ti, tm, tv, tl, 2)
+    (torch.from_numpy(w).cuda() * d).sum().backward()
+    _, codes = oracle.gdt(img, m, 5.0, np.float32(0.6), 2, return_codes=True)
+    lt, vt = oracle.param_terms(w, img, m, codes, 5.0, np.float32(0.6), 2)
+    _sum_close(tl.grad.item(), lt, "autograd dL/dlambda")
+    _sum_close(tv.grad.item(), vt, "autograd dL/dv")
+    wi, wm = oracle.backward(w, img, codes, 5.0, np.float32(0.6), 2)
+    _bits(ti.grad.cpu().numpy(), wi, "autograd grad_image")
+    _bits(tm.grad.cpu().numpy(), wm, "autograd grad_mask")
+
+
+def test_derived_entries_on_empty_inputs(fgx):
+    img = torch.empty((0, 1, 8, 8), device="cuda")
+    m = torch.empty((0, 1, 8, 8), device="cuda")
+    assert fgx.signed_geodesic(img, m, 1.0, 0.5, 2).numel() == 0
+    assert fgx.euclidean(m, 1.0, 2).numel() == 0
+    d, saved = fgx.forward_train(img, m, 1.0, 0.5, 2)
+    gl, gv, lt, vt, _, _ = fgx.backward_params(torch.empty_like(m), img, m, saved, 1.0, 0.5, 2)
+    assert gl.item() == 0.0 and gv.item() == 0.0
