@@ -132,6 +132,24 @@ int fgx_geodesic_noalloc(int ndim, const float* image, const float* mask, float*
  * (FGX_ERR_TIMEOUT).  Returns FGX_ERR_CUDA if the copy fails. */
 int fgx_workspace_status(const void* workspace, void* stream);
 
+/* ---------------------------------------------------------- autotune ---- */
+
+/* Times each of the n candidate option sets on the caller's buffers (the
+ * forward of fgx_geodesic2d, ndim = 2, D = 1, spacing NULL, or of
+ * fgx_geodesic3d) and writes the index of the fastest to *best_index and its
+ * mean time in milliseconds to *best_ms (host memory).  Each candidate runs
+ * once untimed and then `reps` times between CUDA events on `stream`; the
+ * call synchronises the stream (it is a setup step, not for a captured graph).
+ * The workspace must hold every candidate's (the largest
+ * fgx_geodesic_workspace_size over them).  A candidate the call does not
+ * support (status FGX_ERR_UNSUPPORTED) is skipped; another error ends the
+ * call with that status.  dist holds the last candidate's result. */
+int fgx_autotune(int ndim, const float* image, const float* mask, float* dist, int64_t B,
+                 int64_t C, int64_t D, int64_t H, int64_t W, const float spacing[3], float v,
+                 float lambda, int iterations, void* workspace, size_t workspace_bytes,
+                 const fgx_options* candidates, int n, int reps, int* best_index, float* best_ms,
+                 void* stream);
+
 /* ------------------------------------------------ derived transforms ---- */
 
 /* Euclidean-only transform (lambda = 0): the cost of a step is its

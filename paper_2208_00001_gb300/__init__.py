@@ -93,6 +93,9 @@ _SIGS = {
     "fgx_geodesic3d": ([_vp, _vp, _vp, _i64, _i64, _i64, _i64, _i64, _vp, _f32, _f32, _i32, _vp,
                         _sz, _vp, _vp], _i32),
     "fgx_workspace_status": ([_vp, _vp], _i32),
+    "fgx_autotune": ([_i32, _vp, _vp, _vp, _i64, _i64, _i64, _i64, _i64, _vp, _f32, _f32, _i32,
+                      _vp, _sz, _vp, _i32, _i32, ctypes.POINTER(_i32), ctypes.POINTER(_f32), _vp],
+                     _i32),
     "fgx_params_workspace_size": ([_i32, _i64, _i64, _i64, _i64, _i64, _i32, _vp,
                                    ctypes.POINTER(_sz)], _i32),
     "fgx_geodesic_bwd_params": ([_i32, _vp, _vp, _vp, _vp, _sz, _vp, _vp, _vp, _vp, _vp, _vp,
@@ -212,11 +215,65 @@ def _workspace(nbytes, device):
     return torch.empty(max(int(nbytes), 256), dtype=torch.uint8, device=device)
 
 
+# Tile geometries the 2D autotuner tries: (lines between ring refreshes,
+# owned columns) with 4 * 32 = 128 region columns per tile; the first is the
+# default.  Long single images favour long refresh blocks, many concurrent
+# tiles (batches) shorter ones with wider owned parts.
+TILE_CANDIDATES_2D = ((0, 0), (32, 64), (24, 80), (16, 96), (8, 112))
+_tuned = {}
+
+
+def autotune(image, mask, v, lam, iterations, spacing=None, reps=3, candidates=None):
+    """Times the 2D tile geometries on these inputs (fgx_autotune) and
+    returns the fastest as an options dict (None: the default), cached per
+    shape, channel count, lambda = 0 or not and iterations.  3D calls keep the
+    plane tiles (None)."""
+    ndim = image.dim() - 2
+    B, C, D, H, W = _shape(image, mask, ndim)
+    key = (ndim, B, C, D, H, W, float(lam) == 0.0, int(iterations), image.device.index)
+    if key in _tuned:
+        return _tuned[key]
+    if ndim != 2:
+        _tuned[key] = None
+        return None
+    cands = candidates or TILE_CANDIDATES_2D
+    opts = (Options * len(cands))(*[Options(tile_lines=k, tile_width=t) for k, t in cands])
+    dev = image.device
+    with torch.cuda.device(dev):
+        need = 0
+        for o in opts:  # a candidate that cannot be planned is skipped by the tuner
+            try:
+                need = max(need, workspace_size(2, B, C, 1, H, W, o))
+            except FgxError:
+                pass
+        ws = _workspace(need, dev)
+        out = torch.empty_like(mask)
+        best = ctypes.c_int32(-1)
+        ms = ctypes.c_float(0.0)
+        _check(lib().fgx_autotune(2, _ptr(image), _ptr(mask), _ptr(out), B, C, 1, H, W, None,
+                                  float(v), float(lam), int(iterations), _ptr(ws), ws.numel(),
+                                  ctypes.cast(opts, ctypes.c_void_p), len(cands), int(reps),
+                                  ctypes.byref(best), ctypes.byref(ms), _stream()),
+               "fgx_autotune")
+    k, t = cands[best.value]
+    _tuned[key] = None if (k, t) == (0, 0) else dict(tile_lines=k, tile_width=t)
+    return _tuned[key]
+
+
+def _resolve(options, image, mask, v, lam, iterations, spacing=None):
+    if isinstance(options, str):
+        if options != "auto":
+            raise ValueError(f"options: a dict, Options, None or 'auto', not {options!r}")
+        return autotune(image, mask, v, lam, iterations, spacing)
+    return options
+
+
 def geodesic2d(image, mask, v, lam, iterations, out=None, options=None, workspace=None,
                check=False):
     """2D transform.  image (B,C,H,W), mask (B,1,H,W), float32 CUDA tensors.
     Returns dist (B,1,H,W).  check=True synchronises and raises on a device
-    timeout."""
+    timeout.  options='auto' uses the autotuned tile geometry for this shape."""
+    options = _resolve(options, image, mask, v, lam, iterations)
     B, C, D, H, W = _shape(image, mask, 2)
     dev = image.device
     with torch.cuda.device(dev):
@@ -240,6 +297,7 @@ def _spacing(spacing):
 def geodesic3d(image, mask, spacing, v, lam, iterations, out=None, options=None, workspace=None,
                check=False):
     """3D transform.  image (B,C,D,H,W), mask (B,1,D,H,W); spacing (sD,sH,sW)."""
+    options = _resolve(options, image, mask, v, lam, iterations, spacing)
     B, C, D, H, W = _shape(image, mask, 3)
     dev = image.device
     with torch.cuda.device(dev):
@@ -369,7 +427,8 @@ def saved_size(ndim, B, D, H, W, iterations):
 
 def forward_train(image, mask, v, lam, iterations, spacing=None, options=None, check=False):
     """Forward that records parent codes.  Returns (dist, saved uint8 tensor
-    [iterations*passes, B, D*H*W])."""
+    [iterations*passes, B, D*H*W]).  options='auto': the autotuned geometry."""
+    options = _resolve(options, image, mask, v, lam, iterations, spacing)
     ndim = image.dim() - 2
     B, C, D, H, W = _shape(image, mask, ndim)
     dev = image.device
@@ -494,6 +553,11 @@ class BatchedPlan:
 
     def __init__(self, instances, options=None):
         self.instances = list(instances)
+        if isinstance(options, str):
+            if options != "auto":
+                raise ValueError("options: a dict, Options, None or 'auto'")
+            options = self._tune()
+        self.options = options
         self.outputs = []
         arr = (Instance * max(1, len(self.instances)))()
         dev = None
@@ -523,6 +587,29 @@ class BatchedPlan:
                                              _opt(self._opt), ctypes.byref(self.plan), _stream()),
                    "fgx_batched_prepare")
         self.device = dev
+
+    def _tune(self, reps=2):
+        """The fastest 2D tile geometry for this set of instances (timed runs
+        of a plan per candidate; 3D instances keep their plane tiles)."""
+        best, best_t = None, None
+        for k, t in TILE_CANDIDATES_2D:
+            opts = None if (k, t) == (0, 0) else dict(tile_lines=k, tile_width=t)
+            try:
+                plan = BatchedPlan(self.instances, opts)
+            except FgxError:
+                continue
+            plan.run()
+            s = torch.cuda.Event(enable_timing=True)
+            e = torch.cuda.Event(enable_timing=True)
+            s.record()
+            for _ in range(reps):
+                plan.run()
+            e.record()
+            e.synchronize()
+            ms = s.elapsed_time(e) / reps
+            if best_t is None or ms < best_t:
+                best, best_t = opts, ms
+        return best
 
     def run(self, check=False):
         with torch.cuda.device(self.device):

@@ -326,6 +326,56 @@ int fgx_geodesic3d(const float* image, const float* mask, float* dist, int64_t B
                        nullptr, 0, workspace, workspace_bytes, opt, stream, true);
 }
 
+int fgx_autotune(int ndim, const float* image, const float* mask, float* dist, int64_t B,
+                 int64_t C, int64_t D, int64_t H, int64_t W, const float spacing[3], float v,
+                 float lambda, int iterations, void* workspace, size_t workspace_bytes,
+                 const fgx_options* candidates, int n, int reps, int* best_index, float* best_ms,
+                 void* stream) {
+    if (!candidates || n < 1 || reps < 1 || !best_index || !best_ms) return FGX_ERR_ARG;
+    if (ndim != 2 && ndim != 3) return FGX_ERR_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess) return FGX_ERR_CUDA;
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return FGX_ERR_CUDA;
+    }
+    auto call = [&](const fgx_options* o) {
+        return ndim == 2 ? fgx_geodesic2d(image, mask, dist, B, C, H, W, v, lambda, iterations,
+                                          workspace, workspace_bytes, o, stream)
+                         : fgx_geodesic3d(image, mask, dist, B, C, D, H, W, spacing, v, lambda,
+                                          iterations, workspace, workspace_bytes, o, stream);
+    };
+    int st = FGX_OK, best = -1;
+    float best_t = 0.f;
+    for (int i = 0; i < n && st == FGX_OK; ++i) {
+        int r = call(candidates + i);
+        if (r == FGX_ERR_UNSUPPORTED) continue;
+        if (r != FGX_OK) { st = r; break; }
+        if (cudaEventRecord(e0, s) != cudaSuccess) { st = FGX_ERR_CUDA; break; }
+        for (int k = 0; k < reps && r == FGX_OK; ++k) r = call(candidates + i);
+        if (r != FGX_OK) { st = r; break; }
+        float ms = 0.f;
+        if (cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+            cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+            st = FGX_ERR_CUDA;
+            break;
+        }
+        ms /= (float)reps;
+        if (best < 0 || ms < best_t) {
+            best = i;
+            best_t = ms;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (st != FGX_OK) return st;
+    if (best < 0) return FGX_ERR_UNSUPPORTED;
+    *best_index = best;
+    *best_ms = best_t;
+    return FGX_OK;
+}
+
 int fgx_euclidean2d(const float* mask, float* dist, int64_t B, int64_t H, int64_t W, float v,
                     int iterations, void* workspace, size_t workspace_bytes,
                     const fgx_options* opt, void* stream) {
