@@ -553,10 +553,28 @@ class BatchedPlan:
 
     def __init__(self, instances, options=None):
         self.instances = list(instances)
+        self._parts = None
         if isinstance(options, str):
             if options != "auto":
                 raise ValueError("options: a dict, Options, None or 'auto'")
-            options = self._tune()
+            i2 = [i for i, inst in enumerate(self.instances) if inst[0].dim() == 4]
+            i3 = [i for i, inst in enumerate(self.instances) if inst[0].dim() != 4]
+            options = self._tune([self.instances[i] for i in i2]) if i2 else None
+            if options is not None and i3:
+                # tile options would also move the 3D instances to the tiled
+                # engine: the 2D instances get their own plan with the tuned
+                # geometry, the 3D ones keep the plane tiles
+                self._parts = [(i2, BatchedPlan([self.instances[i] for i in i2], options)),
+                               (i3, BatchedPlan([self.instances[i] for i in i3], None))]
+                self.options = options
+                self.outputs = [None] * len(self.instances)
+                for idx, part in self._parts:
+                    for j, i in enumerate(idx):
+                        self.outputs[i] = part.outputs[j]
+                self.plan = self._parts[0][1].plan
+                self.workspace = self._parts[0][1].workspace
+                self.device = self._parts[0][1].device
+                return
         self.options = options
         self.outputs = []
         arr = (Instance * max(1, len(self.instances)))()
@@ -588,14 +606,15 @@ class BatchedPlan:
                    "fgx_batched_prepare")
         self.device = dev
 
-    def _tune(self, reps=2):
-        """The fastest 2D tile geometry for this set of instances (timed runs
-        of a plan per candidate; 3D instances keep their plane tiles)."""
+    @staticmethod
+    def _tune(instances, reps=2):
+        """The fastest 2D tile geometry for these (2D) instances: timed runs
+        of a plan per candidate."""
         best, best_t = None, None
         for k, t in TILE_CANDIDATES_2D:
             opts = None if (k, t) == (0, 0) else dict(tile_lines=k, tile_width=t)
             try:
-                plan = BatchedPlan(self.instances, opts)
+                plan = BatchedPlan(instances, opts)
             except FgxError:
                 continue
             plan.run()
@@ -611,7 +630,22 @@ class BatchedPlan:
                 best, best_t = opts, ms
         return best
 
+    def status(self):
+        """Synchronises and returns the device status of the last run (the
+        first failure over the plan's parts)."""
+        if self._parts:
+            for _, part in self._parts:
+                st = part.status()
+                if st != OK:
+                    return st
+            return OK
+        return workspace_status(self.workspace)
+
     def run(self, check=False):
+        if self._parts:
+            for _, part in self._parts:
+                part.run(check=check)
+            return self.outputs
         with torch.cuda.device(self.device):
             _check(lib().fgx_batched_run(ctypes.byref(self.plan), _stream()), "fgx_batched_run")
             if check:
