@@ -247,11 +247,13 @@ def test_error_codes(fgx):
     L = fgx.lib()
     dev = torch.zeros((1, 1, 8, 8), device="cuda")
     host = torch.zeros((1, 1, 8, 8))
-    ws = torch.zeros(4096, dtype=torch.uint8, device="cuda")
+    WS = fgx.workspace_size(2, 1, 1, 1, 8, 8)
+    ws = torch.zeros(WS, dtype=torch.uint8, device="cuda")
     s = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
     P = lambda t: ctypes.c_void_p(t.data_ptr())  # noqa: E731
 
-    def call(img, m, d, lam=0.5, v=1.0, its=2, wsb=4096, H=8, W=8):
+    def call(img, m, d, lam=0.5, v=1.0, its=2, wsb=None, H=8, W=8):
+        wsb = WS if wsb is None else wsb
         return L.fgx_geodesic2d(P(img), P(m), P(d), 1, 1, H, W, v, lam, its, P(ws), wsb, None, s)
 
     out = torch.zeros_like(dev)
@@ -265,15 +267,15 @@ def test_error_codes(fgx):
     assert call(dev, dev, out, wsb=8) == fgx.ERR_WORKSPACE
     assert call(dev, dev, dev) == fgx.ERR_ARG  # dist aliases image
     assert call(dev, dev, out, H=-1) == fgx.ERR_SHAPE
-    assert L.fgx_geodesic2d(None, P(dev), P(out), 1, 1, 8, 8, 1.0, 0.5, 1, P(ws), 4096, None,
+    assert L.fgx_geodesic2d(None, P(dev), P(out), 1, 1, 8, 8, 1.0, 0.5, 1, P(ws), WS, None,
                             s) == fgx.ERR_ARG
     bad = fgx.Options()
     bad.size = 3
-    assert L.fgx_geodesic2d(P(dev), P(dev), P(out), 1, 1, 8, 8, 1.0, 0.5, 1, P(ws), 4096,
+    assert L.fgx_geodesic2d(P(dev), P(dev), P(out), 1, 1, 8, 8, 1.0, 0.5, 1, P(ws), WS,
                             ctypes.byref(bad), s) == fgx.ERR_ARG
     sp = (ctypes.c_float * 3)(1.0, 0.0, 1.0)
     d3 = torch.zeros((1, 1, 2, 8, 8), device="cuda")
     o3 = torch.zeros_like(d3)
-    assert L.fgx_geodesic3d(P(d3), P(d3), P(o3), 1, 1, 2, 8, 8, sp, 1.0, 0.5, 1, P(ws), 4096,
+    assert L.fgx_geodesic3d(P(d3), P(d3), P(o3), 1, 1, 2, 8, 8, sp, 1.0, 0.5, 1, P(ws), WS,
                             None, s) == fgx.ERR_ARG
     torch.cuda.synchronize()
