@@ -30,20 +30,34 @@ MUTANTS = [
     ("wrong sign of the parent's image term",
      "gi[ch * N + yi] = gi[ch * N + yi] - w * d;", "gi[ch * N + yi] = gi[ch * N + yi] + w * d;"),
     ("sum of differences instead of squares", "di2 = di2 + d * d;", "di2 = di2 + d;"),
+    ("d c / d lambda with the wrong sign", "REAL dc = (di2 - s2[k]) / (c + c);",
+     "REAL dc = (s2[k] - di2) / (c + c);"),
+    ("d c / d lambda without the factor 1/2", "REAL dc = (di2 - s2[k]) / (c + c);",
+     "REAL dc = (di2 - s2[k]) / c;"),
+    ("lambda term from the parent's adjoint", "*lt = *lt + g[xi] * dc;",
+     "*lt = *lt + g[yi] * dc;"),
+    ("v terms without the mask", "v_terms[i] = mask[i] * G[i];", "v_terms[i] = G[i];"),
+    ("signed transform without the complement",
+     "comp = (np.float32(1.0) - m).astype(np.float32)", "comp = m.copy()", "__init__.py"),
+    ("signed transform with the terms swapped", "return (a - b).astype(np.float32)",
+     "return (b - a).astype(np.float32)", "__init__.py"),
 ]
 
 
-@pytest.mark.parametrize("label,old,new", MUTANTS, ids=[m[0] for m in MUTANTS])
-def test_pins_reject_planted_mistake(tmp_path, label, old, new):
+@pytest.mark.parametrize("mutant", MUTANTS, ids=[m[0] for m in MUTANTS])
+def test_pins_reject_planted_mistake(tmp_path, mutant):
+    label, old, new = mutant[:3]
+    fname = mutant[3] if len(mutant) > 3 else "gdt_core.inc"
     for d in ("oracle", "tests", "workloads"):
         shutil.copytree(os.path.join(ROOT, d), tmp_path / d,
                         ignore=shutil.ignore_patterns("_build", "__pycache__"))
     shutil.copy(os.path.join(ROOT, "pytest.ini"), tmp_path / "pytest.ini")
-    src = tmp_path / "oracle" / "gdt_core.inc"
+    src = tmp_path / "oracle" / fname
     text = src.read_text()
     assert old in text, label
     src.write_text(text.replace(old, new))
     r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q",
-                        "tests/test_oracle_pins.py", "tests/test_oracle_backward.py"],
+                        "tests/test_oracle_pins.py", "tests/test_oracle_backward.py",
+                        "tests/test_oracle_derived.py"],
                        cwd=tmp_path, capture_output=True, text=True, timeout=900)
     assert r.returncode != 0, f"pins did not catch: {label}\n{r.stdout[-2000:]}"
