@@ -67,3 +67,24 @@ def test_size_queries_without_device_do_not_crash(libpath):
                                          ctypes.c_int64(1), ctypes.c_int64(8), ctypes.c_int64(8),
                                          None, ctypes.byref(n))
     assert st == -7  # FGX_ERR_DEVICE
+
+
+def test_header_compiles_as_c(tmp_path):
+    """include/fgx.h is plain C (C99): a C caller can include it and take the
+    address of every declared entry point."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    names = _declared()
+    src = tmp_path / "use_fgx.c"
+    src.write_text('#include "fgx.h"\n'
+                   "typedef void (*entry)(void);\n"
+                   "entry entry_points[] = {\n" +
+                   "".join(f"    (entry){n},\n" for n in names) +
+                   "};\nint main(void) { return entry_points[0] == 0; }\n")
+    r = subprocess.run([cc, "-std=c99", "-Wall", "-Werror", "-pedantic", "-fsyntax-only",
+                        "-I", os.path.join(ROOT, "include"), str(src)],
+                       capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
