@@ -1231,10 +1231,12 @@ __device__ __forceinline__ float grad_cost3(const float* img, int64_t x, int64_t
 // own thread only).  With lambda_terms, each voxel also sums, over the
 // applications in the same order, its adjoint times d c / d lambda of its own
 // parent edge, (di2 - s2) / (c + c).
-template <bool IMG>
+template <int CC, bool IMG>
 __global__ void __launch_bounds__(256) grad3d_kernel(const Grad3DArgs a) {
+    // CC > 0: the CC channel sums stay in registers (written once at the end);
+    // CC == 0: any channel count, accumulated in the output array
     const float lam = a.lambda;
-    const int C = (int)a.C;
+    const int C = CC > 0 ? CC : (int)a.C;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.B * a.N;
          i += (int64_t)gridDim.x * blockDim.x) {
         const int64_t b = i / a.N, e = i - b * a.N;
@@ -1243,8 +1245,29 @@ __global__ void __launch_bounds__(256) grad3d_kernel(const Grad3DArgs a) {
         const float* img = a.image + b * a.C * a.N;
         float* gout = IMG ? a.grad_image + b * a.C * a.N + e : nullptr;
         float lt = 0.0f;
-        if (IMG)
+        float gi[CC > 0 ? CC : 1];
+#pragma unroll
+        for (int ch = 0; ch < (CC > 0 ? CC : 1); ++ch) gi[ch] = 0.0f;
+        if (IMG && CC == 0)
             for (int ch = 0; ch < C; ++ch) gout[ch * a.N] = 0.0f;
+        // g -= wgt (I(x) - I(y))  or  g += wgt (I(x) - I(y)), per channel
+        auto add_term = [&](float wgt, int64_t x, int64_t y, bool minus) {
+            if (CC > 0) {
+#pragma unroll
+                for (int ch = 0; ch < (CC > 0 ? CC : 1); ++ch) {
+                    const float term =
+                        __fmul_rn(wgt, __fsub_rn(img[ch * a.N + x], img[ch * a.N + y]));
+                    gi[ch] = minus ? __fsub_rn(gi[ch], term) : __fadd_rn(gi[ch], term);
+                }
+            } else {
+                for (int ch = 0; ch < C; ++ch) {
+                    const float term =
+                        __fmul_rn(wgt, __fsub_rn(img[ch * a.N + x], img[ch * a.N + y]));
+                    gout[ch * a.N] = minus ? __fsub_rn(gout[ch * a.N], term)
+                                           : __fadd_rn(gout[ch * a.N], term);
+                }
+            }
+        };
         for (int t = a.T - 1; t >= 0; --t) {
             const PassGeom& g = a.pass[t % kMaxPasses];
             const int64_t line = g.axis == 0 ? dd : (g.axis == 1 ? hh : ww);
@@ -1255,19 +1278,14 @@ __global__ void __launch_bounds__(256) grad3d_kernel(const Grad3DArgs a) {
             // children on the next plane of the forward sweep, offset order
             const int64_t cl = line + g.dir;
             if (IMG && cl >= 0 && cl < g.L) {
+#pragma unroll
                 for (int k = 0; k < 9; ++k) {
                     const int64_t cp = p - (k / 3 - 1), cq = q - (k % 3 - 1);
                     if (cp < 0 || cp >= g.P || cq < 0 || cq >= g.Q) continue;
                     const int64_t x = cl * g.sl + cp * g.sp + cq * g.sq;
                     if (cd[x] != k + 1) continue;
                     const float c = grad_cost3(img, x, e, C, a.N, g.t[k], lam);
-                    if (c > 0.0f) {
-                        const float wgt = __fdiv_rn(__fmul_rn(A[x], lam), c);
-                        for (int ch = 0; ch < C; ++ch)
-                            gout[ch * a.N] = __fsub_rn(
-                                gout[ch * a.N],
-                                __fmul_rn(wgt, __fsub_rn(img[ch * a.N + x], img[ch * a.N + e])));
-                    }
+                    if (c > 0.0f) add_term(__fdiv_rn(__fmul_rn(A[x], lam), c), x, e, true);
                 }
             }
             // own parent on the previous plane of the forward sweep
@@ -1286,16 +1304,14 @@ __global__ void __launch_bounds__(256) grad3d_kernel(const Grad3DArgs a) {
                             lt = __fadd_rn(lt, __fmul_rn(A[e], __fdiv_rn(__fsub_rn(di2, s2),
                                                                          __fadd_rn(c, c))));
                         }
-                        if (IMG) {
-                            const float wgt = __fdiv_rn(__fmul_rn(A[e], lam), c);
-                            for (int ch = 0; ch < C; ++ch)
-                                gout[ch * a.N] = __fadd_rn(
-                                    gout[ch * a.N],
-                                    __fmul_rn(wgt, __fsub_rn(img[ch * a.N + e], img[ch * a.N + y])));
-                        }
+                        if (IMG) add_term(__fdiv_rn(__fmul_rn(A[e], lam), c), e, y, false);
                     }
                 }
             }
+        }
+        if (IMG && CC > 0) {
+#pragma unroll
+            for (int ch = 0; ch < (CC > 0 ? CC : 1); ++ch) gout[ch * a.N] = gi[ch];
         }
         if (a.lambda_terms) a.lambda_terms[i] = lt;
     }
@@ -1428,8 +1444,12 @@ int run_adj3d(const SweepArgs& f, const float* grad_dist, const float* image,
         for (int i = 0; i < kMaxPasses; ++i) g.pass[i] = f.pass[i];
         const int64_t n = f.B * f.N;
         const int gg = (int)std::min<int64_t>((n + 255) / 256, (int64_t)sms * 8);
-        if (grad_image) grad3d_kernel<true><<<std::max(gg, 1), 256, 0, s>>>(g);
-        else grad3d_kernel<false><<<std::max(gg, 1), 256, 0, s>>>(g);
+        const int gb = std::max(gg, 1);
+        if (!grad_image) grad3d_kernel<0, false><<<gb, 256, 0, s>>>(g);
+        else if (f.C == 1) grad3d_kernel<1, true><<<gb, 256, 0, s>>>(g);
+        else if (f.C == 2) grad3d_kernel<2, true><<<gb, 256, 0, s>>>(g);
+        else if (f.C == 3) grad3d_kernel<3, true><<<gb, 256, 0, s>>>(g);
+        else grad3d_kernel<0, true><<<gb, 256, 0, s>>>(g);
         if (cudaGetLastError() != cudaSuccess) return FGX_ERR_CUDA;
     }
     return FGX_OK;
