@@ -1231,17 +1231,20 @@ __device__ __forceinline__ float grad_cost3(const float* img, int64_t x, int64_t
 // own thread only).  With lambda_terms, each voxel also sums, over the
 // applications in the same order, its adjoint times d c / d lambda of its own
 // parent edge, (di2 - s2) / (c + c).
-template <int CC, bool IMG>
+template <int CC, bool IMG, typename Idx>
 __global__ void __launch_bounds__(256) grad3d_kernel(const Grad3DArgs a) {
     // CC > 0: the CC channel sums stay in registers (written once at the end);
-    // CC == 0: any channel count, accumulated in the output array
+    // CC == 0: any channel count, accumulated in the output array.  Idx: the
+    // index type within one instance (32-bit when every offset fits)
     const float lam = a.lambda;
     const int C = CC > 0 ? CC : (int)a.C;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.B * a.N;
          i += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t b = i / a.N, e = i - b * a.N;
-        const int64_t dd = e / (a.H * a.W), rem = e - dd * a.H * a.W;
-        const int64_t hh = rem / a.W, ww = rem - hh * a.W;
+        const int64_t b = i / a.N;
+        const Idx e = (Idx)(i - b * a.N);
+        const Idx HW = (Idx)(a.H * a.W), Wd = (Idx)a.W;
+        const Idx dd = e / HW, rem = e - dd * HW;
+        const Idx hh = rem / Wd, ww = rem - hh * Wd;
         const float* img = a.image + b * a.C * a.N;
         float* gout = IMG ? a.grad_image + b * a.C * a.N + e : nullptr;
         float lt = 0.0f;
@@ -1251,7 +1254,7 @@ __global__ void __launch_bounds__(256) grad3d_kernel(const Grad3DArgs a) {
         if (IMG && CC == 0)
             for (int ch = 0; ch < C; ++ch) gout[ch * a.N] = 0.0f;
         // g -= wgt (I(x) - I(y))  or  g += wgt (I(x) - I(y)), per channel
-        auto add_term = [&](float wgt, int64_t x, int64_t y, bool minus) {
+        auto add_term = [&](float wgt, Idx x, Idx y, bool minus) {
             if (CC > 0) {
 #pragma unroll
                 for (int ch = 0; ch < (CC > 0 ? CC : 1); ++ch) {
@@ -1270,19 +1273,21 @@ __global__ void __launch_bounds__(256) grad3d_kernel(const Grad3DArgs a) {
         };
         for (int t = a.T - 1; t >= 0; --t) {
             const PassGeom& g = a.pass[t % kMaxPasses];
-            const int64_t line = g.axis == 0 ? dd : (g.axis == 1 ? hh : ww);
-            const int64_t p = g.axis == 0 ? hh : dd;
-            const int64_t q = g.axis == 2 ? hh : ww;
+            const Idx line = g.axis == 0 ? dd : (g.axis == 1 ? hh : ww);
+            const Idx p = g.axis == 0 ? hh : dd;
+            const Idx q = g.axis == 2 ? hh : ww;
+            const Idx L = (Idx)g.L, P = (Idx)g.P, Q = (Idx)g.Q;
+            const Idx sl = (Idx)g.sl, sp = (Idx)g.sp, sq = (Idx)g.sq;
             const float* A = a.Astore + ((int64_t)t * a.B + b) * a.N;
             const uint8_t* cd = a.codes + ((int64_t)t * a.B + b) * a.N;
             // children on the next plane of the forward sweep, offset order
-            const int64_t cl = line + g.dir;
-            if (IMG && cl >= 0 && cl < g.L) {
+            const Idx cl = line + g.dir;
+            if (IMG && cl >= 0 && cl < L) {
 #pragma unroll
                 for (int k = 0; k < 9; ++k) {
-                    const int64_t cp = p - (k / 3 - 1), cq = q - (k % 3 - 1);
-                    if (cp < 0 || cp >= g.P || cq < 0 || cq >= g.Q) continue;
-                    const int64_t x = cl * g.sl + cp * g.sp + cq * g.sq;
+                    const Idx cp = p - (k / 3 - 1), cq = q - (k % 3 - 1);
+                    if (cp < 0 || cp >= P || cq < 0 || cq >= Q) continue;
+                    const Idx x = cl * sl + cp * sp + cq * sq;
                     if (cd[x] != k + 1) continue;
                     const float c = grad_cost3(img, x, e, C, a.N, g.t[k], lam);
                     if (c > 0.0f) add_term(__fdiv_rn(__fmul_rn(A[x], lam), c), x, e, true);
@@ -1290,12 +1295,12 @@ __global__ void __launch_bounds__(256) grad3d_kernel(const Grad3DArgs a) {
             }
             // own parent on the previous plane of the forward sweep
             const int code = cd[e];
-            const int64_t pl = line - g.dir;
-            if (code >= 1 && code <= 9 && pl >= 0 && pl < g.L) {
+            const Idx pl = line - g.dir;
+            if (code >= 1 && code <= 9 && pl >= 0 && pl < L) {
                 const int k = code - 1;
-                const int64_t pp = p + (k / 3 - 1), pq = q + (k % 3 - 1);
-                if (pp >= 0 && pp < g.P && pq >= 0 && pq < g.Q) {
-                    const int64_t y = pl * g.sl + pp * g.sp + pq * g.sq;
+                const Idx pp = p + (k / 3 - 1), pq = q + (k % 3 - 1);
+                if (pp >= 0 && pp < P && pq >= 0 && pq < Q) {
+                    const Idx y = pl * sl + pp * sp + pq * sq;
                     float di2;
                     const float c = grad_cost3(img, e, y, C, a.N, g.t[k], lam, &di2);
                     if (c > 0.0f) {
@@ -1445,11 +1450,17 @@ int run_adj3d(const SweepArgs& f, const float* grad_dist, const float* image,
         const int64_t n = f.B * f.N;
         const int gg = (int)std::min<int64_t>((n + 255) / 256, (int64_t)sms * 8);
         const int gb = std::max(gg, 1);
-        if (!grad_image) grad3d_kernel<0, false><<<gb, 256, 0, s>>>(g);
-        else if (f.C == 1) grad3d_kernel<1, true><<<gb, 256, 0, s>>>(g);
-        else if (f.C == 2) grad3d_kernel<2, true><<<gb, 256, 0, s>>>(g);
-        else if (f.C == 3) grad3d_kernel<3, true><<<gb, 256, 0, s>>>(g);
-        else grad3d_kernel<0, true><<<gb, 256, 0, s>>>(g);
+        // 32-bit offsets within an instance when every one fits (C * N < 2^31)
+        if (f.C * f.N < ((int64_t)1 << 31)) {
+            if (!grad_image) grad3d_kernel<0, false, int><<<gb, 256, 0, s>>>(g);
+            else if (f.C == 1) grad3d_kernel<1, true, int><<<gb, 256, 0, s>>>(g);
+            else if (f.C == 2) grad3d_kernel<2, true, int><<<gb, 256, 0, s>>>(g);
+            else if (f.C == 3) grad3d_kernel<3, true, int><<<gb, 256, 0, s>>>(g);
+            else grad3d_kernel<0, true, int><<<gb, 256, 0, s>>>(g);
+        } else {
+            if (!grad_image) grad3d_kernel<0, false, int64_t><<<gb, 256, 0, s>>>(g);
+            else grad3d_kernel<0, true, int64_t><<<gb, 256, 0, s>>>(g);
+        }
         if (cudaGetLastError() != cudaSuccess) return FGX_ERR_CUDA;
     }
     return FGX_OK;
