@@ -132,6 +132,15 @@ int fgx_geodesic_noalloc(int ndim, const float* image, const float* mask, float*
  * (FGX_ERR_TIMEOUT).  Returns FGX_ERR_CUDA if the copy fails. */
 int fgx_workspace_status(const void* workspace, void* stream);
 
+/* Failure detection check: launches one block that waits, with the bounded
+ * wait every inter-block hand-over of the library uses, on a tag in the
+ * workspace that nothing writes.  After timeout_ms (1..10000) the wait gives
+ * up and records FGX_ERR_TIMEOUT in the workspace status word, which
+ * fgx_workspace_status then returns; the context stays usable.  The
+ * workspace needs 264 bytes; the call clears them first. */
+int fgx_probe_wait_timeout(void* workspace, size_t workspace_bytes, int timeout_ms,
+                           void* stream);
+
 /* ---------------------------------------------------------- autotune ---- */
 
 /* Times each of the n candidate option sets on the caller's buffers (the

@@ -93,6 +93,7 @@ _SIGS = {
     "fgx_geodesic3d": ([_vp, _vp, _vp, _i64, _i64, _i64, _i64, _i64, _vp, _f32, _f32, _i32, _vp,
                         _sz, _vp, _vp], _i32),
     "fgx_workspace_status": ([_vp, _vp], _i32),
+    "fgx_probe_wait_timeout": ([_vp, _sz, _i32, _vp], _i32),
     "fgx_autotune": ([_i32, _vp, _vp, _vp, _i64, _i64, _i64, _i64, _i64, _vp, _f32, _f32, _i32,
                       _vp, _sz, _vp, _i32, _i32, ctypes.POINTER(_i32), ctypes.POINTER(_f32), _vp],
                      _i32),

@@ -326,6 +326,19 @@ int fgx_geodesic3d(const float* image, const float* mask, float* dist, int64_t B
                        nullptr, 0, workspace, workspace_bytes, opt, stream, true);
 }
 
+int fgx_probe_wait_timeout(void* workspace, size_t workspace_bytes, int timeout_ms,
+                           void* stream) {
+    if (!workspace || workspace_bytes < kHeaderBytes + 8) return FGX_ERR_WORKSPACE;
+    if (timeout_ms < 1 || timeout_ms > 10000) return FGX_ERR_ARG;
+    if (!is_device_ptr(workspace)) return FGX_ERR_NOT_DEVICE_PTR;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (cudaMemsetAsync(workspace, 0, kHeaderBytes + 8, s) != cudaSuccess) return FGX_ERR_CUDA;
+    char* w = (char*)workspace;
+    launch_wait_probe((const unsigned long long*)(w + kHeaderBytes), (int*)w,
+                      (long long)timeout_ms * 1000000LL, stream);
+    return cudaGetLastError() == cudaSuccess ? FGX_OK : FGX_ERR_CUDA;
+}
+
 int fgx_autotune(int ndim, const float* image, const float* mask, float* dist, int64_t B,
                  int64_t C, int64_t D, int64_t H, int64_t W, const float spacing[3], float v,
                  float lambda, int iterations, void* workspace, size_t workspace_bytes,

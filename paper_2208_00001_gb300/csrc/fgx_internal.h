@@ -197,6 +197,11 @@ int run_adj3d(const SweepArgs& f, const float* grad_dist, const float* image,
 int run_param_sums(const float* mask, const float* g0, float* v_terms, const float* lambda_terms,
                    double* grad_lambda, double* grad_v, int64_t n, int sms, void* stream);
 
+// Failure-detection check (wait_probe.cu): one bounded wait on a tag that
+// nothing writes.
+void launch_wait_probe(const unsigned long long* tag, int* status, long long timeout_ns,
+                       void* stream);
+
 // Signed transform GDT(M) - GDT(1 - M) (signed.cu): workspace bytes for a
 // forward workspace of `forward_bytes` and n elements, and the run.
 size_t signed_workspace_bytes(size_t forward_bytes, int64_t n);

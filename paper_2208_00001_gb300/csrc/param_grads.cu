@@ -60,3 +60,4 @@ int run_param_sums(const float* mask, const float* g0, float* v_terms, const flo
 }
 
 }  // namespace fgx
+
