@@ -88,3 +88,35 @@ def test_header_compiles_as_c(tmp_path):
                         "-I", os.path.join(ROOT, "include"), str(src)],
                        capture_output=True, text=True)
     assert r.returncode == 0, r.stderr
+
+
+@pytest.mark.parametrize("cname,pyname", [("fgx_options", "Options"),
+                                          ("fgx_instance", "Instance"),
+                                          ("fgx_batched_plan", "BatchedPlanC")])
+def test_binding_structs_match_the_header(tmp_path, cname, pyname):
+    """The binding's ctypes mirrors of the header's structs have the C sizes
+    and field offsets (compiled with the host C compiler)."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    import paper_2208_00001_gb300 as fgx
+    py = getattr(fgx, pyname)
+    fields = [f[0] for f in py._fields_]
+    src = tmp_path / "sizes.c"
+    src.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "fgx.h"\n'
+                   "int main(void) {\n"
+                   f'    printf("%zu\\n", sizeof({cname}));\n' +
+                   "".join(f'    printf("%zu\\n", offsetof({cname}, {f.rstrip("_")}));\n'
+                           for f in fields) +  # lambda_ mirrors the C field lambda
+                   "    return 0;\n}\n")
+    exe = tmp_path / "sizes"
+    r = subprocess.run([cc, "-std=c99", "-I", os.path.join(ROOT, "include"), str(src), "-o",
+                        str(exe)], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    out = [int(x) for x in subprocess.run([str(exe)], capture_output=True,
+                                          text=True).stdout.split()]
+    assert out[0] == ctypes.sizeof(py), (cname, out[0], ctypes.sizeof(py))
+    for f, off in zip(fields, out[1:]):
+        assert getattr(py, f).offset == off, (cname, f)
