@@ -81,3 +81,12 @@ def test_euclidean_ignores_the_image():
     img = rng.uniform(0, 1, (1, 3, 11, 9)).astype(np.float32)
     np.testing.assert_array_equal(oracle.euclidean(m, 3.0, 2),
                                   oracle.gdt(img, m, 3.0, 0.0, 2))
+
+
+def test_signed_golden_fixture():
+    from tests import pins
+    g = pins.load_golden("signed_3x3_centre.txt")
+    img = np.array(g["image"], np.float32).reshape(1, 1, 3, 3)
+    m = np.array(g["mask"], np.float32).reshape(1, 1, 3, 3)
+    got = oracle.signed_gdt(img, m, g["v"], g["lambda"], int(g["iterations"]))
+    np.testing.assert_array_equal(got.reshape(-1), np.array(g["expect"], np.float32))
