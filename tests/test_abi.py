@@ -120,3 +120,23 @@ def test_binding_structs_match_the_header(tmp_path, cname, pyname):
     assert out[0] == ctypes.sizeof(py), (cname, out[0], ctypes.sizeof(py))
     for f, off in zip(fields, out[1:]):
         assert getattr(py, f).offset == off, (cname, f)
+
+
+def test_no_gpu_reports_no_device(libpath):
+    """Without a usable GPU the library answers FGX_ERR_DEVICE (no CPU path,
+    no crash) and the binding raises."""
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    lib = ctypes.CDLL(libpath)
+    f = lib.fgx_geodesic_workspace_size
+    f.argtypes = [ctypes.c_int32] + [ctypes.c_int64] * 5 + [ctypes.c_void_p,
+                                                           ctypes.POINTER(ctypes.c_size_t)]
+    f.restype = ctypes.c_int32
+    n = ctypes.c_size_t(0)
+    assert f(2, 1, 1, 1, 64, 64, None, ctypes.byref(n)) == -7  # FGX_ERR_DEVICE
+    import paper_2208_00001_gb300 as fgx
+    with pytest.raises(fgx.FgxError):
+        fgx.workspace_size(2, 1, 1, 1, 64, 64)
+    with pytest.raises(ValueError):
+        fgx.geodesic2d(torch.zeros(1, 1, 8, 8), torch.zeros(1, 1, 8, 8), 1.0, 0.5, 1)
