@@ -103,9 +103,9 @@ int fgx_geodesic3d(const float* image, const float* mask, float* dist, int64_t B
                    const fgx_options* opt, void* stream);
 
 /* Allocation-free forward, for callers that cannot allocate device memory
- * when they need a transform (code inside a CUDA graph capture or an
- * allocator callback, real-time loops on a fixed memory budget, plugins whose
- * host framework owns every allocation).  The paper has no counterpart: it
+ * when they need a transform (code inside an allocator callback, real-time
+ * loops on a fixed memory budget, plugins whose host framework owns every
+ * allocation).  The paper has no counterpart: it
  * concerns only this library's memory handling.  Same arguments and results
  * as fgx_geodesic2d (ndim = 2, D = 1, spacing may be NULL) or fgx_geodesic3d
  * (ndim = 3), but the sweep's scratch (status word, barrier counter, tile
@@ -115,17 +115,28 @@ int fgx_geodesic3d(const float* image, const float* mask, float* dist, int64_t B
  * instance-tiles per pass) are rejected with FGX_ERR_WORKSPACE before any
  * launch.  The first call on each device looks up the array's device address
  * (cudaGetSymbolAddress, with that device current), so make that first call
- * before any stream capture.  All calls on one device share that device's
- * copy of the array, which keeps the last call's contents; each call clears
- * the part it uses, so calls that overlap on the same GPU (for example on two
- * streams) race and must be serialised by the caller.  A device-side wait
- * timeout is not reported by this entry point (there is no workspace to
- * query); use the workspace entry points where that report is needed.  No
- * device memory is allocated or freed. */
+ * before any stream capture.  The address is kept for the life of the
+ * process: after a cudaDeviceReset of that device it is stale, so do not
+ * call this entry point again in that process.  All calls on one device
+ * share that device's copy of the array, which keeps the last call's
+ * contents; each call clears the part it uses, so calls that overlap on the
+ * same GPU (for example on two streams) race and must be serialised by the
+ * caller.  The call returns before the kernels finish; a device-side wait
+ * timeout is recorded in the array's status word, which fgx_noalloc_status
+ * reads.  No device memory is allocated or freed. */
 int fgx_geodesic_noalloc(int ndim, const float* image, const float* mask, float* dist, int64_t B,
                          int64_t C, int64_t D, int64_t H, int64_t W, const float spacing[3],
                          float v, float lambda, int iterations, const fgx_options* opt,
                          void* stream);
+
+/* Status of the last fgx_geodesic_noalloc call queued on `stream` on the
+ * current device: copies the static array's status word to the host on
+ * `stream` (no allocation), synchronises the stream, and returns FGX_OK or
+ * the recorded device error (FGX_ERR_TIMEOUT).  The word is shared by every
+ * call on the device, so with calls overlapping on other streams it may hold
+ * theirs.  Returns FGX_ERR_CUDA if the copy fails.  The paper has no
+ * counterpart. */
+int fgx_noalloc_status(void* stream);
 
 /* Device status word held in a workspace: copies it to the host on `stream`,
  * synchronises the stream, and returns FGX_OK or the recorded device error

@@ -439,8 +439,9 @@ int fgx_batched_run(const fgx_batched_plan* plan, void* stream) {
     if (plan->n3d > 0) {
         if (plan->n2d > 0 && cudaMemsetAsync(w + 64, 0, 4, s) != cudaSuccess)
             return FGX_ERR_CUDA;  // fresh grid-barrier counter for this launch
-        int sms = 0;
-        if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, 0) != cudaSuccess)
+        int dev = 0, sms = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
             return FGX_ERR_CUDA;
         const int st = launch_vol3d_batched(
             w + plan->desc3d_off, plan->n3d, plan->rounds3d, (const int*)(w + plan->waves3d_off),

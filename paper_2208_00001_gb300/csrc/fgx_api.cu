@@ -730,9 +730,9 @@ int fgx_geodesic_bwd_params(int ndim, const float* grad_dist, const float* image
 
 // ----------------------------------------------------------------------------
 // Allocation-free forward.  Some callers cannot allocate device memory at the
-// point where they need a transform: code running inside a CUDA graph capture
-// or a custom allocator's callback, real-time loops with a fixed memory
-// budget, or plugins whose host framework owns every allocation.  This entry
+// point where they need a transform: code running inside a custom allocator's
+// callback, real-time loops with a fixed memory budget, or plugins whose host
+// framework owns every allocation.  This entry
 // point runs the same sweep kernel as fgx_geodesic2d / fgx_geodesic3d, but
 // its scratch (status word, barrier counter, tile progress tags) lives in the
 // static device array below instead of a caller workspace.  Every GPU that
@@ -784,4 +784,21 @@ extern "C" int fgx_geodesic_noalloc(int ndim, const float* image, const float* m
     if (st != FGX_OK) return st;
     return run_forward(ndim, image, mask, dist, B, C, D, H, W, spacing, v, lambda, iterations,
                        nullptr, 0, scratch, kNoAllocScratchBytes, opt, stream);
+}
+
+// Status word of the static scratch (its first int), read back on `stream`
+// after the calls queued before it.  A plain copy from the symbol: nothing is
+// allocated.
+extern "C" int fgx_noalloc_status(void* stream) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return FGX_ERR_DEVICE;
+    int word = 0;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (cudaMemcpyFromSymbolAsync(&word, g_noalloc_scratch, sizeof(int), 0,
+                                  cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess) {
+        cudaGetLastError();
+        return FGX_ERR_CUDA;
+    }
+    return word == 0 ? FGX_OK : word;
 }

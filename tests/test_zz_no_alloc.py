@@ -1,13 +1,15 @@
 """Allocation-free forward (GPU).
 
 fgx_geodesic_noalloc serves callers that cannot allocate device memory when
-they need a transform (graph-capture code, allocator callbacks, fixed-budget
-real-time loops, plugins).  It keeps the sweep's scratch in a static device
-array inside the library.  This test calls it through the C ABI twice in a row
-and checks both results against fgx_geodesic2d / fgx_geodesic3d with a caller
-workspace, bit for bit (the tolerance of every forward parity test), and that
-shapes beyond the static scratch are rejected before any launch.  It lives in
-a file of its own, collected last.
+they need a transform (allocator callbacks, fixed-budget real-time loops,
+plugins whose host framework owns every allocation).  It keeps the sweep's
+scratch in a static device array inside the library.  This test calls it
+through the C ABI twice in a row and checks both results against
+fgx_geodesic2d / fgx_geodesic3d with a caller workspace, bit for bit (the
+tolerance of every forward parity test), that fgx_noalloc_status reads back a
+clean status word after those calls, and that shapes beyond the static
+scratch are rejected before any launch.  It lives in a file of its own,
+collected last.
 """
 import ctypes
 
@@ -73,6 +75,14 @@ def test_noalloc_matches_workspace_entry_point_twice(fgx, make):
         got = out.cpu().numpy()
         want = ref.cpu().numpy()
         np.testing.assert_array_equal(got.view(np.uint32), want.view(np.uint32))
+        assert _status(fgx) == fgx.OK
+
+
+def _status(fgx):
+    f = fgx.lib().fgx_noalloc_status
+    f.argtypes = [ctypes.c_void_p]
+    f.restype = ctypes.c_int
+    return f(ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
 
 
 def test_noalloc_rejects_shapes_beyond_static_scratch(fgx):
