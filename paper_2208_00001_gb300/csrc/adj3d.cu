@@ -1,0 +1,690 @@
+// 3D reverse sweep on register-blocked plane tiles (the adjoint of the
+// Implementation section's six passes per iteration; tiles, warp roles and
+// ring exchange as in the forward plane-tile kernel).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+
+#include "device_sync.cuh"
+#include "fgx_internal.h"
+
+// ---------------------------------------------------------- 3D reverse sweep --
+//
+// The adjoint of the 3D raster scan on the same plane tiles.  For the pass
+// applications in reverse order and the planes of each in reverse sweep
+// order, the adjoint of voxel e is A[e] = G_in[e] + sum over the nine stencil
+// offsets k (in order) of A[x_k] for the child x_k of the next plane of the
+// forward sweep that chose e (code k+1); a child that did not contributes
+// -0.0 (an exact identity).  The adjoint handed to the previous application
+// is A[e] if e kept its value (code 0), else 0; after the first application
+// dL/dM = v * that adjoint.  A needs the 3 x 3 children exactly as the
+// forward needs the 3 x 3 parents, so the tiles, warps, boundary-row
+// exchange and ring refresh are the forward's.  The adjoint lives in two
+// buffers (a pass never writes the one it reads: sums are not idempotent);
+// with the image gradient wanted, A of every application is stored and a
+// separate kernel adds the gradient terms per voxel in the fixed order.
+
+namespace fgx {
+namespace {
+
+using namespace dev;
+
+constexpr int kRows = 4;                  // region rows per compute thread
+constexpr int kCW = 8;                    // compute warps
+constexpr int kPW = 4;                    // producer warps
+constexpr int kRP = kRows * kCW;          // region rows
+constexpr int kRQ = 32;                   // region columns (one per lane)
+constexpr int kRing = 4;                  // ring width = steps between refreshes
+constexpr int kTP = kRP - 2 * kRing;      // owned rows of a tile
+constexpr int kTQ = kRQ - 2 * kRing;      // owned columns of a tile
+constexpr int kPlane = kRP * kRQ;         // region voxels
+constexpr int kChunk = kRing;             // planes per staging chunk
+constexpr int kNst = 3;                   // chunks in the staging ring
+constexpr int kBlock3 = (kCW + kPW) * 32;
+constexpr int kXWords = kTP * kTQ;        // published words per tile and parity
+#define kInf3 __int_as_float(0x7f800000)
+
+__device__ __forceinline__ unsigned int saddr3(const void* p) {
+    return (unsigned int)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init3(unsigned long long* b, unsigned int count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(saddr3(b)), "r"(count)
+                 : "memory");
+}
+__device__ __forceinline__ void mbar_arrive3(unsigned long long* b) {
+    asm volatile("mbarrier.arrive.release.cta.shared::cta.b64 _, [%0];" ::"r"(saddr3(b))
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_try3(unsigned long long* b, unsigned int parity) {
+    unsigned int ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.acquire.cta.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(saddr3(b)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// Bounded wait for the phase of parity `parity` of *b (false on timeout or
+// an earlier failure recorded in the status word).
+__device__ __noinline__ bool mbar_wait3(unsigned long long* b, unsigned int parity, int* status,
+                                        long long timeout_ns) {
+    if (mbar_try3(b, parity)) return true;
+    const long long t0 = gtimer();
+    for (;;) {
+        if (mbar_try3(b, parity)) return true;
+        if (status_of(status) != 0) return false;
+        if (gtimer() - t0 > timeout_ns) {
+            record_timeout(status);
+            return false;
+        }
+    }
+}
+// Compute-warp barrier (the producer warps never join it).
+__device__ __forceinline__ void compute_sync() {
+    asm volatile("bar.sync 1, %0;" ::"n"(kCW * 32) : "memory");
+}
+
+// Position of one tile of one pass application.
+struct Tile3 {
+    const PassGeom* g;
+    float* dist;       // distances of this instance in the pass's layout
+    const float* img;  // intensities of this instance in the pass's layout
+    int64_t csl, csp, csq;  // strides of line, p and q in the image order of the codes
+    int jp, jq, ntq, tile;
+    int64_t b;
+    int L, nch;
+    int64_t p0, q0;  // plane coordinates of region row 0 and column 0
+};
+
+// Exchange area and failure reporting of one launch.
+struct XLink3 {
+    unsigned long long* xbuf;  // [B][max_tiles][2 parities][kXWords]
+    int max_tiles;
+    int* status;
+    long long timeout_ns;
+};
+
+// Ring refresh after step s: publish the owned voxels of plane s, then take
+// every ring voxel inside the volume from the tile that owns it.
+__device__ bool exchange3(const XLink3& a, const Tile3& t, int w, unsigned int tg, int par,
+                          float (&d)[kRows]) {
+    const PassGeom& g = *t.g;
+    const int lane = threadIdx.x & 31;
+    unsigned long long* base = a.xbuf + (size_t)t.b * a.max_tiles * 2 * kXWords;
+    unsigned long long* mine = base + ((size_t)t.tile * 2 + par) * kXWords;
+    const bool qown = lane >= kRing && lane < kRing + kTQ;
+    const int64_t q = t.q0 + lane;
+    const bool qin = q >= 0 && q < g.Q;
+    const unsigned long long* src[kRows];
+    bool need[kRows];
+#pragma unroll
+    for (int i = 0; i < kRows; ++i) {
+        const int r = w * kRows + i;
+        const bool pown = r >= kRing && r < kRing + kTP;
+        const unsigned long long word =
+            ((unsigned long long)tg << 32) | (unsigned int)__float_as_uint(d[i]);
+        if (pown && qown) st_relaxed_u64(mine + (r - kRing) * kTQ + (lane - kRing), word);
+        const int64_t p = t.p0 + r;
+        need[i] = !(pown && qown) && qin && p >= 0 && p < g.P;
+        src[i] = nullptr;
+        if (need[i]) {
+            const int op = (int)(p / kTP), oq = (int)(q / kTQ);
+            const int lr = (int)(p - (int64_t)op * kTP), lq = (int)(q - (int64_t)oq * kTQ);
+            src[i] = base + ((size_t)(op * t.ntq + oq) * 2 + par) * kXWords + lr * kTQ + lq;
+        }
+    }
+    long long t0 = 0;
+    for (unsigned int it = 0;; ++it) {
+        bool done = true;
+#pragma unroll
+        for (int i = 0; i < kRows; ++i) {
+            if (!need[i]) continue;
+            const unsigned long long wv = ld_relaxed_u64(src[i]);
+            if ((unsigned int)(wv >> 32) == tg) {
+                d[i] = __uint_as_float((unsigned int)wv);
+                need[i] = false;
+            } else {
+                done = false;
+            }
+        }
+        if (__all_sync(0xffffffffu, done)) return true;
+        // the status word and the clock are read every 16th poll only
+        if ((it & 15u) == 15u) {
+            int fail = 0;
+            if (lane == 0) {
+                const long long now = gtimer();
+                if (t0 == 0) t0 = now;
+                if (status_of(a.status) != 0) fail = 1;
+                else if (now - t0 > a.timeout_ns) {
+                    record_timeout(a.status);
+                    fail = 1;
+                }
+            }
+            if (__shfl_sync(0xffffffffu, fail, 0)) return false;
+        }
+    }
+}
+
+struct Adj3DArgs {
+    const float* grad_dist;   // [B][N]
+    const uint8_t* codes;     // [T][B][N]
+    float* grad_mask;         // [B][N] or null
+    float* g0;                // [B][N] adjoint of D0, or null
+    float* G[2];              // [B][N] adjoint buffers
+    float* Astore;            // [T][B][N] adjoint of every application, or null
+    int64_t B, N;
+    float v;
+    int T;
+    PassGeom pass[kMaxPasses];
+    int ntp[kMaxPasses], ntq[kMaxPasses];
+    int max_tiles;
+    unsigned long long* xbuf;
+    unsigned int* barrier;
+    int* status;
+    long long timeout_ns;
+};
+
+struct AdjHead3 {
+    unsigned long long full[kNst], empty[kNst];
+    float rowtop[2][kCW][kRQ];
+    float rowbot[2][kCW][kRQ];
+};
+static_assert(sizeof(AdjHead3) % 16 == 0, "stage must stay 16-byte aligned");
+
+// followed by [kNst][kChunk][kPlane] adjoint values and as many code bytes
+size_t adj3_smem_bytes() {
+    return sizeof(AdjHead3) + (size_t)kNst * kChunk * kPlane * (sizeof(float) + 1);
+}
+
+// Producer warps: the incoming adjoint and the codes of the application,
+// plane after plane in reverse sweep order (0 outside the volume).  Plain
+// loads of a whole chunk first, then the stores and one release arrival per
+// thread.
+__device__ bool adj_producer3(const Adj3DArgs& a, const Tile3& t, const float* gsrc,
+                              const uint8_t* csrc, AdjHead3& h, float* stg, uint8_t* stc,
+                              unsigned int cb) {
+    const PassGeom& g = *t.g;
+    const int lane = threadIdx.x & 31, pw = (threadIdx.x >> 5) - kCW;
+    const int64_t q = t.q0 + lane;
+    const bool qin = q >= 0 && q < g.Q;
+    for (int c = 0; c < t.nch; ++c) {
+        const unsigned int gc = cb + c;
+        const int slot = (int)(gc % kNst);
+        if (gc >= (unsigned)kNst &&
+            !__all_sync(0xffffffffu, mbar_wait3(&h.empty[slot], ((gc / kNst) & 1u) ^ 1u,
+                                                a.status, a.timeout_ns)))
+            return false;
+        float gv[kChunk][kRP / kPW];
+        unsigned int cv[kChunk][kRP / kPW];
+#pragma unroll
+        for (int j = 0; j < kChunk; ++j) {
+            const int s = c * kChunk + j;
+            const int64_t line = g.dir > 0 ? (t.L - 1 - s) : s;
+#pragma unroll
+            for (int rr = 0; rr < kRP / kPW; ++rr) {
+                const int64_t p = t.p0 + pw + kPW * rr;
+                const bool in = s < t.L && qin && p >= 0 && p < g.P;
+                const int64_t off = line * g.sl + p * g.sp + q * g.sq;
+                gv[j][rr] = in ? __ldcg(gsrc + off) : 0.0f;
+                cv[j][rr] = in ? (unsigned int)__ldg(csrc + off) : 0u;
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < kChunk; ++j)
+#pragma unroll
+            for (int rr = 0; rr < kRP / kPW; ++rr) {
+                const int r = pw + kPW * rr;
+                stg[((size_t)slot * kChunk + j) * kPlane + r * kRQ + lane] = gv[j][rr];
+                stc[((size_t)slot * kChunk + j) * kPlane + r * kRQ + lane] = (uint8_t)cv[j][rr];
+            }
+        mbar_arrive3(&h.full[slot]);  // every lane releases its own stores
+    }
+    return true;
+}
+
+// Compute warps: planes 0 .. L-1 of the reverse sweep.
+__device__ bool adj_compute3(const Adj3DArgs& a, const Tile3& t, int t_app, AdjHead3& h,
+                             const float* stg, const uint8_t* stc, unsigned int cb, float* gdst,
+                             float* gmask, float* adst, float* g0) {
+    const PassGeom& g = *t.g;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int64_t q = t.q0 + lane;
+    const bool qin = q >= 0 && q < g.Q;
+    const bool qown = lane >= kRing && lane < kRing + kTQ;
+    bool own[kRows];
+    int64_t goff[kRows];
+#pragma unroll
+    for (int i = 0; i < kRows; ++i) {
+        const int r = w * kRows + i;
+        const int64_t p = t.p0 + r;
+        own[i] = qin && p >= 0 && p < g.P && qown && r >= kRing && r < kRing + kTP;
+        goff[i] = p * g.sp + q * g.sq;
+    }
+    const int cl = max(lane - 1, 0), cr = min(lane + 1, kRQ - 1);
+    const int rows0 = w * kRows;
+    const float nz = __int_as_float(0x80000000);
+    bool failed = false;
+    float ap[kRows];  // adjoint of the previous plane of the reverse sweep
+#pragma unroll
+    for (int i = 0; i < kRows; ++i) ap[i] = nz;
+    const unsigned int tag_base = ((unsigned int)(t_app + 1)) << 16;
+    int xi = 0;
+    for (int s = 0; s < t.L; ++s) {
+        const unsigned int gc = cb + s / kChunk;
+        const int j = s % kChunk;
+        const int slot = (int)(gc % kNst);
+        if (j == 0 && !failed &&
+            !__all_sync(0xffffffffu, mbar_wait3(&h.full[slot], (gc / kNst) & 1u, a.status,
+                                                a.timeout_ns)))
+            failed = true;
+        const int rb = s & 1;
+        h.rowtop[rb][w][lane] = ap[0];
+        h.rowbot[rb][w][lane] = ap[kRows - 1];
+        compute_sync();
+        if (threadIdx.x == 0 && s >= 2 && (s - 2) % kChunk == kChunk - 1)
+            mbar_arrive3(&h.empty[(cb + (s - 2) / kChunk) % kNst]);
+        // children: adjoints of the previous plane (3 x 3 around each voxel)
+        float col[kRows + 2], lft[kRows + 2], rgt[kRows + 2];
+        col[0] = w > 0 ? h.rowbot[rb][w - 1][lane] : nz;
+#pragma unroll
+        for (int i = 0; i < kRows; ++i) col[i + 1] = ap[i];
+        col[kRows + 1] = w < kCW - 1 ? h.rowtop[rb][w + 1][lane] : nz;
+#pragma unroll
+        for (int k = 0; k < kRows + 2; ++k) {
+            lft[k] = __shfl_up_sync(0xffffffffu, col[k], 1);
+            rgt[k] = __shfl_down_sync(0xffffffffu, col[k], 1);
+            if (lane == 0) lft[k] = nz;
+            if (lane == 31) rgt[k] = nz;
+        }
+        // their codes (plane s-1 of this application; none before the first)
+        unsigned int cc[kRows + 2][3];
+        if (s > 0) {
+            const unsigned int gcp = cb + (s - 1) / kChunk;
+            const uint8_t* Pc = stc + ((size_t)(gcp % kNst) * kChunk + (s - 1) % kChunk) * kPlane;
+#pragma unroll
+            for (int k = 0; k < kRows + 2; ++k) {
+                const int rr = min(max(rows0 + k - 1, 0), kRP - 1);
+                cc[k][0] = Pc[rr * kRQ + cl];
+                cc[k][1] = Pc[rr * kRQ + lane];
+                cc[k][2] = Pc[rr * kRQ + cr];
+            }
+        } else {
+#pragma unroll
+            for (int k = 0; k < kRows + 2; ++k) cc[k][0] = cc[k][1] = cc[k][2] = 0u;
+        }
+        const float* Sg = stg + ((size_t)slot * kChunk + j) * kPlane;
+        const uint8_t* Sc = stc + ((size_t)slot * kChunk + j) * kPlane;
+        const int64_t lo = (int64_t)(g.dir > 0 ? (t.L - 1 - s) : s) * g.sl;
+        float na[kRows];
+#pragma unroll
+        for (int i = 0; i < kRows; ++i) {
+            float acc = Sg[(rows0 + i) * kRQ + lane];
+#pragma unroll
+            for (int k = 0; k < 9; ++k) {
+                // child of offset k = (dp, dq) sits at (row - dp, column - dq)
+                const int dp = k / 3 - 1, dq = k % 3 - 1;
+                const int rk = i + 1 - dp;
+                const float ax = dq > 0 ? lft[rk] : (dq == 0 ? col[rk] : rgt[rk]);
+                const unsigned int cx = cc[rk][1 - dq];
+                acc = __fadd_rn(acc, cx == (unsigned int)(k + 1) ? ax : nz);
+            }
+            na[i] = acc;
+            if (own[i]) {
+                const float gout = Sc[(rows0 + i) * kRQ + lane] != 0 ? 0.0f : acc;
+                if (gmask) gmask[lo + goff[i]] = __fmul_rn(a.v, gout);
+                if (g0) g0[lo + goff[i]] = gout;
+                if (gdst) gdst[lo + goff[i]] = gout;
+                if (adst) adst[lo + goff[i]] = acc;
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < kRows; ++i) ap[i] = na[i];
+        if (s >= kRing && s % kRing == 0 && s + 1 < t.L) {
+            if (!failed && !exchange3(XLink3{a.xbuf, a.max_tiles, a.status, a.timeout_ns}, t, w,
+                                      tag_base | (unsigned int)(xi + 1), xi & 1, ap))
+                failed = true;
+            ++xi;
+        }
+    }
+    compute_sync();
+    if (threadIdx.x == 0) {
+        for (int c = max(0, t.nch - 2); c < t.nch; ++c) {
+            const int last = min(c * kChunk + kChunk - 1, t.L - 1);
+            if (last >= t.L - 2) mbar_arrive3(&h.empty[(cb + c) % kNst]);
+        }
+    }
+    return !failed;
+}
+
+template <bool STORE_A>
+__global__ void __launch_bounds__(kBlock3, 1) adj3d_kernel(const Adj3DArgs a) {
+    extern __shared__ __align__(16) unsigned char smem3[];
+    AdjHead3& h = *reinterpret_cast<AdjHead3*>(smem3);
+    float* stg = reinterpret_cast<float*>(smem3 + sizeof(AdjHead3));
+    uint8_t* stc = reinterpret_cast<uint8_t*>(stg + (size_t)kNst * kChunk * kPlane);
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < kNst; ++i) {
+            mbar_init3(&h.full[i], kPW * 32);  // one arrival per producer thread
+            mbar_init3(&h.empty[i], 1);
+        }
+    }
+    __syncthreads();
+    unsigned int epoch = 1;
+    unsigned int cb = 0;
+    int in_idx = -1;  // the first application reads the caller's dL/dD
+    bool alive = true;
+    for (int t_app = a.T - 1; t_app >= 0 && alive; --t_app) {
+        const int pass = t_app % kMaxPasses;
+        const PassGeom& g = a.pass[pass];
+        const int ntiles = a.ntp[pass] * a.ntq[pass];
+        const int per_wave = gridDim.x / ntiles;
+        const int64_t nwaves = (a.B + per_wave - 1) / per_wave;
+        const int L = (int)g.L;
+        const int nch = (L + kChunk - 1) / kChunk;
+        const int out_idx = in_idx == 0 ? 1 : 0;
+        for (int64_t wv = 0; wv < nwaves; ++wv) {
+            if ((int)blockIdx.x >= per_wave * ntiles) continue;
+            const int64_t b = wv * per_wave + blockIdx.x / ntiles;
+            if (b >= a.B) continue;
+            Tile3 t;
+            t.g = &g;
+            t.tile = blockIdx.x % ntiles;
+            t.jp = t.tile / a.ntq[pass];
+            t.jq = t.tile % a.ntq[pass];
+            t.ntq = a.ntq[pass];
+            t.b = b;
+            t.L = L;
+            t.nch = nch;
+            t.p0 = (int64_t)t.jp * kTP - kRing;
+            t.q0 = (int64_t)t.jq * kTQ - kRing;
+            const float* gsrc = (in_idx < 0 ? a.grad_dist : a.G[in_idx]) + b * a.N;
+            if ((int)(threadIdx.x >> 5) >= kCW) {
+                adj_producer3(a, t, gsrc, a.codes + ((int64_t)t_app * a.B + b) * a.N, h, stg,
+                              stc, cb);
+            } else {
+                float* gdst = t_app > 0 ? a.G[out_idx] + b * a.N : nullptr;
+                float* gmask = (t_app == 0 && a.grad_mask) ? a.grad_mask + b * a.N : nullptr;
+                float* adst = STORE_A ? a.Astore + ((int64_t)t_app * a.B + b) * a.N : nullptr;
+                float* g0 = (t_app == 0 && a.g0) ? a.g0 + b * a.N : nullptr;
+                adj_compute3(a, t, a.T - 1 - t_app, h, stg, stc, cb, gdst, gmask, adst, g0);
+            }
+            cb += (unsigned int)nch;
+        }
+        alive = grid_barrier(a.barrier, epoch++, a.status, a.timeout_ns);
+        in_idx = out_idx;
+    }
+}
+
+struct Grad3DArgs {
+    const float* image;       // [B][C][N]
+    const uint8_t* codes;     // [T][B][N]
+    const float* Astore;      // [T][B][N]
+    float* grad_image;        // [B][C][N], or null
+    float* lambda_terms;      // [B][N] per-voxel terms of dL/dlambda, or null
+    int64_t B, C, N;
+    int64_t D, H, W;
+    float lambda;
+    int T;
+    PassGeom pass[kMaxPasses];
+    float s2[kMaxPasses][9];  // |offset|^2 of every pass and stencil offset
+};
+
+__device__ __forceinline__ float grad_cost3(const float* img, int64_t x, int64_t y, int C,
+                                            int64_t n, float t, float lam,
+                                            float* di2_out = nullptr) {
+    float di2 = 0.0f;
+    for (int ch = 0; ch < C; ++ch) {
+        const float d = __fsub_rn(img[ch * n + x], img[ch * n + y]);
+        di2 = __fadd_rn(di2, __fmul_rn(d, d));
+    }
+    if (di2_out) *di2_out = di2;
+    return __fsqrt_rn(__fadd_rn(t, __fmul_rn(lam, di2)));
+}
+
+// Image gradient of the 3D reverse sweep, one thread per voxel, pass
+// applications in reverse order: per application the terms of the children
+// that chose the voxel (offset order), then the term of its own parent.
+// The gradient accumulates in the output array (each voxel is touched by its
+// own thread only).  With lambda_terms, each voxel also sums, over the
+// applications in the same order, its adjoint times d c / d lambda of its own
+// parent edge, (di2 - s2) / (c + c).
+template <int CC, bool IMG, typename Idx>
+__global__ void __launch_bounds__(256) grad3d_kernel(const Grad3DArgs a) {
+    // CC > 0: the CC channel sums stay in registers (written once at the end);
+    // CC == 0: any channel count, accumulated in the output array.  Idx: the
+    // index type within one instance (32-bit when every offset fits)
+    const float lam = a.lambda;
+    const int C = CC > 0 ? CC : (int)a.C;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.B * a.N;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t b = i / a.N;
+        const Idx e = (Idx)(i - b * a.N);
+        const Idx HW = (Idx)(a.H * a.W), Wd = (Idx)a.W;
+        const Idx dd = e / HW, rem = e - dd * HW;
+        const Idx hh = rem / Wd, ww = rem - hh * Wd;
+        const float* img = a.image + b * a.C * a.N;
+        float* gout = IMG ? a.grad_image + b * a.C * a.N + e : nullptr;
+        float lt = 0.0f;
+        float gi[CC > 0 ? CC : 1];
+#pragma unroll
+        for (int ch = 0; ch < (CC > 0 ? CC : 1); ++ch) gi[ch] = 0.0f;
+        if (IMG && CC == 0)
+            for (int ch = 0; ch < C; ++ch) gout[ch * a.N] = 0.0f;
+        // g -= wgt (I(x) - I(y))  or  g += wgt (I(x) - I(y)), per channel
+        auto add_term = [&](float wgt, Idx x, Idx y, bool minus) {
+            if (CC > 0) {
+#pragma unroll
+                for (int ch = 0; ch < (CC > 0 ? CC : 1); ++ch) {
+                    const float term =
+                        __fmul_rn(wgt, __fsub_rn(img[ch * a.N + x], img[ch * a.N + y]));
+                    gi[ch] = minus ? __fsub_rn(gi[ch], term) : __fadd_rn(gi[ch], term);
+                }
+            } else {
+                for (int ch = 0; ch < C; ++ch) {
+                    const float term =
+                        __fmul_rn(wgt, __fsub_rn(img[ch * a.N + x], img[ch * a.N + y]));
+                    gout[ch * a.N] = minus ? __fsub_rn(gout[ch * a.N], term)
+                                           : __fadd_rn(gout[ch * a.N], term);
+                }
+            }
+        };
+        for (int t = a.T - 1; t >= 0; --t) {
+            const PassGeom& g = a.pass[t % kMaxPasses];
+            const Idx line = g.axis == 0 ? dd : (g.axis == 1 ? hh : ww);
+            const Idx p = g.axis == 0 ? hh : dd;
+            const Idx q = g.axis == 2 ? hh : ww;
+            const Idx L = (Idx)g.L, P = (Idx)g.P, Q = (Idx)g.Q;
+            const Idx sl = (Idx)g.sl, sp = (Idx)g.sp, sq = (Idx)g.sq;
+            const float* A = a.Astore + ((int64_t)t * a.B + b) * a.N;
+            const uint8_t* cd = a.codes + ((int64_t)t * a.B + b) * a.N;
+            // children on the next plane of the forward sweep, offset order
+            const Idx cl = line + g.dir;
+            if (IMG && cl >= 0 && cl < L) {
+#pragma unroll
+                for (int k = 0; k < 9; ++k) {
+                    const Idx cp = p - (k / 3 - 1), cq = q - (k % 3 - 1);
+                    if (cp < 0 || cp >= P || cq < 0 || cq >= Q) continue;
+                    const Idx x = cl * sl + cp * sp + cq * sq;
+                    if (cd[x] != k + 1) continue;
+                    const float c = grad_cost3(img, x, e, C, a.N, g.t[k], lam);
+                    if (c > 0.0f) add_term(__fdiv_rn(__fmul_rn(A[x], lam), c), x, e, true);
+                }
+            }
+            // own parent on the previous plane of the forward sweep
+            const int code = cd[e];
+            const Idx pl = line - g.dir;
+            if (code >= 1 && code <= 9 && pl >= 0 && pl < L) {
+                const int k = code - 1;
+                const Idx pp = p + (k / 3 - 1), pq = q + (k % 3 - 1);
+                if (pp >= 0 && pp < P && pq >= 0 && pq < Q) {
+                    const Idx y = pl * sl + pp * sp + pq * sq;
+                    float di2;
+                    const float c = grad_cost3(img, e, y, C, a.N, g.t[k], lam, &di2);
+                    if (c > 0.0f) {
+                        if (a.lambda_terms) {
+                            const float s2 = a.s2[t % kMaxPasses][k];
+                            lt = __fadd_rn(lt, __fmul_rn(A[e], __fdiv_rn(__fsub_rn(di2, s2),
+                                                                         __fadd_rn(c, c))));
+                        }
+                        if (IMG) add_term(__fdiv_rn(__fmul_rn(A[e], lam), c), e, y, false);
+                    }
+                }
+            }
+        }
+        if (IMG && CC > 0) {
+#pragma unroll
+            for (int ch = 0; ch < (CC > 0 ? CC : 1); ++ch) gout[ch * a.N] = gi[ch];
+        }
+        if (a.lambda_terms) a.lambda_terms[i] = lt;
+    }
+}
+
+struct Adj3DPlan {
+    int grid = 0, max_tiles = 0;
+    int ntp[kMaxPasses] = {}, ntq[kMaxPasses] = {};
+    size_t xbuf_off = 0, g_off[2] = {}, a_off = 0, total = 0;
+};
+
+bool plan_adj3d(const SweepArgs& f, int iterations, const fgx_options* opt, int sms,
+                Adj3DPlan* p) {
+    if (f.ndim != 3 || iterations <= 0) return false;
+    if (opt && (opt->tile_lines || opt->tile_width || opt->tile_height)) return false;
+    int max_tiles = 1;
+    for (int i = 0; i < kMaxPasses; ++i) {
+        const PassGeom& g = f.pass[i];
+        p->ntp[i] = (int)std::max<int64_t>(1, (g.P + kTP - 1) / kTP);
+        p->ntq[i] = (int)std::max<int64_t>(1, (g.Q + kTQ - 1) / kTQ);
+        if ((int64_t)p->ntp[i] * p->ntq[i] > (1 << 20)) return false;
+        max_tiles = std::max(max_tiles, p->ntp[i] * p->ntq[i]);
+    }
+    p->max_tiles = max_tiles;
+    const size_t smem = adj3_smem_bytes();
+    if (cudaFuncSetAttribute(adj3d_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem) != cudaSuccess ||
+        cudaFuncSetAttribute(adj3d_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem) != cudaSuccess)
+        return false;
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, adj3d_kernel<true>, kBlock3,
+                                                      smem) != cudaSuccess ||
+        per_sm < 1)
+        return false;
+    int64_t grid = (int64_t)per_sm * sms;
+    if (opt && opt->max_blocks) grid = std::min<int64_t>(grid, opt->max_blocks);
+    grid = std::min<int64_t>(grid, std::max<int64_t>(1, f.B * max_tiles));
+    if (grid < max_tiles) return false;
+    p->grid = (int)grid;
+    auto al = [](size_t x) { return (x + 255) & ~size_t(255); };
+    size_t off = kHeaderBytes;
+    p->xbuf_off = off;
+    off += al((size_t)std::max<int64_t>(f.B, 1) * max_tiles * 2 * kXWords * 8);
+    for (int i = 0; i < 2; ++i) {
+        p->g_off[i] = off;
+        off += al((size_t)f.B * f.N * 4);
+    }
+    p->a_off = off;
+    off += al((size_t)iterations * kMaxPasses * f.B * f.N * 4);
+    p->total = off;
+    return true;
+}
+
+}  // namespace
+
+size_t adj3d_workspace_bytes(const SweepArgs& f, int iterations, const fgx_options* opt,
+                             int sms) {
+    Adj3DPlan p;
+    return plan_adj3d(f, iterations, opt, sms, &p) ? p.total : 0;
+}
+
+int run_adj3d(const SweepArgs& f, const float* grad_dist, const float* image,
+              const uint8_t* codes, float* grad_image, float* grad_mask, float v, int iterations,
+              void* workspace, size_t ws_bytes, const fgx_options* opt, int sms, void* stream,
+              float* g0, float* lambda_terms, const float* s2) {
+    if (lambda_terms && !s2) return FGX_ERR_ARG;
+    Adj3DPlan p;
+    if (!plan_adj3d(f, iterations, opt, sms, &p)) return FGX_ERR_UNSUPPORTED;
+    if (ws_bytes < p.total) return FGX_ERR_WORKSPACE;
+    char* w = (char*)workspace;
+    Adj3DArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.grad_dist = grad_dist;
+    a.codes = codes;
+    a.grad_mask = grad_mask;
+    a.g0 = g0;
+    a.G[0] = (float*)(w + p.g_off[0]);
+    a.G[1] = (float*)(w + p.g_off[1]);
+    const bool need_a = grad_image || lambda_terms;  // the per-voxel pass needs every A
+    a.Astore = need_a ? (float*)(w + p.a_off) : nullptr;
+    a.B = f.B;
+    a.N = f.N;
+    a.v = v;
+    a.T = iterations * kMaxPasses;
+    for (int i = 0; i < kMaxPasses; ++i) {
+        a.pass[i] = f.pass[i];
+        a.ntp[i] = p.ntp[i];
+        a.ntq[i] = p.ntq[i];
+    }
+    a.max_tiles = p.max_tiles;
+    a.xbuf = (unsigned long long*)(w + p.xbuf_off);
+    a.barrier = (unsigned int*)(w + 64);
+    a.status = (int*)w;
+    a.timeout_ns = f.timeout_ns;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (cudaMemsetAsync(workspace, 0, p.g_off[0], s) != cudaSuccess) return FGX_ERR_CUDA;
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    cfg.gridDim = dim3((unsigned)p.grid);
+    cfg.blockDim = dim3(kBlock3);
+    cfg.dynamicSmemBytes = adj3_smem_bytes();
+    cfg.stream = s;
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    if (cudaLaunchKernelEx(&cfg, need_a ? adj3d_kernel<true> : adj3d_kernel<false>, a) !=
+        cudaSuccess)
+        return FGX_ERR_CUDA;
+    if (need_a) {
+        Grad3DArgs g;
+        std::memset(&g, 0, sizeof(g));
+        g.image = image;
+        g.codes = codes;
+        g.Astore = a.Astore;
+        g.grad_image = grad_image;
+        g.lambda_terms = lambda_terms;
+        if (s2)
+            for (int i = 0; i < kMaxPasses; ++i)
+                for (int k = 0; k < 9; ++k) g.s2[i][k] = s2[i * 9 + k];
+        g.B = f.B;
+        g.C = f.C;
+        g.N = f.N;
+        g.D = f.pass[0].L;        // extent of the axis of the first pass pair (D)
+        g.H = f.pass[2].L;
+        g.W = f.pass[4].L;
+        g.lambda = f.lambda;
+        g.T = a.T;
+        for (int i = 0; i < kMaxPasses; ++i) g.pass[i] = f.pass[i];
+        const int64_t n = f.B * f.N;
+        const int gg = (int)std::min<int64_t>((n + 255) / 256, (int64_t)sms * 8);
+        const int gb = std::max(gg, 1);
+        // 32-bit offsets within an instance when every one fits (C * N < 2^31)
+        if (f.C * f.N < ((int64_t)1 << 31)) {
+            if (!grad_image) grad3d_kernel<0, false, int><<<gb, 256, 0, s>>>(g);
+            else if (f.C == 1) grad3d_kernel<1, true, int><<<gb, 256, 0, s>>>(g);
+            else if (f.C == 2) grad3d_kernel<2, true, int><<<gb, 256, 0, s>>>(g);
+            else if (f.C == 3) grad3d_kernel<3, true, int><<<gb, 256, 0, s>>>(g);
+            else grad3d_kernel<0, true, int><<<gb, 256, 0, s>>>(g);
+        } else {
+            if (!grad_image) grad3d_kernel<0, false, int64_t><<<gb, 256, 0, s>>>(g);
+            else grad3d_kernel<0, true, int64_t><<<gb, 256, 0, s>>>(g);
+        }
+        if (cudaGetLastError() != cudaSuccess) return FGX_ERR_CUDA;
+    }
+    return FGX_OK;
+}
+
+}  // namespace fgx
