@@ -4,16 +4,17 @@
 //
 // Decomposition.  One cooperative persistent launch runs all passes.  For a
 // pass along one axis the plane (P x Q voxels) is cut into tiles of
-// kTP x kTQ owned voxels; one thread block per tile computes a region of
-// kRP x kRQ = 32 x 32 voxels: the tile plus a ring of kRing voxels on every
-// side.  Eight compute warps each hold four region rows: lane q owns column q
+// (32 - 2K) x (32 - 2K) owned voxels; one thread block per tile computes a
+// region of kRP x kRQ = 32 x 32 voxels: the tile plus a ring of K voxels on
+// every side, K = 4 or 8 per pass (the planner takes 8 where the larger tile
+// count still fits the grid: half the ring refreshes for the same region).  Eight compute warps each hold four region rows: lane q owns column q
 // of the region and keeps the four distances of its rows in registers.  A
 // plane step needs the 3 x 3 parents of every voxel: the own column's rows
 // come from registers plus the two boundary rows of the warps above and below
 // (shared memory, one named barrier of the compute warps per step), the
 // neighbouring columns by warp shuffles.  The dependency cone shrinks the
 // exact part of the region by one voxel per side and step, so the owned
-// voxels stay exact for kRing steps; then every block publishes its owned
+// voxels stay exact for K steps; then every block publishes its owned
 // voxels as 64-bit (value, tag) words and refreshes its ring from the
 // owners' words (bounded polling, no fences: every word carries its own
 // tag).  Passes are separated by a grid barrier.  Ring voxels are recomputed
@@ -63,21 +64,22 @@ constexpr int kCW = 8;                    // compute warps
 constexpr int kPW = 4;                    // producer warps (cp.async staging)
 constexpr int kRP = kRows * kCW;          // region rows
 constexpr int kRQ = 32;                   // region columns (one per lane)
-constexpr int kRing = 4;                  // ring width = steps between refreshes
-constexpr int kTP = kRP - 2 * kRing;      // owned rows of a tile
-constexpr int kTQ = kRQ - 2 * kRing;      // owned columns of a tile
+constexpr int kRing = 4;                  // narrow ring width = steps between refreshes
+constexpr int kRingWide = 8;              // wide ring width
+constexpr int kTP = kRP - 2 * kRing;      // owned rows of a narrow-ring tile (the most)
+constexpr int kTQ = kRQ - 2 * kRing;      // owned columns of a narrow-ring tile
 constexpr int kChunk = 4;                 // planes per staging chunk
 constexpr int kNst = 3;                   // chunks in the staging ring
 constexpr int kSlots = kNst * kChunk;     // staged planes
 constexpr int kArr = (kRP + 2) * kRQ;     // floats of one staged array (spare row above and below)
 constexpr int kMaxCI = 3;                 // intensity channels the stage holds
-constexpr int kXWords = kTP * kTQ;        // published words per tile and parity
+constexpr int kXWords = kTP * kTQ;        // published words per tile and parity (room for the most)
 constexpr int kRangeFlagOffset = 32;      // workspace header: intensity range flag
 constexpr int kTransposeWarps = 8;        // warps of a block that transpose (8 shared tiles)
 constexpr int kMaps = 6;
 #define kInf3 __int_as_float(0x7f800000)
 
-static_assert(kChunk == kRing && (kChunk & (kChunk - 1)) == 0, "chunk = ring width, a power of 2");
+static_assert(kRing % kChunk == 0 && kRingWide % kChunk == 0, "refreshes at chunk boundaries");
 
 enum { kModeConst = 0, kModeAbs = 1, kModeGeneral = 2 };
 // Tensor maps of one call: distances and intensities in the layouts of the
@@ -97,6 +99,7 @@ struct Vol3DArgs {  // aligned as CUtensorMap (the descriptor arrays of batched 
     int mode;
     PassGeom pass[kMaxPasses];
     int ntp[kMaxPasses], ntq[kMaxPasses];
+    int ring[kMaxPasses];      // ring width K of each pass (4 or 8)
     int max_tiles;
     unsigned long long* xbuf;  // [B][max_tiles][2 parities][kXWords]
     unsigned int* barrier;
@@ -201,6 +204,7 @@ struct Tile3 {
     uint8_t* codes;    // this application's codes of the instance (image order), or null
     int64_t csl, csp, csq;  // strides of line, p and q in the image order of the codes
     int tile, ntq, L, nch;
+    int K, tp, tq;     // ring width and owned extents (tp = tq = 32 - 2K)
     int p0, q0;        // plane coordinates of region row 0 and column 0
     int64_t b;
     // tensor maps of the pass and the order of the box coordinates: the
@@ -364,7 +368,7 @@ __device__ __forceinline__ float cost3(const float (&ix)[CI > 0 ? CI : 1],
     return __fsqrt_rn(__fadd_rn(t, __fmul_rn(lam, di2)));
 }
 
-// Compute warps of one tile: plane steps 1 .. L-1, ring refresh every kRing
+// Compute warps of one tile: plane steps 1 .. L-1, ring refresh every K
 // steps, owned voxels written to the distance map (and with CODES their
 // parent codes: 0 if the voxel kept its value, else 1 + the lowest stencil
 // offset whose candidate is the strictly smaller minimum).  With TMA, thread
@@ -379,7 +383,8 @@ __device__ bool compute3(const Vol3DArgs& a, const Tile3& t, int t_app, Head3& h
     const int rows0 = w * kRows;
     const int q = t.q0 + lane;
     const bool qin = q >= 0 && q < g.Q;
-    const bool qown = lane >= kRing && lane < kRing + kTQ;
+    const int K = t.K, tp = t.tp, tq = t.tq;
+    const bool qown = lane >= K && lane < K + tq;
     const int64_t line0 = g.dir > 0 ? 0 : (int64_t)(t.L - 1);
     const int64_t dsl = g.dir > 0 ? g.sl : -g.sl;
     const int64_t dcl = g.dir > 0 ? t.csl : -t.csl;
@@ -392,15 +397,15 @@ __device__ bool compute3(const Vol3DArgs& a, const Tile3& t, int t_app, Head3& h
         const int r = rows0 + i;
         const int p = t.p0 + r;
         valid[i] = qin && p >= 0 && p < g.P;
-        const bool pown = r >= kRing && r < kRing + kTP;
+        const bool pown = r >= K && r < K + tp;
         own[i] = valid[i] && qown && pown;
         dp[i] = t.dist + line0 * g.sl + (int64_t)p * g.sp + (int64_t)q * g.sq;
         if (CODES) cp[i] = t.codes + line0 * t.csl + (int64_t)p * t.csp + (int64_t)q * t.csq;
-        xmine[i] = own[i] ? (r - kRing) * kTQ + (lane - kRing) : -1;
+        xmine[i] = own[i] ? (r - K) * tq + (lane - K) : -1;
         xsrc[i] = -1;
         if (valid[i] && !(pown && qown)) {
-            const int op = p / kTP, oq = q / kTQ;
-            xsrc[i] = (op * t.ntq + oq) * 2 * kXWords + (p - op * kTP) * kTQ + (q - oq * kTQ);
+            const int op = p / tp, oq = q / tq;
+            xsrc[i] = (op * t.ntq + oq) * 2 * kXWords + (p - op * tp) * tq + (q - oq * tq);
         }
     }
     const float lam = a.lambda;
@@ -517,7 +522,7 @@ __device__ bool compute3(const Vol3DArgs& a, const Tile3& t, int t_app, Head3& h
                 if (CODES) *cp[i] = (uint8_t)code;
             }
         }
-        if ((s & (kRing - 1)) == 0 && s + 1 < t.L) {
+        if ((s & (K - 1)) == 0 && s + 1 < t.L) {
             if (!failed && !exchange3(a, t.b, t.tile, tag_base | (unsigned int)(xi + 1), xi & 1, d,
                                       xmine, xsrc))
                 failed = true;
@@ -681,8 +686,10 @@ __global__ void __launch_bounds__(TMA ? kCW * 32 : (kCW + kPW) * 32, 1)
             t.csq = on_t ? a.W : g.sq;
             t.L = L;
             t.nch = nch;
-            t.p0 = (t.tile / t.ntq) * kTP - kRing;
-            t.q0 = (t.tile % t.ntq) * kTQ - kRing;
+            t.K = a.ring[pass];
+            t.tp = t.tq = kRP - 2 * t.K;
+            t.p0 = (t.tile / t.ntq) * t.tp - t.K;
+            t.q0 = (t.tile % t.ntq) * t.tq - t.K;
             t.map_d = pass < 2 ? kMapDistD : (pass < 4 ? kMapDistH : kMapDistW);
             t.map_i = t.map_d + 3;
             t.rows_z = pass == 2 || pass == 3;
@@ -771,8 +778,10 @@ __global__ void __launch_bounds__(kBlockBatched3, 1) vol3d_batched_kernel(const 
             t.csq = g.sq;
             t.L = (int)g.L;
             t.nch = t.L > 1 ? (t.L + kChunk - 1) / kChunk : 0;
-            t.p0 = (t.tile / t.ntq) * kTP - kRing;
-            t.q0 = (t.tile % t.ntq) * kTQ - kRing;
+            t.K = a.ring[pass];
+            t.tp = t.tq = kRP - 2 * t.K;
+            t.p0 = (t.tile / t.ntq) * t.tp - t.K;
+            t.q0 = (t.tile % t.ntq) * t.tq - t.K;
             t.map_d = t.map_i = t.rows_z = 0;
             if (t.nch > 0) run_item3(a, t, r, h, stage, cb);
             cb += (unsigned int)t.nch;
@@ -863,17 +872,26 @@ bool make_maps(Vol3DArgs& a) {
 
 struct Vol3DPlan {
     int mode = 0, CI = 0, grid = 0, max_tiles = 0;
-    int ntp[kMaxPasses] = {}, ntq[kMaxPasses] = {};
+    int ntp[kMaxPasses] = {}, ntq[kMaxPasses] = {}, ring[kMaxPasses] = {};
     size_t smem = 0, ws_bytes = 0;
     size_t zero_bytes = 0;             // header and exchange words (cleared per call)
     size_t distT_off = 0, imageT_off = 0;  // transposed copies for the W passes
 };
 
+int64_t tiles_of(const PassGeom& g, int K) {
+    const int64_t t = kRP - 2 * K;
+    return std::max<int64_t>(1, (g.P + t - 1) / t) * std::max<int64_t>(1, (g.Q + t - 1) / t);
+}
+
 // Whether the 3D call fits this kernel (at most kMaxCI channels in the
 // general cost, every tile of a pass co-resident, no tile-shape options),
-// and its launch geometry.
+// and its launch geometry.  Per pass the ring is 8 wide where its tiles
+// still fit the grid in about as few waves as the narrow ring's: a plane
+// step with the narrow ring costs about two units (the step and a quarter of
+// a refresh that takes as long as four steps' arithmetic), with the wide ring
+// about 1.5.  `wide` = false keeps every pass narrow (batched launches).
 bool plan_vol3d(const SweepArgs& f, const fgx_options* opt, int sms, Vol3DPlan* vp,
-                bool any_mode = false) {
+                bool any_mode = false, bool wide = true) {
     if (f.ndim != 3) return false;
     if (opt && (opt->tile_lines || opt->tile_width || opt->tile_height)) return false;
     vp->mode = f.cost_mode == kCostConst ? kModeConst
@@ -889,15 +907,6 @@ bool plan_vol3d(const SweepArgs& f, const fgx_options* opt, int sms, Vol3DPlan* 
     for (int i = 0; i < kMaxPasses; ++i)
         if (f.pass[i].L >= (1 << 30) || f.pass[i].P >= (1 << 30) || f.pass[i].Q >= (1 << 30))
             return false;
-    int max_tiles = 1;
-    for (int i = 0; i < kMaxPasses; ++i) {
-        const PassGeom& g = f.pass[i];
-        vp->ntp[i] = (int)std::max<int64_t>(1, (g.P + kTP - 1) / kTP);
-        vp->ntq[i] = (int)std::max<int64_t>(1, (g.Q + kTQ - 1) / kTQ);
-        if ((int64_t)vp->ntp[i] * vp->ntq[i] > (1 << 20)) return false;
-        max_tiles = std::max(max_tiles, vp->ntp[i] * vp->ntq[i]);
-    }
-    vp->max_tiles = max_tiles;
     vp->smem = stage_bytes(vp->CI);
     // occupancy of the cp.async variant (the larger block) bounds both
     Vol3DKernel k = pick_kernel(vp->mode, vp->CI, false, false);
@@ -909,13 +918,33 @@ bool plan_vol3d(const SweepArgs& f, const fgx_options* opt, int sms, Vol3DPlan* 
                                                       vp->smem) != cudaSuccess ||
         per_sm < 1)
         return false;
-    int64_t grid = (int64_t)per_sm * sms;
-    if (opt && opt->max_blocks) grid = std::min<int64_t>(grid, opt->max_blocks);
-    grid = std::min<int64_t>(grid, std::max<int64_t>(1, f.B * max_tiles));
-    if (grid < max_tiles) return false;
-    vp->grid = (int)grid;
+    int64_t cap = (int64_t)per_sm * sms;
+    if (opt && opt->max_blocks) cap = std::min<int64_t>(cap, opt->max_blocks);
+    const int64_t B = std::max<int64_t>(f.B, 1);
+    auto waves = [&](int64_t n) { return (B + cap / n - 1) / (cap / n); };
+    int64_t max_tiles = 1, xtiles = 1;
+    for (int i = 0; i < kMaxPasses; ++i) {
+        const PassGeom& g = f.pass[i];
+        const int64_t n4 = tiles_of(g, kRing), n8 = tiles_of(g, kRingWide);
+        if (n4 > (1 << 20) || n4 > cap) return false;
+        int K = kRing;
+        if (n8 <= cap) {
+            xtiles = std::max(xtiles, n8);
+            if (wide && 3 * waves(n8) <= 4 * waves(n4)) K = kRingWide;
+        }
+        xtiles = std::max(xtiles, n4);
+        const int t = kRP - 2 * K;
+        vp->ring[i] = K;
+        vp->ntp[i] = (int)std::max<int64_t>(1, (g.P + t - 1) / t);
+        vp->ntq[i] = (int)std::max<int64_t>(1, (g.Q + t - 1) / t);
+        max_tiles = std::max<int64_t>(max_tiles, (int64_t)vp->ntp[i] * vp->ntq[i]);
+    }
+    // the exchange area has room for either ring choice of every pass, so a
+    // workspace sized by the size query serves every call of that shape
+    vp->max_tiles = (int)xtiles;
+    vp->grid = (int)std::min<int64_t>(cap, B * max_tiles);
     auto al = [](size_t x) { return (x + 255) & ~size_t(255); };
-    vp->zero_bytes = kHeaderBytes + (size_t)std::max<int64_t>(f.B, 1) * max_tiles * 2 * kXWords * 8;
+    vp->zero_bytes = kHeaderBytes + (size_t)B * xtiles * 2 * kXWords * 8;
     vp->distT_off = al(vp->zero_bytes);
     vp->imageT_off = vp->distT_off + al((size_t)f.B * f.N * 4);
     vp->ws_bytes = vp->imageT_off + al((size_t)f.B * f.C * f.N * 4);
@@ -957,6 +986,7 @@ int run_vol3d(const SweepArgs& f, const float* image, const float* mask, float* 
         a.pass[i] = f.pass[i];
         a.ntp[i] = vp.ntp[i];
         a.ntq[i] = vp.ntq[i];
+        a.ring[i] = vp.ring[i];
     }
     a.max_tiles = vp.max_tiles;
     char* w = (char*)workspace;
@@ -1024,7 +1054,7 @@ bool vol3d_instance_desc(void* desc, const fgx_instance& it, const SweepArgs& f,
                          const fgx_options* opt, int sms, char* hdr, int* range_flag, char* xb,
                          size_t* xbytes, int* ci, int* max_tiles, int tiles[kMaxPasses]) {
     Vol3DPlan vp;
-    if (!plan_vol3d(f, opt, sms, &vp)) return false;
+    if (!plan_vol3d(f, opt, sms, &vp, false, false)) return false;
     *xbytes = (size_t)vp.max_tiles * 2 * kXWords * 8;
     *ci = vp.CI;
     *max_tiles = vp.max_tiles;
@@ -1046,6 +1076,7 @@ bool vol3d_instance_desc(void* desc, const fgx_instance& it, const SweepArgs& f,
         a.pass[i] = f.pass[i];
         a.ntp[i] = vp.ntp[i];
         a.ntq[i] = vp.ntq[i];
+        a.ring[i] = vp.ring[i];
     }
     a.max_tiles = vp.max_tiles;
     a.xbuf = (unsigned long long*)xb;

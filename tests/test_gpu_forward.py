@@ -135,6 +135,22 @@ def test_plane_tiles_3d_bit_exact(fgx, lam, tiny):
     assert_bit_exact(gpu_run(fgx, case, options=dict(max_blocks=20)), want)
 
 
+@pytest.mark.parametrize("shape", [(20, 36, 44), (19, 35, 45)])
+@pytest.mark.parametrize("opts", [None, dict(max_blocks=10)])
+def test_plane_tiles_3d_rings_and_staging(fgx, shape, opts):
+    """Two volumes of three channels (general cost, lambda = 0.6): rows that
+    are multiples of 4 floats are staged by tensor copies, others by
+    per-lane copies; with the whole grid the planner takes the 8-wide ring
+    (16 x 16 owned tiles), with 10 blocks the 4-wide one in waves."""
+    rng = np.random.default_rng(sum(shape))
+    img = rng.uniform(0, 1, (2, 3) + shape).astype(np.float32)
+    m = rng.uniform(0, 1, (2, 1) + shape).astype(np.float32)
+    m[0, 0, 2, 3, 4] = 0
+    m[1, 0, -1, -2, -3] = 0
+    case = workloads.Case("rings3d", img, m, 50.0, 0.6, 2, (1.5, 1.0, 0.5))
+    assert_bit_exact(gpu_run(fgx, case, options=opts), oracle_run(case))
+
+
 def test_batch_of_images_bit_exact(fgx):
     rng = np.random.default_rng(7)
     img = rng.uniform(0, 1, (5, 2, 70, 90)).astype(np.float32)
