@@ -297,8 +297,11 @@ int fgx_geodesic3d_fwd_train(const float* image, const float* mask, float* dist,
                              size_t workspace_bytes, const fgx_options* opt, void* stream);
 
 /* Scratch bytes for the backward of `iterations` iterations: status, the
- * adjoint buffers, the codes in the line layout of each pass application and
- * (2D) the adjoint of every pass application for the image gradient. */
+ * adjoint buffers, and (2D) the codes in the line layout of each pass
+ * application and the adjoint of every pass application for the image
+ * gradient.  The 3D reverse sweep adds each application's image-gradient
+ * terms right after sweeping it, so its scratch does not grow with the
+ * iterations (two adjoint buffers and the adjoint of one application). */
 int fgx_backward_workspace_size(int ndim, int64_t B, int64_t C, int64_t D, int64_t H, int64_t W,
                                 int iterations, const fgx_options* opt, size_t* bytes);
 
@@ -320,6 +323,56 @@ int fgx_geodesic3d_bwd(const float* grad_dist, const float* image, const void* s
                        int64_t C, int64_t D, int64_t H, int64_t W, const float spacing[3],
                        float v, float lambda, int iterations, void* workspace,
                        size_t workspace_bytes, const fgx_options* opt, void* stream);
+
+/* ---------------------------------------------- checkpointed 3D training ----
+ *
+ * Training with less memory kept between the forward and the backward
+ * (Summary and Statement of need: the transform as a differentiable layer on
+ * 3D volumes).  Instead of one parent code byte per voxel and pass
+ * application, the forward keeps the distance map at the start of every
+ * `interval`-th iteration (iterations interval, 2*interval, ...; the
+ * starting map v*M is rebuilt from the mask).  The backward replays each
+ * segment of `interval` iterations once from its checkpoint, recording that
+ * segment's codes in the workspace, and sweeps the segment's pass
+ * applications in reverse; gradients equal fgx_geodesic3d_bwd's bit for
+ * bit.  The kept buffer shrinks from 6 bytes per voxel and iteration to
+ * 4 / interval bytes per voxel and iteration (0 with interval >= iterations);
+ * the backward does one more forward's arithmetic and holds one segment's
+ * codes (6 * interval bytes per voxel) in its workspace.  Only the 3D
+ * plane-tile kernels take this path (at most 3 channels where the image is
+ * read, no tile-shape options): otherwise FGX_ERR_UNSUPPORTED. */
+
+/* Bytes of the buffer kept between fgx_geodesic3d_fwd_checkpoint and
+ * fgx_geodesic3d_bwd_checkpoint: (ceil(iterations / interval) - 1) float
+ * maps of B*D*H*W, layout [checkpoint][B][D][H][W].  interval >= 1. */
+int fgx_checkpoint_saved_size(int64_t B, int64_t D, int64_t H, int64_t W, int iterations,
+                              int interval, size_t* bytes);
+
+/* Scratch bytes of both checkpointed calls (status word at offset 0, read by
+ * fgx_workspace_status after either call). */
+int fgx_checkpoint_workspace_size(int64_t B, int64_t C, int64_t D, int64_t H, int64_t W,
+                                  int iterations, int interval, const fgx_options* opt,
+                                  size_t* bytes);
+
+/* Forward of fgx_geodesic3d (same arguments and result) that also writes the
+ * checkpoints into `saved` (device memory, fgx_checkpoint_saved_size
+ * bytes; nullable when that is 0). */
+int fgx_geodesic3d_fwd_checkpoint(const float* image, const float* mask, float* dist, int64_t B,
+                                  int64_t C, int64_t D, int64_t H, int64_t W,
+                                  const float spacing[3], float v, float lambda, int iterations,
+                                  int interval, void* saved, size_t saved_bytes, void* workspace,
+                                  size_t workspace_bytes, const fgx_options* opt, void* stream);
+
+/* Backward of fgx_geodesic3d_bwd through the checkpoints of
+ * fgx_geodesic3d_fwd_checkpoint (same image, mask, v, lambda, spacing,
+ * iterations and interval).  grad_image and grad_mask as in
+ * fgx_geodesic3d_bwd (at least one non-NULL). */
+int fgx_geodesic3d_bwd_checkpoint(const float* grad_dist, const float* image, const float* mask,
+                                  const void* saved, size_t saved_bytes, float* grad_image,
+                                  float* grad_mask, int64_t B, int64_t C, int64_t D, int64_t H,
+                                  int64_t W, const float spacing[3], float v, float lambda,
+                                  int iterations, int interval, void* workspace,
+                                  size_t workspace_bytes, const fgx_options* opt, void* stream);
 
 /* Scratch bytes of fgx_geodesic_bwd_params: the reverse sweep's workspace
  * (fgx_backward_workspace_size) plus three arrays of B*D*H*W floats. */

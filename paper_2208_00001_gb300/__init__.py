@@ -126,6 +126,16 @@ _SIGS = {
                             _i32, _vp, _sz, _vp, _vp], _i32),
     "fgx_geodesic3d_bwd": ([_vp, _vp, _vp, _sz, _vp, _vp, _i64, _i64, _i64, _i64, _i64, _vp,
                             _f32, _f32, _i32, _vp, _sz, _vp, _vp], _i32),
+    "fgx_checkpoint_saved_size": ([_i64, _i64, _i64, _i64, _i32, _i32, ctypes.POINTER(_sz)],
+                                  _i32),
+    "fgx_checkpoint_workspace_size": ([_i64, _i64, _i64, _i64, _i64, _i32, _i32, _vp,
+                                       ctypes.POINTER(_sz)], _i32),
+    "fgx_geodesic3d_fwd_checkpoint": ([_vp, _vp, _vp, _i64, _i64, _i64, _i64, _i64, _vp, _f32,
+                                       _f32, _i32, _i32, _vp, _sz, _vp, _sz, _vp, _vp], _i32),
+    "fgx_geodesic3d_bwd_checkpoint": ([_vp, _vp, _vp, _vp, _sz, _vp, _vp, _i64, _i64, _i64,
+                                       _i64, _i64, _vp, _f32, _f32, _i32, _i32, _vp, _sz, _vp,
+                                       _vp], _i32),
+    "fgx_noalloc_status": ([_vp], _i32),
 }
 
 
@@ -501,28 +511,111 @@ def backward(grad_dist, image, saved, v, lam, iterations, spacing=None, need_ima
     return gi, gm
 
 
+def checkpoint_saved_size(B, D, H, W, iterations, interval):
+    n = ctypes.c_size_t(0)
+    _check(lib().fgx_checkpoint_saved_size(B, D, H, W, int(iterations), int(interval),
+                                           ctypes.byref(n)), "checkpoint saved size")
+    return n.value
+
+
+def checkpoint_workspace_size(B, C, D, H, W, iterations, interval, options=None):
+    n = ctypes.c_size_t(0)
+    _check(lib().fgx_checkpoint_workspace_size(B, C, D, H, W, int(iterations), int(interval),
+                                               _opt(options), ctypes.byref(n)),
+           "checkpoint workspace size")
+    return n.value
+
+
+def forward_checkpoint(image, mask, v, lam, iterations, interval, spacing=None, options=None,
+                       check=False):
+    """3D forward that keeps the distance map at the start of every
+    `interval`-th iteration instead of parent codes.  Returns (dist, saved
+    float32 tensor [checkpoints, B, D*H*W], possibly empty)."""
+    if image.dim() != 5:
+        raise ValueError("checkpointed training is 3D: image (B, C, D, H, W)")
+    B, C, D, H, W = _shape(image, mask, 3)
+    dev = image.device
+    with torch.cuda.device(dev):
+        dist = torch.empty_like(mask)
+        nbytes = checkpoint_saved_size(B, D, H, W, iterations, interval)
+        saved = torch.empty((nbytes // 4 // max(B * D * H * W, 1), B, D * H * W),
+                            dtype=torch.float32, device=dev)
+        ws = _workspace(checkpoint_workspace_size(B, C, D, H, W, iterations, interval, options),
+                        dev)
+        st = lib().fgx_geodesic3d_fwd_checkpoint(
+            _ptr(image), _ptr(mask), _ptr(dist), B, C, D, H, W, _spacing(spacing), float(v),
+            float(lam), int(iterations), int(interval), _ptr(saved) if saved.numel() else None,
+            saved.numel() * 4, _ptr(ws), ws.numel(), _opt(options), _stream())
+        _check(st, "forward_checkpoint")
+        if check:
+            _check(workspace_status(ws), "forward_checkpoint (device)")
+    return dist, saved
+
+
+def backward_checkpoint(grad_dist, image, mask, saved, v, lam, iterations, interval,
+                        spacing=None, need_image=True, need_mask=True, options=None,
+                        check=False):
+    """Reverse sweep through the checkpoints of :func:`forward_checkpoint`
+    (each segment replayed once).  Returns (grad_image or None, grad_mask or
+    None), equal bit for bit to :func:`backward`'s."""
+    _check_tensor(grad_dist, "grad_dist")
+    B, C, D, H, W = _shape(image, grad_dist, 3)
+    dev = image.device
+    with torch.cuda.device(dev):
+        gi = torch.empty_like(image) if need_image else None
+        gm = torch.empty_like(grad_dist) if need_mask else None
+        if gi is None and gm is None:
+            return None, None
+        ws = _workspace(checkpoint_workspace_size(B, C, D, H, W, iterations, interval, options),
+                        dev)
+        st = lib().fgx_geodesic3d_bwd_checkpoint(
+            _ptr(grad_dist), _ptr(image), _ptr(mask), _ptr(saved) if saved.numel() else None,
+            saved.numel() * 4, _ptr(gi), _ptr(gm), B, C, D, H, W, _spacing(spacing), float(v),
+            float(lam), int(iterations), int(interval), _ptr(ws), ws.numel(), _opt(options),
+            _stream())
+        _check(st, "backward_checkpoint")
+        if check:
+            _check(workspace_status(ws), "backward_checkpoint (device)")
+    return gi, gm
+
+
 class GeodesicFn(torch.autograd.Function):
     """Differentiable transform: the forward records argmin parent codes, the
     backward runs the reverse sweep through them (dL/dimage, dL/dmask, and
-    dL/dv, dL/dlambda when v or lam is a tensor that requires grad)."""
+    dL/dv, dL/dlambda when v or lam is a tensor that requires grad).  3D with
+    checkpoint=k: the forward keeps the distance map every k iterations
+    instead of the codes and the backward replays each segment (image and
+    mask gradients only)."""
 
     @staticmethod
-    def forward(ctx, image, mask, v, lam, iterations, spacing=None, options=None):
+    def forward(ctx, image, mask, v, lam, iterations, spacing=None, options=None,
+                checkpoint=None):
         vf, lf = float(v), float(lam)
-        dist, saved = forward_train(image.detach().contiguous(), mask.detach().contiguous(), vf,
-                                    lf, iterations, spacing=spacing, options=options)
+        if checkpoint:
+            if any(torch.is_tensor(x) and x.requires_grad for x in (v, lam)):
+                raise ValueError("checkpointed training gives image and mask gradients only")
+            dist, saved = forward_checkpoint(image.detach().contiguous(),
+                                             mask.detach().contiguous(), vf, lf, iterations,
+                                             int(checkpoint), spacing=spacing, options=options)
+        else:
+            dist, saved = forward_train(image.detach().contiguous(), mask.detach().contiguous(),
+                                        vf, lf, iterations, spacing=spacing, options=options)
         ctx.save_for_backward(image.detach(), mask.detach(), saved)
-        ctx.params = (vf, lf, iterations, spacing, options)
+        ctx.params = (vf, lf, iterations, spacing, options, checkpoint)
         ctx.scalar_like = (v, lam)
         return dist
 
     @staticmethod
     def backward(ctx, grad_dist):
         image, mask, saved = ctx.saved_tensors
-        v, lam, iterations, spacing, options = ctx.params
+        v, lam, iterations, spacing, options, checkpoint = ctx.params
         need_i, need_m, need_v, need_l = ctx.needs_input_grad[:4]
         gv = gl = None
-        if need_v or need_l:
+        if checkpoint:
+            gi, gm = backward_checkpoint(grad_dist.contiguous(), image, mask, saved, v, lam,
+                                         iterations, int(checkpoint), spacing=spacing,
+                                         need_image=need_i, need_mask=need_m, options=options)
+        elif need_v or need_l:
             dl, dv, _, _, gi, gm = backward_params(grad_dist.contiguous(), image, mask, saved, v,
                                                    lam, iterations, spacing=spacing,
                                                    need_image=need_i, need_mask=need_m,
@@ -536,13 +629,15 @@ class GeodesicFn(torch.autograd.Function):
             gi, gm = backward(grad_dist.contiguous(), image, saved, v, lam, iterations,
                               spacing=spacing, need_image=need_i, need_mask=need_m,
                               options=options)
-        return gi, gm, gv, gl, None, None, None
+        return gi, gm, gv, gl, None, None, None, None
 
 
-def geodesic_autograd(image, mask, v, lam, iterations, spacing=None, options=None):
+def geodesic_autograd(image, mask, v, lam, iterations, spacing=None, options=None,
+                      checkpoint=None):
     """Autograd entry point: dist = GeodesicFn(image, mask, ...); v and lam
-    may be floats or 0-d tensors (then their gradients are returned too)."""
-    return GeodesicFn.apply(image, mask, v, lam, iterations, spacing, options)
+    may be floats or 0-d tensors (then their gradients are returned too).
+    checkpoint=k (3D): keep distance maps every k iterations instead of codes."""
+    return GeodesicFn.apply(image, mask, v, lam, iterations, spacing, options, checkpoint)
 
 
 class BatchedPlan:

@@ -171,14 +171,16 @@ __device__ bool exchange3(const XLink3& a, const Tile3& t, int w, unsigned int t
 
 struct Adj3DArgs {
     const float* grad_dist;   // [B][N]
-    const uint8_t* codes;     // [T][B][N]
+    const uint8_t* codes;     // [t_hi - t_lo][B][N]: codes of applications t_lo .. t_hi-1
     float* grad_mask;         // [B][N] or null
     float* g0;                // [B][N] adjoint of D0, or null
     float* G[2];              // [B][N] adjoint buffers
-    float* Astore;            // [T][B][N] adjoint of every application, or null
+    float* A;                 // [B][N] adjoint of the current application (gradient terms), or null
     int64_t B, N;
     float v;
-    int T;
+    int T;                    // pass applications of the whole transform
+    int t_lo, t_hi;           // applications of this launch
+    int in_first;             // adjoint of application t_hi-1: -1 = grad_dist, else G[in_first]
     PassGeom pass[kMaxPasses];
     int ntp[kMaxPasses], ntq[kMaxPasses];
     int max_tiles;
@@ -186,6 +188,13 @@ struct Adj3DArgs {
     unsigned int* barrier;
     int* status;
     long long timeout_ns;
+    // image-gradient and lambda terms, added per application
+    const float* image;       // [B][C][N]
+    float* grad_image;        // [B][C][N] accumulator (cleared by the host), or null
+    float* lambda_terms;      // [B][N] accumulator (cleared by the host), or null
+    int64_t C, D, H, W;
+    float lambda;
+    float s2[kMaxPasses][9];  // |offset|^2 of every pass and stencil offset
 };
 
 struct AdjHead3 {
@@ -360,6 +369,116 @@ __device__ bool adj_compute3(const Adj3DArgs& a, const Tile3& t, int t_app, AdjH
     return !failed;
 }
 
+__device__ __forceinline__ float grad_cost3(const float* img, int x, int y, int C, int n,
+                                            float t, float lam, float* di2_out = nullptr) {
+    float di2 = 0.0f;
+    for (int ch = 0; ch < C; ++ch) {
+        const float d = __fsub_rn(img[ch * n + x], img[ch * n + y]);
+        di2 = __fadd_rn(di2, __fmul_rn(d, d));
+    }
+    if (di2_out) *di2_out = di2;
+    return __fsqrt_rn(__fadd_rn(t, __fmul_rn(lam, di2)));
+}
+
+// Image-gradient and lambda terms of pass application t, one thread per
+// voxel (grid-stride), added to the accumulators in place: the terms of the
+// children (next plane of the forward sweep) that chose the voxel, in
+// offset order, then the term of its own parent.  Applications run in
+// reverse order, so every voxel receives its terms in the order of the
+// sequential reverse sweep.  CC > 0: exactly CC channels, summed in
+// registers; CC == 0: any channel count, summed in the accumulator.
+template <int CC>
+__device__ void grad_app3(const Adj3DArgs& a, int t) {
+    const float lam = a.lambda;
+    const int C = CC > 0 ? CC : (int)a.C;
+    const int n = (int)a.N;
+    const PassGeom& g = a.pass[t % kMaxPasses];
+    const int L = (int)g.L, P = (int)g.P, Q = (int)g.Q;
+    const int sl = (int)g.sl, sp = (int)g.sp, sq = (int)g.sq;
+    const int HW = (int)(a.H * a.W), Wd = (int)a.W;
+    const float* s2t = a.s2[t % kMaxPasses];
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.B * a.N;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t b = i / a.N;
+        const int e = (int)(i - b * a.N);
+        const int dd = e / HW, rem = e - dd * HW;
+        const int hh = rem / Wd, ww = rem - hh * Wd;
+        const float* img = a.image + b * a.C * a.N;
+        float* gout = a.grad_image ? a.grad_image + b * a.C * a.N + e : nullptr;
+        const float* A = a.A + b * a.N;
+        const uint8_t* cd = a.codes + ((int64_t)(t - a.t_lo) * a.B + b) * a.N;
+        float gi[CC > 0 ? CC : 1];
+        if (CC > 0 && gout) {
+#pragma unroll
+            for (int ch = 0; ch < (CC > 0 ? CC : 1); ++ch) gi[ch] = gout[ch * a.N];
+        }
+        // g -= wgt (I(x) - I(y))  or  g += wgt (I(x) - I(y)), per channel
+        auto add_term = [&](float wgt, int x, int y, bool minus) {
+            if (CC > 0) {
+#pragma unroll
+                for (int ch = 0; ch < (CC > 0 ? CC : 1); ++ch) {
+                    const float term = __fmul_rn(wgt, __fsub_rn(img[ch * n + x], img[ch * n + y]));
+                    gi[ch] = minus ? __fsub_rn(gi[ch], term) : __fadd_rn(gi[ch], term);
+                }
+            } else {
+                for (int ch = 0; ch < C; ++ch) {
+                    const float term = __fmul_rn(wgt, __fsub_rn(img[ch * n + x], img[ch * n + y]));
+                    gout[ch * a.N] = minus ? __fsub_rn(gout[ch * a.N], term)
+                                           : __fadd_rn(gout[ch * a.N], term);
+                }
+            }
+        };
+        const int line = g.axis == 0 ? dd : (g.axis == 1 ? hh : ww);
+        const int p = g.axis == 0 ? hh : dd;
+        const int q = g.axis == 2 ? hh : ww;
+        // children on the next plane of the forward sweep, offset order
+        const int cl = line + g.dir;
+        if (gout && cl >= 0 && cl < L) {
+#pragma unroll
+            for (int k = 0; k < 9; ++k) {
+                const int cp = p - (k / 3 - 1), cq = q - (k % 3 - 1);
+                if (cp < 0 || cp >= P || cq < 0 || cq >= Q) continue;
+                const int x = cl * sl + cp * sp + cq * sq;
+                if (cd[x] != k + 1) continue;
+                const float c = grad_cost3(img, x, e, C, n, g.t[k], lam);
+                if (c > 0.0f) add_term(__fdiv_rn(__fmul_rn(A[x], lam), c), x, e, true);
+            }
+        }
+        // own parent on the previous plane of the forward sweep
+        const int code = cd[e];
+        const int pl = line - g.dir;
+        if (code >= 1 && code <= 9 && pl >= 0 && pl < L) {
+            const int k = code - 1;
+            const int pp = p + (k / 3 - 1), pq = q + (k % 3 - 1);
+            if (pp >= 0 && pp < P && pq >= 0 && pq < Q) {
+                const int y = pl * sl + pp * sp + pq * sq;
+                float di2;
+                const float c = grad_cost3(img, e, y, C, n, g.t[k], lam, &di2);
+                if (c > 0.0f) {
+                    if (a.lambda_terms)
+                        a.lambda_terms[i] = __fadd_rn(
+                            a.lambda_terms[i],
+                            __fmul_rn(A[e], __fdiv_rn(__fsub_rn(di2, s2t[k]), __fadd_rn(c, c))));
+                    if (gout) add_term(__fdiv_rn(__fmul_rn(A[e], lam), c), e, y, false);
+                }
+            }
+        }
+        if (CC > 0 && gout) {
+#pragma unroll
+            for (int ch = 0; ch < (CC > 0 ? CC : 1); ++ch) gout[ch * a.N] = gi[ch];
+        }
+    }
+}
+
+// The terms of one application as a launch of its own (full occupancy: the
+// per-voxel gathers need many loads in flight).
+template <int CC>
+__global__ void __launch_bounds__(256) grad3d_kernel(const Adj3DArgs a, int t) {
+    grad_app3<CC>(a, t);
+}
+
+// Pass applications t_hi-1 down to t_lo.  STORE_A: also write the adjoint of
+// the (single) application into a.A for the gradient kernel.
 template <bool STORE_A>
 __global__ void __launch_bounds__(kBlock3, 1) adj3d_kernel(const Adj3DArgs a) {
     extern __shared__ __align__(16) unsigned char smem3[];
@@ -375,9 +494,9 @@ __global__ void __launch_bounds__(kBlock3, 1) adj3d_kernel(const Adj3DArgs a) {
     __syncthreads();
     unsigned int epoch = 1;
     unsigned int cb = 0;
-    int in_idx = -1;  // the first application reads the caller's dL/dD
+    int in_idx = a.in_first;  // -1: the caller's dL/dD
     bool alive = true;
-    for (int t_app = a.T - 1; t_app >= 0 && alive; --t_app) {
+    for (int t_app = a.t_hi - 1; t_app >= a.t_lo && alive; --t_app) {
         const int pass = t_app % kMaxPasses;
         const PassGeom& g = a.pass[pass];
         const int ntiles = a.ntp[pass] * a.ntq[pass];
@@ -403,12 +522,13 @@ __global__ void __launch_bounds__(kBlock3, 1) adj3d_kernel(const Adj3DArgs a) {
             t.q0 = (int64_t)t.jq * kTQ - kRing;
             const float* gsrc = (in_idx < 0 ? a.grad_dist : a.G[in_idx]) + b * a.N;
             if ((int)(threadIdx.x >> 5) >= kCW) {
-                adj_producer3(a, t, gsrc, a.codes + ((int64_t)t_app * a.B + b) * a.N, h, stg,
-                              stc, cb);
+                adj_producer3(a, t, gsrc,
+                              a.codes + ((int64_t)(t_app - a.t_lo) * a.B + b) * a.N, h, stg, stc,
+                              cb);
             } else {
                 float* gdst = t_app > 0 ? a.G[out_idx] + b * a.N : nullptr;
                 float* gmask = (t_app == 0 && a.grad_mask) ? a.grad_mask + b * a.N : nullptr;
-                float* adst = STORE_A ? a.Astore + ((int64_t)t_app * a.B + b) * a.N : nullptr;
+                float* adst = STORE_A ? a.A + b * a.N : nullptr;
                 float* g0 = (t_app == 0 && a.g0) ? a.g0 + b * a.N : nullptr;
                 adj_compute3(a, t, a.T - 1 - t_app, h, stg, stc, cb, gdst, gmask, adst, g0);
             }
@@ -419,140 +539,23 @@ __global__ void __launch_bounds__(kBlock3, 1) adj3d_kernel(const Adj3DArgs a) {
     }
 }
 
-struct Grad3DArgs {
-    const float* image;       // [B][C][N]
-    const uint8_t* codes;     // [T][B][N]
-    const float* Astore;      // [T][B][N]
-    float* grad_image;        // [B][C][N], or null
-    float* lambda_terms;      // [B][N] per-voxel terms of dL/dlambda, or null
-    int64_t B, C, N;
-    int64_t D, H, W;
-    float lambda;
-    int T;
-    PassGeom pass[kMaxPasses];
-    float s2[kMaxPasses][9];  // |offset|^2 of every pass and stencil offset
-};
-
-__device__ __forceinline__ float grad_cost3(const float* img, int64_t x, int64_t y, int C,
-                                            int64_t n, float t, float lam,
-                                            float* di2_out = nullptr) {
-    float di2 = 0.0f;
-    for (int ch = 0; ch < C; ++ch) {
-        const float d = __fsub_rn(img[ch * n + x], img[ch * n + y]);
-        di2 = __fadd_rn(di2, __fmul_rn(d, d));
-    }
-    if (di2_out) *di2_out = di2;
-    return __fsqrt_rn(__fadd_rn(t, __fmul_rn(lam, di2)));
-}
-
-// Image gradient of the 3D reverse sweep, one thread per voxel, pass
-// applications in reverse order: per application the terms of the children
-// that chose the voxel (offset order), then the term of its own parent.
-// The gradient accumulates in the output array (each voxel is touched by its
-// own thread only).  With lambda_terms, each voxel also sums, over the
-// applications in the same order, its adjoint times d c / d lambda of its own
-// parent edge, (di2 - s2) / (c + c).
-template <int CC, bool IMG, typename Idx>
-__global__ void __launch_bounds__(256) grad3d_kernel(const Grad3DArgs a) {
-    // CC > 0: the CC channel sums stay in registers (written once at the end);
-    // CC == 0: any channel count, accumulated in the output array.  Idx: the
-    // index type within one instance (32-bit when every offset fits)
-    const float lam = a.lambda;
-    const int C = CC > 0 ? CC : (int)a.C;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.B * a.N;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t b = i / a.N;
-        const Idx e = (Idx)(i - b * a.N);
-        const Idx HW = (Idx)(a.H * a.W), Wd = (Idx)a.W;
-        const Idx dd = e / HW, rem = e - dd * HW;
-        const Idx hh = rem / Wd, ww = rem - hh * Wd;
-        const float* img = a.image + b * a.C * a.N;
-        float* gout = IMG ? a.grad_image + b * a.C * a.N + e : nullptr;
-        float lt = 0.0f;
-        float gi[CC > 0 ? CC : 1];
-#pragma unroll
-        for (int ch = 0; ch < (CC > 0 ? CC : 1); ++ch) gi[ch] = 0.0f;
-        if (IMG && CC == 0)
-            for (int ch = 0; ch < C; ++ch) gout[ch * a.N] = 0.0f;
-        // g -= wgt (I(x) - I(y))  or  g += wgt (I(x) - I(y)), per channel
-        auto add_term = [&](float wgt, Idx x, Idx y, bool minus) {
-            if (CC > 0) {
-#pragma unroll
-                for (int ch = 0; ch < (CC > 0 ? CC : 1); ++ch) {
-                    const float term =
-                        __fmul_rn(wgt, __fsub_rn(img[ch * a.N + x], img[ch * a.N + y]));
-                    gi[ch] = minus ? __fsub_rn(gi[ch], term) : __fadd_rn(gi[ch], term);
-                }
-            } else {
-                for (int ch = 0; ch < C; ++ch) {
-                    const float term =
-                        __fmul_rn(wgt, __fsub_rn(img[ch * a.N + x], img[ch * a.N + y]));
-                    gout[ch * a.N] = minus ? __fsub_rn(gout[ch * a.N], term)
-                                           : __fadd_rn(gout[ch * a.N], term);
-                }
-            }
-        };
-        for (int t = a.T - 1; t >= 0; --t) {
-            const PassGeom& g = a.pass[t % kMaxPasses];
-            const Idx line = g.axis == 0 ? dd : (g.axis == 1 ? hh : ww);
-            const Idx p = g.axis == 0 ? hh : dd;
-            const Idx q = g.axis == 2 ? hh : ww;
-            const Idx L = (Idx)g.L, P = (Idx)g.P, Q = (Idx)g.Q;
-            const Idx sl = (Idx)g.sl, sp = (Idx)g.sp, sq = (Idx)g.sq;
-            const float* A = a.Astore + ((int64_t)t * a.B + b) * a.N;
-            const uint8_t* cd = a.codes + ((int64_t)t * a.B + b) * a.N;
-            // children on the next plane of the forward sweep, offset order
-            const Idx cl = line + g.dir;
-            if (IMG && cl >= 0 && cl < L) {
-#pragma unroll
-                for (int k = 0; k < 9; ++k) {
-                    const Idx cp = p - (k / 3 - 1), cq = q - (k % 3 - 1);
-                    if (cp < 0 || cp >= P || cq < 0 || cq >= Q) continue;
-                    const Idx x = cl * sl + cp * sp + cq * sq;
-                    if (cd[x] != k + 1) continue;
-                    const float c = grad_cost3(img, x, e, C, a.N, g.t[k], lam);
-                    if (c > 0.0f) add_term(__fdiv_rn(__fmul_rn(A[x], lam), c), x, e, true);
-                }
-            }
-            // own parent on the previous plane of the forward sweep
-            const int code = cd[e];
-            const Idx pl = line - g.dir;
-            if (code >= 1 && code <= 9 && pl >= 0 && pl < L) {
-                const int k = code - 1;
-                const Idx pp = p + (k / 3 - 1), pq = q + (k % 3 - 1);
-                if (pp >= 0 && pp < P && pq >= 0 && pq < Q) {
-                    const Idx y = pl * sl + pp * sp + pq * sq;
-                    float di2;
-                    const float c = grad_cost3(img, e, y, C, a.N, g.t[k], lam, &di2);
-                    if (c > 0.0f) {
-                        if (a.lambda_terms) {
-                            const float s2 = a.s2[t % kMaxPasses][k];
-                            lt = __fadd_rn(lt, __fmul_rn(A[e], __fdiv_rn(__fsub_rn(di2, s2),
-                                                                         __fadd_rn(c, c))));
-                        }
-                        if (IMG) add_term(__fdiv_rn(__fmul_rn(A[e], lam), c), e, y, false);
-                    }
-                }
-            }
-        }
-        if (IMG && CC > 0) {
-#pragma unroll
-            for (int ch = 0; ch < (CC > 0 ? CC : 1); ++ch) gout[ch * a.N] = gi[ch];
-        }
-        if (a.lambda_terms) a.lambda_terms[i] = lt;
-    }
-}
-
 struct Adj3DPlan {
     int grid = 0, max_tiles = 0;
     int ntp[kMaxPasses] = {}, ntq[kMaxPasses] = {};
     size_t xbuf_off = 0, g_off[2] = {}, a_off = 0, total = 0;
 };
 
+using Adj3DKernel = void (*)(Adj3DArgs);
+Adj3DKernel adj_kernel(bool store_a) {
+    return store_a ? adj3d_kernel<true> : adj3d_kernel<false>;
+}
+
 bool plan_adj3d(const SweepArgs& f, int iterations, const fgx_options* opt, int sms,
                 Adj3DPlan* p) {
     if (f.ndim != 3 || iterations <= 0) return false;
     if (opt && (opt->tile_lines || opt->tile_width || opt->tile_height)) return false;
+    // offsets within one instance (image channels included) are int
+    if (f.C * f.N >= ((int64_t)1 << 31)) return false;
     int max_tiles = 1;
     for (int i = 0; i < kMaxPasses; ++i) {
         const PassGeom& g = f.pass[i];
@@ -563,13 +566,12 @@ bool plan_adj3d(const SweepArgs& f, int iterations, const fgx_options* opt, int 
     }
     p->max_tiles = max_tiles;
     const size_t smem = adj3_smem_bytes();
-    if (cudaFuncSetAttribute(adj3d_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)smem) != cudaSuccess ||
-        cudaFuncSetAttribute(adj3d_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)smem) != cudaSuccess)
-        return false;
+    for (Adj3DKernel k : {adj_kernel(false), adj_kernel(true)})
+        if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+            cudaSuccess)
+            return false;
     int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, adj3d_kernel<true>, kBlock3,
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, adj_kernel(true), kBlock3,
                                                       smem) != cudaSuccess ||
         per_sm < 1)
         return false;
@@ -586,8 +588,10 @@ bool plan_adj3d(const SweepArgs& f, int iterations, const fgx_options* opt, int 
         p->g_off[i] = off;
         off += al((size_t)f.B * f.N * 4);
     }
+    // the adjoint of one pass application (the gradient terms use it
+    // before the next application's sweep overwrites it)
     p->a_off = off;
-    off += al((size_t)iterations * kMaxPasses * f.B * f.N * 4);
+    off += al((size_t)f.B * f.N * 4);
     p->total = off;
     return true;
 }
@@ -603,11 +607,15 @@ size_t adj3d_workspace_bytes(const SweepArgs& f, int iterations, const fgx_optio
 int run_adj3d(const SweepArgs& f, const float* grad_dist, const float* image,
               const uint8_t* codes, float* grad_image, float* grad_mask, float v, int iterations,
               void* workspace, size_t ws_bytes, const fgx_options* opt, int sms, void* stream,
-              float* g0, float* lambda_terms, const float* s2) {
+              float* g0, float* lambda_terms, const float* s2, int t_lo, int t_hi, int in_first,
+              int* in_next, bool clear) {
     if (lambda_terms && !s2) return FGX_ERR_ARG;
     Adj3DPlan p;
     if (!plan_adj3d(f, iterations, opt, sms, &p)) return FGX_ERR_UNSUPPORTED;
     if (ws_bytes < p.total) return FGX_ERR_WORKSPACE;
+    const int T = iterations * kMaxPasses;
+    if (t_hi < 0) t_hi = T;
+    if (t_lo < 0 || t_hi > T || t_lo >= t_hi) return FGX_ERR_ARG;
     char* w = (char*)workspace;
     Adj3DArgs a;
     std::memset(&a, 0, sizeof(a));
@@ -617,12 +625,15 @@ int run_adj3d(const SweepArgs& f, const float* grad_dist, const float* image,
     a.g0 = g0;
     a.G[0] = (float*)(w + p.g_off[0]);
     a.G[1] = (float*)(w + p.g_off[1]);
-    const bool need_a = grad_image || lambda_terms;  // the per-voxel pass needs every A
-    a.Astore = need_a ? (float*)(w + p.a_off) : nullptr;
+    const bool grad = grad_image || lambda_terms;
+    a.A = grad ? (float*)(w + p.a_off) : nullptr;
     a.B = f.B;
     a.N = f.N;
     a.v = v;
-    a.T = iterations * kMaxPasses;
+    a.T = T;
+    a.t_lo = t_lo;
+    a.t_hi = t_hi;
+    a.in_first = in_first;
     for (int i = 0; i < kMaxPasses; ++i) {
         a.pass[i] = f.pass[i];
         a.ntp[i] = p.ntp[i];
@@ -633,8 +644,30 @@ int run_adj3d(const SweepArgs& f, const float* grad_dist, const float* image,
     a.barrier = (unsigned int*)(w + 64);
     a.status = (int*)w;
     a.timeout_ns = f.timeout_ns;
+    a.image = image;
+    a.grad_image = grad_image;
+    a.lambda_terms = lambda_terms;
+    a.C = f.C;
+    a.D = f.pass[0].L;  // extent of the axis of the first pass pair (D)
+    a.H = f.pass[2].L;
+    a.W = f.pass[4].L;
+    a.lambda = f.lambda;
+    if (s2)
+        for (int i = 0; i < kMaxPasses; ++i)
+            for (int k = 0; k < 9; ++k) a.s2[i][k] = s2[i * 9 + k];
     cudaStream_t s = (cudaStream_t)stream;
-    if (cudaMemsetAsync(workspace, 0, p.g_off[0], s) != cudaSuccess) return FGX_ERR_CUDA;
+    // header and exchange words; a later range of the same call keeps the
+    // status word (offset 0) that earlier ranges may have set
+    const size_t from = clear ? 0 : 64;
+    if (cudaMemsetAsync(w + from, 0, p.g_off[0] - from, s) != cudaSuccess) return FGX_ERR_CUDA;
+    if (clear) {
+        if (grad_image && cudaMemsetAsync(grad_image, 0, (size_t)(f.B * f.C * f.N) * 4, s) !=
+                              cudaSuccess)
+            return FGX_ERR_CUDA;
+        if (lambda_terms &&
+            cudaMemsetAsync(lambda_terms, 0, (size_t)(f.B * f.N) * 4, s) != cudaSuccess)
+            return FGX_ERR_CUDA;
+    }
     cudaLaunchConfig_t cfg = {};
     cudaLaunchAttribute attr[1];
     cfg.gridDim = dim3((unsigned)p.grid);
@@ -645,44 +678,35 @@ int run_adj3d(const SweepArgs& f, const float* grad_dist, const float* image,
     attr[0].val.cooperative = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    if (cudaLaunchKernelEx(&cfg, need_a ? adj3d_kernel<true> : adj3d_kernel<false>, a) !=
-        cudaSuccess)
-        return FGX_ERR_CUDA;
-    if (need_a) {
-        Grad3DArgs g;
-        std::memset(&g, 0, sizeof(g));
-        g.image = image;
-        g.codes = codes;
-        g.Astore = a.Astore;
-        g.grad_image = grad_image;
-        g.lambda_terms = lambda_terms;
-        if (s2)
-            for (int i = 0; i < kMaxPasses; ++i)
-                for (int k = 0; k < 9; ++k) g.s2[i][k] = s2[i * 9 + k];
-        g.B = f.B;
-        g.C = f.C;
-        g.N = f.N;
-        g.D = f.pass[0].L;        // extent of the axis of the first pass pair (D)
-        g.H = f.pass[2].L;
-        g.W = f.pass[4].L;
-        g.lambda = f.lambda;
-        g.T = a.T;
-        for (int i = 0; i < kMaxPasses; ++i) g.pass[i] = f.pass[i];
+    if (!grad) {
+        if (cudaLaunchKernelEx(&cfg, adj_kernel(false), a) != cudaSuccess) return FGX_ERR_CUDA;
+    } else {
+        // one application per sweep launch, each followed by its gradient
+        // terms (applications in reverse order, as the accumulation needs)
         const int64_t n = f.B * f.N;
-        const int gg = (int)std::min<int64_t>((n + 255) / 256, (int64_t)sms * 8);
-        const int gb = std::max(gg, 1);
-        // 32-bit offsets within an instance when every one fits (C * N < 2^31)
-        if (f.C * f.N < ((int64_t)1 << 31)) {
-            if (!grad_image) grad3d_kernel<0, false, int><<<gb, 256, 0, s>>>(g);
-            else if (f.C == 1) grad3d_kernel<1, true, int><<<gb, 256, 0, s>>>(g);
-            else if (f.C == 2) grad3d_kernel<2, true, int><<<gb, 256, 0, s>>>(g);
-            else if (f.C == 3) grad3d_kernel<3, true, int><<<gb, 256, 0, s>>>(g);
-            else grad3d_kernel<0, true, int><<<gb, 256, 0, s>>>(g);
-        } else {
-            if (!grad_image) grad3d_kernel<0, false, int64_t><<<gb, 256, 0, s>>>(g);
-            else grad3d_kernel<0, true, int64_t><<<gb, 256, 0, s>>>(g);
+        const int gg = (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256,
+                                                                   (int64_t)sms * 8));
+        int idx = in_first;
+        for (int t = t_hi - 1; t >= t_lo; --t) {
+            a.t_lo = t;
+            a.t_hi = t + 1;
+            a.in_first = idx;
+            // the codes of application t sit at (t - t_lo) of the caller's range
+            a.codes = codes + (size_t)(t - t_lo) * (size_t)n;
+            if (t != t_hi - 1 && cudaMemsetAsync(w + 64, 0, 4, s) != cudaSuccess)
+                return FGX_ERR_CUDA;  // fresh grid-barrier counter
+            if (cudaLaunchKernelEx(&cfg, adj_kernel(true), a) != cudaSuccess)
+                return FGX_ERR_CUDA;
+            if (f.C == 1) grad3d_kernel<1><<<gg, 256, 0, s>>>(a, t);
+            else grad3d_kernel<0><<<gg, 256, 0, s>>>(a, t);
+            if (cudaGetLastError() != cudaSuccess) return FGX_ERR_CUDA;
+            idx = idx == 0 ? 1 : 0;
         }
-        if (cudaGetLastError() != cudaSuccess) return FGX_ERR_CUDA;
+    }
+    if (in_next) {
+        int idx = in_first;
+        for (int t = t_hi - 1; t >= t_lo; --t) idx = idx == 0 ? 1 : 0;
+        *in_next = idx;
     }
     return FGX_OK;
 }

@@ -627,6 +627,55 @@ int run_backward(int ndim, const float* grad_dist, const float* image, const voi
     return launch_adjoint(a, bp.grid, bp.smem, stream);
 }
 
+// ---------------------------------------------------- checkpointed 3D training
+//
+// The training forward keeps D at the start of every `interval`-th
+// iteration instead of the parent codes; the backward replays each segment
+// of `interval` iterations from its checkpoint (D0 = v M from the mask for
+// the first) with codes into the workspace, then sweeps that segment's pass
+// applications in reverse.  Every segment is replayed once, so the backward
+// costs one extra forward.
+
+struct CkptLayout {
+    int k = 0, nseg = 0;          // iterations per segment, segments
+    size_t adj = 0, fwd = 0;      // workspace bytes of the reverse sweep and the replay
+    size_t fwd_off = 0, dwork_off = 0, codes_off = 0, total = 0;
+};
+
+int plan_checkpoint(int64_t B, int64_t C, int64_t D, int64_t H, int64_t W,
+                    const float spacing[3], float lambda, int iterations, int interval,
+                    const fgx_options* opt, Plan* pl, CkptLayout* L) {
+    if (iterations < 1 || interval < 1) return FGX_ERR_ARG;
+    int st = plan_forward(3, B, C, D, H, W, spacing, lambda, iterations, opt, pl);
+    if (st != FGX_OK) return st;
+    if (!vol3d_supports(pl->args, opt, pl->sms)) return FGX_ERR_UNSUPPORTED;
+    L->k = std::min(interval, iterations);
+    L->nseg = (iterations + L->k - 1) / L->k;
+    L->adj = adj3d_workspace_bytes(pl->args, L->k, opt, pl->sms);
+    L->fwd = vol3d_workspace_bytes(pl->args, opt, pl->sms);
+    if (!L->adj || !L->fwd) return FGX_ERR_UNSUPPORTED;
+    const size_t n = (size_t)(B * D * H * W);
+    L->fwd_off = align256(L->adj);
+    L->dwork_off = align256(L->fwd_off + L->fwd);
+    L->codes_off = align256(L->dwork_off + n * sizeof(float));
+    L->total = L->codes_off + (size_t)L->k * kMaxPasses * n;
+    return FGX_OK;
+}
+
+// The first status word keeps the first device error of the call.
+__global__ void merge_status_kernel(int* dst, const int* src) {
+    if (*dst == 0 && *src != 0) *dst = *src;
+}
+
+int check_3d_args(const float spacing[3], float v, float lambda, int iterations) {
+    if (!(std::isfinite(v) && v > 0.f)) return FGX_ERR_ARG;
+    if (!(lambda >= 0.f && lambda <= 1.f)) return FGX_ERR_ARG;
+    if (iterations < 0 || !spacing) return FGX_ERR_ARG;
+    for (int i = 0; i < 3; ++i)
+        if (!finite_pos(spacing[i])) return FGX_ERR_ARG;
+    return FGX_OK;
+}
+
 struct ParamsLayout {
     size_t g0_off, lt_off, vt_off, total;
 };
@@ -682,6 +731,138 @@ int fgx_geodesic3d_bwd(const float* grad_dist, const float* image, const void* s
     return run_backward(3, grad_dist, image, saved, saved_bytes, grad_image, grad_mask, B, C, D,
                         H, W, spacing, v, lambda, iterations, workspace, workspace_bytes, opt,
                         stream);
+}
+
+int fgx_checkpoint_saved_size(int64_t B, int64_t D, int64_t H, int64_t W, int iterations,
+                              int interval, size_t* bytes) {
+    if (!bytes || interval < 1) return FGX_ERR_ARG;
+    if (B < 0 || D < 0 || H < 0 || W < 0 || iterations < 0) return FGX_ERR_SHAPE;
+    const int k = std::max(1, std::min(interval, std::max(iterations, 1)));
+    const int nseg = (iterations + k - 1) / k;
+    *bytes = (size_t)std::max(nseg - 1, 0) * (size_t)(B * D * H * W) * sizeof(float);
+    return FGX_OK;
+}
+
+int fgx_checkpoint_workspace_size(int64_t B, int64_t C, int64_t D, int64_t H, int64_t W,
+                                  int iterations, int interval, const fgx_options* opt,
+                                  size_t* bytes) {
+    if (!bytes) return FGX_ERR_ARG;
+    const float unit[3] = {1.f, 1.f, 1.f};
+    Plan pl;
+    CkptLayout L;
+    const int st = plan_checkpoint(B, C, D, H, W, unit, 0.5f, std::max(iterations, 1), interval,
+                                   opt, &pl, &L);
+    if (st != FGX_OK) return st;
+    *bytes = L.total;
+    return FGX_OK;
+}
+
+int fgx_geodesic3d_fwd_checkpoint(const float* image, const float* mask, float* dist, int64_t B,
+                                  int64_t C, int64_t D, int64_t H, int64_t W,
+                                  const float spacing[3], float v, float lambda, int iterations,
+                                  int interval, void* saved, size_t saved_bytes, void* workspace,
+                                  size_t workspace_bytes, const fgx_options* opt, void* stream) {
+    int st = check_3d_args(spacing, v, lambda, iterations);
+    if (st != FGX_OK) return st;
+    if (interval < 1) return FGX_ERR_ARG;
+    const int64_t n = B * D * H * W;
+    if (iterations == 0 || n == 0)
+        return run_forward(3, image, mask, dist, B, C, D, H, W, spacing, v, lambda, iterations,
+                           nullptr, 0, workspace, workspace_bytes, opt, stream, true);
+    Plan pl;
+    CkptLayout L;
+    if ((st = plan_checkpoint(B, C, D, H, W, spacing, lambda, iterations, interval, opt, &pl,
+                              &L)) != FGX_OK)
+        return st;
+    if (!image || !mask || !dist) return FGX_ERR_ARG;
+    if (!is_device_ptr(image) || !is_device_ptr(mask) || !is_device_ptr(dist))
+        return FGX_ERR_NOT_DEVICE_PTR;
+    if (overlaps(dist, (size_t)n * 4, image, (size_t)(n * C) * 4)) return FGX_ERR_ARG;
+    const size_t need = (size_t)(L.nseg - 1) * (size_t)n * sizeof(float);
+    if (need && (!saved || saved_bytes < need)) return FGX_ERR_WORKSPACE;
+    if (need && !is_device_ptr(saved)) return FGX_ERR_NOT_DEVICE_PTR;
+    if (!workspace || workspace_bytes < L.total) return FGX_ERR_WORKSPACE;
+    if (!is_device_ptr(workspace)) return FGX_ERR_NOT_DEVICE_PTR;
+    cudaStream_t s = (cudaStream_t)stream;
+    char* w = (char*)workspace;
+    // the caller reads the status word at offset 0; every segment's launch
+    // clears its own (at the replay region) and its first error is merged
+    if (cudaMemsetAsync(w, 0, kHeaderBytes, s) != cudaSuccess) return FGX_ERR_CUDA;
+    for (int seg = 0; seg < L.nseg; ++seg) {
+        SweepArgs f = pl.args;
+        f.iterations = std::min(L.k, iterations - seg * L.k);
+        if (seg > 0 && cudaMemcpyAsync((char*)saved + (size_t)(seg - 1) * n * sizeof(float), dist,
+                                       (size_t)n * sizeof(float), cudaMemcpyDeviceToDevice,
+                                       s) != cudaSuccess)
+            return FGX_ERR_CUDA;
+        st = run_vol3d(f, image, mask, dist, nullptr, v, w + L.fwd_off, L.fwd, opt, pl.sms, stream,
+                       seg > 0);
+        if (st != FGX_OK) return st;
+        merge_status_kernel<<<1, 1, 0, s>>>((int*)w, (const int*)(w + L.fwd_off));
+        if (cudaGetLastError() != cudaSuccess) return FGX_ERR_CUDA;
+    }
+    return FGX_OK;
+}
+
+int fgx_geodesic3d_bwd_checkpoint(const float* grad_dist, const float* image, const float* mask,
+                                  const void* saved, size_t saved_bytes, float* grad_image,
+                                  float* grad_mask, int64_t B, int64_t C, int64_t D, int64_t H,
+                                  int64_t W, const float spacing[3], float v, float lambda,
+                                  int iterations, int interval, void* workspace,
+                                  size_t workspace_bytes, const fgx_options* opt, void* stream) {
+    int st = check_3d_args(spacing, v, lambda, iterations);
+    if (st != FGX_OK) return st;
+    if (interval < 1) return FGX_ERR_ARG;
+    const int64_t n = B * D * H * W;
+    if (iterations == 0 || n == 0)
+        return run_backward(3, grad_dist, image, nullptr, 0, grad_image, grad_mask, B, C, D, H, W,
+                            spacing, v, lambda, iterations, workspace, workspace_bytes, opt,
+                            stream);
+    Plan pl;
+    CkptLayout L;
+    if ((st = plan_checkpoint(B, C, D, H, W, spacing, lambda, iterations, interval, opt, &pl,
+                              &L)) != FGX_OK)
+        return st;
+    if (!grad_dist || !image || !mask || (!grad_image && !grad_mask)) return FGX_ERR_ARG;
+    for (const void* p : {(const void*)grad_dist, (const void*)image, (const void*)mask})
+        if (!is_device_ptr(p)) return FGX_ERR_NOT_DEVICE_PTR;
+    if ((grad_image && !is_device_ptr(grad_image)) || (grad_mask && !is_device_ptr(grad_mask)))
+        return FGX_ERR_NOT_DEVICE_PTR;
+    const size_t need = (size_t)(L.nseg - 1) * (size_t)n * sizeof(float);
+    if (need && (!saved || saved_bytes < need)) return FGX_ERR_WORKSPACE;
+    if (need && !is_device_ptr(saved)) return FGX_ERR_NOT_DEVICE_PTR;
+    if (!workspace || workspace_bytes < L.total) return FGX_ERR_WORKSPACE;
+    if (!is_device_ptr(workspace)) return FGX_ERR_NOT_DEVICE_PTR;
+    float s2[kMaxPasses * 9];
+    for (int i = 0; i < kMaxPasses; ++i) pass_offsets_t(3, kSched3D[i][0], spacing, 0.0f, s2 + 9 * i);
+    cudaStream_t s = (cudaStream_t)stream;
+    char* w = (char*)workspace;
+    float* dwork = (float*)(w + L.dwork_off);
+    uint8_t* codes = (uint8_t*)(w + L.codes_off);
+    int in_idx = -1;
+    for (int seg = L.nseg - 1; seg >= 0; --seg) {
+        SweepArgs f = pl.args;
+        f.iterations = std::min(L.k, iterations - seg * L.k);
+        if (seg > 0 && cudaMemcpyAsync(dwork, (const char*)saved + (size_t)(seg - 1) * n * 4,
+                                       (size_t)n * 4, cudaMemcpyDeviceToDevice,
+                                       s) != cudaSuccess)
+            return FGX_ERR_CUDA;
+        // replay of the segment's iterations, recording their codes
+        st = run_vol3d(f, image, mask, dwork, codes, v, w + L.fwd_off, L.fwd, opt, pl.sms, stream,
+                       seg > 0);
+        if (st != FGX_OK) return st;
+        const int t_lo = seg * L.k * kMaxPasses;
+        const int t_hi = t_lo + f.iterations * kMaxPasses;
+        st = run_adj3d(pl.args, grad_dist, image, codes, grad_image, grad_mask, v, iterations, w,
+                       L.adj, opt, pl.sms, stream, nullptr, nullptr, s2, t_lo, t_hi, in_idx,
+                       &in_idx, seg == L.nseg - 1);
+        if (st != FGX_OK) return st;
+        // the reverse sweep's status word (offset 0; cleared only by the
+        // first range) also takes the replay's first error
+        merge_status_kernel<<<1, 1, 0, s>>>((int*)w, (const int*)(w + L.fwd_off));
+        if (cudaGetLastError() != cudaSuccess) return FGX_ERR_CUDA;
+    }
+    return FGX_OK;
 }
 
 int fgx_params_workspace_size(int ndim, int64_t B, int64_t C, int64_t D, int64_t H, int64_t W,

@@ -140,9 +140,10 @@ int chain2d_geometry(int64_t H, int64_t W, const fgx_options* opt, int* K, int* 
 // when the call does not fit that kernel (the tiled engine runs it instead).
 size_t vol3d_workspace_bytes(const SweepArgs& f, const fgx_options* opt, int sms);
 bool vol3d_supports(const SweepArgs& f, const fgx_options* opt, int sms);
+// resume: start from the distances already in `dist` instead of v * M.
 int run_vol3d(const SweepArgs& f, const float* image, const float* mask, float* dist,
               uint8_t* codes, float v, void* workspace, size_t ws_bytes, const fgx_options* opt,
-              int sms, void* stream);
+              int sms, void* stream, bool resume = false);
 
 // Batched 2D instances on the line-chain kernel (chain2d.cu): the size of
 // one instance's argument block, filling it (buffers: exchange words at xb,
@@ -186,10 +187,18 @@ int run_adj2d(const float* grad_dist, const float* image, const uint8_t* codes,
 // per-voxel image gradient when grad_image is wanted).
 size_t adj3d_workspace_bytes(const SweepArgs& f, int iterations, const fgx_options* opt,
                              int sms);
+// Reverse sweep of pass applications [t_lo, t_hi) (t_hi < 0: all of them)
+// of a transform of `iterations` iterations; `codes` holds the codes of
+// those applications.  in_first: the adjoint of application t_hi - 1 is
+// grad_dist (-1) or the workspace's adjoint buffer 0 / 1; *in_next (nullable)
+// receives the buffer that holds the adjoint handed to application t_lo - 1.
+// clear: zero the gradient accumulators first (the first range of a call).
 int run_adj3d(const SweepArgs& f, const float* grad_dist, const float* image,
               const uint8_t* codes, float* grad_image, float* grad_mask, float v, int iterations,
               void* workspace, size_t ws_bytes, const fgx_options* opt, int sms, void* stream,
-              float* g0 = nullptr, float* lambda_terms = nullptr, const float* s2 = nullptr);
+              float* g0 = nullptr, float* lambda_terms = nullptr, const float* s2 = nullptr,
+              int t_lo = 0, int t_hi = -1, int in_first = -1, int* in_next = nullptr,
+              bool clear = true);
 
 // Parameter gradients (param_grads.cu): v_terms = mask * g0 per element, then
 // grad_lambda / grad_v (device doubles, nullable) = float64 sums of

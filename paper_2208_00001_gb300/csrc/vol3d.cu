@@ -546,13 +546,16 @@ __device__ bool compute3(const Vol3DArgs& a, const Tile3& t, int t_app, Head3& h
     return !failed;
 }
 
-// D0 = v * M, and the intensity range test that allows |d| as the cost.
+// D0 = v * M (unless dist is null: a call that resumes from the distances
+// already in place), and the intensity range test that allows |d| as the
+// cost.
 __global__ void __launch_bounds__(256) init3d_kernel(const float* mask, float* dist, float v,
                                                      int64_t n, const float* image, int64_t ni,
                                                      int* range_flag) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
-        dist[i] = __fmul_rn(v, mask[i]);
+    if (dist)
+        for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
+            dist[i] = __fmul_rn(v, mask[i]);
     if (!range_flag) return;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < ni; i += stride) {
         const float x = fabsf(image[i]);
@@ -965,7 +968,7 @@ size_t vol3d_workspace_bytes(const SweepArgs& f, const fgx_options* opt, int sms
 
 int run_vol3d(const SweepArgs& f, const float* image, const float* mask, float* dist,
               uint8_t* codes, float v, void* workspace, size_t ws_bytes, const fgx_options* opt,
-              int sms, void* stream) {
+              int sms, void* stream, bool resume) {
     Vol3DPlan vp;
     if (!plan_vol3d(f, opt, sms, &vp)) return FGX_ERR_UNSUPPORTED;
     if (ws_bytes < vp.ws_bytes) return FGX_ERR_WORKSPACE;
@@ -1018,7 +1021,8 @@ int run_vol3d(const SweepArgs& f, const float* image, const float* mask, float* 
         return FGX_ERR_CUDA;
     const int64_t n = f.B * f.N;
     const int ig = (int)std::min<int64_t>((n + 255) / 256, (int64_t)sms * 16);
-    init3d_kernel<<<std::max(ig, 1), 256, 0, s>>>(mask, dist, v, n, image, f.B * f.C * f.N,
+    init3d_kernel<<<std::max(ig, 1), 256, 0, s>>>(mask, resume ? nullptr : dist, v, n, image,
+                                                 f.B * f.C * f.N,
                                                  vp.mode == kModeAbs ? range_flag : nullptr);
     if (cudaGetLastError() != cudaSuccess) return FGX_ERR_CUDA;
     if (a.imageT && f.iterations > 0) {

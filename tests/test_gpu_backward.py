@@ -211,3 +211,72 @@ def test_autograd_function(fgx):
     # forward value equals the plain forward
     plain = fgx.geodesic2d(img.detach(), m.detach(), case.v, case.lam, case.iterations)
     _bits_equal(d.detach().cpu().numpy(), plain.cpu().numpy(), "autograd forward")
+
+
+# ------------------------------------------------------- checkpointed 3D training
+
+def _ckpt_case(C=2, lam=0.6, iterations=3, shape=(18, 33, 41)):
+    rng = np.random.default_rng(77 + C)
+    img = rng.uniform(0, 1, (2, C) + shape).astype(np.float32)
+    m = rng.uniform(0, 1, (2, 1) + shape).astype(np.float32)
+    m[0, 0, 2, 3, 4] = 0
+    m[1, 0, -2, -3, -4] = 0
+    w = rng.uniform(-1, 1, m.shape).astype(np.float32)
+    return workloads.Case("ckpt3d", img, m, 8.0, lam, iterations, (2.0, 1.0, 0.75)), w
+
+
+@pytest.mark.parametrize("interval", [1, 2, 3, 5])
+@pytest.mark.parametrize("C,lam", [(2, 0.6), (1, 1.0)])
+def test_checkpointed_backward_equals_oracle(fgx, interval, C, lam):
+    """Forward keeping distance maps every `interval` iterations, backward
+    replaying each segment: the distances equal the plain forward's and the
+    gradients equal the oracle's reverse sweep bit for bit (3 iterations: 3,
+    2, 1 and 1 segments)."""
+    case, w = _ckpt_case(C, lam)
+    img = torch.from_numpy(case.image).cuda()
+    m = torch.from_numpy(case.mask).cuda()
+    d, saved = fgx.forward_checkpoint(img, m, case.v, case.lam, case.iterations, interval,
+                                      spacing=case.spacing, check=True)
+    nseg = -(-case.iterations // interval)
+    assert saved.shape[0] == nseg - 1
+    want_d, want_codes = oracle.gdt(case.image, case.mask, case.v, case.lam, case.iterations,
+                                    spacing=case.spacing, return_codes=True, threads=THREADS)
+    _bits_equal(d.cpu().numpy(), want_d, "dist")
+    gi, gm = fgx.backward_checkpoint(torch.from_numpy(w).cuda(), img, m, saved, case.v,
+                                     case.lam, case.iterations, interval, spacing=case.spacing,
+                                     check=True)
+    wi, wm = _oracle(case, w, want_codes)
+    _bits_equal(gi.cpu().numpy(), wi, "grad_image")
+    _bits_equal(gm.cpu().numpy(), wm, "grad_mask")
+
+
+def test_checkpointed_autograd_matches_codes_mode(fgx):
+    """GeodesicFn with checkpoint=1 and without: same forward, same image and
+    mask gradients (the differentiable 3D workload's generator, smaller)."""
+    case = workloads.diff3d(shape=(20, 36, 44), v=10.0)
+    w = torch.from_numpy(case.extra["w"]).cuda()
+    grads = []
+    for ck in (None, 1):
+        img = torch.from_numpy(case.image).cuda().requires_grad_(True)
+        m = torch.from_numpy(case.mask).cuda().requires_grad_(True)
+        d = fgx.geodesic_autograd(img, m, case.v, case.lam, case.iterations,
+                                  spacing=case.spacing, checkpoint=ck)
+        (w * d).sum().backward()
+        grads.append((d.detach().cpu().numpy(), img.grad.cpu().numpy(), m.grad.cpu().numpy()))
+    for a, b, what in zip(grads[0], grads[1], ("dist", "grad_image", "grad_mask")):
+        _bits_equal(b, a, what)
+
+
+def test_backward_3d_scratch_does_not_grow_with_iterations(fgx):
+    """The 3D reverse sweep keeps the adjoint of one pass application, not of
+    every one: its scratch is the same for 1 and 8 iterations, and the
+    checkpointed kept buffer is 4/interval bytes per voxel and iteration."""
+    B, C, D, H, W = 1, 1, 64, 64, 64
+    n = D * H * W
+    s1 = fgx.backward_workspace_size(3, B, C, D, H, W, 1)
+    s8 = fgx.backward_workspace_size(3, B, C, D, H, W, 8)
+    assert s1 == s8
+    assert s8 < 16 * n
+    assert fgx.saved_size(3, B, D, H, W, 8) == 8 * 6 * n
+    assert fgx.checkpoint_saved_size(B, D, H, W, 8, 2) == 3 * 4 * n
+    assert fgx.checkpoint_saved_size(B, D, H, W, 8, 8) == 0
