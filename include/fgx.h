@@ -186,8 +186,8 @@ int fgx_euclidean3d(const float* mask, float* dist, int64_t B, int64_t D, int64_
                     const float spacing[3], float v, int iterations, void* workspace,
                     size_t workspace_bytes, const fgx_options* opt, void* stream);
 
-/* Scratch bytes of fgx_signed_geodesic2d / 3d: the forward's workspace plus
- * one distance map of B * D * H * W floats. */
+/* Scratch bytes of fgx_signed_geodesic2d / 3d: the workspace of a forward of
+ * 2B instances plus 2B masks and 2B distance maps of D * H * W floats. */
 int fgx_signed_workspace_size(int ndim, int64_t B, int64_t C, int64_t D, int64_t H, int64_t W,
                               const fgx_options* opt, size_t* bytes);
 
@@ -197,9 +197,9 @@ int fgx_signed_workspace_size(int ndim, int64_t B, int64_t C, int64_t D, int64_t
  * same image (1 - M and the difference rounded to float32).  Negative inside
  * the region where M = 0, positive where M = 1; swapping M and 1 - M negates
  * the result exactly.  Arguments as fgx_geodesic2d / 3d; dist may alias mask
- * but not image.  The two transforms run one after the other on `stream`
- * with the single-call kernels; a device wait timeout in either is reported
- * by fgx_workspace_status. */
+ * but not image.  Both transforms of every instance run as one launch of 2B
+ * transforms of the same B images; a device wait timeout is reported by
+ * fgx_workspace_status. */
 int fgx_signed_geodesic2d(const float* image, const float* mask, float* dist, int64_t B,
                           int64_t C, int64_t H, int64_t W, float v, float lambda, int iterations,
                           void* workspace, size_t workspace_bytes, const fgx_options* opt,
@@ -208,6 +208,32 @@ int fgx_signed_geodesic3d(const float* image, const float* mask, float* dist, in
                           int64_t C, int64_t D, int64_t H, int64_t W, const float spacing[3],
                           float v, float lambda, int iterations, void* workspace,
                           size_t workspace_bytes, const fgx_options* opt, void* stream);
+
+/* Geodesic symmetric filtering of a segmentation (the paper names GSF among
+ * the applications of the transform, without a definition; reading used
+ * here, after the geodesic morphology of GeoS).  F in [0, 1] marks the
+ * object (F = 1) against the background (F = 0); S(X) = GDT(1 - X) - GDT(X)
+ * is the signed distance of the object of an indicator X (negative inside),
+ * i.e. fgx_signed_geodesic of the mask 1 - X.  Then
+ *   erosion   F_e = [S(F) < -theta_e],   dilation  F_d = [S(F) < theta_d],
+ *   out       = [(S(F_e) + S(F_d)) + (theta_d - theta_e) < 0]
+ * (1.0 / 0.0 floats; each sum and difference rounded to float32, the
+ * thresholds' difference computed in float32 on the host).  Objects thinner
+ * than the erosion vanish, holes narrower than the dilation close, and the
+ * boundary of a large object stays where it was.  theta_d, theta_e >= 0,
+ * finite.  The six transforms run as two launches over the same B images:
+ * 2B transforms (1 - F and F), then 4B (1 - F_e, F_e, 1 - F_d, F_d).  Other
+ * arguments and errors as fgx_geodesic2d / 3d; out [B][1][...] may alias
+ * mask but not image. */
+int fgx_gsf_workspace_size(int ndim, int64_t B, int64_t C, int64_t D, int64_t H, int64_t W,
+                           const fgx_options* opt, size_t* bytes);
+int fgx_gsf2d(const float* image, const float* mask, float* out, int64_t B, int64_t C, int64_t H,
+              int64_t W, float v, float lambda, int iterations, float theta_d, float theta_e,
+              void* workspace, size_t workspace_bytes, const fgx_options* opt, void* stream);
+int fgx_gsf3d(const float* image, const float* mask, float* out, int64_t B, int64_t C, int64_t D,
+              int64_t H, int64_t W, const float spacing[3], float v, float lambda,
+              int iterations, float theta_d, float theta_e, void* workspace,
+              size_t workspace_bytes, const fgx_options* opt, void* stream);
 
 /* ------------------------------------------------------------ batched ---- */
 

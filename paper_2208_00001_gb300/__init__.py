@@ -111,6 +111,12 @@ _SIGS = {
                                _sz, _vp, _vp], _i32),
     "fgx_signed_geodesic3d": ([_vp, _vp, _vp, _i64, _i64, _i64, _i64, _i64, _vp, _f32, _f32,
                                _i32, _vp, _sz, _vp, _vp], _i32),
+    "fgx_gsf_workspace_size": ([_i32, _i64, _i64, _i64, _i64, _i64, _vp, ctypes.POINTER(_sz)],
+                               _i32),
+    "fgx_gsf2d": ([_vp, _vp, _vp, _i64, _i64, _i64, _i64, _f32, _f32, _i32, _f32, _f32, _vp, _sz,
+                   _vp, _vp], _i32),
+    "fgx_gsf3d": ([_vp, _vp, _vp, _i64, _i64, _i64, _i64, _i64, _vp, _f32, _f32, _i32, _f32,
+                   _f32, _vp, _sz, _vp, _vp], _i32),
     "fgx_batched_workspace_size": ([_vp, _i32, _vp, ctypes.POINTER(_sz)], _i32),
     "fgx_geodesic_batched": ([_vp, _i32, _vp, _sz, _vp, _vp], _i32),
     "fgx_batched_prepare": ([_vp, _i32, _vp, _sz, _vp, _vp, _vp], _i32),
@@ -419,6 +425,41 @@ def signed_geodesic(image, mask, v, lam, iterations, spacing=None, out=None, opt
         _check(st, "fgx_signed_geodesic")
         if check:
             _check(workspace_status(ws), "fgx_signed_geodesic (device)")
+    return out
+
+
+def gsf_workspace_size(ndim, B, C, D, H, W, options=None):
+    n = ctypes.c_size_t(0)
+    _check(lib().fgx_gsf_workspace_size(ndim, B, C, D, H, W, _opt(options), ctypes.byref(n)),
+           "gsf workspace size")
+    return n.value
+
+
+def gsf(image, indicator, v, lam, iterations, theta_d, theta_e, spacing=None, out=None,
+        options=None, workspace=None, check=False):
+    """Geodesic symmetric filtering of a segmentation indicator (1 = object):
+    erosion by theta_e and dilation by theta_d in geodesic distance, combined
+    symmetrically; returns 1.0 / 0.0 floats of the indicator's shape."""
+    ndim = image.dim() - 2
+    B, C, D, H, W = _shape(image, indicator, ndim)
+    dev = image.device
+    with torch.cuda.device(dev):
+        if out is None:
+            out = torch.empty_like(indicator)
+        ws = workspace if workspace is not None else _workspace(
+            gsf_workspace_size(ndim, B, C, D, H, W, options), dev)
+        if ndim == 2:
+            st = lib().fgx_gsf2d(_ptr(image), _ptr(indicator), _ptr(out), B, C, H, W, float(v),
+                                 float(lam), int(iterations), float(theta_d), float(theta_e),
+                                 _ptr(ws), ws.numel(), _opt(options), _stream())
+        else:
+            st = lib().fgx_gsf3d(_ptr(image), _ptr(indicator), _ptr(out), B, C, D, H, W,
+                                 _spacing(spacing), float(v), float(lam), int(iterations),
+                                 float(theta_d), float(theta_e), _ptr(ws), ws.numel(),
+                                 _opt(options), _stream())
+        _check(st, "fgx_gsf")
+        if check:
+            _check(workspace_status(ws), "fgx_gsf (device)")
     return out
 
 

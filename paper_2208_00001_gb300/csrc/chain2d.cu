@@ -56,6 +56,7 @@ struct Chain2DArgs {
     float* dist;         // [B][H][W]
     uint8_t* codes;      // [iterations * 4][B][H][W] parent codes, or null
     int B, C, H, W, Wp, Hp;
+    int nimg;            // distinct images: instance b reads image b % nimg
     float v, lambda;
     int iterations;
     int table;           // 1: cost tables, 0: constant costs (lambda = 0)
@@ -652,7 +653,7 @@ __device__ __forceinline__ void init_tile(const Chain2DArgs& a, int b) {
     const int64_t N = (int64_t)a.H * a.W;
     const int w0 = blockIdx.x * kInitTile, h0 = blockIdx.y * kInitTile;
     const int tx = threadIdx.x, ty = threadIdx.y;
-    const float* img = a.image + (int64_t)b * a.C * N;
+    const float* img = a.image + (int64_t)(b % a.nimg) * a.C * N;
     if (CC > 0 && a.table) {
         // rows h0-1 .. h0+32, columns w0-1 .. w0+32 (0 outside the image)
         for (int idx = ty * 32 + tx; idx < kHalo * kHalo; idx += 256) {
@@ -1015,6 +1016,7 @@ size_t fill_chain_args(Chain2DArgs* a, const float* image, const float* mask, fl
     a->dist = dist;
     a->codes = codes;
     a->B = (int)B;
+    a->nimg = (int)std::max<int64_t>(B, 1);
     a->C = (int)C;
     a->H = (int)H;
     a->W = (int)W;
@@ -1103,7 +1105,8 @@ size_t chain2d_workspace_bytes(int64_t B, int64_t C, int64_t H, int64_t W,
 
 int run_chain2d(const float* image, const float* mask, float* dist, uint8_t* codes, int64_t B,
                 int64_t C, int64_t H, int64_t W, float v, float lambda, int iterations,
-                void* workspace, size_t ws_bytes, const fgx_options* opt, int sms, void* stream) {
+                void* workspace, size_t ws_bytes, const fgx_options* opt, int sms, void* stream,
+                int64_t nimg) {
     Chain2DArgs a;
     char* p = (char*)workspace;
     size_t xbytes = 0;
@@ -1114,6 +1117,7 @@ int run_chain2d(const float* image, const float* mask, float* dist, uint8_t* cod
                                         iterations, opt, p, p + kHeaderBytes,
                                         p + kHeaderBytes + xbytes, &xbytes, kMaxSeg);
     if (ws_bytes < need) return FGX_ERR_WORKSPACE;
+    if (nimg > 0) a.nimg = (int)nimg;
     const int max_tiles = a.max_tiles;
 
     const size_t smem = sizeof(TileSmem);

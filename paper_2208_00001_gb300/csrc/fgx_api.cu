@@ -131,6 +131,7 @@ int plan_forward(int ndim, int64_t B, int64_t C, int64_t D, int64_t H, int64_t W
     a.B = B;
     a.C = C;
     a.N = D * H * W;
+    a.nimg = std::max<int64_t>(B, 1);
     a.ndim = ndim;
     a.lambda = lambda;
     a.iterations = iterations;
@@ -199,7 +200,7 @@ int run_forward(int ndim, const float* image, const float* mask, float* dist, in
                 int64_t D, int64_t H, int64_t W, const float spacing[3], float v, float lambda,
                 int iterations, uint8_t* codes, size_t codes_bytes, void* workspace,
                 size_t ws_bytes, const fgx_options* opt, void* stream,
-                bool fast_kernels = false) {
+                bool fast_kernels = false, int64_t nimg = 0) {
     if (!(std::isfinite(v) && v > 0.f)) return FGX_ERR_ARG;
     if (!(lambda >= 0.f && lambda <= 1.f)) return FGX_ERR_ARG;
     if (iterations < 0) return FGX_ERR_ARG;
@@ -224,8 +225,11 @@ int run_forward(int ndim, const float* image, const float* mask, float* dist, in
     if (!mask || !dist || (!image && lambda != 0.f)) return FGX_ERR_ARG;
     if ((image && !is_device_ptr(image)) || !is_device_ptr(mask) || !is_device_ptr(dist))
         return FGX_ERR_NOT_DEVICE_PTR;
+    // nimg: instance b reads image b % nimg (a batch of transforms of the
+    // same images; internal callers only)
+    if (nimg <= 0) nimg = B;
     const size_t nb = (size_t)(B * N) * sizeof(float);
-    if (image && overlaps(dist, nb, image, (size_t)(B * C * N) * sizeof(float)))
+    if (image && overlaps(dist, nb, image, (size_t)(nimg * C * N) * sizeof(float)))
         return FGX_ERR_ARG;
     const size_t need_codes = (size_t)iterations * pl.args.npass * (size_t)(B * N);
     if (codes) {
@@ -238,18 +242,19 @@ int run_forward(int ndim, const float* image, const float* mask, float* dist, in
         if (!workspace || ws_bytes < pl.chain_bytes) return FGX_ERR_WORKSPACE;
         if (!is_device_ptr(workspace)) return FGX_ERR_NOT_DEVICE_PTR;
         return run_chain2d(image, mask, dist, codes, B, C, H, W, v, lambda, iterations,
-                           workspace, ws_bytes, opt, pl.sms, stream);
+                           workspace, ws_bytes, opt, pl.sms, stream, nimg);
     }
     if (fast_kernels && ndim == 3 && pl.vol3d_bytes && workspace &&
         ws_bytes >= pl.vol3d_bytes && vol3d_supports(pl.args, opt, pl.sms)) {
         if (!is_device_ptr(workspace)) return FGX_ERR_NOT_DEVICE_PTR;
         return run_vol3d(pl.args, image, mask, dist, codes, v, workspace, ws_bytes, opt, pl.sms,
-                         stream);
+                         stream, false, nimg);
     }
     if (!workspace || ws_bytes < pl.ws_bytes) return FGX_ERR_WORKSPACE;
     if (!is_device_ptr(workspace)) return FGX_ERR_NOT_DEVICE_PTR;
     SweepArgs& a = pl.args;
     a.image = image;
+    a.nimg = nimg;
     a.mask = mask;
     a.dist = dist;
     a.v = v;
@@ -264,6 +269,15 @@ int run_forward(int ndim, const float* image, const float* mask, float* dist, in
 }
 
 }  // namespace
+
+int run_forward_batch(int ndim, const float* image, int64_t nimg, const float* mask, float* dist,
+                      int64_t B, int64_t C, int64_t D, int64_t H, int64_t W,
+                      const float spacing[3], float v, float lambda, int iterations,
+                      void* workspace, size_t ws_bytes, const fgx_options* opt, void* stream) {
+    if (nimg < 1 || (B > 0 && B % nimg)) return FGX_ERR_ARG;
+    return run_forward(ndim, image, mask, dist, B, C, D, H, W, spacing, v, lambda, iterations,
+                       nullptr, 0, workspace, ws_bytes, opt, stream, true, nimg);
+}
 
 int plan_instance(int ndim, int64_t C, int64_t D, int64_t H, int64_t W, const float spacing[3],
                   float lambda, const fgx_options* opt, SweepArgs* args, int* sms) {
@@ -406,7 +420,7 @@ int fgx_euclidean3d(const float* mask, float* dist, int64_t B, int64_t D, int64_
 int fgx_signed_workspace_size(int ndim, int64_t B, int64_t C, int64_t D, int64_t H, int64_t W,
                               const fgx_options* opt, size_t* bytes) {
     size_t fwd = 0;
-    const int st = fgx_geodesic_workspace_size(ndim, B, C, D, H, W, opt, &fwd);
+    const int st = fgx_geodesic_workspace_size(ndim, 2 * B, C, D, H, W, opt, &fwd);
     if (st != FGX_OK) return st;
     *bytes = signed_workspace_bytes(fwd, B * D * H * W);
     return FGX_OK;

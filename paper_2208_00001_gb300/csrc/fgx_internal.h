@@ -34,10 +34,11 @@ struct PassGeom {
 enum { kCostGeneral = 0, kCostAbs = 1, kCostConst = 2 };
 
 struct SweepArgs {
-    const float* image;  // [B][C][N]
+    const float* image;  // [nimg][C][N]
     const float* mask;   // [B][N]
     float* dist;         // [B][N]
     int64_t B, C, N;
+    int64_t nimg;        // distinct images: instance b reads image b % nimg
     int ndim;
     float v, lambda;
     int iterations, npass;
@@ -143,7 +144,7 @@ bool vol3d_supports(const SweepArgs& f, const fgx_options* opt, int sms);
 // resume: start from the distances already in `dist` instead of v * M.
 int run_vol3d(const SweepArgs& f, const float* image, const float* mask, float* dist,
               uint8_t* codes, float v, void* workspace, size_t ws_bytes, const fgx_options* opt,
-              int sms, void* stream, bool resume = false);
+              int sms, void* stream, bool resume = false, int64_t nimg = 0);
 
 // Batched 2D instances on the line-chain kernel (chain2d.cu): the size of
 // one instance's argument block, filling it (buffers: exchange words at xb,
@@ -213,6 +214,14 @@ void launch_wait_probe(const unsigned long long* tag, int* status, long long tim
 
 // Signed transform GDT(M) - GDT(1 - M) (signed.cu): workspace bytes for a
 // forward workspace of `forward_bytes` and n elements, and the run.
+// Forward of B transforms of nimg images (B a multiple of nimg; instance b
+// reads image b % nimg) with the library's fast kernels; the workspace of
+// fgx_geodesic_workspace_size(ndim, B, C, D, H, W).
+int run_forward_batch(int ndim, const float* image, int64_t nimg, const float* mask, float* dist,
+                      int64_t B, int64_t C, int64_t D, int64_t H, int64_t W,
+                      const float spacing[3], float v, float lambda, int iterations,
+                      void* workspace, size_t ws_bytes, const fgx_options* opt, void* stream);
+
 size_t signed_workspace_bytes(size_t forward_bytes, int64_t n);
 int run_signed(int ndim, const float* image, const float* mask, float* dist, int64_t B,
                int64_t C, int64_t D, int64_t H, int64_t W, const float spacing[3], float v,
@@ -221,7 +230,8 @@ int run_signed(int ndim, const float* image, const float* mask, float* dist, int
 
 int run_chain2d(const float* image, const float* mask, float* dist, uint8_t* codes, int64_t B,
                 int64_t C, int64_t H, int64_t W, float v, float lambda, int iterations,
-                void* workspace, size_t ws_bytes, const fgx_options* opt, int sms, void* stream);
+                void* workspace, size_t ws_bytes, const fgx_options* opt, int sms, void* stream,
+                int64_t nimg = 0);
 
 // Adjoint launchers (adjoint_kernel.cu)
 int launch_adjoint(const AdjointArgs& a, int grid, size_t smem, void* stream);

@@ -267,7 +267,7 @@ __global__ void __launch_bounds__(kThreads, 2) sweep_kernel(const SweepArgs a) {
                 const int64_t b = w * per_wave + blockIdx.x / ntiles;
                 if (b < a.B) {
                     TileJob j;
-                    j.img = a.image + b * a.C * a.N;
+                    j.img = a.image + (b % a.nimg) * a.C * a.N;
                     j.dist = a.dist + b * a.N;
                     j.codes = a.codes ? a.codes + ((int64_t)t_app * a.B + b) * a.N : nullptr;
                     j.flags = a.flags + b * a.max_tiles;

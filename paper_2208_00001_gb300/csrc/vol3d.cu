@@ -94,6 +94,7 @@ struct Vol3DArgs {  // aligned as CUtensorMap (the descriptor arrays of batched 
     float* dist;         // [B][N]
     uint8_t* codes;      // [iterations * 6][B][N] parent codes, or null
     int64_t B, C, N;
+    int64_t nimg;        // distinct images: instance b reads image b % nimg
     float v, lambda;
     int iterations;
     int mode;
@@ -109,7 +110,7 @@ struct Vol3DArgs {  // aligned as CUtensorMap (the descriptor arrays of batched 
     // W passes on transposed copies (planes of those passes have H as their
     // contiguous axis, so staging loads and result stores are coalesced):
     float* distT;              // [B][W][D][H], or null (W passes on dist itself)
-    float* imageT;             // [B][C][W][D][H] (cost modes that read intensities)
+    float* imageT;             // [nimg][C][W][D][H] (cost modes that read intensities)
     int64_t D, H, W;
 };
 
@@ -237,7 +238,7 @@ __device__ void tma_chunk(const Vol3DArgs& a, const Tile3& t, Head3& h, float* s
 #pragma unroll
         for (int ch = 0; ch < CI; ++ch)
             tma_load4(dst + (unsigned int)((1 + ch) * kArr * 4), &a.tmap[t.map_i], t.q0, y, z,
-                      (int)(t.b * a.C) + ch, mb);
+                      (int)((t.b % a.nimg) * a.C) + ch, mb);
     }
 }
 
@@ -682,7 +683,7 @@ __global__ void __launch_bounds__(TMA ? kCW * 32 : (kCW + kPW) * 32, 1)
             t.ntq = a.ntq[pass];
             t.b = b;
             t.dist = (on_t ? a.distT : a.dist) + b * a.N;
-            t.img = (on_t ? a.imageT : a.image) + b * a.C * a.N;
+            t.img = (on_t ? a.imageT : a.image) + (b % a.nimg) * a.C * a.N;
             t.codes = CODES ? a.codes + ((int64_t)t_app * a.B + b) * a.N : nullptr;
             t.csl = on_t ? 1 : g.sl;
             t.csp = on_t ? a.H * a.W : g.sp;
@@ -860,7 +861,7 @@ bool make_map(CUtensorMap* m, const void* base, uint64_t d0, uint64_t d1, uint64
 // H (the W passes on the transposed copies) multiples of 4.
 bool make_maps(Vol3DArgs& a) {
     const uint64_t D = (uint64_t)a.D, H = (uint64_t)a.H, W = (uint64_t)a.W;
-    const uint64_t B = (uint64_t)a.B, BC = (uint64_t)(a.B * a.C);
+    const uint64_t B = (uint64_t)a.B, BC = (uint64_t)(a.nimg * a.C);
     if (W % 4 || H % 4 || !a.distT) return false;
     if (D > (1u << 30) || H > (1u << 30) || W > (1u << 30) || BC > (1u << 30)) return false;
     bool ok = make_map(&a.tmap[kMapDistD], a.dist, W, H, D, B, kRQ, kRP, 1, true) &&
@@ -968,7 +969,7 @@ size_t vol3d_workspace_bytes(const SweepArgs& f, const fgx_options* opt, int sms
 
 int run_vol3d(const SweepArgs& f, const float* image, const float* mask, float* dist,
               uint8_t* codes, float v, void* workspace, size_t ws_bytes, const fgx_options* opt,
-              int sms, void* stream, bool resume) {
+              int sms, void* stream, bool resume, int64_t nimg) {
     Vol3DPlan vp;
     if (!plan_vol3d(f, opt, sms, &vp)) return FGX_ERR_UNSUPPORTED;
     if (ws_bytes < vp.ws_bytes) return FGX_ERR_WORKSPACE;
@@ -981,6 +982,7 @@ int run_vol3d(const SweepArgs& f, const float* image, const float* mask, float* 
     a.B = f.B;
     a.C = f.C;
     a.N = f.N;
+    a.nimg = nimg > 0 ? nimg : std::max<int64_t>(f.B, 1);
     a.v = v;
     a.lambda = f.lambda;
     a.iterations = f.iterations;
@@ -1022,11 +1024,11 @@ int run_vol3d(const SweepArgs& f, const float* image, const float* mask, float* 
     const int64_t n = f.B * f.N;
     const int ig = (int)std::min<int64_t>((n + 255) / 256, (int64_t)sms * 16);
     init3d_kernel<<<std::max(ig, 1), 256, 0, s>>>(mask, resume ? nullptr : dist, v, n, image,
-                                                 f.B * f.C * f.N,
+                                                 a.nimg * f.C * f.N,
                                                  vp.mode == kModeAbs ? range_flag : nullptr);
     if (cudaGetLastError() != cudaSuccess) return FGX_ERR_CUDA;
     if (a.imageT && f.iterations > 0) {
-        transpose_image3d_kernel<<<sms * 8, 256, 0, s>>>(image, a.imageT, f.B * f.C,
+        transpose_image3d_kernel<<<sms * 8, 256, 0, s>>>(image, a.imageT, a.nimg * f.C,
                                                           a.D * a.H, a.W);
         if (cudaGetLastError() != cudaSuccess) return FGX_ERR_CUDA;
     }
@@ -1070,6 +1072,7 @@ bool vol3d_instance_desc(void* desc, const fgx_instance& it, const SweepArgs& f,
     a.mask = it.mask;
     a.dist = it.dist;
     a.B = 1;
+    a.nimg = 1;
     a.C = f.C;
     a.N = f.N;
     a.v = it.v;

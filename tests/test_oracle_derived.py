@@ -90,3 +90,71 @@ def test_signed_golden_fixture():
     m = np.array(g["mask"], np.float32).reshape(1, 1, 3, 3)
     got = oracle.signed_gdt(img, m, g["v"], g["lambda"], int(g["iterations"]))
     np.testing.assert_array_equal(got.reshape(-1), np.array(g["expect"], np.float32))
+
+
+# ------------------------------------------------ geodesic symmetric filtering
+# The reading (the paper names GSF without defining it): S(X) = GDT(1 - X) -
+# GDT(X) for an indicator X (1 = object), erosion [S(F) < -theta_e],
+# dilation [S(F) < theta_d], result [(S(F_e) + S(F_d)) + theta_d - theta_e < 0].
+
+@pytest.mark.parametrize("td,te", [(1.5, 2.5), (2.5, 1.5), (0.7, 0.7), (3.2, 0.0)])
+def test_gsf_keeps_a_half_plane(td, te):
+    """At lambda = 0 a half-plane object stays the same half-plane: erosion
+    and dilation shift its edge by whole steps in opposite directions and
+    the symmetric combination puts it back (a wrong sign of either term or
+    of theta_d - theta_e moves the edge)."""
+    H, W, x0 = 6, 16, 7
+    f = np.zeros((1, 1, H, W), np.float32)
+    f[..., x0:] = 1.0
+    img = np.random.default_rng(1).uniform(0, 1, (1, 1, H, W)).astype(np.float32)
+    np.testing.assert_array_equal(oracle.gsf(img, f, 1e10, 0.0, 2, td, te), f)
+
+
+def test_gsf_keeps_a_half_space_3d_anisotropic():
+    D, H, W, d0 = 9, 4, 5, 4
+    f = np.zeros((1, 1, D, H, W), np.float32)
+    f[:, :, d0:] = 1.0
+    img = np.zeros((1, 1, D, H, W), np.float32)
+    got = oracle.gsf(img, f, 1e10, 0.0, 2, 5.5, 3.0, spacing=(2.5, 1.0, 1.0))
+    np.testing.assert_array_equal(got, f)
+
+
+def test_gsf_removes_thin_objects_and_fills_narrow_holes():
+    """A 3 x 3 object vanishes under an erosion of 2.5 (its centre is 2 steps
+    from the background); a one-pixel hole in a large object closes under a
+    dilation of 1.5; both survive smaller thresholds."""
+    img = np.zeros((1, 1, 30, 30), np.float32)
+    f = np.zeros((1, 1, 30, 30), np.float32)
+    f[..., 3:6, 3:6] = 1.0          # small object
+    f[..., 12:28, 10:28] = 1.0      # large object ...
+    f[..., 20, 19] = 0.0            # ... with a one-pixel hole
+    out = oracle.gsf(img, f, 1e10, 0.0, 2, 1.5, 2.5)
+    assert out[..., 3:6, 3:6].sum() == 0
+    assert out[0, 0, 20, 19] == 1.0
+    assert out[..., 14:26, 12:26].min() == 1.0
+    kept = oracle.gsf(img, f, 1e10, 0.0, 2, 0.5, 0.5)
+    assert kept[..., 4, 4] == 1.0 and kept[0, 0, 20, 19] == 0.0
+
+
+@pytest.mark.parametrize("lam", [0.0, 0.4, 0.9])
+def test_gsf_with_zero_thresholds_is_the_identity(lam):
+    """With positive step costs (lambda < 1) S(F) < 0 exactly inside a binary
+    object and > 0 outside, so zero thresholds reproduce F."""
+    rng = np.random.default_rng(7)
+    img = rng.uniform(0, 1, (2, 2, 15, 19)).astype(np.float32)
+    f = (rng.uniform(0, 1, (2, 1, 15, 19)) < 0.4).astype(np.float32)
+    np.testing.assert_array_equal(oracle.gsf(img, f, 1e10, lam, 2, 0.0, 0.0), f)
+
+
+@pytest.mark.parametrize("lam", [0.3, 1.0])
+def test_gsf_complement_symmetry(lam):
+    """Filtering the background with the thresholds swapped gives the
+    complement: S(1 - F) = -S(F) exactly, so erosion and dilation trade
+    places and every sum changes sign (thresholds chosen off the distances
+    that occur, so no comparison ties)."""
+    rng = np.random.default_rng(8)
+    img = rng.uniform(0, 1, (1, 1, 21, 24)).astype(np.float32)
+    f = (rng.uniform(0, 1, (1, 1, 21, 24)) < 0.5).astype(np.float32)
+    a = oracle.gsf(img, f, 1e10, lam, 2, 1.23456, 0.87654)
+    b = oracle.gsf(img, (1 - f).astype(np.float32), 1e10, lam, 2, 0.87654, 1.23456)
+    np.testing.assert_array_equal(a, 1 - b)

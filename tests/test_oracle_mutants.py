@@ -14,6 +14,10 @@ import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
+PINS = ["tests/test_oracle_pins.py", "tests/test_oracle_backward.py",
+        "tests/test_oracle_derived.py"]
+DERIVED = ["tests/test_oracle_derived.py"]  # pins of the derived transforms alone
+
 MUTANTS = [
     ("drop the W term of |x-y|^2", "REAL s2 = (e0 * e0 + e1 * e1) + e2 * e2;",
      "REAL s2 = (e0 * e0 + e1 * e1);"),
@@ -41,6 +45,16 @@ MUTANTS = [
      "comp = (np.float32(1.0) - m).astype(np.float32)", "comp = m.copy()", "__init__.py"),
     ("signed transform with the terms swapped", "return (a - b).astype(np.float32)",
      "return (b - a).astype(np.float32)", "__init__.py"),
+    ("GSF threshold difference with the wrong sign", "c = np.float32(td - te)",
+     "c = np.float32(te - td)", "__init__.py", DERIVED),
+    ("GSF erosion on the wrong side", "f_e = (s < -te).astype(np.float32)",
+     "f_e = (s < te).astype(np.float32)", "__init__.py", DERIVED),
+    ("GSF signed distance of the background",
+     "        comp = (np.float32(1.0) - x).astype(np.float32)\n",
+     "        comp = x.copy()\n", "__init__.py", DERIVED),
+    ("GSF erosion in place of the dilation",
+     "total = (signed_of_object(f_e) + signed_of_object(f_d))",
+     "total = (signed_of_object(f_e) + signed_of_object(f_e))", "__init__.py", DERIVED),
 ]
 
 
@@ -48,6 +62,7 @@ MUTANTS = [
 def test_pins_reject_planted_mistake(tmp_path, mutant):
     label, old, new = mutant[:3]
     fname = mutant[3] if len(mutant) > 3 else "gdt_core.inc"
+    pins = mutant[4] if len(mutant) > 4 else PINS
     for d in ("oracle", "tests", "workloads"):
         shutil.copytree(os.path.join(ROOT, d), tmp_path / d,
                         ignore=shutil.ignore_patterns("_build", "__pycache__"))
@@ -56,8 +71,6 @@ def test_pins_reject_planted_mistake(tmp_path, mutant):
     text = src.read_text()
     assert old in text, label
     src.write_text(text.replace(old, new))
-    r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q",
-                        "tests/test_oracle_pins.py", "tests/test_oracle_backward.py",
-                        "tests/test_oracle_derived.py"],
+    r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", *pins],
                        cwd=tmp_path, capture_output=True, text=True, timeout=900)
     assert r.returncode != 0, f"pins did not catch: {label}\n{r.stdout[-2000:]}"
