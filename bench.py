@@ -249,7 +249,7 @@ def _roof(bytes_, t, peak):
 
 EXTRAS = ("2d_plain_256", "2d_large_lambda0", "2d_large_lambda1", "2d_large_lambda0.5_it4",
           "3d_volume_128x256x256", "signed_2d_large", "batched_64x2d_16x3d",
-          "diff_2d_8x512x512", "diff_3d_96x160x160")
+          "diff_2d_8x512x512", "diff_3d_96x160x160", "fast_math")
 
 
 def measure_extras(fgx, dev, flush, stream, peak, steps=5, only=None):
@@ -295,6 +295,32 @@ def measure_extras(fgx, dev, flush, stream, peak, steps=5, only=None):
                      "roofline": _roof(fwd_bytes(c), t, peak),
                      "device_status": fgx.status_string(st)}
 
+    if want("fast_math"):
+        # the fast-math variant beside the exact forward on the workloads
+        # whose costs use the general formula (lambda = 0.5 with 3 channels,
+        # lambda = 0.75)
+        fm = {}
+        for name, make in [("2d_large_lambda0.5", lambda: workloads.large2d()),
+                           ("diff_3d_96x160x160_fwd", lambda: workloads.diff3d())]:
+            c = make()
+            img = torch.from_numpy(c.image).to(dev)
+            m = torch.from_numpy(c.mask).to(dev)
+            o = torch.empty_like(m)
+            dims = [img.shape[0], img.shape[1]] + ([1] if c.ndim == 2 else []) + list(
+                img.shape[2:])
+            res = {}
+            for label, opts in (("exact", None), ("fast_math", dict(fast_math=1))):
+                ws = torch.empty(fgx.workspace_size(c.ndim, *dims, options=opts),
+                                 dtype=torch.uint8, device=dev)
+                fn = lambda: fgx.geodesic(img, m, c.v, c.lam, c.iterations,  # noqa: E731
+                                          spacing=c.spacing, out=o, options=opts, workspace=ws)
+                fn()
+                fn()
+                t = _device_time(fn, steps, flush, stream)
+                res[label] = {"ms": t * 1e3,
+                              "mvox_per_s_per_iter": c.voxels * c.iterations / t / 1e6}
+            fm[name] = res
+        out["fast_math"] = fm
     if want("signed_2d_large"):
         c = workloads.large2d()
         img = torch.from_numpy(c.image).to(dev)

@@ -72,6 +72,13 @@ typedef struct fgx_options {
                            * speculatively (exact results; a segment whose start line
                            * changes runs again); 0 = as many as one block per SM
                            * allows, 1 = off, n = at most n (up to 8) */
+    int32_t fast_math;    /* forward without parent codes: 1 = edge costs
+                           * sqrt.approx(fma(lambda, di2, t_k)) (the intensity sum
+                           * fused too) instead of the IEEE-rounded sequence; results
+                           * within 1e-5 relative of the exact transform instead of
+                           * bit-exact.  Only where the general cost formula applies
+                           * (lambda != 0, and not lambda = 1 with one channel, whose
+                           * |d| cost is exact and cheap); 0 = exact */
 } fgx_options;
 
 /* Human-readable name of a status code (static string). */

@@ -46,12 +46,12 @@ class Options(ctypes.Structure):
     _fields_ = [("size", ctypes.c_uint32), ("tile_lines", ctypes.c_int32),
                 ("tile_width", ctypes.c_int32), ("tile_height", ctypes.c_int32),
                 ("max_blocks", ctypes.c_int32), ("timeout_ms", ctypes.c_int32),
-                ("segments", ctypes.c_int32)]
+                ("segments", ctypes.c_int32), ("fast_math", ctypes.c_int32)]
 
     def __init__(self, tile_lines=0, tile_width=0, tile_height=0, max_blocks=0, timeout_ms=0,
-                 segments=0):
+                 segments=0, fast_math=0):
         super().__init__(ctypes.sizeof(Options), tile_lines, tile_width, tile_height, max_blocks,
-                         timeout_ms, segments)
+                         timeout_ms, segments, fast_math)
 
 
 class Instance(ctypes.Structure):

@@ -60,6 +60,7 @@ struct Chain2DArgs {
     float v, lambda;
     int iterations;
     int table;           // 1: cost tables, 0: constant costs (lambda = 0)
+    int fast;            // tables with fused multiply-adds and the approximate root
     float tv[3], th[3];  // (1 - lambda) * s2 of the row-edge and column-edge offsets
     float cv[3], chh[3]; // sqrt of the above (constant-cost mode)
     float* Dw;           // [B][H][Wp]
@@ -89,13 +90,13 @@ using namespace chain;
 // Cost of the undirected edge between a and b (same channel stride n), in the
 // fixed arithmetic order: di2 = sum_ch (I(a)-I(b))^2, c = sqrt(t + lambda*di2).
 __device__ __forceinline__ float edge_cost(const float* ia, const float* ib, int C, int64_t n,
-                                           float t, float lam) {
+                                           float t, float lam, bool fast) {
     float di2 = 0.0f;
     for (int ch = 0; ch < C; ++ch) {
         const float d = __fsub_rn(__ldg(ia + ch * n), __ldg(ib + ch * n));
-        di2 = __fadd_rn(di2, __fmul_rn(d, d));
+        di2 = fast ? __fmaf_rn(d, d, di2) : __fadd_rn(di2, __fmul_rn(d, d));
     }
-    return __fsqrt_rn(__fadd_rn(t, __fmul_rn(lam, di2)));
+    return fast ? fast_sqrt(__fmaf_rn(lam, di2, t)) : __fsqrt_rn(__fadd_rn(t, __fmul_rn(lam, di2)));
 }
 
 // Producer/consumer organisation of one tile, three warps.  The chain warp
@@ -689,17 +690,24 @@ __device__ __forceinline__ void init_tile(const Chain2DArgs& a, int b) {
                     const float self = tile[c][hl + 1][tx + 1];
                     const float x = __fsub_rn(tile[c][hl + 2][tx + k], self);
                     const float y = __fsub_rn(tile[c][hl + k][tx + 2], self);
-                    dv = __fadd_rn(dv, __fmul_rn(x, x));
-                    dh = __fadd_rn(dh, __fmul_rn(y, y));
+                    dv = a.fast ? __fmaf_rn(x, x, dv) : __fadd_rn(dv, __fmul_rn(x, x));
+                    dh = a.fast ? __fmaf_rn(y, y, dh) : __fadd_rn(dh, __fmul_rn(y, y));
                 }
-                if (has_v) cv = __fsqrt_rn(__fadd_rn(a.tv[k], __fmul_rn(a.lambda, dv)));
-                if (has_h) ch = __fsqrt_rn(__fadd_rn(a.th[k], __fmul_rn(a.lambda, dh)));
+                if (a.fast) {
+                    if (has_v) cv = fast_sqrt(__fmaf_rn(a.lambda, dv, a.tv[k]));
+                    if (has_h) ch = fast_sqrt(__fmaf_rn(a.lambda, dh, a.th[k]));
+                } else {
+                    if (has_v) cv = __fsqrt_rn(__fadd_rn(a.tv[k], __fmul_rn(a.lambda, dv)));
+                    if (has_h) ch = __fsqrt_rn(__fadd_rn(a.th[k], __fmul_rn(a.lambda, dh)));
+                }
             } else {
                 const float* self = img + (int64_t)h * a.W + w;
                 if (has_v)
-                    cv = edge_cost(img + (int64_t)(h + 1) * a.W + wn, self, a.C, N, a.tv[k], a.lambda);
+                    cv = edge_cost(img + (int64_t)(h + 1) * a.W + wn, self, a.C, N, a.tv[k],
+                                   a.lambda, a.fast);
                 if (has_h)
-                    ch = edge_cost(img + (int64_t)hn * a.W + w + 1, self, a.C, N, a.th[k], a.lambda);
+                    ch = edge_cost(img + (int64_t)hn * a.W + w + 1, self, a.C, N, a.th[k],
+                                   a.lambda, a.fast);
             }
             if (h < a.H && w < a.Wp) a.Ev[(((int64_t)b * 3 + k) * a.H + h) * a.Wp + w] = cv;
             eh[k][tx][hl] = ch;  // [w local][h local]
@@ -1026,6 +1034,9 @@ size_t fill_chain_args(Chain2DArgs* a, const float* image, const float* mask, fl
     a->lambda = lambda;
     a->iterations = iterations;
     a->table = lambda != 0.0f;
+    // fast math where the general formula applies (the lambda = 1 single
+    // channel cost sqrt(d*d) stays exact), never for recorded codes
+    a->fast = opt && opt->fast_math && lambda != 0.0f && !(lambda == 1.0f && C == 1) && !codes;
     const float unit[3] = {1.f, 1.f, 1.f};
     float t9[9];
     pass_offsets_t(2, 1, unit, lambda, t9);  // pass along H: offsets along W

@@ -117,7 +117,8 @@ int plan_forward(int ndim, int64_t B, int64_t C, int64_t D, int64_t H, int64_t W
                  Plan* pl) {
     if (opt && opt->size != sizeof(fgx_options)) return FGX_ERR_ARG;
     if (opt && (opt->tile_lines < 0 || opt->tile_width < 0 || opt->tile_height < 0 ||
-                opt->max_blocks < 0 || opt->timeout_ms < 0 || opt->segments < 0))
+                opt->max_blocks < 0 || opt->timeout_ms < 0 || opt->segments < 0 ||
+                opt->fast_math < 0 || opt->fast_math > 1))
         return FGX_ERR_ARG;
     if (ndim != 2 && ndim != 3) return FGX_ERR_ARG;
     if (B < 0 || C < 1 || D < 0 || H < 0 || W < 0) return FGX_ERR_SHAPE;
@@ -176,7 +177,8 @@ int plan_forward(int ndim, int64_t B, int64_t C, int64_t D, int64_t H, int64_t W
     a.smem_region = (int)region;
     a.kmax = kmax;
     a.cost_mode = lambda == 0.0f ? kCostConst
-                  : (lambda == 1.0f && C == 1) ? kCostAbs : kCostGeneral;
+                  : (lambda == 1.0f && C == 1) ? kCostAbs
+                  : (opt && opt->fast_math) ? kCostFast : kCostGeneral;
     pl->smem = sweep_smem_bytes(a.cost_mode == kCostConst ? 0 : C, (int)region, kmax);
     if (pl->smem > 200 * 1024) return FGX_ERR_UNSUPPORTED;
     int per_sm = 0;
@@ -232,6 +234,8 @@ int run_forward(int ndim, const float* image, const float* mask, float* dist, in
     if (image && overlaps(dist, nb, image, (size_t)(nimg * C * N) * sizeof(float)))
         return FGX_ERR_ARG;
     const size_t need_codes = (size_t)iterations * pl.args.npass * (size_t)(B * N);
+    // recorded codes come from the exact costs (fast math serves inference)
+    if (codes && pl.args.cost_mode == kCostFast) pl.args.cost_mode = kCostGeneral;
     if (codes) {
         if (codes_bytes < need_codes) return FGX_ERR_WORKSPACE;
         if (!is_device_ptr(codes)) return FGX_ERR_NOT_DEVICE_PTR;

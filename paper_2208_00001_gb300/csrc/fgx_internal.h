@@ -30,8 +30,18 @@ struct PassGeom {
     float c[9];          // sqrt(t) (the cost itself when lambda = 0)
 };
 
-// Edge-cost evaluation modes of the tiled engine (see sweep_kernel.cu).
-enum { kCostGeneral = 0, kCostAbs = 1, kCostConst = 2 };
+// Edge-cost evaluation modes of the tiled engine (see sweep_kernel.cu);
+// kCostFast: the general formula with a fused multiply-add and the
+// approximate square root (fgx_options.fast_math).
+enum { kCostGeneral = 0, kCostAbs = 1, kCostConst = 2, kCostFast = 3 };
+
+// sqrt.approx.f32 of the fast-math edge cost (one hardware approximation,
+// relative error about 2^-22; not the IEEE-rounded root).
+__device__ __forceinline__ float fast_sqrt(float x) {
+    float r;
+    asm("sqrt.approx.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
 
 struct SweepArgs {
     const float* image;  // [nimg][C][N]

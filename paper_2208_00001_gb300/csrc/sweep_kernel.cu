@@ -48,6 +48,8 @@ __device__ __forceinline__ void cp_wait_all() { asm volatile("cp.async.wait_grou
 //  kCostAbs:     lambda = 1 and one channel: c = sqrt_rn(fl(d*d)) = |d| exactly
 //                for 2^-63 <= |d| <= 2^63 and d = 0 (square root elsewhere)
 //  kCostConst:   lambda = 0: c = sqrt_rn(t_k), the pass's constant per offset
+//  kCostFast:    the general formula with fused multiply-adds and the
+//                approximate square root (fast-math option)
 // Offsets are unrolled at compile time; the shared previous-line buffers carry
 // a one-element border of +inf so that neighbours outside the domain never
 // win the min and need no bounds test.
@@ -195,6 +197,14 @@ __device__ bool sweep_tile(const TileJob& j, const PassGeom& g, float* smem) {
                             const unsigned int ub = __float_as_uint(ad);
                             if ((ub - 0x20000000u) <= 0x3F000000u || ub == 0u) c = ad;
                             else c = __fsqrt_rn(__fmul_rn(d, d));
+                        } else if (MODE == kCostFast) {
+                            float di2 = 0.0f;
+                            for (int ch = 0; ch < C; ++ch) {
+                                const float d = __fsub_rn(sI[(size_t)ch * KM * R + e],
+                                                          pI[ch * R + ys]);
+                                di2 = __fmaf_rn(d, d, di2);
+                            }
+                            c = fast_sqrt(__fmaf_rn(lam, di2, g.t[bit]));
                         } else {
                             float di2 = 0.0f;
                             for (int ch = 0; ch < C; ++ch) {
@@ -236,10 +246,12 @@ __device__ bool run_tile(int ndim, int mode, const TileJob& j, const PassGeom& g
     if (ndim == 3) {
         if (mode == kCostAbs) FGX_TILE(3, kCostAbs);
         if (mode == kCostConst) FGX_TILE(3, kCostConst);
+        if (mode == kCostFast) FGX_TILE(3, kCostFast);
         FGX_TILE(3, kCostGeneral);
     }
     if (mode == kCostAbs) FGX_TILE(2, kCostAbs);
     if (mode == kCostConst) FGX_TILE(2, kCostConst);
+    if (mode == kCostFast) FGX_TILE(2, kCostFast);
     FGX_TILE(2, kCostGeneral);
 #undef FGX_TILE
 }

@@ -43,7 +43,9 @@
 //    checks that every intensity is 0 or has magnitude in [2^-40, 2^62],
 //    which bounds every difference to that range; otherwise each candidate
 //    is checked and falls back to the square root;
-//  general: sqrt_rn(t_k + lambda * sum_ch (I(x)-I(y))^2).
+//  general: sqrt_rn(t_k + lambda * sum_ch (I(x)-I(y))^2);
+//  fast (fast-math option, forward without codes): the general formula with
+//    fused multiply-adds and the approximate square root.
 #include <cuda.h>  // CUtensorMap and its encoder's signature (the encoder is looked up at run time)
 #include <cuda_runtime.h>
 
@@ -81,7 +83,7 @@ constexpr int kMaps = 6;
 
 static_assert(kRing % kChunk == 0 && kRingWide % kChunk == 0, "refreshes at chunk boundaries");
 
-enum { kModeConst = 0, kModeAbs = 1, kModeGeneral = 2 };
+enum { kModeConst = 0, kModeAbs = 1, kModeGeneral = 2, kModeFast = 3 };
 // Tensor maps of one call: distances and intensities in the layouts of the
 // D passes ([D][H][W], box = one plane tile), the H passes (same arrays, box
 // spanning D) and the W passes (the [W][D][H] copies).
@@ -364,9 +366,11 @@ __device__ __forceinline__ float cost3(const float (&ix)[CI > 0 ? CI : 1],
 #pragma unroll
     for (int ch = 0; ch < CI; ++ch) {
         const float d = __fsub_rn(ix[ch], iy[ch]);
-        di2 = ch == 0 ? __fmul_rn(d, d) : __fadd_rn(di2, __fmul_rn(d, d));
+        di2 = ch == 0 ? __fmul_rn(d, d)
+                      : (MODE == kModeFast ? __fmaf_rn(d, d, di2) : __fadd_rn(di2, __fmul_rn(d, d)));
     }
-    return __fsqrt_rn(__fadd_rn(t, __fmul_rn(lam, di2)));
+    return MODE == kModeFast ? fast_sqrt(__fmaf_rn(lam, di2, t))
+                             : __fsqrt_rn(__fadd_rn(t, __fmul_rn(lam, di2)));
 }
 
 // Compute warps of one tile: plane steps 1 .. L-1, ring refresh every K
@@ -745,6 +749,13 @@ __device__ bool run_item3(const Vol3DArgs& a, const Tile3& t, int t_app, Head3& 
     if (a.mode == kModeAbs)
         return run_tile3<kModeAbs, 1, false, false>(a, t, t_app, h, stage, cb,
                                                     *a.range_flag != 0);
+    if (a.mode == kModeFast) {
+        if (a.C == 1)
+            return run_tile3<kModeFast, 1, false, false>(a, t, t_app, h, stage, cb, false);
+        if (a.C == 2)
+            return run_tile3<kModeFast, 2, false, false>(a, t, t_app, h, stage, cb, false);
+        return run_tile3<kModeFast, 3, false, false>(a, t, t_app, h, stage, cb, false);
+    }
     if (a.C == 1)
         return run_tile3<kModeGeneral, 1, false, false>(a, t, t_app, h, stage, cb, false);
     if (a.C == 2)
@@ -807,6 +818,12 @@ template <bool CODES, bool TMA>
 Vol3DKernel pick_kernel_t(int mode, int CI) {
     if (mode == kModeConst) return vol3d_kernel<kModeConst, 0, CODES, TMA>;
     if (mode == kModeAbs) return vol3d_kernel<kModeAbs, 1, CODES, TMA>;
+    // the fast-math mode serves forwards without codes only
+    if (mode == kModeFast && !CODES) {
+        if (CI == 1) return vol3d_kernel<kModeFast, 1, false, TMA>;
+        if (CI == 2) return vol3d_kernel<kModeFast, 2, false, TMA>;
+        return vol3d_kernel<kModeFast, 3, false, TMA>;
+    }
     if (CI == 1) return vol3d_kernel<kModeGeneral, 1, CODES, TMA>;
     if (CI == 2) return vol3d_kernel<kModeGeneral, 2, CODES, TMA>;
     return vol3d_kernel<kModeGeneral, 3, CODES, TMA>;
@@ -899,7 +916,8 @@ bool plan_vol3d(const SweepArgs& f, const fgx_options* opt, int sms, Vol3DPlan* 
     if (f.ndim != 3) return false;
     if (opt && (opt->tile_lines || opt->tile_width || opt->tile_height)) return false;
     vp->mode = f.cost_mode == kCostConst ? kModeConst
-               : f.cost_mode == kCostAbs ? kModeAbs : kModeGeneral;
+               : f.cost_mode == kCostAbs ? kModeAbs
+               : f.cost_mode == kCostFast ? kModeFast : kModeGeneral;
     vp->CI = vp->mode == kModeConst ? 0 : (int)f.C;
     // a workspace-size query covers every cost mode: plan the cheapest one
     if (any_mode) {
