@@ -28,6 +28,7 @@
 // need as 64-bit words (value, tag) and polls the neighbours' words until the
 // tags match (bounded wait); the ring is then refreshed.  Passes are
 // separated by a grid barrier.
+#include <cuda.h>  // CUtensorMap and its encoder's signature (the encoder is looked up at run time)
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -83,6 +84,10 @@ struct Chain2DArgs {
     unsigned int* segflag;   // [B][kMaxSeg][2]: boundary changed (phase A, re-run), tag t_app + 1;
                              // then [4]: 1 + the last application of each pass with re-runs
     unsigned int* ckpt;      // [B][kMaxSeg][kMaxCk]: re-run checkpoints (arrivals | changed << 16)
+    // tensor maps of the single-call launch (box: the 128 region columns of a
+    // chunk of kCh lines): Dw, Dt, Ev, Eh; tma = 0: per-lane copies instead
+    CUtensorMap tmap[4];
+    int tma;
 };
 
 using namespace dev;
@@ -237,6 +242,81 @@ __device__ __forceinline__ TileGeo tile_geo(const Chain2DArgs& a, int t_app, int
     return g;
 }
 
+// Input ring layouts.  Per-lane copies fill in[slot][line][array][4 + column]
+// (padded rows, +inf padding); tensor copies fill dense boxes of the region
+// columns of a chunk, [slot][array][row][column], starting at the first
+// 128-byte boundary of the ring, rows in increasing line order (row
+// kCh-1-j holds step j of a backward pass).  A row pointer points at region
+// column 0; the chain also reads one element before it and one after the
+// 128 columns (the edge lanes' neighbouring costs, whose parents are +inf).
+__device__ __forceinline__ const float* tma_ring(const TileSmem& sm) {
+    const unsigned int a0 = saddr(&sm.in[0][0][0][0]);
+    return &sm.in[0][0][0][0] + (((128u - (a0 & 127u)) & 127u) >> 2);
+}
+template <bool TMA, bool fwd>
+__device__ __forceinline__ const float* ring_row(const TileSmem& sm, const float* tbase, int slot,
+                                                 int j, int arr) {
+    if (!TMA) return &sm.in[slot][j][arr][4];
+    return tbase + ((slot * 4 + arr) * kCh + (fwd ? j : kCh - 1 - j)) * kRegion;
+}
+
+// Producer with tensor copies (one elected thread): chunk c of the tile is
+// one box of kCh lines x 128 region columns per array (distances, then the
+// three edge-cost rows), issued once the chain has released the slot and
+// completed on the slot's mbarrier by transaction count.  Outside the array
+// the copies fill NaN, which never wins a min (like the +inf of the padding).
+// The edge rows of a forward step s are rows s-1 of the table, of a backward
+// step its own line; the first line of a sweep has no parents and reads the
+// fill.  After a failed wait the copies in flight are waited for (bounded)
+// before returning.
+template <bool fwd, bool table>
+__device__ bool producer_tma(const Chain2DArgs& a, const TileGeo& g, TileSmem& sm,
+                             unsigned int cb, int b, bool vert) {
+    if ((threadIdx.x & 31) != 0) return true;
+    const float* tbase = tma_ring(sm);
+    const CUtensorMap* md = &a.tmap[vert ? 0 : 1];
+    const CUtensorMap* me = &a.tmap[vert ? 2 : 3];
+    const unsigned int bytes = (unsigned int)((table ? 4 : 1) * kCh * kRegion * 4);
+    bool ok = true;
+    int issued = 0;
+    for (int c = 0; c < g.nch; ++c) {
+        const unsigned int gc = cb + c;
+        const int slot = slot_of(gc, kNci);
+        if (gc >= (unsigned)kNci && !mbar_wait(&sm.done[slot], empty_parity(gc, kNci), a)) {
+            ok = false;
+            break;
+        }
+        if (c >= *(volatile int*)&sm.stop_chunk) {
+            // a re-run that stopped early: the chunk is only handed over
+            mbar_arrive(&sm.in_full[slot]);
+            continue;
+        }
+        const int s = g.s0 + c * kCh;
+        const int y = fwd ? s : g.L - kCh - s;  // first line of the box
+        mbar_expect_tx(&sm.in_full[slot], bytes);
+        tma_load3(ring_row<true, true>(sm, tbase, slot, 0, 0), md, g.r0, y, b, &sm.in_full[slot]);
+        if (table) {
+            const int ye = fwd ? s - 1 : y;
+#pragma unroll
+            for (int k = 0; k < 3; ++k)
+                tma_load3(ring_row<true, true>(sm, tbase, slot, 0, 1 + k), me, g.r0, ye, 3 * b + k,
+                          &sm.in_full[slot]);
+        }
+        issued = c + 1;
+    }
+    if (!ok) {
+        // let this block's copies land before the shared memory is reused
+        for (int c = max(0, issued - kNci); c < issued; ++c) {
+            const unsigned int gc = cb + c;
+            const long long t0 = gtimer();
+            while (!mbar_test(&sm.in_full[slot_of(gc, kNci)], full_parity(gc, kNci)) &&
+                   gtimer() - t0 <= a.timeout_ns) {
+            }
+        }
+    }
+    return ok;
+}
+
 // Producer warp: chunk c of the tile goes to ring slot (cb + c) % kNci once
 // the chain has released that slot.  The edge row between steps s-1 and s is
 // row s-1 of the table in a forward pass and row L-1-s in a backward one;
@@ -310,12 +390,33 @@ __device__ bool flusher_tile(const Chain2DArgs& a, const TileGeo& g, TileSmem& s
             if (lane == 0) mbar_arrive(&sm.out_empty[slot]);
             continue;
         }
+        // The chunk's values go to registers first and the output slot is
+        // handed back before the global stores: the chain waits for the slot,
+        // not for the stores (an arrival after them would wait for them).
+        // With codes, the slot is handed back after the codes are written.
+        constexpr int kTc = kRegion / 16;  // column groups per lane (transposed)
+        float4 v[fwd ? kCh : 1];
+        float tv[fwd ? 1 : kTc][4];
+        const int jj = lane & (kCh - 1);
         if (fwd) {
-            // rows of the output array: each lane writes its own four columns
-            float4 v[kCh];
 #pragma unroll
             for (int j = 0; j < kCh; ++j)
                 v[j] = *reinterpret_cast<const float4*>(&sm.out[slot][j][4 * lane]);
+        } else {
+#pragma unroll
+            for (int it = 0; it < kTc; ++it)
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int col = (lane >> 3) + 16 * it + 4 * u;
+                    tv[fwd ? 0 : it][u] = col < ncol ? sm.out[slot][jj][off + col] : 0.0f;
+                }
+        }
+        if (!codes) {
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&sm.out_empty[slot]);
+        }
+        if (fwd) {
+            // rows of the output array: each lane writes its own four columns
 #pragma unroll
             for (int j = 0; j < kCh; ++j) {
                 if (j >= nl) break;
@@ -331,23 +432,16 @@ __device__ bool flusher_tile(const Chain2DArgs& a, const TileGeo& g, TileSmem& s
             }
         } else {
             // transposed: consecutive lanes write consecutive lines of a column
-            // (four columns per warp-wide store, four stores in flight)
-            const int jj = lane & (kCh - 1);
+            // (four columns per warp-wide store)
             const int line = L - 1 - (s0 + jj);
-            for (int col0 = lane >> 3; col0 < ncol; col0 += 16) {
-                float v[4];
+#pragma unroll
+            for (int it = 0; it < kTc; ++it)
 #pragma unroll
                 for (int u = 0; u < 4; ++u) {
-                    const int col = col0 + 4 * u;
-                    v[u] = col < ncol ? sm.out[slot][jj][off + col] : 0.0f;
-                }
-#pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    const int col = col0 + 4 * u;
+                    const int col = (lane >> 3) + 16 * it + 4 * u;
                     if (col < ncol && jj < nl)
-                        g.out[(int64_t)(g.q0 + col) * g.out_ld + line] = v[u];
+                        g.out[(int64_t)(g.q0 + col) * g.out_ld + line] = tv[fwd ? 0 : it][u];
                 }
-            }
         }
         if (codes) {
             if (g.codes_rows) {
@@ -369,9 +463,9 @@ __device__ bool flusher_tile(const Chain2DArgs& a, const TileGeo& g, TileSmem& s
                 for (int col = lane >> 3; col < ncol; col += 4)
                     if (jj < nl) g.codes[(int64_t)(g.q0 + col) * L + line] = sm.outc[slot][jj][off + col];
             }
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&sm.out_empty[slot]);
         }
-        __syncwarp();
-        if (lane == 0) mbar_arrive(&sm.out_empty[slot]);
     }
     return true;
 }
@@ -390,9 +484,10 @@ struct LineIn {
 // from the padding or the neighbouring lane's range); in a backward step the
 // parent sits on the next line and the cost is E_k[x].
 template <bool fwd, bool table>
-__device__ __forceinline__ void load_line(const float (*p)[kRow], int lane, LineIn& r, float k0,
+__device__ __forceinline__ void load_line(const float* r0, const float* r1, const float* r2,
+                                          const float* r3, int lane, LineIn& r, float k0,
                                           float k1, float k2) {
-    const float4 o = *reinterpret_cast<const float4*>(&p[0][4 + 4 * lane]);
+    const float4 o = *reinterpret_cast<const float4*>(r0 + 4 * lane);
     r.dold[0] = o.x; r.dold[1] = o.y; r.dold[2] = o.z; r.dold[3] = o.w;
     if (!table) {
 #pragma unroll
@@ -403,12 +498,12 @@ __device__ __forceinline__ void load_line(const float (*p)[kRow], int lane, Line
         }
         return;
     }
-    const float4 e0 = *reinterpret_cast<const float4*>(&p[1][4 + 4 * lane]);
-    const float4 e1 = *reinterpret_cast<const float4*>(&p[2][4 + 4 * lane]);
-    const float4 e2 = *reinterpret_cast<const float4*>(&p[3][4 + 4 * lane]);
+    const float4 e0 = *reinterpret_cast<const float4*>(r1 + 4 * lane);
+    const float4 e1 = *reinterpret_cast<const float4*>(r2 + 4 * lane);
+    const float4 e2 = *reinterpret_cast<const float4*>(r3 + 4 * lane);
     if (fwd) {
-        const float e2m = p[3][3 + 4 * lane];
-        const float e0p = p[1][8 + 4 * lane];
+        const float e2m = r3[4 * lane - 1];
+        const float e0p = r1[4 * lane + 4];
         r.c0[0] = e2m;  r.c0[1] = e2.x; r.c0[2] = e2.y; r.c0[3] = e2.z;
         r.c2[0] = e0.y; r.c2[1] = e0.z; r.c2[2] = e0.w; r.c2[3] = e0p;
     } else {
@@ -532,10 +627,18 @@ __device__ __forceinline__ bool checkpoint(const Chain2DArgs& a, const TileGeo& 
 // first line of the sweep, which has no parents) runs with +inf parents and
 // so keeps the old values.  AHEAD lines of input are held in registers ahead
 // of the step that uses them.
-template <bool fwd, bool table, bool codes, int AHEAD, bool CK>
+template <bool fwd, bool table, bool codes, int AHEAD, bool CK, bool TMA>
 __device__ bool chain_tile(const Chain2DArgs& a, const TileGeo& g, int t_app, int b, int tile,
                            TileSmem& sm, unsigned int cb, float k0, float k1, float k2) {
     constexpr int NB = AHEAD == 1 ? 2 : 4;  // register buffers (divides kCh)
+    const float* tbase = TMA ? tma_ring(sm) : nullptr;
+    auto load = [&](int slot, int j, LineIn& r) {
+        load_line<fwd, table>(ring_row<TMA, fwd>(sm, tbase, slot, j, 0),
+                              ring_row<TMA, fwd>(sm, tbase, slot, j, 1),
+                              ring_row<TMA, fwd>(sm, tbase, slot, j, 2),
+                              ring_row<TMA, fwd>(sm, tbase, slot, j, 3), threadIdx.x & 31, r, k0,
+                              k1, k2);
+    };
     const int lane = threadIdx.x & 31;
     const int c0 = g.r0 + 4 * lane;
     bool valid[4];
@@ -558,8 +661,7 @@ __device__ bool chain_tile(const Chain2DArgs& a, const TileGeo& g, int t_app, in
     RingPos o0(cb, kNo), o1 = o0.next(kNo);
     if (!__all_sync(0xffffffffu, mbar_wait(&sm.in_full[i0.slot], i0.par, a))) return false;
 #pragma unroll
-    for (int j = 0; j < AHEAD; ++j)
-        load_line<fwd, table>(sm.in[i0.slot][j], lane, buf[j], k0, k1, k2);
+    for (int j = 0; j < AHEAD; ++j) load(i0.slot, j, buf[j]);
     int next_refresh = g.multi ? g.K : 0x7fffffff;
     int blk = 0;
     // Hand-overs are tested one chunk in advance (non-blocking) so the test's
@@ -604,15 +706,12 @@ __device__ bool chain_tile(const Chain2DArgs& a, const TileGeo& g, int t_app, in
             if (lane == 0) mbar_arrive(&sm.done[slot]);
             continue;
         }
-        const float(*cur)[4][kRow] = sm.in[slot];
-        const float(*nxt)[4][kRow] = sm.in[nslot];
 #pragma unroll
         for (int j = 0; j < kCh; ++j) {
             const int nj = j + AHEAD;
             float left, right;
             chain_shuffle(dp, lane, left, right);
-            load_line<fwd, table>(nj < kCh ? cur[nj] : nxt[nj - kCh], lane, buf[nj % NB], k0, k1,
-                                  k2);
+            load(nj < kCh ? slot : nslot, nj < kCh ? nj : nj - kCh, buf[nj % NB]);
             chain_step<!table, codes>(dp, left, right, buf[j % NB], valid,
                                       &sm.out[oslot][j][4 * lane], &sm.outc[oslot][j][4 * lane]);
         }
@@ -745,7 +844,7 @@ __global__ void __launch_bounds__(256) chain2d_init_batched_kernel(const Chain2D
 
 // Not inlined: the pass driver calls it from two places, and each variant's
 // chain loop keeps its own register allocation.
-template <bool fwd, bool table, bool codes, bool CK = false>
+template <bool fwd, bool table, bool codes, bool CK, bool TMA>
 __device__ __noinline__ bool run_tile(const Chain2DArgs& a, int t_app, int pass, int b, int tile,
                          TileSmem& sm, unsigned int cb, int seg, bool rerun, int nseg) {
     const TileGeo g = tile_geo(a, t_app, pass, b, tile, seg, rerun, nseg);
@@ -755,30 +854,32 @@ __device__ __noinline__ bool run_tile(const Chain2DArgs& a, int t_app, int pass,
         const float k0 = vert ? a.cv[0] : a.chh[0];
         const float k1 = vert ? a.cv[1] : a.chh[1];
         const float k2 = vert ? a.cv[2] : a.chh[2];
-        return chain_tile<fwd, table, codes, table ? 2 : 1, CK>(a, g, t_app, b, tile, sm, cb, k0, k1,
-                                                            k2);
+        return chain_tile<fwd, table, codes, table ? 2 : 1, CK, TMA>(a, g, t_app, b, tile, sm, cb,
+                                                                 k0, k1, k2);
     }
-    if (warp == 1) return producer_tile<fwd, table>(a, g, sm, cb);
+    if (warp == 1)
+        return TMA ? producer_tma<fwd, table>(a, g, sm, cb, b, pass < 2)
+                   : producer_tile<fwd, table>(a, g, sm, cb);
     return flusher_tile<fwd, codes>(a, g, sm, cb);
 }
 
-template <bool codes>
+template <bool codes, bool TMA>
 __device__ __forceinline__ bool run_pass_tile(const Chain2DArgs& a, bool fwd, int t_app, int pass,
                                               int b, int tile, TileSmem& sm, unsigned int cb,
                                               int seg = 0, bool rerun = false, int nseg = 1) {
     // re-runs of in-place passes carry the early-stop checkpoints
     const bool ck = rerun && seg > 0 && !codes;
     if (fwd && a.table && ck)
-        return run_tile<true, true, false, true>(a, t_app, pass, b, tile, sm, cb, seg, rerun, nseg);
+        return run_tile<true, true, false, true, TMA>(a, t_app, pass, b, tile, sm, cb, seg, rerun, nseg);
     if (fwd && ck)
-        return run_tile<true, false, false, true>(a, t_app, pass, b, tile, sm, cb, seg, rerun, nseg);
+        return run_tile<true, false, false, true, TMA>(a, t_app, pass, b, tile, sm, cb, seg, rerun, nseg);
     if (fwd && a.table)
-        return run_tile<true, true, codes>(a, t_app, pass, b, tile, sm, cb, seg, rerun, nseg);
+        return run_tile<true, true, codes, false, TMA>(a, t_app, pass, b, tile, sm, cb, seg, rerun, nseg);
     if (fwd)
-        return run_tile<true, false, codes>(a, t_app, pass, b, tile, sm, cb, seg, rerun, nseg);
+        return run_tile<true, false, codes, false, TMA>(a, t_app, pass, b, tile, sm, cb, seg, rerun, nseg);
     if (a.table)
-        return run_tile<false, true, codes>(a, t_app, pass, b, tile, sm, cb, seg, rerun, nseg);
-    return run_tile<false, false, codes>(a, t_app, pass, b, tile, sm, cb, seg, rerun, nseg);
+        return run_tile<false, true, codes, false, TMA>(a, t_app, pass, b, tile, sm, cb, seg, rerun, nseg);
+    return run_tile<false, false, codes, false, TMA>(a, t_app, pass, b, tile, sm, cb, seg, rerun, nseg);
 }
 
 // Speculative segments of one pass application (all images in one wave: the
@@ -796,7 +897,7 @@ __device__ __forceinline__ bool run_pass_tile(const Chain2DArgs& a, bool fwd, in
 // first run's values as old values and stops as soon as a whole line equals
 // them (checkpoints every ring refresh).  Every block takes the same decisions
 // from the same flags, so all blocks meet the same grid barriers.
-template <bool codes>
+template <bool codes, bool TMA>
 __device__ bool run_pass_segments(const Chain2DArgs& a, int t_app, int pass, int S, int ntiles,
                                   TileSmem& sm, unsigned int& cb, unsigned int& epoch,
                                   uint8_t* rr) {
@@ -824,7 +925,7 @@ __device__ bool run_pass_segments(const Chain2DArgs& a, int t_app, int pass, int
     // phase A.2: all segments at once
     bool ok = true;
     if (active) {
-        ok = run_pass_tile<codes>(a, fwd, t_app, pass, b, tile, sm, cb, seg, false, S);
+        ok = run_pass_tile<codes, TMA>(a, fwd, t_app, pass, b, tile, sm, cb, seg, false, S);
         const TileGeo g = tile_geo(a, t_app, pass, b, tile, seg, false, S);
         cb += (unsigned int)g.nch;
     }
@@ -852,7 +953,7 @@ __device__ bool run_pass_segments(const Chain2DArgs& a, int t_app, int pass, int
             *(a.segflag + (int64_t)a.B * kMaxSeg * 2 + pass) = (unsigned int)(t_app + 1);
         const int bb = u / ntiles;
         if (u < a.B * ntiles && rr[bb]) {
-            ok = run_pass_tile<codes>(a, fwd, t_app, pass, bb, tile, sm, cb, j, true, S);
+            ok = run_pass_tile<codes, TMA>(a, fwd, t_app, pass, bb, tile, sm, cb, j, true, S);
             const TileGeo g = tile_geo(a, t_app, pass, bb, tile, j, true, S);
             cb += (unsigned int)g.nch;
         }
@@ -865,8 +966,9 @@ __device__ bool run_pass_segments(const Chain2DArgs& a, int t_app, int pass, int
 
 // One persistent launch for all passes; `codes` selects the variant that also
 // records the parent codes.
-template <bool codes>
-__global__ void __launch_bounds__(kBlockThreads, 1) chain2d_kernel(const Chain2DArgs a) {
+template <bool codes, bool TMA>
+__global__ void __launch_bounds__(kBlockThreads, 1)
+    chain2d_kernel(const __grid_constant__ Chain2DArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     TileSmem& sm = *reinterpret_cast<TileSmem*>(smem_raw);
     const int64_t N = (int64_t)a.H * a.W;
@@ -882,12 +984,17 @@ __global__ void __launch_bounds__(kBlockThreads, 1) chain2d_kernel(const Chain2D
         (&sm.in[0][0][0][0])[i] = kInf;
     if (threadIdx.x == 0) {
         for (int i = 0; i < kNci; ++i) {
-            mbar_init(&sm.in_full[i], 32);  // one asynchronous arrival per producer lane
+            // one transaction-counted arrival (tensor copies) or one
+            // asynchronous arrival per producer lane
+            mbar_init(&sm.in_full[i], TMA ? 1 : 32);
             mbar_init(&sm.done[i], 1);
         }
         for (int i = 0; i < kNo; ++i) mbar_init(&sm.out_empty[i], 1);
         sm.stop_chunk = 0x7fffffff;
+        if (TMA) asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
+    // the ring's initial +inf (ordinary stores) before tensor copies write it
+    if (TMA) asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     __syncthreads();
     unsigned long long* timeline = (unsigned long long*)((char*)a.status + 128);
     if (blockIdx.x == 0 && threadIdx.x == 0)
@@ -908,7 +1015,7 @@ __global__ void __launch_bounds__(kBlockThreads, 1) chain2d_kernel(const Chain2D
                                ld_relaxed_u32(a.segflag + (int64_t)a.B * kMaxSeg * 2 + pass) !=
                                    (unsigned int)(t_app - 4 + 1);
         if (speculate && a.B <= kMaxSegImages && a.B * S * ntiles <= (int)gridDim.x) {
-            alive = run_pass_segments<codes>(a, t_app, pass, S, ntiles, sm, cb, epoch, rerun);
+            alive = run_pass_segments<codes, TMA>(a, t_app, pass, S, ntiles, sm, cb, epoch, rerun);
             if (blockIdx.x == 0 && threadIdx.x == 0 && t_app + 2 < 16)
                 timeline[t_app + 2] = (unsigned long long)gtimer();
             continue;
@@ -922,7 +1029,7 @@ __global__ void __launch_bounds__(kBlockThreads, 1) chain2d_kernel(const Chain2D
                 if (b < a.B) {
                     const int tile = blockIdx.x % ntiles;
                     const bool fwd = (pass == 0 || pass == 2);
-                    ok = run_pass_tile<codes>(a, fwd, t_app, pass, b, tile, sm, cb);
+                    ok = run_pass_tile<codes, TMA>(a, fwd, t_app, pass, b, tile, sm, cb);
                     cb += (unsigned int)((L + kCh - 1) / kCh);
                 }
             }
@@ -972,7 +1079,7 @@ __global__ void __launch_bounds__(kBlockThreads, 1) chain2d_batched_kernel(const
             const int item = bt.wave_items[(int64_t)wv * gridDim.x + blockIdx.x];
             if (item < 0) continue;
             const Chain2DArgs& a = bt.desc[item >> 16];
-            ok = run_pass_tile<false>(a, fwd, r, pass, 0, item & 0xffff, sm, cb);
+            ok = run_pass_tile<false, false>(a, fwd, r, pass, 0, item & 0xffff, sm, cb);
             const int L = pass < 2 ? a.H : a.W;
             cb += (unsigned int)((L + kCh - 1) / kCh);
         }
@@ -1131,8 +1238,22 @@ int run_chain2d(const float* image, const float* mask, float* dist, uint8_t* cod
     if (nimg > 0) a.nimg = (int)nimg;
     const int max_tiles = a.max_tiles;
 
+    // tensor copies of the producer: boxes of 128 region columns x kCh lines
+    // of the distance rows (Dw, Dt) and the cost tables (Ev, Eh: 3 rows per
+    // image); region starts are multiples of 4 columns (K and T are)
+    {
+        const uint32_t box[3] = {(uint32_t)kRegion, (uint32_t)kCh, 1};
+        const uint64_t Bn = (uint64_t)B, Wp = (uint64_t)a.Wp, Hp = (uint64_t)a.Hp;
+        const uint64_t dw[3] = {Wp, (uint64_t)H, Bn}, dt[3] = {Hp, (uint64_t)W, Bn};
+        const uint64_t ev[3] = {Wp, (uint64_t)H, 3 * Bn}, eh[3] = {Hp, (uint64_t)W, 3 * Bn};
+        a.tma = encode_map_f32(&a.tmap[0], a.Dw, 3, dw, box, true) &&
+                encode_map_f32(&a.tmap[1], a.Dt, 3, dt, box, true) &&
+                (!a.table || (encode_map_f32(&a.tmap[2], a.Ev, 3, ev, box, true) &&
+                              encode_map_f32(&a.tmap[3], a.Eh, 3, eh, box, true)));
+    }
     const size_t smem = sizeof(TileSmem);
-    auto kernel = codes ? chain2d_kernel<true> : chain2d_kernel<false>;
+    auto kernel = codes ? (a.tma ? chain2d_kernel<true, true> : chain2d_kernel<true, false>)
+                        : (a.tma ? chain2d_kernel<false, true> : chain2d_kernel<false, false>);
     if (cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)smem) != cudaSuccess)
         return FGX_ERR_CUDA;

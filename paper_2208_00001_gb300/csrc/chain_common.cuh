@@ -43,6 +43,24 @@ __device__ __forceinline__ void mbar_arrive(unsigned long long* b) {
     asm volatile("mbarrier.arrive.release.cta.shared::cta.b64 _, [%0];" ::"r"(saddr(b))
                  : "memory");
 }
+// One arrival on *b that also expects `bytes` of tensor copies to complete
+// the phase.
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long* b, unsigned int bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.release.cta.shared::cta.b64 _, [%0], %1;" ::"r"(
+                     saddr(b)),
+                 "r"(bytes)
+                 : "memory");
+}
+// One box of a 3D tensor map (x innermost) into shared memory at `dst`,
+// completed on *mbar by transaction count.
+__device__ __forceinline__ void tma_load3(const void* dst, const void* map, int x, int y, int z,
+                                          unsigned long long* mbar) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(saddr(dst)),
+        "l"(map), "r"(x), "r"(y), "r"(z), "r"(saddr(mbar))
+        : "memory");
+}
 // One arrival on *b once every cp.async this thread issued so far has landed.
 __device__ __forceinline__ void cp_async_arrive_noinc(unsigned long long* b) {
     asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(saddr(b))

@@ -224,6 +224,15 @@ void launch_wait_probe(const unsigned long long* tag, int* status, long long tim
 
 // Signed transform GDT(M) - GDT(1 - M) (signed.cu): workspace bytes for a
 // forward workspace of `forward_bytes` and n elements, and the run.
+// Encodes a float32 tiled tensor map (a CUtensorMap of 128 bytes at `map`)
+// of rank 1..5: dims innermost first, the tensor dense (pitch of dimension i
+// = the product of the lower dims, in floats), box extents per dimension;
+// NaN fill outside the tensor when nan_fill, else zero.  False when the
+// driver's encoder is unavailable or the layout cannot be encoded (base not
+// 16-byte aligned, a pitch not a multiple of 16 bytes).
+bool encode_map_f32(void* map, const void* base, int rank, const uint64_t* dims,
+                    const uint32_t* box, bool nan_fill);
+
 // Forward of B transforms of nimg images (B a multiple of nimg; instance b
 // reads image b % nimg) with the library's fast kernels; the workspace of
 // fgx_geodesic_workspace_size(ndim, B, C, D, H, W).

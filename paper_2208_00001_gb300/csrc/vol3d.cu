@@ -835,42 +835,13 @@ Vol3DKernel pick_kernel(int mode, int CI, bool codes, bool tma) {
 }
 int block_threads(bool tma) { return tma ? kCW * 32 : (kCW + kPW) * 32; }
 
-// cuTensorMapEncodeTiled, looked up once through the runtime (no link-time
-// dependency on the driver library).
-using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
-                                   const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
-                                   const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
-                                   CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
-EncodeTiledFn encoder() {
-    static EncodeTiledFn fn = [] {
-        void* p = nullptr;
-        cudaDriverEntryPointQueryResult q;
-        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000,
-                                             cudaEnableDefault, &q) != cudaSuccess ||
-            q != cudaDriverEntryPointSuccess) {
-            cudaGetLastError();
-            return (EncodeTiledFn) nullptr;
-        }
-        return reinterpret_cast<EncodeTiledFn>(p);
-    }();
-    return fn;
-}
-
 // A float32 tensor map of dims (d0 innermost .. d3) with box (b0, b1, b2, 1);
 // NaN fill outside the tensor for distances, zero for intensities.
 bool make_map(CUtensorMap* m, const void* base, uint64_t d0, uint64_t d1, uint64_t d2,
               uint64_t d3, uint32_t b0, uint32_t b1, uint32_t b2, bool nan_fill) {
-    EncodeTiledFn enc = encoder();
-    if (!enc || ((uintptr_t)base & 15u) || ((d0 * 4) & 15u)) return false;
-    const cuuint64_t dims[4] = {d0, d1, d2, d3};
-    const cuuint64_t strides[3] = {d0 * 4, d0 * d1 * 4, d0 * d1 * d2 * 4};
-    const cuuint32_t box[4] = {b0, b1, b2, 1};
-    const cuuint32_t estr[4] = {1, 1, 1, 1};
-    return enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, const_cast<void*>(base), dims, strides, box,
-               estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-               CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
-               nan_fill ? CU_TENSOR_MAP_FLOAT_OOB_FILL_NAN_REQUEST_ZERO_FMA
-                        : CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+    const uint64_t dims[4] = {d0, d1, d2, d3};
+    const uint32_t box[4] = {b0, b1, b2, 1};
+    return encode_map_f32(m, base, 4, dims, box, nan_fill);
 }
 
 // Tensor maps of a call (false: stage with cp.async).  The rows of every
@@ -974,6 +945,49 @@ bool plan_vol3d(const SweepArgs& f, const fgx_options* opt, int sms, Vol3DPlan* 
 }
 
 }  // namespace
+
+// cuTensorMapEncodeTiled, looked up once through the runtime (no link-time
+// dependency on the driver library).
+using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                                   const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                                   const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                   CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+static EncodeTiledFn tensor_map_encoder() {
+    static EncodeTiledFn fn = [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000,
+                                             cudaEnableDefault, &q) != cudaSuccess ||
+            q != cudaDriverEntryPointSuccess) {
+            cudaGetLastError();
+            return (EncodeTiledFn) nullptr;
+        }
+        return reinterpret_cast<EncodeTiledFn>(p);
+    }();
+    return fn;
+}
+
+bool encode_map_f32(void* map, const void* base, int rank, const uint64_t* dims,
+                    const uint32_t* box, bool nan_fill) {
+    EncodeTiledFn enc = tensor_map_encoder();
+    if (!enc || rank < 1 || rank > 5 || ((uintptr_t)base & 15u) || ((dims[0] * 4) & 15u))
+        return false;
+    cuuint64_t d[5], str[4];
+    cuuint32_t b[5], e[5];
+    uint64_t pitch = 4;
+    for (int i = 0; i < rank; ++i) {
+        d[i] = dims[i];
+        b[i] = box[i];
+        e[i] = 1;
+        if (i > 0) str[i - 1] = pitch;
+        pitch *= dims[i];
+    }
+    return enc(static_cast<CUtensorMap*>(map), CU_TENSOR_MAP_DATA_TYPE_FLOAT32, (cuuint32_t)rank,
+               const_cast<void*>(base), d, str, b, e, CU_TENSOR_MAP_INTERLEAVE_NONE,
+               CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+               nan_fill ? CU_TENSOR_MAP_FLOAT_OOB_FILL_NAN_REQUEST_ZERO_FMA
+                        : CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
 
 bool vol3d_supports(const SweepArgs& f, const fgx_options* opt, int sms) {
     Vol3DPlan vp;
