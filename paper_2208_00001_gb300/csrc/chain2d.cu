@@ -112,8 +112,9 @@ __device__ __forceinline__ float edge_cost(const float* ia, const float* ib, int
 // finished chunks to global memory, transposed where the pass requires.
 // Waits, ring exchanges and hand-overs happen only between chunks, so the
 // per-line code has no branches.
-constexpr int kCh = 8;              // lines per chunk
-constexpr int kNci = 5;             // chunks in the input ring
+constexpr int kCh = 16;             // lines per chunk (staging and hand-over unit)
+constexpr int kSub = 8;             // ring refreshes fall on multiples of kSub lines
+constexpr int kNci = 4;             // chunks in the input ring
 constexpr int kNo = 3;              // chunks in the output ring
 constexpr int kRow = kRegion + 8;   // floats per input row: 4 pad | 128 | 4 pad
 constexpr int kOutLd = kRegion + 4; // floats per output row (conflict-free transposes)
@@ -235,7 +236,7 @@ __device__ __forceinline__ TileGeo tile_geo(const Chain2DArgs& a, int t_app, int
     const bool fwd = pass == 0 || pass == 2;
     if (seg > 0 && rerun && fwd) {
         g.ck = a.ckpt + ((int64_t)b * kMaxSeg + seg) * kMaxCk;
-        const int base = g.multi ? g.K / kCh : 5;
+        const int base = g.multi ? max(1, g.K / kCh) : 3;
         const int npts = (g.nch + base - 1) / base;
         g.ck_every = base * ((npts + kMaxCk - 2) / (kMaxCk - 1));
     }
@@ -390,33 +391,18 @@ __device__ bool flusher_tile(const Chain2DArgs& a, const TileGeo& g, TileSmem& s
             if (lane == 0) mbar_arrive(&sm.out_empty[slot]);
             continue;
         }
-        // The chunk's values go to registers first and the output slot is
-        // handed back before the global stores: the chain waits for the slot,
-        // not for the stores (an arrival after them would wait for them).
-        // With codes, the slot is handed back after the codes are written.
-        constexpr int kTc = kRegion / 16;  // column groups per lane (transposed)
-        float4 v[fwd ? kCh : 1];
-        float tv[fwd ? 1 : kTc][4];
-        const int jj = lane & (kCh - 1);
         if (fwd) {
+            // rows of the output array: each lane writes its own four
+            // columns; the values go to registers first and the output slot
+            // is handed back before the global stores (without codes)
+            float4 v[kCh];
 #pragma unroll
             for (int j = 0; j < kCh; ++j)
                 v[j] = *reinterpret_cast<const float4*>(&sm.out[slot][j][4 * lane]);
-        } else {
-#pragma unroll
-            for (int it = 0; it < kTc; ++it)
-#pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    const int col = (lane >> 3) + 16 * it + 4 * u;
-                    tv[fwd ? 0 : it][u] = col < ncol ? sm.out[slot][jj][off + col] : 0.0f;
-                }
-        }
-        if (!codes) {
-            __syncwarp();
-            if (lane == 0) mbar_arrive(&sm.out_empty[slot]);
-        }
-        if (fwd) {
-            // rows of the output array: each lane writes its own four columns
+            if (!codes) {
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&sm.out_empty[slot]);
+            }
 #pragma unroll
             for (int j = 0; j < kCh; ++j) {
                 if (j >= nl) break;
@@ -431,17 +417,16 @@ __device__ bool flusher_tile(const Chain2DArgs& a, const TileGeo& g, TileSmem& s
                 }
             }
         } else {
-            // transposed: consecutive lanes write consecutive lines of a column
-            // (four columns per warp-wide store)
+            // transposed: consecutive lanes write consecutive lines of a
+            // column (32 / kCh columns per warp-wide store)
+            const int jj = lane & (kCh - 1);
             const int line = L - 1 - (s0 + jj);
-#pragma unroll
-            for (int it = 0; it < kTc; ++it)
-#pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    const int col = (lane >> 3) + 16 * it + 4 * u;
-                    if (col < ncol && jj < nl)
-                        g.out[(int64_t)(g.q0 + col) * g.out_ld + line] = tv[fwd ? 0 : it][u];
-                }
+            for (int col = lane / kCh; col < ncol; col += 32 / kCh)
+                if (jj < nl) g.out[(int64_t)(g.q0 + col) * g.out_ld + line] = sm.out[slot][jj][off + col];
+            if (!codes) {
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&sm.out_empty[slot]);
+            }
         }
         if (codes) {
             if (g.codes_rows) {
@@ -460,7 +445,7 @@ __device__ bool flusher_tile(const Chain2DArgs& a, const TileGeo& g, TileSmem& s
                 // horizontal pass: the lines are columns of the image
                 const int jj = lane & (kCh - 1);
                 const int line = fwd ? s0 + jj : L - 1 - (s0 + jj);
-                for (int col = lane >> 3; col < ncol; col += 4)
+                for (int col = lane / kCh; col < ncol; col += 32 / kCh)
                     if (jj < nl) g.codes[(int64_t)(g.q0 + col) * L + line] = sm.outc[slot][jj][off + col];
             }
             __syncwarp();
@@ -687,12 +672,6 @@ __device__ bool chain_tile(const Chain2DArgs& a, const TileGeo& g, int t_app, in
         i2 = i2.next(kNci);
         o0 = o1;
         o1 = o1.next(kNo);
-        if (!skip && c * kCh == next_refresh) {
-            if (!exchange(a, g, b, tile, tag_base | (unsigned int)(blk + 1), blk & 1, dp, valid))
-                return false;
-            next_refresh += g.K;
-            ++blk;
-        }
         if (CK && !skip && c > 0 && c % g.ck_every == 0) {
             if (!checkpoint(a, g, c / g.ck_every, dp, buf[(kCh - 1) % NB].dold, c0, ck_prev,
                             skip))
@@ -708,6 +687,13 @@ __device__ bool chain_tile(const Chain2DArgs& a, const TileGeo& g, int t_app, in
         }
 #pragma unroll
         for (int j = 0; j < kCh; ++j) {
+            if (j % kSub == 0 && !skip && c * kCh + j == next_refresh) {
+                if (!exchange(a, g, b, tile, tag_base | (unsigned int)(blk + 1), blk & 1, dp,
+                              valid))
+                    return false;
+                next_refresh += g.K;
+                ++blk;
+            }
             const int nj = j + AHEAD;
             float left, right;
             chain_shuffle(dp, lane, left, right);
@@ -1094,13 +1080,13 @@ __global__ void __launch_bounds__(kBlockThreads, 1) chain2d_batched_kernel(const
 
 int chain2d_geometry(int64_t H, int64_t W, const fgx_options* opt, int* K, int* T, int* tv,
                      int* th) {
-    // K: lines between ring refreshes, a whole number of chunks; T >= K so a
-    // ring never reaches past the neighbouring tile
+    // K: lines between ring refreshes, a multiple of kSub lines; T >= K so
+    // a ring never reaches past the neighbouring tile
     int k = (opt && opt->tile_lines) ? opt->tile_lines : 40;
-    k = std::max(kCh, std::min(40, (k + kCh - 1) / kCh * kCh));
+    k = std::max(kSub, std::min(40, (k + kSub - 1) / kSub * kSub));
     int t = kRegion - 2 * k;
-    if (opt && opt->tile_width) t = std::min(t, std::max(kCh, opt->tile_width & ~3));
-    if (t < k) k = t / kCh * kCh;
+    if (opt && opt->tile_width) t = std::min(t, std::max(kSub, opt->tile_width & ~3));
+    if (t < k) k = t / kSub * kSub;
     *K = k;
     *T = t;
     // a line that fits one region is one tile, unless a tile width is forced
