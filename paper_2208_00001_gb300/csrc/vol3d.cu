@@ -7,8 +7,9 @@
 // (32 - 2K) x (32 - 2K) owned voxels; one thread block per tile computes a
 // region of kRP x kRQ = 32 x 32 voxels: the tile plus a ring of K voxels on
 // every side, K = 4 or 8 per pass (the planner takes 8 where the larger tile
-// count still fits the grid: half the ring refreshes for the same region).  Eight compute warps each hold four region rows: lane q owns column q
-// of the region and keeps the four distances of its rows in registers.  A
+// count still fits the grid: half the ring refreshes for the same region).
+// Sixteen compute warps each hold two region rows: lane q owns column q of
+// the region and keeps the two distances of its rows in registers.  A
 // plane step needs the 3 x 3 parents of every voxel: the own column's rows
 // come from registers plus the two boundary rows of the warps above and below
 // (shared memory, one named barrier of the compute warps per step), the
@@ -28,11 +29,13 @@
 // above and below the region, so every parent load of a lane is one base
 // register plus a constant offset.  Two ways to fill it:
 //  * tensor memory accelerator (when every plane row of the pass layout is
-//    16-byte aligned): one compute thread copies each plane tile as one box
-//    (cp.async.bulk.tensor) as soon as its chunk slot is free, completed on
-//    the slot's mbarrier by transaction count; outside the volume the copy
-//    fills distances with NaN (a NaN candidate never wins fminf, exactly like
-//    +inf) and intensities with 0;
+//    16-byte aligned): one producer warp copies the plane tiles of a chunk
+//    as boxes (cp.async.bulk.tensor, one box per lane) as soon as the chunk
+//    slot is free, completed on the slot's mbarrier by transaction count;
+//    outside the volume the copy fills distances with NaN (a NaN candidate
+//    never wins fminf, exactly like +inf) and intensities with 0.  Issuing
+//    the copies from a compute thread put them on the plane steps' critical
+//    path (about a quarter of the step time, measured);
 //  * otherwise four producer warps copy the tile with per-lane 4-byte
 //    cp.async (voxels outside the volume: distance +inf, intensity 0).
 //
@@ -61,9 +64,10 @@ namespace {
 
 using namespace dev;
 
-constexpr int kRows = 4;                  // region rows per compute thread
-constexpr int kCW = 8;                    // compute warps
+constexpr int kRows = 2;                  // region rows per compute thread
+constexpr int kCW = 16;                   // compute warps
 constexpr int kPW = 4;                    // producer warps (cp.async staging)
+constexpr int kTW = 1;                    // producer warps (tensor copies)
 constexpr int kRP = kRows * kCW;          // region rows
 constexpr int kRQ = 32;                   // region columns (one per lane)
 constexpr int kRing = 4;                  // narrow ring width = steps between refreshes
@@ -221,27 +225,59 @@ struct Stage3 {
     static constexpr int kPlaneF = (1 + CI) * kArr;
 };
 
-// TMA: chunk c of the tile (global chunk count gc) into its slot; one thread.
+// TMA: chunk c of the tile (global chunk count gc) into its slot, issued by
+// the lanes of one warp: lane l copies array l % (1 + CI) of plane l / (1 + CI)
+// of the chunk (one box each), all completed on the slot's mbarrier.
 template <int CI>
 __device__ void tma_chunk(const Vol3DArgs& a, const Tile3& t, Head3& h, float* stage,
                           unsigned int gc, int c) {
     constexpr int PF = Stage3<CI>::kPlaneF;
+    const int lane = threadIdx.x & 31;
     const int slot = (int)(gc % kNst);
     const int jn = min(kChunk, t.L - c * kChunk);
     const unsigned int mb = saddr3(&h.full[slot]);
-    mbar_expect_tx3(&h.full[slot], (unsigned int)(jn * (1 + CI) * kRP * kRQ * 4));
-    const int dir = t.g->dir;
-    for (int j = 0; j < jn; ++j) {
+    if (lane == 0) mbar_expect_tx3(&h.full[slot], (unsigned int)(jn * (1 + CI) * kRP * kRQ * 4));
+    __syncwarp();
+    if (lane < jn * (1 + CI)) {
+        const int j = lane / (1 + CI), arr = lane - j * (1 + CI);
         const int s = c * kChunk + j;
-        const int line = dir > 0 ? s : t.L - 1 - s;
-        const unsigned int dst = saddr3(stage + (slot * kChunk + j) * PF + kRQ);
+        const int line = t.g->dir > 0 ? s : t.L - 1 - s;
+        const unsigned int dst = saddr3(stage + (slot * kChunk + j) * PF + kRQ + arr * kArr);
         const int y = t.rows_z ? line : t.p0, z = t.rows_z ? t.p0 : line;
-        tma_load4(dst, &a.tmap[t.map_d], t.q0, y, z, (int)t.b, mb);
-#pragma unroll
-        for (int ch = 0; ch < CI; ++ch)
-            tma_load4(dst + (unsigned int)((1 + ch) * kArr * 4), &a.tmap[t.map_i], t.q0, y, z,
-                      (int)((t.b % a.nimg) * a.C) + ch, mb);
+        const int w4 = arr == 0 ? (int)t.b : (int)((t.b % a.nimg) * a.C) + arr - 1;
+        tma_load4(dst, &a.tmap[arr == 0 ? t.map_d : t.map_i], t.q0, y, z, w4, mb);
     }
+}
+
+// Producer warp (tensor copies): every chunk of the tile into the ring once
+// the compute warps have released its slot.  On a failure it stops issuing.
+// Either way it waits (bounded) until its last copies have landed.
+template <int CI>
+__device__ bool producer3_tma(const Vol3DArgs& a, const Tile3& t, Head3& h, float* stage,
+                              unsigned int cb) {
+    // shared memory written by ordinary stores (transposes) is handed to the
+    // tensor copies
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    int c = 0;
+    bool ok = true;
+    for (; c < t.nch; ++c) {
+        const unsigned int gc = cb + c;
+        const int slot = (int)(gc % kNst);
+        if (gc >= (unsigned)kNst &&
+            !__all_sync(0xffffffffu, mbar_wait3(&h.empty[slot], ((gc / kNst) & 1u) ^ 1u,
+                                                a.status, a.timeout_ns))) {
+            ok = false;
+            break;
+        }
+        tma_chunk<CI>(a, t, h, stage, gc, c);
+    }
+    // the last copies of the tile have landed before the warp moves on (after
+    // a failure the compute warps may no longer wait for them)
+    if ((threadIdx.x & 31) == 0)
+        for (int k = max(0, c - kNst); k < c; ++k)
+            mbar_drain3(&h.full[(cb + k) % kNst], ((cb + k) / kNst) & 1u, a.timeout_ns);
+    __syncwarp();
+    return ok;
 }
 
 // Producer warps (cp.async staging): planes of old distances and intensities
@@ -423,14 +459,6 @@ __device__ bool compute3(const Vol3DArgs& a, const Tile3& t, int t_app, Head3& h
     // this lane's element (region row rows0, column lane) of array 0 of ring plane 0
     const float* S = stage + (1 + rows0) * kRQ + lane;
     int cur = (int)(cb % kNst) * kChunk * PF;
-    int issued = 0;  // TMA: chunks of this tile issued so far (thread 0)
-    if (TMA && threadIdx.x == 0) {
-        // shared memory written by ordinary stores (previous transposes) is
-        // handed to the tensor copies
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        for (; issued < min(kNst, t.nch); ++issued)
-            tma_chunk<CI>(a, t, h, stage, cb + issued, issued);
-    }
     // After a failure (timeout, or one reported by another block) the warps
     // keep stepping through the named barriers with every wait skipped, so
     // that no compute warp is left waiting for one that gave up.
@@ -462,16 +490,8 @@ __device__ bool compute3(const Vol3DArgs& a, const Tile3& t, int t_app, Head3& h
         compute_sync();
         // plane s-2 is no longer read by any compute warp: its chunk slot is
         // free once it was the chunk's last plane
-        if (threadIdx.x == 0 && s >= 2 && ((s - 2) & (kChunk - 1)) == kChunk - 1) {
-            if (TMA) {
-                if (!failed && issued < t.nch) {
-                    tma_chunk<CI>(a, t, h, stage, cb + issued, issued);
-                    ++issued;
-                }
-            } else {
-                mbar_arrive3(&h.empty[(cb + (s - 2) / kChunk) % kNst]);
-            }
-        }
+        if (threadIdx.x == 0 && s >= 2 && ((s - 2) & (kChunk - 1)) == kChunk - 1)
+            mbar_arrive3(&h.empty[(cb + (s - 2) / kChunk) % kNst]);
         float col[kRows + 2], lft[kRows + 2], rgt[kRows + 2];
         col[0] = w > 0 ? h.rowbot[rb][w - 1][lane] : kInf3;
 #pragma unroll
@@ -536,16 +556,10 @@ __device__ bool compute3(const Vol3DArgs& a, const Tile3& t, int t_app, Head3& h
     }
     compute_sync();
     if (threadIdx.x == 0) {
-        if (TMA) {
-            // after a failure, let this tile's copies still in flight land
-            for (int c = max(0, issued - kNst); c < issued; ++c)
-                mbar_drain3(&h.full[(cb + c) % kNst], ((cb + c) / kNst) & 1u, a.timeout_ns);
-        } else {
-            // free the chunks still held (those whose last plane is one of the last two)
-            for (int c = max(0, t.nch - 2); c < t.nch; ++c) {
-                const int last = min(c * kChunk + kChunk - 1, t.L - 1);
-                if (last >= t.L - 2) mbar_arrive3(&h.empty[(cb + c) % kNst]);
-            }
+        // free the chunks still held (those whose last plane is one of the last two)
+        for (int c = max(0, t.nch - 2); c < t.nch; ++c) {
+            const int last = min(c * kChunk + kChunk - 1, t.L - 1);
+            if (last >= t.L - 2) mbar_arrive3(&h.empty[(cb + c) % kNst]);
         }
     }
     return !failed;
@@ -621,7 +635,8 @@ __global__ void __launch_bounds__(256) transpose_image3d_kernel(const float* ima
 template <int MODE, int CI, bool CODES, bool TMA>
 __device__ __forceinline__ bool run_tile3(const Vol3DArgs& a, const Tile3& t, int t_app, Head3& h,
                                           float* stage, unsigned int cb, bool checked) {
-    if (!TMA && (int)(threadIdx.x >> 5) >= kCW) return producer3<CI>(a, t, h, stage, cb);
+    if ((int)(threadIdx.x >> 5) >= kCW)
+        return TMA ? producer3_tma<CI>(a, t, h, stage, cb) : producer3<CI>(a, t, h, stage, cb);
     if (MODE == kModeAbs && checked)
         return compute3<MODE, CI, true, CODES, TMA>(a, t, t_app, h, stage, cb);
     return compute3<MODE, CI, false, CODES, TMA>(a, t, t_app, h, stage, cb);
@@ -648,7 +663,7 @@ __device__ __forceinline__ void init_barriers3(Head3& h, bool tma) {
 }
 
 template <int MODE, int CI, bool CODES, bool TMA>
-__global__ void __launch_bounds__(TMA ? kCW * 32 : (kCW + kPW) * 32, 1)
+__global__ void __launch_bounds__(TMA ? (kCW + kTW) * 32 : (kCW + kPW) * 32, 1)
     vol3d_kernel(const __grid_constant__ Vol3DArgs a) {
     extern __shared__ __align__(128) unsigned char smem3[];
     Head3& h = *reinterpret_cast<Head3*>(smem3);
@@ -833,7 +848,7 @@ Vol3DKernel pick_kernel(int mode, int CI, bool codes, bool tma) {
         return codes ? pick_kernel_t<true, true>(mode, CI) : pick_kernel_t<false, true>(mode, CI);
     return codes ? pick_kernel_t<true, false>(mode, CI) : pick_kernel_t<false, false>(mode, CI);
 }
-int block_threads(bool tma) { return tma ? kCW * 32 : (kCW + kPW) * 32; }
+int block_threads(bool tma) { return tma ? (kCW + kTW) * 32 : (kCW + kPW) * 32; }
 
 // A float32 tensor map of dims (d0 innermost .. d3) with box (b0, b1, b2, 1);
 // NaN fill outside the tensor for distances, zero for intensities.
