@@ -120,11 +120,11 @@ int fgx_geodesic3d(const float* image, const float* mask, float* dist, int64_t B
  * of a caller workspace; every GPU that loads the library holds it until the
  * process exits.  Shapes whose scratch would exceed 64 KiB (about 8,000
  * instance-tiles per pass) are rejected with FGX_ERR_WORKSPACE before any
- * launch.  The first call on each device looks up the array's device address
- * (cudaGetSymbolAddress, with that device current), so make that first call
- * before any stream capture.  The address is kept for the life of the
- * process: after a cudaDeviceReset of that device it is stale, so do not
- * call this entry point again in that process.  All calls on one device
+ * launch.  Each call made outside stream capture looks up the array's
+ * device address (cudaGetSymbolAddress, with that device current); a call on
+ * a capturing stream uses the address found by the last such call on that
+ * device, so make the first call on each device before any stream capture.
+ * All calls on one device
  * share that device's copy of the array, which keeps the last call's
  * contents; each call clears the part it uses, so calls that overlap on the
  * same GPU (for example on two streams) race and must be serialised by the

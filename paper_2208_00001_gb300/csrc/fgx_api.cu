@@ -941,17 +941,25 @@ namespace {
 constexpr size_t kNoAllocScratchBytes = 64 * 1024;
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
 
-// Device address of g_noalloc_scratch, looked up once per device with that
-// device current.  In host code the array's name is only a host-side stand-in,
-// so the kernel must be given this address, never the name.
-int noalloc_scratch_address(void** out) {
+// Device address of g_noalloc_scratch on the current device.  In host code
+// the array's name is only a host-side stand-in, so the kernel must be given
+// this address, never the name.  The address is looked up again on every
+// call made outside stream capture (a device reset reloads the module and
+// may move the array); while `stream` is capturing, the last address found
+// on this device is used.
+int noalloc_scratch_address(cudaStream_t stream, void** out) {
     static std::mutex mu;
     static void* addr[64];
     static bool done[64];
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return FGX_ERR_DEVICE;
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(stream, &cap) != cudaSuccess) {
+        cudaGetLastError();
+        return FGX_ERR_CUDA;
+    }
     std::lock_guard<std::mutex> lock(mu);
-    if (!done[dev]) {
+    if (!done[dev] || cap == cudaStreamCaptureStatusNone) {
         void* p = nullptr;
         if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess) {
             cudaGetLastError();
@@ -979,7 +987,7 @@ extern "C" int fgx_geodesic_noalloc(int ndim, const float* image, const float* m
     if (st != FGX_OK) return st;
     if (pl.ws_bytes > kNoAllocScratchBytes) return FGX_ERR_WORKSPACE;  // beyond the static limit
     void* scratch = nullptr;
-    st = noalloc_scratch_address(&scratch);
+    st = noalloc_scratch_address((cudaStream_t)stream, &scratch);
     if (st != FGX_OK) return st;
     return run_forward(ndim, image, mask, dist, B, C, D, H, W, spacing, v, lambda, iterations,
                        nullptr, 0, scratch, kNoAllocScratchBytes, opt, stream);
