@@ -45,11 +45,11 @@ struct Schedule {
     std::vector<int> v_index;
     std::vector<std::vector<int>> v_tiles;
     std::vector<SweepArgs> v_args;
-    std::vector<size_t> v_xoff;
+    std::vector<size_t> v_xoff, v_woff;
     std::vector<int> v_round_waves, v_wave_items;
     int v_grid = 0, v_rounds = 0, v_ci = 0, v_max_tiles = 0;
     int sms = 0;
-    size_t v_smem = 0, v_xbuf_bytes = 0;
+    size_t v_smem = 0, v_xbuf_bytes = 0, v_work_bytes = 0, v_work_off = 0;
     size_t v_flag_off = 0, v_xbuf_off = 0, v_desc_off = 0, v_waves_off = 0, v_items_off = 0;
 };
 
@@ -172,10 +172,10 @@ int build_schedule(const fgx_instance* items, int n, const fgx_options* opt, boo
                            &sms);
         if (st != FGX_OK) return st;
         if (it.ndim == 3) {
-            size_t xb = 0;
+            size_t xb = 0, wb = 0;
             int ci = 0, mt = 0, tiles[kMaxPasses];
-            if (vol3d_instance_desc(nullptr, it, a, opt, sms, nullptr, nullptr, nullptr, &xb, &ci,
-                                    &mt, tiles)) {
+            if (vol3d_instance_desc(nullptr, it, a, opt, sms, nullptr, nullptr, nullptr, nullptr,
+                                    &xb, &wb, &ci, &mt, tiles)) {
                 if (check_ptrs) {
                     if (!it.image || !it.mask || !it.dist) return FGX_ERR_ARG;
                     if (!device_pointer(it.image) || !device_pointer(it.mask) ||
@@ -192,6 +192,8 @@ int build_schedule(const fgx_instance* items, int n, const fgx_options* opt, boo
                 S->v_args.push_back(a);
                 S->v_xoff.push_back(S->v_xbuf_bytes);
                 S->v_xbuf_bytes += al256(xb);
+                S->v_woff.push_back(S->v_work_bytes);
+                S->v_work_bytes += al256(wb);
                 S->v_ci = std::max(S->v_ci, ci);
                 S->v_max_tiles = std::max(S->v_max_tiles, mt);
                 S->v_rounds = std::max(S->v_rounds, it.iterations * kMaxPasses);
@@ -307,7 +309,7 @@ int build_schedule(const fgx_instance* items, int n, const fgx_options* opt, boo
     S->flags_bytes = al256((size_t)std::max(flags_total, 1) * 8);
     // layout: header | engine tags | chain exchange words | plane-tile range
     // flags and exchange words (the cleared prefix) | engine tables | chain
-    // tables | plane-tile tables | chain buffers
+    // tables | plane-tile tables | chain buffers | plane-tile working copies
     S->c_xbuf_off = kHeaderBytes + S->flags_bytes;
     S->v_flag_off = S->c_xbuf_off + al256(S->c_xbuf_bytes);
     S->v_xbuf_off = S->v_flag_off + al256(S->v_index.size() * sizeof(int));
@@ -321,7 +323,8 @@ int build_schedule(const fgx_instance* items, int n, const fgx_options* opt, boo
     S->v_waves_off = S->v_desc_off + al256(S->v_index.size() * vol3d_desc_size() + 1);
     S->v_items_off = S->v_waves_off + al256(S->v_round_waves.size() * sizeof(int) + 1);
     S->c_sec_off = S->v_items_off + al256(S->v_wave_items.size() * sizeof(int) + 1);
-    S->total = S->c_sec_off + al256(S->c_sec_bytes);
+    S->v_work_off = S->c_sec_off + al256(S->c_sec_bytes);
+    S->total = S->v_work_off + al256(S->v_work_bytes);
     return FGX_OK;
 }
 
@@ -370,11 +373,12 @@ int fgx_batched_prepare(const fgx_instance* items, int n, void* workspace,
     }
     std::vector<unsigned char> vdesc(S.v_index.size() * vol3d_desc_size());
     for (size_t k = 0; k < S.v_index.size(); ++k) {
-        size_t xb = 0;
+        size_t xb = 0, wb = 0;
         int ci = 0, mt = 0, tiles[kMaxPasses];
         if (!vol3d_instance_desc(vdesc.data() + k * vol3d_desc_size(), items[S.v_index[k]],
                                  S.v_args[k], opt, S.sms, w, (int*)(w + S.v_flag_off) + k,
-                                 w + S.v_xbuf_off + S.v_xoff[k], &xb, &ci, &mt, tiles))
+                                 w + S.v_xbuf_off + S.v_xoff[k], w + S.v_work_off + S.v_woff[k],
+                                 &xb, &wb, &ci, &mt, tiles))
             return FGX_ERR_UNSUPPORTED;
     }
     if (!put(S.desc_off, S.desc.data(), S.desc.size() * sizeof(InstDesc)) ||

@@ -171,12 +171,17 @@ int launch_chain2d_batched(const void* desc, int n, int init_channels, int max_w
 
 // Batched 3D instances on the plane-tile kernel (vol3d.cu): argument block
 // size, filling one (false when the instance does not fit the kernel; with
-// desc null only the sizes), launch geometry and the launch (D0 and range
-// tests of every instance, then the rounds).
+// desc null only the sizes), launch geometry and the launch (D0, working
+// copies and range tests of every instance, the rounds, then the results
+// copied out of the pitched working copies).
 size_t vol3d_desc_size();
+// Arguments of one batched 3D instance (desc null: sizes only).  `work`:
+// the instance's working copies (*wbytes bytes: pitched distances and image
+// where W is not a multiple of 4, the W passes' transposed copies).
 bool vol3d_instance_desc(void* desc, const fgx_instance& it, const SweepArgs& f,
                          const fgx_options* opt, int sms, char* hdr, int* range_flag, char* xb,
-                         size_t* xbytes, int* ci, int* max_tiles, int tiles[kMaxPasses]);
+                         char* work, size_t* xbytes, size_t* wbytes, int* ci, int* max_tiles,
+                         int tiles[kMaxPasses]);
 int vol3d_batched_geometry(int sms, int max_ci, const fgx_options* opt, int* grid, size_t* smem);
 int launch_vol3d_batched(const void* desc, int n, int rounds, const int* round_waves,
                          const int* wave_items, int grid, size_t smem, char* hdr,
@@ -225,13 +230,13 @@ void launch_wait_probe(const unsigned long long* tag, int* status, long long tim
 // Signed transform GDT(M) - GDT(1 - M) (signed.cu): workspace bytes for a
 // forward workspace of `forward_bytes` and n elements, and the run.
 // Encodes a float32 tiled tensor map (a CUtensorMap of 128 bytes at `map`)
-// of rank 1..5: dims innermost first, the tensor dense (pitch of dimension i
-// = the product of the lower dims, in floats), box extents per dimension;
-// NaN fill outside the tensor when nan_fill, else zero.  False when the
-// driver's encoder is unavailable or the layout cannot be encoded (base not
-// 16-byte aligned, a pitch not a multiple of 16 bytes).
+// of rank 1..5: dims innermost first, rows of row_pitch floats (0: dims[0])
+// and every higher dimension dense over the lower ones, box extents per
+// dimension; NaN fill outside the tensor when nan_fill, else zero.  False
+// when the driver's encoder is unavailable or the layout cannot be encoded
+// (base not 16-byte aligned, a pitch not a multiple of 16 bytes).
 bool encode_map_f32(void* map, const void* base, int rank, const uint64_t* dims,
-                    const uint32_t* box, bool nan_fill);
+                    const uint32_t* box, bool nan_fill, uint64_t row_pitch = 0);
 
 // Forward of B transforms of nimg images (B a multiple of nimg; instance b
 // reads image b % nimg) with the library's fast kernels; the workspace of

@@ -118,6 +118,14 @@ struct Vol3DArgs {  // aligned as CUtensorMap (the descriptor arrays of batched 
     float* distT;              // [B][W][D][H], or null (W passes on dist itself)
     float* imageT;             // [nimg][C][W][D][H] (cost modes that read intensities)
     int64_t D, H, W;
+    // batched instances: the passes run on pitched working copies (rows of
+    // Wp floats in [D][H][Wp], of Hp floats in the W passes' [W][D][Hp]) so
+    // that every staged row starts on a 16-byte boundary; `out` and
+    // `image_src` are the caller's arrays when dist / image are such copies
+    // (null when they are the caller's own)
+    int64_t Wp, Hp;
+    float* out;
+    const float* image_src;
 };
 
 struct Head3 {
@@ -731,9 +739,12 @@ __global__ void __launch_bounds__(TMA ? (kCW + kTW) * 32 : (kCW + kPW) * 32, 1)
 
 // Batched launch: work list of (instance, tile) items per round, one round
 // per pass application, grid barrier between rounds; every instance has its
-// own arguments (cost mode, planes, exchange words, range flag).
+// own arguments (cost mode, planes, exchange words, range flag, tensor maps)
+// and runs on pitched working copies, so every plane is staged by tensor
+// copies.
 struct Vol3DBatch {
     const Vol3DArgs* desc;
+    int n;                    // instances
     int rounds;
     const int* round_waves;   // [rounds + 1]
     const int* wave_items;    // [waves][gridDim.x]: (instance << 16) | tile, or -1
@@ -742,81 +753,208 @@ struct Vol3DBatch {
     long long timeout_ns;
 };
 
-// D0 = v * M and the intensity range test of instance blockIdx.y.
+// One 32 x 32 tile of a transpose between the two pitched layouts of an
+// instance, by one warp: forward from [D][H][sp] to [W][D][dp] (sp, dp: row
+// pitches), back the other way.  unit = (d, tile row, tile column) over the
+// H x W plane of slice d.  `tile`: this warp's 32 x 33 floats of shared
+// memory.  The sources may have been written by other blocks of the same
+// launch: read through L2.
+__device__ void transpose_unit(const float* src, float* dst, int64_t D, int64_t H, int64_t W,
+                               int64_t sp, int64_t dp, bool back, int64_t unit, float* tile) {
+    const int lane = threadIdx.x & 31;
+    const int64_t th = (H + 31) / 32, tw = (W + 31) / 32;
+    const int64_t d = unit / (th * tw), rem = unit - d * (th * tw);
+    const int64_t h0 = (rem / tw) * 32, w0 = (rem % tw) * 32;
+    float v[32];
+    if (!back) {
+        // rows h0 + y, columns w0 + lane of slice d
+#pragma unroll
+        for (int y = 0; y < 32; ++y) {
+            const int64_t h = h0 + y, w = w0 + lane;
+            v[y] = (h < H && w < W) ? __ldcg(src + (d * H + h) * sp + w) : 0.0f;
+        }
+    } else {
+        // rows w0 + y, columns h0 + lane of the transposed slice d
+#pragma unroll
+        for (int y = 0; y < 32; ++y) {
+            const int64_t w = w0 + y, h = h0 + lane;
+            v[y] = (h < H && w < W) ? __ldcg(src + (w * D + d) * sp + h) : 0.0f;
+        }
+    }
+#pragma unroll
+    for (int y = 0; y < 32; ++y) tile[y * 33 + lane] = v[y];
+    __syncwarp();
+#pragma unroll
+    for (int y = 0; y < 32; ++y) {
+        const float x = tile[lane * 33 + y];
+        if (!back) {
+            const int64_t w = w0 + y, h = h0 + lane;
+            if (w < W && h < H) dst[(w * D + d) * dp + h] = x;
+        } else {
+            const int64_t h = h0 + y, w = w0 + lane;
+            if (w < W && h < H) dst[(d * H + h) * dp + w] = x;
+        }
+    }
+    __syncwarp();
+}
+
+__device__ __forceinline__ int64_t transpose_units(const Vol3DArgs& a) {
+    return a.D * ((a.H + 31) / 32) * ((a.W + 31) / 32);
+}
+
+// The distance transposes of round r of a batched launch: every instance
+// that applies pass 4 in this round (forward) or applied pass 5 (back).
+// Units are spread over kTransposeWarps warps of every block.
+__device__ void transpose_round(const Vol3DBatch& bt, int r, bool back, float* smem) {
+    const int warp = threadIdx.x >> 5;
+    if (warp < kTransposeWarps) {
+        float* tile = smem + warp * (32 * 33);
+        const int64_t nw = (int64_t)gridDim.x * kTransposeWarps;
+        const int64_t gw = (int64_t)blockIdx.x * kTransposeWarps + warp;
+        int64_t base = 0;
+        for (int k = 0; k < bt.n; ++k) {
+            const Vol3DArgs& a = bt.desc[k];
+            if (r >= a.iterations * kMaxPasses) continue;
+            const int64_t nu = transpose_units(a);
+            for (int64_t u = ((gw - base) % nw + nw) % nw; u < nu; u += nw)
+                transpose_unit(back ? a.distT : a.dist, back ? a.dist : a.distT, a.D, a.H, a.W,
+                               back ? a.Hp : a.Wp, back ? a.Wp : a.Hp, back, u, tile);
+            base += nu;
+        }
+    }
+    __syncthreads();
+}
+
+// D0 = v * M into the working distances of instance blockIdx.y, the pitched
+// copy of its image when it has one, and the intensity range test.
 __global__ void __launch_bounds__(256) init3d_batched_kernel(const Vol3DArgs* desc) {
     const Vol3DArgs& a = desc[blockIdx.y];
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.N; i += stride)
-        a.dist[i] = __fmul_rn(a.v, a.mask[i]);
+    const int64_t HW = a.H * a.W;
+    const float* img = a.image_src ? a.image_src : a.image;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.N; i += stride) {
+        const float d0 = __fmul_rn(a.v, a.mask[i]);
+        if (a.out) {
+            const int64_t z = i / HW, y = (i - z * HW) / a.W, x = i - z * HW - y * a.W;
+            a.dist[(z * a.H + y) * a.Wp + x] = d0;
+        } else {
+            a.dist[i] = d0;
+        }
+    }
+    if (a.image_src && a.mode != kModeConst)
+        for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.C * a.N;
+             i += stride) {
+            const int64_t z = i / HW, y = (i - z * HW) / a.W, x = i - z * HW - y * a.W;
+            const_cast<float*>(a.image)[(z * a.H + y) * a.Wp + x] = a.image_src[i];
+        }
     if (a.mode != kModeAbs) return;
     int* flag = const_cast<int*>(a.range_flag);
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.C * a.N; i += stride) {
-        const float x = fabsf(a.image[i]);
+        const float x = fabsf(img[i]);
         const bool ok = x == 0.0f || (x >= 0x1p-40f && x <= 0x1p62f);
         if (!ok && *(volatile int*)flag == 0) atomicOr(flag, 1);
+    }
+}
+
+// The image of instance blockIdx.y in the W passes' layout [C][W][D][Hp],
+// from the caller's image (channel slices stacked along D).
+__global__ void __launch_bounds__(256) transpose_image3d_batched_kernel(const Vol3DArgs* desc) {
+    __shared__ float smem[8 * 32 * 33];
+    const Vol3DArgs& a = desc[blockIdx.y];
+    if (a.mode == kModeConst || !a.imageT) return;
+    const float* src = a.image_src ? a.image_src : a.image;
+    const int warp = threadIdx.x >> 5;
+    // channel c is slices c*D .. c*D + D - 1 of a [C*D][H][W] stack
+    const int64_t nu = a.C * transpose_units(a);
+    for (int64_t u = (int64_t)blockIdx.x * 8 + warp; u < nu; u += (int64_t)gridDim.x * 8) {
+        const int64_t per = transpose_units(a);
+        const int64_t c = u / per;
+        transpose_unit(src + c * a.N, a.imageT + c * a.W * a.D * a.Hp, a.D, a.H, a.W, a.W, a.Hp,
+                       false, u - c * per, smem + warp * (32 * 33));
+    }
+}
+
+// The caller's distances of the instances that ran on pitched copies.
+__global__ void __launch_bounds__(256) finish3d_batched_kernel(const Vol3DArgs* desc) {
+    const Vol3DArgs& a = desc[blockIdx.y];
+    if (!a.out) return;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int64_t HW = a.H * a.W;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.N; i += stride) {
+        const int64_t z = i / HW, y = (i - z * HW) / a.W, x = i - z * HW - y * a.W;
+        a.out[i] = __ldcg(a.dist + (z * a.H + y) * a.Wp + x);
     }
 }
 
 __device__ bool run_item3(const Vol3DArgs& a, const Tile3& t, int t_app, Head3& h, float* stage,
                           unsigned int cb) {
     if (a.mode == kModeConst)
-        return run_tile3<kModeConst, 0, false, false>(a, t, t_app, h, stage, cb, false);
+        return run_tile3<kModeConst, 0, false, true>(a, t, t_app, h, stage, cb, false);
     if (a.mode == kModeAbs)
-        return run_tile3<kModeAbs, 1, false, false>(a, t, t_app, h, stage, cb,
-                                                    *a.range_flag != 0);
+        return run_tile3<kModeAbs, 1, false, true>(a, t, t_app, h, stage, cb,
+                                                   *a.range_flag != 0);
     if (a.mode == kModeFast) {
         if (a.C == 1)
-            return run_tile3<kModeFast, 1, false, false>(a, t, t_app, h, stage, cb, false);
+            return run_tile3<kModeFast, 1, false, true>(a, t, t_app, h, stage, cb, false);
         if (a.C == 2)
-            return run_tile3<kModeFast, 2, false, false>(a, t, t_app, h, stage, cb, false);
-        return run_tile3<kModeFast, 3, false, false>(a, t, t_app, h, stage, cb, false);
+            return run_tile3<kModeFast, 2, false, true>(a, t, t_app, h, stage, cb, false);
+        return run_tile3<kModeFast, 3, false, true>(a, t, t_app, h, stage, cb, false);
     }
     if (a.C == 1)
-        return run_tile3<kModeGeneral, 1, false, false>(a, t, t_app, h, stage, cb, false);
+        return run_tile3<kModeGeneral, 1, false, true>(a, t, t_app, h, stage, cb, false);
     if (a.C == 2)
-        return run_tile3<kModeGeneral, 2, false, false>(a, t, t_app, h, stage, cb, false);
-    return run_tile3<kModeGeneral, 3, false, false>(a, t, t_app, h, stage, cb, false);
+        return run_tile3<kModeGeneral, 2, false, true>(a, t, t_app, h, stage, cb, false);
+    return run_tile3<kModeGeneral, 3, false, true>(a, t, t_app, h, stage, cb, false);
 }
 
-constexpr int kBlockBatched3 = (kCW + kPW) * 32;
+constexpr int kBlockBatched3 = (kCW + kTW) * 32;
 
 __global__ void __launch_bounds__(kBlockBatched3, 1) vol3d_batched_kernel(const Vol3DBatch bt) {
     extern __shared__ __align__(128) unsigned char smem3[];
     Head3& h = *reinterpret_cast<Head3*>(smem3);
     float* stage = stage_of(smem3);
-    init_barriers3(h, false);
+    init_barriers3(h, true);
     unsigned int epoch = 1;
     unsigned int cb = 0;
     bool alive = true;
     for (int r = 0; r < bt.rounds && alive; ++r) {
+        const int pass = r % kMaxPasses;
+        if (pass == 4) {
+            transpose_round(bt, r, false, stage);
+            if (!(alive = grid_barrier(bt.barrier, epoch++, bt.status, bt.timeout_ns))) break;
+        }
         for (int wv = bt.round_waves[r]; wv < bt.round_waves[r + 1]; ++wv) {
             const int item = bt.wave_items[(int64_t)wv * gridDim.x + blockIdx.x];
             if (item < 0) continue;
             const Vol3DArgs& a = bt.desc[item >> 16];
-            const int pass = r % kMaxPasses;
             const PassGeom& g = a.pass[pass];
+            const bool on_t = pass >= 4;
             Tile3 t;
             t.g = &g;
             t.tile = item & 0xffff;
             t.ntq = a.ntq[pass];
             t.b = 0;
-            t.dist = a.dist;
-            t.img = a.image;
+            t.dist = on_t ? a.distT : a.dist;
+            t.img = on_t ? a.imageT : a.image;
             t.codes = nullptr;
-            t.csl = g.sl;
-            t.csp = g.sp;
-            t.csq = g.sq;
+            t.csl = t.csp = t.csq = 0;
             t.L = (int)g.L;
             t.nch = t.L > 1 ? (t.L + kChunk - 1) / kChunk : 0;
             t.K = a.ring[pass];
             t.tp = t.tq = kRP - 2 * t.K;
             t.p0 = (t.tile / t.ntq) * t.tp - t.K;
             t.q0 = (t.tile % t.ntq) * t.tq - t.K;
-            t.map_d = t.map_i = t.rows_z = 0;
+            t.map_d = pass < 2 ? kMapDistD : (pass < 4 ? kMapDistH : kMapDistW);
+            t.map_i = t.map_d + 3;
+            t.rows_z = pass == 2 || pass == 3;
             if (t.nch > 0) run_item3(a, t, r, h, stage, cb);
             cb += (unsigned int)t.nch;
         }
         alive = grid_barrier(bt.barrier, epoch++, bt.status, bt.timeout_ns);
+        if (alive && pass == 5) {
+            transpose_round(bt, r, true, stage);
+            alive = grid_barrier(bt.barrier, epoch++, bt.status, bt.timeout_ns);
+        }
     }
 }
 
@@ -850,13 +988,15 @@ Vol3DKernel pick_kernel(int mode, int CI, bool codes, bool tma) {
 }
 int block_threads(bool tma) { return tma ? (kCW + kTW) * 32 : (kCW + kPW) * 32; }
 
-// A float32 tensor map of dims (d0 innermost .. d3) with box (b0, b1, b2, 1);
-// NaN fill outside the tensor for distances, zero for intensities.
+// A float32 tensor map of dims (d0 innermost .. d3), rows of `pitch` floats
+// (0: d0), with box (b0, b1, b2, 1); NaN fill outside the tensor for
+// distances, zero for intensities.
 bool make_map(CUtensorMap* m, const void* base, uint64_t d0, uint64_t d1, uint64_t d2,
-              uint64_t d3, uint32_t b0, uint32_t b1, uint32_t b2, bool nan_fill) {
+              uint64_t d3, uint32_t b0, uint32_t b1, uint32_t b2, bool nan_fill,
+              uint64_t pitch = 0) {
     const uint64_t dims[4] = {d0, d1, d2, d3};
     const uint32_t box[4] = {b0, b1, b2, 1};
-    return encode_map_f32(m, base, 4, dims, box, nan_fill);
+    return encode_map_f32(m, base, 4, dims, box, nan_fill, pitch);
 }
 
 // Tensor maps of a call (false: stage with cp.async).  The rows of every
@@ -983,9 +1123,11 @@ static EncodeTiledFn tensor_map_encoder() {
 }
 
 bool encode_map_f32(void* map, const void* base, int rank, const uint64_t* dims,
-                    const uint32_t* box, bool nan_fill) {
+                    const uint32_t* box, bool nan_fill, uint64_t row_pitch) {
     EncodeTiledFn enc = tensor_map_encoder();
-    if (!enc || rank < 1 || rank > 5 || ((uintptr_t)base & 15u) || ((dims[0] * 4) & 15u))
+    const uint64_t rp = row_pitch ? row_pitch : dims[0];
+    if (!enc || rank < 1 || rank > 5 || ((uintptr_t)base & 15u) || ((rp * 4) & 15u) ||
+        rp < dims[0])
         return false;
     cuuint64_t d[5], str[4];
     cuuint32_t b[5], e[5];
@@ -995,7 +1137,7 @@ bool encode_map_f32(void* map, const void* base, int rank, const uint64_t* dims,
         b[i] = box[i];
         e[i] = 1;
         if (i > 0) str[i - 1] = pitch;
-        pitch *= dims[i];
+        pitch *= i == 0 ? rp : dims[i];
     }
     return enc(static_cast<CUtensorMap*>(map), CU_TENSOR_MAP_DATA_TYPE_FLOAT32, (cuuint32_t)rank,
                const_cast<void*>(base), d, str, b, e, CU_TENSOR_MAP_INTERLEAVE_NONE,
@@ -1105,23 +1247,44 @@ size_t vol3d_desc_size() { return sizeof(Vol3DArgs); }
 
 bool vol3d_instance_desc(void* desc, const fgx_instance& it, const SweepArgs& f,
                          const fgx_options* opt, int sms, char* hdr, int* range_flag, char* xb,
-                         size_t* xbytes, int* ci, int* max_tiles, int tiles[kMaxPasses]) {
+                         char* work, size_t* xbytes, size_t* wbytes, int* ci, int* max_tiles,
+                         int tiles[kMaxPasses]) {
     Vol3DPlan vp;
     if (!plan_vol3d(f, opt, sms, &vp, false, false)) return false;
+    const int64_t D = f.pass[0].L, H = f.pass[2].L, W = f.pass[4].L;
+    const int64_t Wp = (W + 3) / 4 * 4, Hp = (H + 3) / 4 * 4;
+    const bool pitched = Wp != W;
+    const bool img = vp.mode != kModeConst;
+    auto al = [](size_t x) { return (x + 255) & ~size_t(255); };
+    // working copies: [pitched dist | pitched image] | transposed dist | transposed image
+    const size_t pd = pitched ? al((size_t)D * H * Wp * 4) : 0;
+    const size_t pi = pitched && img ? al((size_t)f.C * D * H * Wp * 4) : 0;
+    const size_t td = al((size_t)W * D * Hp * 4);
+    const size_t ti = img ? al((size_t)f.C * W * D * Hp * 4) : 0;
     *xbytes = (size_t)vp.max_tiles * 2 * kXWords * 8;
+    *wbytes = pd + pi + td + ti;
     *ci = vp.CI;
     *max_tiles = vp.max_tiles;
     for (int i = 0; i < kMaxPasses; ++i) tiles[i] = vp.ntp[i] * vp.ntq[i];
     if (!desc) return true;
     Vol3DArgs a;
     std::memset(&a, 0, sizeof(a));
-    a.image = it.image;
+    a.image = pitched && img ? (const float*)(work + pd) : it.image;
+    a.image_src = pitched && img ? it.image : nullptr;
     a.mask = it.mask;
-    a.dist = it.dist;
+    a.dist = pitched ? (float*)work : it.dist;
+    a.out = pitched ? it.dist : nullptr;
+    a.distT = (float*)(work + pd + pi);
+    a.imageT = img ? (float*)(work + pd + pi + td) : nullptr;
     a.B = 1;
     a.nimg = 1;
     a.C = f.C;
     a.N = f.N;
+    a.D = D;
+    a.H = H;
+    a.W = W;
+    a.Wp = Wp;
+    a.Hp = Hp;
     a.v = it.v;
     a.lambda = f.lambda;
     a.iterations = it.iterations;
@@ -1132,12 +1295,38 @@ bool vol3d_instance_desc(void* desc, const fgx_instance& it, const SweepArgs& f,
         a.ntq[i] = vp.ntq[i];
         a.ring[i] = vp.ring[i];
     }
+    // strides of the working layouts: [D][H][Wp] for the D and H passes,
+    // [W][D][Hp] for the W passes
+    for (int i = 0; i < 2; ++i) {
+        a.pass[i].sl = H * Wp;
+        a.pass[i].sp = Wp;
+        a.pass[i].sq = 1;
+    }
+    for (int i = 2; i < 4; ++i) {
+        a.pass[i].sl = Wp;
+        a.pass[i].sp = H * Wp;
+        a.pass[i].sq = 1;
+    }
+    for (int i = 4; i < 6; ++i) {
+        a.pass[i].sl = D * Hp;
+        a.pass[i].sp = Hp;
+        a.pass[i].sq = 1;
+    }
     a.max_tiles = vp.max_tiles;
     a.xbuf = (unsigned long long*)xb;
     a.barrier = (unsigned int*)(hdr + 64);
     a.status = (int*)hdr;
     a.range_flag = range_flag;
     a.timeout_ns = f.timeout_ns;
+    const uint64_t C = (uint64_t)f.C;
+    bool ok = make_map(&a.tmap[kMapDistD], a.dist, W, H, D, 1, kRQ, kRP, 1, true, Wp) &&
+              make_map(&a.tmap[kMapDistH], a.dist, W, H, D, 1, kRQ, 1, kRP, true, Wp) &&
+              make_map(&a.tmap[kMapDistW], a.distT, H, D, W, 1, kRQ, kRP, 1, true, Hp);
+    if (img)
+        ok = ok && make_map(&a.tmap[kMapImgD], a.image, W, H, D, C, kRQ, kRP, 1, false, Wp) &&
+             make_map(&a.tmap[kMapImgH], a.image, W, H, D, C, kRQ, 1, kRP, false, Wp) &&
+             make_map(&a.tmap[kMapImgW], a.imageT, H, D, W, C, kRQ, kRP, 1, false, Hp);
+    if (!ok) return false;
     std::memcpy(desc, &a, sizeof(a));
     return true;
 }
@@ -1163,11 +1352,15 @@ int launch_vol3d_batched(const void* desc, int n, int rounds, const int* round_w
                          long long timeout_ns, int sms, void* stream) {
     cudaStream_t s = (cudaStream_t)stream;
     const Vol3DArgs* d = (const Vol3DArgs*)desc;
-    init3d_batched_kernel<<<dim3((unsigned)std::max(1, sms * 4), (unsigned)n), 256, 0, s>>>(d);
+    const dim3 per_inst((unsigned)std::max(1, sms * 4), (unsigned)n);
+    init3d_batched_kernel<<<per_inst, 256, 0, s>>>(d);
     if (cudaGetLastError() != cudaSuccess) return FGX_ERR_CUDA;
     if (rounds == 0) return FGX_OK;
+    transpose_image3d_batched_kernel<<<per_inst, 256, 0, s>>>(d);
+    if (cudaGetLastError() != cudaSuccess) return FGX_ERR_CUDA;
     Vol3DBatch bt;
     bt.desc = d;
+    bt.n = n;
     bt.rounds = rounds;
     bt.round_waves = round_waves;
     bt.wave_items = wave_items;
@@ -1185,6 +1378,8 @@ int launch_vol3d_batched(const void* desc, int n, int rounds, const int* round_w
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     if (cudaLaunchKernelEx(&cfg, vol3d_batched_kernel, bt) != cudaSuccess) return FGX_ERR_CUDA;
+    finish3d_batched_kernel<<<per_inst, 256, 0, s>>>(d);
+    if (cudaGetLastError() != cudaSuccess) return FGX_ERR_CUDA;
     return FGX_OK;
 }
 
