@@ -79,6 +79,12 @@ typedef struct fgx_options {
                            * bit-exact.  Only where the general cost formula applies
                            * (lambda != 0, and not lambda = 1 with one channel, whose
                            * |d| cost is exact and cheap); 0 = exact */
+    int32_t no_cost_tables; /* 3D general cost (exact): 0 = the plane-tile kernel reads
+                             * the edge costs from tables written once per call
+                             * (nine floats per voxel and axis, held in the workspace,
+                             * whose size query then includes them; a workspace too
+                             * small for them computes the costs in every pass instead,
+                             * with identical results); 1 = never (smaller workspace) */
 } fgx_options;
 
 /* Human-readable name of a status code (static string). */
@@ -282,6 +288,8 @@ typedef struct fgx_batched_plan {
     /* 3D instances the plane-tile kernel takes: the plane-tile launch        */
     int32_t n3d, grid3d, rounds3d, smem3d;
     uint64_t desc3d_off, waves3d_off, items3d_off;
+    int32_t tables3d;       /* 1: some 3D instance reads cost tables (staging ring of single planes) */
+    int32_t reserved3d;
 } fgx_batched_plan;
 
 /* Workspace bytes for a batched launch of these instances. */

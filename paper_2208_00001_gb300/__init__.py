@@ -46,12 +46,13 @@ class Options(ctypes.Structure):
     _fields_ = [("size", ctypes.c_uint32), ("tile_lines", ctypes.c_int32),
                 ("tile_width", ctypes.c_int32), ("tile_height", ctypes.c_int32),
                 ("max_blocks", ctypes.c_int32), ("timeout_ms", ctypes.c_int32),
-                ("segments", ctypes.c_int32), ("fast_math", ctypes.c_int32)]
+                ("segments", ctypes.c_int32), ("fast_math", ctypes.c_int32),
+                ("no_cost_tables", ctypes.c_int32)]
 
     def __init__(self, tile_lines=0, tile_width=0, tile_height=0, max_blocks=0, timeout_ms=0,
-                 segments=0, fast_math=0):
+                 segments=0, fast_math=0, no_cost_tables=0):
         super().__init__(ctypes.sizeof(Options), tile_lines, tile_width, tile_height, max_blocks,
-                         timeout_ms, segments, fast_math)
+                         timeout_ms, segments, fast_math, no_cost_tables)
 
 
 class Instance(ctypes.Structure):
@@ -78,7 +79,8 @@ class BatchedPlanC(ctypes.Structure):
                 ("waves2d_off", ctypes.c_uint64), ("items2d_off", ctypes.c_uint64),
                 ("n3d", ctypes.c_int32), ("grid3d", ctypes.c_int32), ("rounds3d", ctypes.c_int32),
                 ("smem3d", ctypes.c_int32), ("desc3d_off", ctypes.c_uint64),
-                ("waves3d_off", ctypes.c_uint64), ("items3d_off", ctypes.c_uint64)]
+                ("waves3d_off", ctypes.c_uint64), ("items3d_off", ctypes.c_uint64),
+                ("tables3d", ctypes.c_int32), ("reserved3d", ctypes.c_int32)]
 
 
 _i64, _i32, _f32, _vp, _sz = (ctypes.c_int64, ctypes.c_int, ctypes.c_float, ctypes.c_void_p,

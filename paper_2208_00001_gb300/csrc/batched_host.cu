@@ -261,7 +261,8 @@ int build_schedule(const fgx_instance* items, int n, const fgx_options* opt, boo
                 &S->round_waves, &S->wave_items);
     // the plane-tile launch for the 3D instances
     if (!S->v_index.empty()) {
-        const int st = vol3d_batched_geometry(sms, S->v_ci, opt, &S->v_grid, &S->v_smem);
+        const int st = vol3d_batched_geometry(sms, S->v_ci, S->v_ci > kMaxChannels3 ? 1 : 0, opt,
+                                              &S->v_grid, &S->v_smem);
         if (st != FGX_OK) return st;
         if (S->v_max_tiles > S->v_grid) return FGX_ERR_UNSUPPORTED;
         pack_rounds((int)S->v_index.size(), S->v_rounds, S->v_grid,
@@ -424,6 +425,7 @@ int fgx_batched_prepare(const fgx_instance* items, int n, void* workspace,
     plan->desc3d_off = S.v_desc_off;
     plan->waves3d_off = S.v_waves_off;
     plan->items3d_off = S.v_items_off;
+    plan->tables3d = S.v_ci > kMaxChannels3 ? 1 : 0;
     return FGX_OK;
 }
 
@@ -449,8 +451,8 @@ int fgx_batched_run(const fgx_batched_plan* plan, void* stream) {
             return FGX_ERR_CUDA;
         const int st = launch_vol3d_batched(
             w + plan->desc3d_off, plan->n3d, plan->rounds3d, (const int*)(w + plan->waves3d_off),
-            (const int*)(w + plan->items3d_off), plan->grid3d, (size_t)plan->smem3d, w,
-            timeout_ns, sms, stream);
+            (const int*)(w + plan->items3d_off), plan->grid3d, (size_t)plan->smem3d,
+            plan->tables3d, w, timeout_ns, sms, stream);
         if (st != FGX_OK) return st;
     }
     if (plan->n == 0) return FGX_OK;

@@ -182,9 +182,13 @@ bool vol3d_instance_desc(void* desc, const fgx_instance& it, const SweepArgs& f,
                          const fgx_options* opt, int sms, char* hdr, int* range_flag, char* xb,
                          char* work, size_t* xbytes, size_t* wbytes, int* ci, int* max_tiles,
                          int tiles[kMaxPasses]);
-int vol3d_batched_geometry(int sms, int max_ci, const fgx_options* opt, int* grid, size_t* smem);
+// max_ci: the most staged intensity arrays of an instance (kMaxChannels3 +
+// 1 and more: cost tables); tables: the staging ring of single planes.
+constexpr int kMaxChannels3 = 3;
+int vol3d_batched_geometry(int sms, int max_ci, int tables, const fgx_options* opt, int* grid,
+                           size_t* smem);
 int launch_vol3d_batched(const void* desc, int n, int rounds, const int* round_waves,
-                         const int* wave_items, int grid, size_t smem, char* hdr,
+                         const int* wave_items, int grid, size_t smem, int tables, char* hdr,
                          long long timeout_ns, int sms, void* stream);
 
 // 2D reverse sweep on warp chains (adj2d.cu).

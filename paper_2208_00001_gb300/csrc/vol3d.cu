@@ -74,20 +74,30 @@ constexpr int kRing = 4;                  // narrow ring width = steps between r
 constexpr int kRingWide = 8;              // wide ring width
 constexpr int kTP = kRP - 2 * kRing;      // owned rows of a narrow-ring tile (the most)
 constexpr int kTQ = kRQ - 2 * kRing;      // owned columns of a narrow-ring tile
-constexpr int kChunk = 4;                 // planes per staging chunk
-constexpr int kNst = 3;                   // chunks in the staging ring
-constexpr int kSlots = kNst * kChunk;     // staged planes
 constexpr int kArr = (kRP + 2) * kRQ;     // floats of one staged array (spare row above and below)
 constexpr int kMaxCI = 3;                 // intensity channels the stage holds
+constexpr int kTabArrays = 9;             // staged arrays of a cost-table pass (one per parent)
 constexpr int kXWords = kTP * kTQ;        // published words per tile and parity (room for the most)
 constexpr int kRangeFlagOffset = 32;      // workspace header: intensity range flag
 constexpr int kTransposeWarps = 8;        // warps of a block that transpose (8 shared tiles)
 constexpr int kMaps = 6;
 #define kInf3 __int_as_float(0x7f800000)
 
-static_assert(kRing % kChunk == 0 && kRingWide % kChunk == 0, "refreshes at chunk boundaries");
+// Staging ring geometry R: kNst chunks of kChunk planes.  R = 0: 12 planes
+// of up to 1 + kMaxCI arrays; R = 1: 5 planes of 1 + kTabArrays arrays (the
+// cost-table mode), a chunk a plane.
+template <int R>
+struct Ring3 {
+    static constexpr int kChunk = R == 0 ? 4 : 1;
+    static constexpr int kNst = R == 0 ? 3 : 5;
+    static constexpr int kSlots = kNst * kChunk;
+    static_assert(kRing % kChunk == 0 && kRingWide % kChunk == 0, "refreshes at chunk boundaries");
+};
+constexpr int kNstMax = 5;
 
-enum { kModeConst = 0, kModeAbs = 1, kModeGeneral = 2, kModeFast = 3 };
+// Edge-cost modes of the plane-tile kernel; kModeTable: the general cost read
+// from tables written once per call (nine per voxel and axis).
+enum { kModeConst = 0, kModeAbs = 1, kModeGeneral = 2, kModeFast = 3, kModeTable = 4 };
 // Tensor maps of one call: distances and intensities in the layouts of the
 // D passes ([D][H][W], box = one plane tile), the H passes (same arrays, box
 // spanning D) and the W passes (the [W][D][H] copies).
@@ -126,10 +136,11 @@ struct Vol3DArgs {  // aligned as CUtensorMap (the descriptor arrays of batched 
     int64_t Wp, Hp;
     float* out;
     const float* image_src;
+    float* tables;  // batched cost tables: D axis, H axis ([9][D][H][Wp] each), W axis ([9][W][D][Hp])
 };
 
 struct Head3 {
-    unsigned long long full[kNst], empty[kNst];
+    unsigned long long full[kNstMax], empty[kNstMax];
     float rowtop[2][kCW][kRQ];  // first row of each warp, per step parity
     float rowbot[2][kCW][kRQ];  // last row of each warp
 };
@@ -236,10 +247,11 @@ struct Stage3 {
 // TMA: chunk c of the tile (global chunk count gc) into its slot, issued by
 // the lanes of one warp: lane l copies array l % (1 + CI) of plane l / (1 + CI)
 // of the chunk (one box each), all completed on the slot's mbarrier.
-template <int CI>
+template <int CI, int R>
 __device__ void tma_chunk(const Vol3DArgs& a, const Tile3& t, Head3& h, float* stage,
                           unsigned int gc, int c) {
     constexpr int PF = Stage3<CI>::kPlaneF;
+    constexpr int kNst = Ring3<R>::kNst, kChunk = Ring3<R>::kChunk;
     const int lane = threadIdx.x & 31;
     const int slot = (int)(gc % kNst);
     const int jn = min(kChunk, t.L - c * kChunk);
@@ -252,7 +264,7 @@ __device__ void tma_chunk(const Vol3DArgs& a, const Tile3& t, Head3& h, float* s
         const int line = t.g->dir > 0 ? s : t.L - 1 - s;
         const unsigned int dst = saddr3(stage + (slot * kChunk + j) * PF + kRQ + arr * kArr);
         const int y = t.rows_z ? line : t.p0, z = t.rows_z ? t.p0 : line;
-        const int w4 = arr == 0 ? (int)t.b : (int)((t.b % a.nimg) * a.C) + arr - 1;
+        const int w4 = arr == 0 ? (int)t.b : (int)((t.b % a.nimg) * CI) + arr - 1;
         tma_load4(dst, &a.tmap[arr == 0 ? t.map_d : t.map_i], t.q0, y, z, w4, mb);
     }
 }
@@ -260,9 +272,10 @@ __device__ void tma_chunk(const Vol3DArgs& a, const Tile3& t, Head3& h, float* s
 // Producer warp (tensor copies): every chunk of the tile into the ring once
 // the compute warps have released its slot.  On a failure it stops issuing.
 // Either way it waits (bounded) until its last copies have landed.
-template <int CI>
+template <int CI, int R>
 __device__ bool producer3_tma(const Vol3DArgs& a, const Tile3& t, Head3& h, float* stage,
                               unsigned int cb) {
+    constexpr int kNst = Ring3<R>::kNst;
     // shared memory written by ordinary stores (transposes) is handed to the
     // tensor copies
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -277,7 +290,7 @@ __device__ bool producer3_tma(const Vol3DArgs& a, const Tile3& t, Head3& h, floa
             ok = false;
             break;
         }
-        tma_chunk<CI>(a, t, h, stage, gc, c);
+        tma_chunk<CI, R>(a, t, h, stage, gc, c);
     }
     // the last copies of the tile have landed before the warp moves on (after
     // a failure the compute warps may no longer wait for them)
@@ -292,10 +305,11 @@ __device__ bool producer3_tma(const Vol3DArgs& a, const Tile3& t, Head3& h, floa
 // into the ring, chunk after chunk, once the compute warps have released the
 // slot.  Voxels outside the volume are staged with distance +inf and
 // intensity 0 (finite costs: a square root never sees an infinite argument).
-template <int CI>
+template <int CI, int R>
 __device__ bool producer3(const Vol3DArgs& a, const Tile3& t, Head3& h, float* stage,
                           unsigned int cb) {
     constexpr int PF = Stage3<CI>::kPlaneF;
+    constexpr int kNst = Ring3<R>::kNst, kChunk = Ring3<R>::kChunk;
     constexpr int NR = kRP / kPW;  // rows per producer lane
     const PassGeom& g = *t.g;
     const int lane = threadIdx.x & 31, pw = (threadIdx.x >> 5) - kCW;
@@ -420,13 +434,15 @@ __device__ __forceinline__ float cost3(const float (&ix)[CI > 0 ? CI : 1],
 // Compute warps of one tile: plane steps 1 .. L-1, ring refresh every K
 // steps, owned voxels written to the distance map (and with CODES their
 // parent codes: 0 if the voxel kept its value, else 1 + the lowest stencil
-// offset whose candidate is the strictly smaller minimum).  With TMA, thread
-// 0 also refills every released chunk slot.
-template <int MODE, int CI, bool CHECKED, bool CODES, bool TMA>
+// offset whose candidate is the strictly smaller minimum).  Thread 0 hands
+// every chunk slot back once no compute warp reads it any more.
+template <int MODE, int CI, bool CHECKED, bool CODES, bool TMA, int R>
 __device__ bool compute3(const Vol3DArgs& a, const Tile3& t, int t_app, Head3& h, float* stage,
                          unsigned int cb) {
-    constexpr int NI = CI > 0 ? CI : 1;
+    constexpr bool kTab = MODE == kModeTable;
+    constexpr int NI = CI > 0 && !kTab ? CI : 1;
     constexpr int PF = Stage3<CI>::kPlaneF;
+    constexpr int kNst = Ring3<R>::kNst, kChunk = Ring3<R>::kChunk, kSlots = Ring3<R>::kSlots;
     const PassGeom& g = *t.g;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int rows0 = w * kRows;
@@ -514,7 +530,27 @@ __device__ bool compute3(const Vol3DArgs& a, const Tile3& t, int t_app, Head3& h
         const float* Sc = S + cur;
         const float* Sp = S + prev;
         float ip[kRows + 2][3][NI], ix[kRows][NI];
-        if (CI > 0) {
+        // cost tables: the costs of the nine parents of every voxel of the
+        // plane in sweep order; a forward sweep reads them at the voxel
+        // (array 1 + k of plane s), a backward sweep at the parent, whose
+        // table holds the same edge under the mirrored offset 8 - k (array
+        // 9 - k of plane s-1, shifted by the offset)
+        float tc[kTab ? kRows : 1][9];
+        if (kTab) {
+            if (g.dir > 0) {
+#pragma unroll
+                for (int i = 0; i < kRows; ++i)
+#pragma unroll
+                    for (int k = 0; k < 9; ++k) tc[i][k] = Sc[(1 + k) * kArr + i * kRQ];
+            } else {
+#pragma unroll
+                for (int i = 0; i < kRows; ++i)
+#pragma unroll
+                    for (int k = 0; k < 9; ++k)
+                        tc[i][k] = Sp[(9 - k) * kArr + (i + k / 3 - 1) * kRQ + (k % 3 - 1)];
+            }
+        }
+        if (CI > 0 && !kTab) {
 #pragma unroll
             for (int k = 0; k < kRows + 2; ++k)
 #pragma unroll
@@ -540,8 +576,9 @@ __device__ bool compute3(const Vol3DArgs& a, const Tile3& t, int t_app, Head3& h
                     const int k = (dpp + 1) * 3 + (dq + 1);
                     const int rk = i + 1 + dpp;
                     const float pd = dq < 0 ? lft[rk] : (dq == 0 ? col[rk] : rgt[rk]);
-                    const float c = cost3<MODE, CI, CHECKED>(ix[i], ip[rk][dq + 1], tk[k], ck[k],
-                                                             lam);
+                    const float c = kTab ? tc[kTab ? i : 0][k]
+                                         : cost3<MODE, NI, CHECKED>(ix[i], ip[rk][dq + 1], tk[k],
+                                                                    ck[k], lam);
                     const float cand = __fadd_rn(pd, c);
                     if (CODES && cand < best) code = (unsigned int)(k + 1);
                     best = fminf(best, cand);
@@ -640,14 +677,76 @@ __global__ void __launch_bounds__(256) transpose_image3d_kernel(const float* ima
     transpose_rw(image, imageT, count, R, W, false, smem, 8);
 }
 
-template <int MODE, int CI, bool CODES, bool TMA>
+// Edge-cost tables of one axis (the general cost, once per call instead of in
+// every pass application): for every voxel x of line l >= 1 of the axis'
+// forward sweep and every stencil offset k, the cost of the edge between x
+// and its parent x - e + (k / 3 - 1, k % 3 - 1) (previous line, in-plane
+// offset along p and q), in exactly the order of the on-the-fly general cost:
+// sqrt_rn(t_k + lambda * sum_ch (I(x) - I(y))^2).  The cost is symmetric bit
+// for bit ((a - b)^2 = (b - a)^2 in rounded arithmetic; t_k depends on the
+// squared offset), so a backward sweep reads the same edge at the parent
+// under the mirrored offset 8 - k.  A parent outside the volume gets the cost
+// of a zero difference (never used: its distance is +inf or NaN).
+// Layouts: the intensities and the table share the pass geometry g (strides
+// sl, sp, sq); channel ch at img + ch * cstride, offset k at tab + k * kstride.
+__device__ void cost_table_axis(const float* img, int64_t cstride, int C, float* tab,
+                                int64_t kstride, const PassGeom& g, float lam, int64_t begin,
+                                int64_t step) {
+    const int64_t total = (g.L - 1) * g.P * g.Q;
+    for (int64_t e = begin; e < total; e += step) {
+        const int64_t q = e % g.Q, r = e / g.Q;
+        const int64_t p = r % g.P, l = 1 + r / g.P;
+        const int64_t ox = l * g.sl + p * g.sp + q * g.sq;
+        float ix[kMaxCI];
+#pragma unroll
+        for (int ch = 0; ch < kMaxCI; ++ch) ix[ch] = ch < C ? img[ch * cstride + ox] : 0.0f;
+#pragma unroll
+        for (int k = 0; k < 9; ++k) {
+            const int64_t pp = p + k / 3 - 1, qq = q + k % 3 - 1;
+            const bool in = pp >= 0 && pp < g.P && qq >= 0 && qq < g.Q;
+            const int64_t oy = (l - 1) * g.sl + pp * g.sp + qq * g.sq;
+            float di2 = 0.0f;
+#pragma unroll
+            for (int ch = 0; ch < kMaxCI; ++ch) {
+                if (ch >= C) break;
+                const float d = __fsub_rn(ix[ch], in ? img[ch * cstride + oy] : ix[ch]);
+                di2 = ch == 0 ? __fmul_rn(d, d) : __fadd_rn(di2, __fmul_rn(d, d));
+            }
+            tab[k * kstride + ox] = __fsqrt_rn(__fadd_rn(g.t[k], __fmul_rn(lam, di2)));
+        }
+    }
+}
+
+// Tables of the three axes of `count` images (blockIdx.y = axis): image i at
+// image + i * istride (D and H axes) or imageT + i * istride (W axis), its
+// tables at tabs[axis] + i * tstride.
+struct CostTables {
+    const float* img[3];
+    float* tab[3];
+    PassGeom g[3];
+    int64_t cstride[3], kstride[3], istride[3], tstride[3];
+    int64_t count;
+    int C;
+    float lam;
+};
+__global__ void __launch_bounds__(256) cost_table3d_kernel(const CostTables ct) {
+    const int ax = blockIdx.y;
+    const int64_t step = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = 0; i < ct.count; ++i)
+        cost_table_axis(ct.img[ax] + i * ct.istride[ax], ct.cstride[ax], ct.C,
+                        ct.tab[ax] + i * ct.tstride[ax], ct.kstride[ax], ct.g[ax], ct.lam,
+                        (int64_t)blockIdx.x * blockDim.x + threadIdx.x, step);
+}
+
+template <int MODE, int CI, bool CODES, bool TMA, int R>
 __device__ __forceinline__ bool run_tile3(const Vol3DArgs& a, const Tile3& t, int t_app, Head3& h,
                                           float* stage, unsigned int cb, bool checked) {
     if ((int)(threadIdx.x >> 5) >= kCW)
-        return TMA ? producer3_tma<CI>(a, t, h, stage, cb) : producer3<CI>(a, t, h, stage, cb);
+        return TMA ? producer3_tma<CI, R>(a, t, h, stage, cb)
+                   : producer3<CI, R>(a, t, h, stage, cb);
     if (MODE == kModeAbs && checked)
-        return compute3<MODE, CI, true, CODES, TMA>(a, t, t_app, h, stage, cb);
-    return compute3<MODE, CI, false, CODES, TMA>(a, t, t_app, h, stage, cb);
+        return compute3<MODE, CI, true, CODES, TMA, R>(a, t, t_app, h, stage, cb);
+    return compute3<MODE, CI, false, CODES, TMA, R>(a, t, t_app, h, stage, cb);
 }
 
 // Shared-memory layout of a block: the head, then the staging ring at the
@@ -660,7 +759,7 @@ __device__ __forceinline__ float* stage_of(unsigned char* smem) {
 
 __device__ __forceinline__ void init_barriers3(Head3& h, bool tma) {
     if (threadIdx.x == 0) {
-        for (int i = 0; i < kNst; ++i) {
+        for (int i = 0; i < kNstMax; ++i) {
             // one transaction-counted arrival (TMA) or one per producer lane
             mbar_init3(&h.full[i], tma ? 1u : (unsigned int)(kPW * 32));
             mbar_init3(&h.empty[i], 1);
@@ -685,21 +784,22 @@ __global__ void __launch_bounds__(TMA ? (kCW + kTW) * 32 : (kCW + kPW) * 32, 1)
     const int napps = a.iterations * kMaxPasses;
     bool alive = true;
     const bool tw = a.distT != nullptr;
-    const int64_t R = a.D * a.H;
+    const int64_t DH = a.D * a.H;  // rows of the transposes
 
     for (int t_app = 0; t_app < napps && alive; ++t_app) {
         const int pass = t_app % kMaxPasses;
         const PassGeom& g = a.pass[pass];
         const bool on_t = tw && pass >= 4;  // this pass runs on the transposed copies
         if (tw && pass == 4) {
-            transpose_rw(a.dist, a.distT, a.B, R, a.W, false, stage, kTransposeWarps);
+            transpose_rw(a.dist, a.distT, a.B, DH, a.W, false, stage, kTransposeWarps);
             if (!(alive = grid_barrier(a.barrier, epoch++, a.status, a.timeout_ns))) break;
         }
         const int ntiles = a.ntp[pass] * a.ntq[pass];
         const int per_wave = gridDim.x / ntiles;
         const int64_t nwaves = (a.B + per_wave - 1) / per_wave;
         const int L = (int)g.L;
-        const int nch = L > 1 ? (L + kChunk - 1) / kChunk : 0;
+        constexpr int RG = MODE == kModeTable ? 1 : 0;  // staging ring geometry
+        const int nch = L > 1 ? (L + Ring3<RG>::kChunk - 1) / Ring3<RG>::kChunk : 0;
         for (int64_t wv = 0; wv < nwaves; ++wv) {
             if ((int)blockIdx.x >= per_wave * ntiles) continue;
             const int64_t b = wv * per_wave + blockIdx.x / ntiles;
@@ -724,12 +824,12 @@ __global__ void __launch_bounds__(TMA ? (kCW + kTW) * 32 : (kCW + kPW) * 32, 1)
             t.map_d = pass < 2 ? kMapDistD : (pass < 4 ? kMapDistH : kMapDistW);
             t.map_i = t.map_d + 3;
             t.rows_z = pass == 2 || pass == 3;
-            if (nch > 0) run_tile3<MODE, CI, CODES, TMA>(a, t, t_app, h, stage, cb, checked);
+            if (nch > 0) run_tile3<MODE, CI, CODES, TMA, RG>(a, t, t_app, h, stage, cb, checked);
             cb += (unsigned int)nch;
         }
         alive = grid_barrier(a.barrier, epoch++, a.status, a.timeout_ns);
         if (alive && tw && pass == 5) {
-            transpose_rw(a.distT, a.dist, a.B, R, a.W, true, stage, kTransposeWarps);
+            transpose_rw(a.distT, a.dist, a.B, DH, a.W, true, stage, kTransposeWarps);
             alive = grid_barrier(a.barrier, epoch++, a.status, a.timeout_ns);
         }
         if (blockIdx.x == 0 && threadIdx.x == 0 && t_app + 1 < 16)
@@ -886,29 +986,50 @@ __global__ void __launch_bounds__(256) finish3d_batched_kernel(const Vol3DArgs* 
     }
 }
 
+// Cost tables of the batched instances that read them (blockIdx.y = instance).
+__global__ void __launch_bounds__(256) cost_table3d_batched_kernel(const Vol3DArgs* desc) {
+    const Vol3DArgs& a = desc[blockIdx.y];
+    if (a.mode != kModeTable) return;
+    const int64_t pl = a.D * a.H * a.Wp, plT = a.W * a.D * a.Hp;
+    const int64_t begin = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t step = (int64_t)gridDim.x * blockDim.x;
+    cost_table_axis(a.image, pl, (int)a.C, a.tables, pl, a.pass[0], a.lambda, begin, step);
+    cost_table_axis(a.image, pl, (int)a.C, a.tables + kTabArrays * pl, pl, a.pass[2], a.lambda,
+                    begin, step);
+    cost_table_axis(a.imageT, plT, (int)a.C, a.tables + 2 * kTabArrays * pl, plT, a.pass[4],
+                    a.lambda, begin, step);
+}
+
+// One batched item in ring geometry R (R = 1 when some instance of the
+// launch reads cost tables: every item then stages planes one by one).
+template <int R>
 __device__ bool run_item3(const Vol3DArgs& a, const Tile3& t, int t_app, Head3& h, float* stage,
                           unsigned int cb) {
     if (a.mode == kModeConst)
-        return run_tile3<kModeConst, 0, false, true>(a, t, t_app, h, stage, cb, false);
+        return run_tile3<kModeConst, 0, false, true, R>(a, t, t_app, h, stage, cb, false);
     if (a.mode == kModeAbs)
-        return run_tile3<kModeAbs, 1, false, true>(a, t, t_app, h, stage, cb,
-                                                   *a.range_flag != 0);
+        return run_tile3<kModeAbs, 1, false, true, R>(a, t, t_app, h, stage, cb,
+                                                      *a.range_flag != 0);
+    if (R == 1 && a.mode == kModeTable)
+        return run_tile3<kModeTable, kTabArrays, false, true, R>(a, t, t_app, h, stage, cb,
+                                                                 false);
     if (a.mode == kModeFast) {
         if (a.C == 1)
-            return run_tile3<kModeFast, 1, false, true>(a, t, t_app, h, stage, cb, false);
+            return run_tile3<kModeFast, 1, false, true, R>(a, t, t_app, h, stage, cb, false);
         if (a.C == 2)
-            return run_tile3<kModeFast, 2, false, true>(a, t, t_app, h, stage, cb, false);
-        return run_tile3<kModeFast, 3, false, true>(a, t, t_app, h, stage, cb, false);
+            return run_tile3<kModeFast, 2, false, true, R>(a, t, t_app, h, stage, cb, false);
+        return run_tile3<kModeFast, 3, false, true, R>(a, t, t_app, h, stage, cb, false);
     }
     if (a.C == 1)
-        return run_tile3<kModeGeneral, 1, false, true>(a, t, t_app, h, stage, cb, false);
+        return run_tile3<kModeGeneral, 1, false, true, R>(a, t, t_app, h, stage, cb, false);
     if (a.C == 2)
-        return run_tile3<kModeGeneral, 2, false, true>(a, t, t_app, h, stage, cb, false);
-    return run_tile3<kModeGeneral, 3, false, true>(a, t, t_app, h, stage, cb, false);
+        return run_tile3<kModeGeneral, 2, false, true, R>(a, t, t_app, h, stage, cb, false);
+    return run_tile3<kModeGeneral, 3, false, true, R>(a, t, t_app, h, stage, cb, false);
 }
 
 constexpr int kBlockBatched3 = (kCW + kTW) * 32;
 
+template <int R>
 __global__ void __launch_bounds__(kBlockBatched3, 1) vol3d_batched_kernel(const Vol3DBatch bt) {
     extern __shared__ __align__(128) unsigned char smem3[];
     Head3& h = *reinterpret_cast<Head3*>(smem3);
@@ -939,7 +1060,7 @@ __global__ void __launch_bounds__(kBlockBatched3, 1) vol3d_batched_kernel(const 
             t.codes = nullptr;
             t.csl = t.csp = t.csq = 0;
             t.L = (int)g.L;
-            t.nch = t.L > 1 ? (t.L + kChunk - 1) / kChunk : 0;
+            t.nch = t.L > 1 ? (t.L + Ring3<R>::kChunk - 1) / Ring3<R>::kChunk : 0;
             t.K = a.ring[pass];
             t.tp = t.tq = kRP - 2 * t.K;
             t.p0 = (t.tile / t.ntq) * t.tp - t.K;
@@ -947,7 +1068,7 @@ __global__ void __launch_bounds__(kBlockBatched3, 1) vol3d_batched_kernel(const 
             t.map_d = pass < 2 ? kMapDistD : (pass < 4 ? kMapDistH : kMapDistW);
             t.map_i = t.map_d + 3;
             t.rows_z = pass == 2 || pass == 3;
-            if (t.nch > 0) run_item3(a, t, r, h, stage, cb);
+            if (t.nch > 0) run_item3<R>(a, t, r, h, stage, cb);
             cb += (unsigned int)t.nch;
         }
         alive = grid_barrier(bt.barrier, epoch++, bt.status, bt.timeout_ns);
@@ -958,10 +1079,13 @@ __global__ void __launch_bounds__(kBlockBatched3, 1) vol3d_batched_kernel(const 
     }
 }
 
-size_t stage_bytes(int CI) {
+// Dynamic shared memory of a block staging 1 + CI arrays a plane in ring
+// geometry R (R = 1: the cost-table ring).
+size_t stage_bytes(int CI, int R = 0) {
     const size_t head = (sizeof(Head3) + 127) & ~size_t(127);
+    const int slots = R ? Ring3<1>::kSlots : Ring3<0>::kSlots;
     // the ring, plus one row of slack for the last lane's right-hand reads
-    const size_t st = (size_t)(kSlots * (1 + CI) * kArr + kRQ) * sizeof(float);
+    const size_t st = (size_t)(slots * (1 + CI) * kArr + kRQ) * sizeof(float);
     return head + st + 128;  // + up to 127 bytes of alignment
 }
 
@@ -982,6 +1106,11 @@ Vol3DKernel pick_kernel_t(int mode, int CI) {
     return vol3d_kernel<kModeGeneral, 3, CODES, TMA>;
 }
 Vol3DKernel pick_kernel(int mode, int CI, bool codes, bool tma) {
+    // cost tables are staged by tensor copies only
+    if (mode == kModeTable)
+        return !tma ? nullptr
+                    : codes ? vol3d_kernel<kModeTable, kTabArrays, true, true>
+                            : vol3d_kernel<kModeTable, kTabArrays, false, true>;
     if (tma)
         return codes ? pick_kernel_t<true, true>(mode, CI) : pick_kernel_t<false, true>(mode, CI);
     return codes ? pick_kernel_t<true, false>(mode, CI) : pick_kernel_t<false, false>(mode, CI);
@@ -1023,6 +1152,10 @@ struct Vol3DPlan {
     size_t smem = 0, ws_bytes = 0;
     size_t zero_bytes = 0;             // header and exchange words (cleared per call)
     size_t distT_off = 0, imageT_off = 0;  // transposed copies for the W passes
+    // cost tables (general cost on tensor-copy layouts): [B][9][N] for the D
+    // axis, then the H axis, then the W axis in its [W][D][H] layout;
+    // ws_bytes includes them when tab_bytes > 0, ws_min_bytes does not
+    size_t tab_off = 0, tab_bytes = 0, ws_min_bytes = 0;
 };
 
 int64_t tiles_of(const PassGeom& g, int K) {
@@ -1096,6 +1229,17 @@ bool plan_vol3d(const SweepArgs& f, const fgx_options* opt, int sms, Vol3DPlan* 
     vp->distT_off = al(vp->zero_bytes);
     vp->imageT_off = vp->distT_off + al((size_t)f.B * f.N * 4);
     vp->ws_bytes = vp->imageT_off + al((size_t)f.B * f.C * f.N * 4);
+    vp->ws_min_bytes = vp->ws_bytes;
+    // the general cost reads tables when every staged row is 16-byte aligned
+    // (the tensor-copy path); a size query (any_mode) covers them
+    const int64_t W = f.pass[4].L, H = f.pass[2].L;
+    const bool tab = (any_mode || vp->mode == kModeGeneral) && W % 4 == 0 && H % 4 == 0 &&
+                     W > 1 && !(opt && opt->no_cost_tables);
+    if (tab) {
+        vp->tab_off = vp->ws_bytes;
+        vp->tab_bytes = al((size_t)f.B * 3 * 9 * f.N * 4);
+        vp->ws_bytes += vp->tab_bytes;
+    }
     return true;
 }
 
@@ -1161,7 +1305,7 @@ int run_vol3d(const SweepArgs& f, const float* image, const float* mask, float* 
               int sms, void* stream, bool resume, int64_t nimg) {
     Vol3DPlan vp;
     if (!plan_vol3d(f, opt, sms, &vp)) return FGX_ERR_UNSUPPORTED;
-    if (ws_bytes < vp.ws_bytes) return FGX_ERR_WORKSPACE;
+    if (ws_bytes < vp.ws_min_bytes) return FGX_ERR_WORKSPACE;
     Vol3DArgs a;
     std::memset(&a, 0, sizeof(a));
     a.image = image;
@@ -1204,6 +1348,27 @@ int run_vol3d(const SweepArgs& f, const float* image, const float* mask, float* 
         }
     }
     const bool tma = make_maps(a);
+    // the general cost from tables when the workspace holds them (tensor
+    // copies only): the intensity maps then address the tables, nine
+    // arrays per image and axis
+    size_t smem = vp.smem;
+    const bool tab = tma && vp.mode == kModeGeneral && vp.tab_bytes > 0 && ws_bytes >= vp.ws_bytes;
+    float* tabs[3] = {nullptr, nullptr, nullptr};
+    if (tab) {
+        const uint64_t D = (uint64_t)a.D, H = (uint64_t)a.H, W = (uint64_t)a.W;
+        const uint64_t n9 = (uint64_t)a.nimg * kTabArrays;
+        tabs[0] = (float*)(w + vp.tab_off);
+        tabs[1] = tabs[0] + n9 * (uint64_t)f.N;
+        tabs[2] = tabs[1] + n9 * (uint64_t)f.N;
+        if (make_map(&a.tmap[kMapImgD], tabs[0], W, H, D, n9, kRQ, kRP, 1, false) &&
+            make_map(&a.tmap[kMapImgH], tabs[1], W, H, D, n9, kRQ, 1, kRP, false) &&
+            make_map(&a.tmap[kMapImgW], tabs[2], H, D, W, n9, kRQ, kRP, 1, false)) {
+            a.mode = kModeTable;
+            smem = stage_bytes(kTabArrays, 1);
+        } else if (!make_maps(a)) {
+            return FGX_ERR_CUDA;  // the intensity maps could be encoded a moment ago
+        }
+    }
     cudaStream_t s = (cudaStream_t)stream;
     if (cudaMemsetAsync(workspace, 0, vp.zero_bytes, s) != cudaSuccess) return FGX_ERR_CUDA;
     // codes of the first plane of every sweep stay 0 (it keeps its values)
@@ -1222,18 +1387,39 @@ int run_vol3d(const SweepArgs& f, const float* image, const float* mask, float* 
         if (cudaGetLastError() != cudaSuccess) return FGX_ERR_CUDA;
     }
     if (f.iterations == 0) return FGX_OK;
+    if (a.mode == kModeTable) {
+        CostTables ct;
+        std::memset(&ct, 0, sizeof(ct));
+        const int src_pass[3] = {0, 2, 4};
+        for (int ax = 0; ax < 3; ++ax) {
+            ct.img[ax] = ax < 2 ? image : a.imageT;
+            ct.tab[ax] = tabs[ax];
+            ct.g[ax] = a.pass[src_pass[ax]];
+            ct.cstride[ax] = f.N;
+            ct.kstride[ax] = f.N;
+            ct.istride[ax] = f.C * f.N;
+            ct.tstride[ax] = kTabArrays * f.N;
+        }
+        ct.count = a.nimg;
+        ct.C = (int)f.C;
+        ct.lam = f.lambda;
+        cost_table3d_kernel<<<dim3((unsigned)(sms * 4), 3), 256, 0, s>>>(ct);
+        if (cudaGetLastError() != cudaSuccess) return FGX_ERR_CUDA;
+    }
     cudaLaunchConfig_t cfg = {};
     cudaLaunchAttribute attr[1];
     cfg.gridDim = dim3((unsigned)vp.grid);
     cfg.blockDim = dim3((unsigned)block_threads(tma));
-    cfg.dynamicSmemBytes = vp.smem;
+    cfg.dynamicSmemBytes = smem;
     cfg.stream = s;
     attr[0].id = cudaLaunchAttributeCooperative;
     attr[0].val.cooperative = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    Vol3DKernel k = pick_kernel(vp.mode, vp.CI, codes != nullptr, tma);
-    if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)vp.smem) !=
+    Vol3DKernel k = a.mode == kModeTable
+                        ? pick_kernel(kModeTable, kTabArrays, codes != nullptr, true)
+                        : pick_kernel(vp.mode, vp.CI, codes != nullptr, tma);
+    if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
         cudaSuccess)
         return FGX_ERR_CUDA;
     if (cudaLaunchKernelEx(&cfg, k, a) != cudaSuccess)
@@ -1255,15 +1441,19 @@ bool vol3d_instance_desc(void* desc, const fgx_instance& it, const SweepArgs& f,
     const int64_t Wp = (W + 3) / 4 * 4, Hp = (H + 3) / 4 * 4;
     const bool pitched = Wp != W;
     const bool img = vp.mode != kModeConst;
+    const bool tab = vp.mode == kModeGeneral && !(opt && opt->no_cost_tables);
     auto al = [](size_t x) { return (x + 255) & ~size_t(255); };
-    // working copies: [pitched dist | pitched image] | transposed dist | transposed image
+    // working copies: [pitched dist | pitched image] | transposed dist |
+    // transposed image | [cost tables of the D, H and W axes]
     const size_t pd = pitched ? al((size_t)D * H * Wp * 4) : 0;
     const size_t pi = pitched && img ? al((size_t)f.C * D * H * Wp * 4) : 0;
     const size_t td = al((size_t)W * D * Hp * 4);
     const size_t ti = img ? al((size_t)f.C * W * D * Hp * 4) : 0;
+    const size_t tb =
+        tab ? al((size_t)kTabArrays * (2 * (size_t)D * H * Wp + (size_t)W * D * Hp) * 4) : 0;
     *xbytes = (size_t)vp.max_tiles * 2 * kXWords * 8;
-    *wbytes = pd + pi + td + ti;
-    *ci = vp.CI;
+    *wbytes = pd + pi + td + ti + tb;
+    *ci = tab ? kTabArrays : vp.CI;
     *max_tiles = vp.max_tiles;
     for (int i = 0; i < kMaxPasses; ++i) tiles[i] = vp.ntp[i] * vp.ntq[i];
     if (!desc) return true;
@@ -1288,7 +1478,8 @@ bool vol3d_instance_desc(void* desc, const fgx_instance& it, const SweepArgs& f,
     a.v = it.v;
     a.lambda = f.lambda;
     a.iterations = it.iterations;
-    a.mode = vp.mode;
+    a.mode = tab ? kModeTable : vp.mode;
+    a.tables = tab ? (float*)(work + pd + pi + td + ti) : nullptr;
     for (int i = 0; i < kMaxPasses; ++i) {
         a.pass[i] = f.pass[i];
         a.ntp[i] = vp.ntp[i];
@@ -1322,23 +1513,35 @@ bool vol3d_instance_desc(void* desc, const fgx_instance& it, const SweepArgs& f,
     bool ok = make_map(&a.tmap[kMapDistD], a.dist, W, H, D, 1, kRQ, kRP, 1, true, Wp) &&
               make_map(&a.tmap[kMapDistH], a.dist, W, H, D, 1, kRQ, 1, kRP, true, Wp) &&
               make_map(&a.tmap[kMapDistW], a.distT, H, D, W, 1, kRQ, kRP, 1, true, Hp);
-    if (img)
+    if (tab) {
+        // the intensity maps address the tables: nine arrays per axis
+        const uint64_t pl = (uint64_t)D * H * Wp;
+        float* tD = a.tables;
+        float* tH = tD + kTabArrays * pl;
+        float* tW = tH + kTabArrays * pl;
+        ok = ok && make_map(&a.tmap[kMapImgD], tD, W, H, D, kTabArrays, kRQ, kRP, 1, false, Wp) &&
+             make_map(&a.tmap[kMapImgH], tH, W, H, D, kTabArrays, kRQ, 1, kRP, false, Wp) &&
+             make_map(&a.tmap[kMapImgW], tW, H, D, W, kTabArrays, kRQ, kRP, 1, false, Hp);
+    } else if (img) {
         ok = ok && make_map(&a.tmap[kMapImgD], a.image, W, H, D, C, kRQ, kRP, 1, false, Wp) &&
              make_map(&a.tmap[kMapImgH], a.image, W, H, D, C, kRQ, 1, kRP, false, Wp) &&
              make_map(&a.tmap[kMapImgW], a.imageT, H, D, W, C, kRQ, kRP, 1, false, Hp);
+    }
     if (!ok) return false;
     std::memcpy(desc, &a, sizeof(a));
     return true;
 }
 
-int vol3d_batched_geometry(int sms, int max_ci, const fgx_options* opt, int* grid, size_t* smem) {
-    *smem = stage_bytes(max_ci);
-    if (cudaFuncSetAttribute(vol3d_batched_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)*smem) != cudaSuccess)
+int vol3d_batched_geometry(int sms, int max_ci, int tables, const fgx_options* opt, int* grid,
+                           size_t* smem) {
+    *smem = stage_bytes(max_ci, tables ? 1 : 0);
+    auto k = tables ? vol3d_batched_kernel<1> : vol3d_batched_kernel<0>;
+    if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)*smem) !=
+        cudaSuccess)
         return FGX_ERR_CUDA;
     int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, vol3d_batched_kernel,
-                                                      kBlockBatched3, *smem) != cudaSuccess ||
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kBlockBatched3, *smem) !=
+            cudaSuccess ||
         per_sm < 1)
         return FGX_ERR_CUDA;
     int64_t g = (int64_t)per_sm * sms;
@@ -1348,7 +1551,7 @@ int vol3d_batched_geometry(int sms, int max_ci, const fgx_options* opt, int* gri
 }
 
 int launch_vol3d_batched(const void* desc, int n, int rounds, const int* round_waves,
-                         const int* wave_items, int grid, size_t smem, char* hdr,
+                         const int* wave_items, int grid, size_t smem, int tables, char* hdr,
                          long long timeout_ns, int sms, void* stream) {
     cudaStream_t s = (cudaStream_t)stream;
     const Vol3DArgs* d = (const Vol3DArgs*)desc;
@@ -1358,6 +1561,10 @@ int launch_vol3d_batched(const void* desc, int n, int rounds, const int* round_w
     if (rounds == 0) return FGX_OK;
     transpose_image3d_batched_kernel<<<per_inst, 256, 0, s>>>(d);
     if (cudaGetLastError() != cudaSuccess) return FGX_ERR_CUDA;
+    if (tables) {
+        cost_table3d_batched_kernel<<<per_inst, 256, 0, s>>>(d);
+        if (cudaGetLastError() != cudaSuccess) return FGX_ERR_CUDA;
+    }
     Vol3DBatch bt;
     bt.desc = d;
     bt.n = n;
@@ -1377,7 +1584,11 @@ int launch_vol3d_batched(const void* desc, int n, int rounds, const int* round_w
     attr[0].val.cooperative = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    if (cudaLaunchKernelEx(&cfg, vol3d_batched_kernel, bt) != cudaSuccess) return FGX_ERR_CUDA;
+    auto k = tables ? vol3d_batched_kernel<1> : vol3d_batched_kernel<0>;
+    if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+        cudaSuccess)
+        return FGX_ERR_CUDA;
+    if (cudaLaunchKernelEx(&cfg, k, bt) != cudaSuccess) return FGX_ERR_CUDA;
     finish3d_batched_kernel<<<per_inst, 256, 0, s>>>(d);
     if (cudaGetLastError() != cudaSuccess) return FGX_ERR_CUDA;
     return FGX_OK;
