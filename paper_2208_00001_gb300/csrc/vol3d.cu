@@ -689,34 +689,44 @@ __global__ void __launch_bounds__(256) transpose_image3d_kernel(const float* ima
 // of a zero difference (never used: its distance is +inf or NaN).
 // Layouts: the intensities and the table share the pass geometry g (strides
 // sl, sp, sq); channel ch at img + ch * cstride, offset k at tab + k * kstride.
-__device__ void cost_table_axis(const float* img, int64_t cstride, int C, float* tab,
-                                int64_t kstride, const PassGeom& g, float lam, int64_t begin,
-                                int64_t step) {
-    const int64_t total = (g.L - 1) * g.P * g.Q;
-    for (int64_t e = begin; e < total; e += step) {
-        const int64_t q = e % g.Q, r = e / g.Q;
-        const int64_t p = r % g.P, l = 1 + r / g.P;
-        const int64_t ox = l * g.sl + p * g.sp + q * g.sq;
-        float ix[kMaxCI];
+template <int C>
+__device__ void cost_table_axis(const float* img, int cstride, float* tab, int kstride,
+                                  const PassGeom& g, float lam, int64_t warp0, int64_t nwarps) {
+    // one warp per line of the plane (lanes along q; no division per voxel),
+    // the nine parent loads of a voxel independent of one another; offsets
+    // within one image fit 32 bits (the planner checks 9 N < 2^31)
+    const int lane = threadIdx.x & 31;
+    const int P = (int)g.P, Q = (int)g.Q, sl = (int)g.sl, sp = (int)g.sp, sq = (int)g.sq;
+    const int64_t rows = (g.L - 1) * g.P;
+    for (int64_t row = warp0; row < rows; row += nwarps) {
+        const int l = 1 + (int)(row / P), p = (int)(row - (int64_t)(l - 1) * P);
+        const int bx = l * sl + p * sp, by = (l - 1) * sl + p * sp;
+        for (int q = lane; q < Q; q += 32) {
+            const int ox = bx + q * sq;
+            float ix[C], iy[9][C];
 #pragma unroll
-        for (int ch = 0; ch < kMaxCI; ++ch) ix[ch] = ch < C ? img[ch * cstride + ox] : 0.0f;
+            for (int ch = 0; ch < C; ++ch) ix[ch] = img[ch * cstride + ox];
 #pragma unroll
-        for (int k = 0; k < 9; ++k) {
-            const int64_t pp = p + k / 3 - 1, qq = q + k % 3 - 1;
-            const bool in = pp >= 0 && pp < g.P && qq >= 0 && qq < g.Q;
-            const int64_t oy = (l - 1) * g.sl + pp * g.sp + qq * g.sq;
-            float di2 = 0.0f;
+            for (int k = 0; k < 9; ++k) {
+                const int dp = k / 3 - 1, dq = k % 3 - 1;
+                const bool in = p + dp >= 0 && p + dp < P && q + dq >= 0 && q + dq < Q;
+                const int oy = by + dp * sp + (q + dq) * sq;
 #pragma unroll
-            for (int ch = 0; ch < kMaxCI; ++ch) {
-                if (ch >= C) break;
-                const float d = __fsub_rn(ix[ch], in ? img[ch * cstride + oy] : ix[ch]);
-                di2 = ch == 0 ? __fmul_rn(d, d) : __fadd_rn(di2, __fmul_rn(d, d));
+                for (int ch = 0; ch < C; ++ch) iy[k][ch] = in ? img[ch * cstride + oy] : ix[ch];
             }
-            tab[k * kstride + ox] = __fsqrt_rn(__fadd_rn(g.t[k], __fmul_rn(lam, di2)));
+#pragma unroll
+            for (int k = 0; k < 9; ++k) {
+                float di2 = 0.0f;
+#pragma unroll
+                for (int ch = 0; ch < C; ++ch) {
+                    const float d = __fsub_rn(ix[ch], iy[k][ch]);
+                    di2 = ch == 0 ? __fmul_rn(d, d) : __fadd_rn(di2, __fmul_rn(d, d));
+                }
+                tab[k * kstride + ox] = __fsqrt_rn(__fadd_rn(g.t[k], __fmul_rn(lam, di2)));
+            }
         }
     }
 }
-
 // Tables of the three axes of `count` images (blockIdx.y = axis): image i at
 // image + i * istride (D and H axes) or imageT + i * istride (W axis), its
 // tables at tabs[axis] + i * tstride.
@@ -729,13 +739,15 @@ struct CostTables {
     int C;
     float lam;
 };
+template <int C>
 __global__ void __launch_bounds__(256) cost_table3d_kernel(const CostTables ct) {
     const int ax = blockIdx.y;
-    const int64_t step = (int64_t)gridDim.x * blockDim.x;
+    const int64_t nw = (int64_t)gridDim.x * (blockDim.x / 32);
+    const int64_t w0 = (int64_t)blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
     for (int64_t i = 0; i < ct.count; ++i)
-        cost_table_axis(ct.img[ax] + i * ct.istride[ax], ct.cstride[ax], ct.C,
-                        ct.tab[ax] + i * ct.tstride[ax], ct.kstride[ax], ct.g[ax], ct.lam,
-                        (int64_t)blockIdx.x * blockDim.x + threadIdx.x, step);
+        cost_table_axis<C>(ct.img[ax] + i * ct.istride[ax], (int)ct.cstride[ax],
+                           ct.tab[ax] + i * ct.tstride[ax], (int)ct.kstride[ax], ct.g[ax], ct.lam,
+                           w0, nw);
 }
 
 template <int MODE, int CI, bool CODES, bool TMA, int R>
@@ -986,18 +998,19 @@ __global__ void __launch_bounds__(256) finish3d_batched_kernel(const Vol3DArgs* 
     }
 }
 
-// Cost tables of the batched instances that read them (blockIdx.y = instance).
+// Cost tables of the batched instances with C channels that read them
+// (blockIdx.y = instance).
+template <int C>
 __global__ void __launch_bounds__(256) cost_table3d_batched_kernel(const Vol3DArgs* desc) {
     const Vol3DArgs& a = desc[blockIdx.y];
-    if (a.mode != kModeTable) return;
-    const int64_t pl = a.D * a.H * a.Wp, plT = a.W * a.D * a.Hp;
-    const int64_t begin = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int64_t step = (int64_t)gridDim.x * blockDim.x;
-    cost_table_axis(a.image, pl, (int)a.C, a.tables, pl, a.pass[0], a.lambda, begin, step);
-    cost_table_axis(a.image, pl, (int)a.C, a.tables + kTabArrays * pl, pl, a.pass[2], a.lambda,
-                    begin, step);
-    cost_table_axis(a.imageT, plT, (int)a.C, a.tables + 2 * kTabArrays * pl, plT, a.pass[4],
-                    a.lambda, begin, step);
+    if (a.mode != kModeTable || a.C != C) return;
+    const int pl = (int)(a.D * a.H * a.Wp), plT = (int)(a.W * a.D * a.Hp);
+    const int64_t w0 = (int64_t)blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
+    const int64_t nw = (int64_t)gridDim.x * (blockDim.x / 32);
+    cost_table_axis<C>(a.image, pl, a.tables, pl, a.pass[0], a.lambda, w0, nw);
+    cost_table_axis<C>(a.image, pl, a.tables + kTabArrays * pl, pl, a.pass[2], a.lambda, w0, nw);
+    cost_table_axis<C>(a.imageT, plT, a.tables + 2 * kTabArrays * pl, plT, a.pass[4], a.lambda,
+                       w0, nw);
 }
 
 // One batched item in ring geometry R (R = 1 when some instance of the
@@ -1234,7 +1247,8 @@ bool plan_vol3d(const SweepArgs& f, const fgx_options* opt, int sms, Vol3DPlan* 
     // (the tensor-copy path); a size query (any_mode) covers them
     const int64_t W = f.pass[4].L, H = f.pass[2].L;
     const bool tab = (any_mode || vp->mode == kModeGeneral) && W % 4 == 0 && H % 4 == 0 &&
-                     W > 1 && !(opt && opt->no_cost_tables);
+                     W > 1 && !(opt && opt->no_cost_tables) &&
+                     (int64_t)kTabArrays * f.N < ((int64_t)1 << 31);
     if (tab) {
         vp->tab_off = vp->ws_bytes;
         vp->tab_bytes = al((size_t)f.B * 3 * 9 * f.N * 4);
@@ -1403,7 +1417,10 @@ int run_vol3d(const SweepArgs& f, const float* image, const float* mask, float* 
         ct.count = a.nimg;
         ct.C = (int)f.C;
         ct.lam = f.lambda;
-        cost_table3d_kernel<<<dim3((unsigned)(sms * 4), 3), 256, 0, s>>>(ct);
+        const dim3 tg((unsigned)(sms * 4), 3);
+        if (f.C == 1) cost_table3d_kernel<1><<<tg, 256, 0, s>>>(ct);
+        else if (f.C == 2) cost_table3d_kernel<2><<<tg, 256, 0, s>>>(ct);
+        else cost_table3d_kernel<3><<<tg, 256, 0, s>>>(ct);
         if (cudaGetLastError() != cudaSuccess) return FGX_ERR_CUDA;
     }
     cudaLaunchConfig_t cfg = {};
@@ -1441,7 +1458,8 @@ bool vol3d_instance_desc(void* desc, const fgx_instance& it, const SweepArgs& f,
     const int64_t Wp = (W + 3) / 4 * 4, Hp = (H + 3) / 4 * 4;
     const bool pitched = Wp != W;
     const bool img = vp.mode != kModeConst;
-    const bool tab = vp.mode == kModeGeneral && !(opt && opt->no_cost_tables);
+    const bool tab = vp.mode == kModeGeneral && !(opt && opt->no_cost_tables) &&
+                     (int64_t)kTabArrays * std::max(D * H * Wp, W * D * Hp) < ((int64_t)1 << 31);
     auto al = [](size_t x) { return (x + 255) & ~size_t(255); };
     // working copies: [pitched dist | pitched image] | transposed dist |
     // transposed image | [cost tables of the D, H and W axes]
@@ -1562,7 +1580,9 @@ int launch_vol3d_batched(const void* desc, int n, int rounds, const int* round_w
     transpose_image3d_batched_kernel<<<per_inst, 256, 0, s>>>(d);
     if (cudaGetLastError() != cudaSuccess) return FGX_ERR_CUDA;
     if (tables) {
-        cost_table3d_batched_kernel<<<per_inst, 256, 0, s>>>(d);
+        cost_table3d_batched_kernel<1><<<per_inst, 256, 0, s>>>(d);
+        cost_table3d_batched_kernel<2><<<per_inst, 256, 0, s>>>(d);
+        cost_table3d_batched_kernel<3><<<per_inst, 256, 0, s>>>(d);
         if (cudaGetLastError() != cudaSuccess) return FGX_ERR_CUDA;
     }
     Vol3DBatch bt;
