@@ -280,7 +280,7 @@ def measure_extras(fgx, dev, flush, stream, peak, steps=5, only=None):
             fn()
         t = _device_time(fn, steps, flush, stream)
         st = fgx.workspace_status(ws)
-        return t, st
+        return t, st, opts
 
     for name, make in [("2d_plain_256", lambda: workloads.plain2d()),
                        ("2d_large_lambda0", lambda: workloads.large2d(lam=0.0)),
@@ -290,9 +290,10 @@ def measure_extras(fgx, dev, flush, stream, peak, steps=5, only=None):
         if not want(name):
             continue
         c = make()
-        t, st = run_case(c)
+        t, st, opts = run_case(c)
         out[name] = {"ms": t * 1e3, "mvox_per_s_per_iter": c.voxels * c.iterations / t / 1e6,
                      "roofline": _roof(fwd_bytes(c), t, peak),
+                     "tile_options": opts or "default (autotuned)",
                      "device_status": fgx.status_string(st)}
 
     if want("fast_math"):

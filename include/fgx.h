@@ -63,7 +63,10 @@ typedef enum fgx_status {
  * sizeof(fgx_options) (forward compatibility). */
 typedef struct fgx_options {
     uint32_t size;
-    int32_t tile_lines;   /* lines per exchange block (ring width); 0 = auto */
+    int32_t tile_lines;   /* lines per exchange block (ring width); 0 = auto.  3D with
+                           * tile_width = tile_height = 0: 4 or 8 sets the ring width
+                           * of every pass of the plane-tile kernel (8 where its tiles
+                           * fit the grid); other values select the tiled engine */
     int32_t tile_width;   /* elements per tile along the inner in-line axis; 0 = auto */
     int32_t tile_height;  /* 3D: elements per tile along the outer in-line axis; 0 = auto */
     int32_t max_blocks;   /* cap on resident thread blocks; 0 = all that fit */

@@ -239,43 +239,52 @@ def _workspace(nbytes, device):
 # default.  Long single images favour long refresh blocks, many concurrent
 # tiles (batches) shorter ones with wider owned parts.
 TILE_CANDIDATES_2D = ((0, 0), (32, 64), (24, 80), (16, 96), (8, 112))
+# 3D: ring widths of the plane-tile kernel (0: the planner's per-pass choice,
+# 4: every pass narrow, 8: every pass wide where its tiles fit the grid).
+RING_CANDIDATES_3D = (0, 4, 8)
 _tuned = {}
 
 
 def autotune(image, mask, v, lam, iterations, spacing=None, reps=3, candidates=None):
-    """Times the 2D tile geometries on these inputs (fgx_autotune) and
-    returns the fastest as an options dict (None: the default), cached per
-    shape, channel count, lambda = 0 or not and iterations.  3D calls keep the
-    plane tiles (None)."""
+    """Times the tile geometries on these inputs (fgx_autotune) and returns
+    the fastest as an options dict (None: the default), cached per shape,
+    channel count, lambda = 0 or not and iterations: 2D the ring width and
+    owned columns of the line tiles, 3D the ring width of the plane tiles."""
     ndim = image.dim() - 2
     B, C, D, H, W = _shape(image, mask, ndim)
     key = (ndim, B, C, D, H, W, float(lam) == 0.0, int(iterations), image.device.index)
     if key in _tuned:
         return _tuned[key]
-    if ndim != 2:
-        _tuned[key] = None
-        return None
-    cands = candidates or TILE_CANDIDATES_2D
-    opts = (Options * len(cands))(*[Options(tile_lines=k, tile_width=t) for k, t in cands])
+    if ndim == 2:
+        cands = candidates or TILE_CANDIDATES_2D
+        opts = [Options(tile_lines=k, tile_width=t) for k, t in cands]
+    else:
+        cands = [(k, 0) for k in (candidates or RING_CANDIDATES_3D)]
+        opts = [Options(tile_lines=k) for k, _ in cands]
+    opts = (Options * len(cands))(*opts)
     dev = image.device
     with torch.cuda.device(dev):
         need = 0
         for o in opts:  # a candidate that cannot be planned is skipped by the tuner
             try:
-                need = max(need, workspace_size(2, B, C, 1, H, W, o))
+                need = max(need, workspace_size(ndim, B, C, D, H, W, o))
             except FgxError:
                 pass
         ws = _workspace(need, dev)
         out = torch.empty_like(mask)
         best = ctypes.c_int32(-1)
         ms = ctypes.c_float(0.0)
-        _check(lib().fgx_autotune(2, _ptr(image), _ptr(mask), _ptr(out), B, C, 1, H, W, None,
-                                  float(v), float(lam), int(iterations), _ptr(ws), ws.numel(),
+        _check(lib().fgx_autotune(ndim, _ptr(image), _ptr(mask), _ptr(out), B, C, D, H, W,
+                                  _spacing(spacing) if ndim == 3 else None, float(v), float(lam),
+                                  int(iterations), _ptr(ws), ws.numel(),
                                   ctypes.cast(opts, ctypes.c_void_p), len(cands), int(reps),
                                   ctypes.byref(best), ctypes.byref(ms), _stream()),
                "fgx_autotune")
     k, t = cands[best.value]
-    _tuned[key] = None if (k, t) == (0, 0) else dict(tile_lines=k, tile_width=t)
+    if (k, t) == (0, 0):
+        _tuned[key] = None
+    else:
+        _tuned[key] = dict(tile_lines=k, tile_width=t) if ndim == 2 else dict(tile_lines=k)
     return _tuned[key]
 
 

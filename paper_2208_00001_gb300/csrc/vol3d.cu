@@ -1186,7 +1186,11 @@ int64_t tiles_of(const PassGeom& g, int K) {
 bool plan_vol3d(const SweepArgs& f, const fgx_options* opt, int sms, Vol3DPlan* vp,
                 bool any_mode = false, bool wide = true) {
     if (f.ndim != 3) return false;
-    if (opt && (opt->tile_lines || opt->tile_width || opt->tile_height)) return false;
+    // tile_lines alone = 4 or 8 forces the ring width of every pass (8 where
+    // the tiles fit the grid); any other tile option selects the tiled engine
+    if (opt && (opt->tile_width || opt->tile_height)) return false;
+    const int force = opt ? opt->tile_lines : 0;
+    if (force && force != kRing && force != kRingWide) return false;
     vp->mode = f.cost_mode == kCostConst ? kModeConst
                : f.cost_mode == kCostAbs ? kModeAbs
                : f.cost_mode == kCostFast ? kModeFast : kModeGeneral;
@@ -1224,7 +1228,8 @@ bool plan_vol3d(const SweepArgs& f, const fgx_options* opt, int sms, Vol3DPlan* 
         int K = kRing;
         if (n8 <= cap) {
             xtiles = std::max(xtiles, n8);
-            if (wide && 3 * waves(n8) <= 4 * waves(n4)) K = kRingWide;
+            if (force ? force == kRingWide : wide && 3 * waves(n8) <= 4 * waves(n4))
+                K = kRingWide;
         }
         xtiles = std::max(xtiles, n4);
         const int t = kRP - 2 * K;

@@ -75,8 +75,19 @@ def test_batched_auto_options_match_plain_calls(fgx):
         _bits(o.cpu().numpy(), want, c.name)
 
 
-def test_autotune_3d_keeps_plane_tiles(fgx):
-    case = workloads.diff3d(shape=(12, 14, 16))
+@pytest.mark.parametrize("shape", [(12, 14, 16), (40, 72, 64)])
+def test_autotune_3d_ring_width(fgx, shape):
+    """The 3D tuner picks a ring width of the plane-tile kernel; every
+    candidate (the planner's choice, all passes narrow, all wide) gives the
+    oracle's result bit for bit."""
+    case = workloads.diff3d(shape=shape)
     img = torch.from_numpy(case.image).cuda()
     m = torch.from_numpy(case.mask).cuda()
-    assert fgx.autotune(img, m, case.v, case.lam, case.iterations) is None
+    choice = fgx.autotune(img, m, case.v, case.lam, case.iterations, spacing=case.spacing)
+    assert choice in (None, dict(tile_lines=4), dict(tile_lines=8))
+    want = oracle.gdt(case.image, case.mask, case.v, case.lam, case.iterations,
+                      spacing=case.spacing, threads=THREADS)
+    for opts in (choice, dict(tile_lines=4), dict(tile_lines=8)):
+        got = fgx.geodesic(img, m, case.v, case.lam, case.iterations, spacing=case.spacing,
+                           options=opts, check=True)
+        _bits(got.cpu().numpy(), want, f"3D ring option {opts}")
