@@ -318,6 +318,21 @@ int fgx_batched_run(const fgx_batched_plan* plan, void* stream);
 int fgx_geodesic_batched(const fgx_instance* items, int n, void* workspace,
                          size_t workspace_bytes, const fgx_options* opt, void* stream);
 
+/* Batch autotuner (no counterpart in the paper, which runs one instance at a
+ * time): prepares and runs the batch once per candidate option set, times
+ * `reps` further runs of each between CUDA events on `stream`, and writes the
+ * index of the fastest to *best_index and its mean time in ms to *best_ms.
+ * The 2D instances take the candidates' line-tile geometry; the 3D instances
+ * keep the plane tiles unless a candidate sets tile_height.  `workspace`
+ * must hold the largest fgx_batched_workspace_size of the candidates it is
+ * to try: a candidate whose plan does not fit it, or that the kernels cannot
+ * run (FGX_ERR_UNSUPPORTED), is skipped.  The instances' outputs hold the
+ * last candidate's results (all candidates give the same results).  Returns
+ * FGX_ERR_UNSUPPORTED when no candidate ran. */
+int fgx_batched_autotune(const fgx_instance* items, int n, void* workspace,
+                         size_t workspace_bytes, const fgx_options* candidates, int ncand,
+                         int reps, int* best_index, float* best_ms, void* stream);
+
 /* ----------------------------------------------------- differentiable ---- */
 
 /* Bytes of the `saved` buffer written by the training forward and read by

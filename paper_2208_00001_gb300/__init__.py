@@ -123,6 +123,8 @@ _SIGS = {
     "fgx_geodesic_batched": ([_vp, _i32, _vp, _sz, _vp, _vp], _i32),
     "fgx_batched_prepare": ([_vp, _i32, _vp, _sz, _vp, _vp, _vp], _i32),
     "fgx_batched_run": ([_vp, _vp], _i32),
+    "fgx_batched_autotune": ([_vp, _i32, _vp, _sz, _vp, _i32, _i32, ctypes.POINTER(_i32),
+                              ctypes.POINTER(_f32), _vp], _i32),
     "fgx_train_saved_size": ([_i32, _i64, _i64, _i64, _i64, _i32, ctypes.POINTER(_sz)], _i32),
     "fgx_geodesic2d_fwd_train": ([_vp, _vp, _vp, _i64, _i64, _i64, _i64, _f32, _f32, _i32, _vp,
                                   _sz, _vp, _sz, _vp, _vp], _i32),
@@ -701,28 +703,13 @@ class BatchedPlan:
 
     def __init__(self, instances, options=None):
         self.instances = list(instances)
-        self._parts = None
         if isinstance(options, str):
             if options != "auto":
                 raise ValueError("options: a dict, Options, None or 'auto'")
+            # the tuned 2D line-tile geometry; the library keeps the plane
+            # tiles of the 3D instances whatever 2D geometry the options carry
             i2 = [i for i, inst in enumerate(self.instances) if inst[0].dim() == 4]
-            i3 = [i for i, inst in enumerate(self.instances) if inst[0].dim() != 4]
             options = self._tune([self.instances[i] for i in i2]) if i2 else None
-            if options is not None and i3:
-                # tile options would also move the 3D instances to the tiled
-                # engine: the 2D instances get their own plan with the tuned
-                # geometry, the 3D ones keep the plane tiles
-                self._parts = [(i2, BatchedPlan([self.instances[i] for i in i2], options)),
-                               (i3, BatchedPlan([self.instances[i] for i in i3], None))]
-                self.options = options
-                self.outputs = [None] * len(self.instances)
-                for idx, part in self._parts:
-                    for j, i in enumerate(idx):
-                        self.outputs[i] = part.outputs[j]
-                self.plan = self._parts[0][1].plan
-                self.workspace = self._parts[0][1].workspace
-                self.device = self._parts[0][1].device
-                return
         self.options = options
         self.outputs = []
         arr = (Instance * max(1, len(self.instances)))()
@@ -756,44 +743,46 @@ class BatchedPlan:
 
     @staticmethod
     def _tune(instances, reps=2):
-        """The fastest 2D tile geometry for these (2D) instances: timed runs
-        of a plan per candidate."""
-        best, best_t = None, None
-        for k, t in TILE_CANDIDATES_2D:
-            opts = None if (k, t) == (0, 0) else dict(tile_lines=k, tile_width=t)
-            try:
-                plan = BatchedPlan(instances, opts)
-            except FgxError:
-                continue
-            plan.run()
-            s = torch.cuda.Event(enable_timing=True)
-            e = torch.cuda.Event(enable_timing=True)
-            s.record()
-            for _ in range(reps):
-                plan.run()
-            e.record()
-            e.synchronize()
-            ms = s.elapsed_time(e) / reps
-            if best_t is None or ms < best_t:
-                best, best_t = opts, ms
-        return best
+        """The fastest 2D line-tile geometry for this batch (fgx_batched_autotune
+        over the 2D candidates; the 3D instances keep the plane tiles)."""
+        cands = TILE_CANDIDATES_2D
+        opts = (Options * len(cands))(*[Options(tile_lines=k, tile_width=t) for k, t in cands])
+        arr = (Instance * max(1, len(instances)))()
+        outs = []
+        dev = None
+        for i, (img, m, v, lam, its, sp) in enumerate(instances):
+            ndim = img.dim() - 2
+            B, C, D, H, W = _shape(img, m, ndim)
+            out = torch.empty_like(m)
+            outs.append(out)
+            dev = img.device
+            sp3 = (1.0, 1.0, 1.0) if ndim == 2 else tuple(float(x) for x in sp)
+            arr[i] = Instance(ndim, C, D, H, W, img.data_ptr(), m.data_ptr(), out.data_ptr(),
+                              (ctypes.c_float * 3)(*sp3), float(v), float(lam), int(its))
+        need = 0
+        for o in opts:
+            n = ctypes.c_size_t(0)
+            if lib().fgx_batched_workspace_size(ctypes.byref(arr), len(instances), ctypes.byref(o),
+                                                ctypes.byref(n)) == OK:
+                need = max(need, n.value)
+        dev = dev or torch.device("cuda")
+        ws = _workspace(need, dev)
+        best = ctypes.c_int32(-1)
+        ms = ctypes.c_float(0.0)
+        with torch.cuda.device(dev):
+            _check(lib().fgx_batched_autotune(ctypes.byref(arr), len(instances), _ptr(ws),
+                                              ws.numel(), ctypes.cast(opts, ctypes.c_void_p),
+                                              len(cands), int(reps), ctypes.byref(best),
+                                              ctypes.byref(ms), _stream()),
+                   "fgx_batched_autotune")
+        k, t = cands[best.value]
+        return None if (k, t) == (0, 0) else dict(tile_lines=k, tile_width=t)
 
     def status(self):
-        """Synchronises and returns the device status of the last run (the
-        first failure over the plan's parts)."""
-        if self._parts:
-            for _, part in self._parts:
-                st = part.status()
-                if st != OK:
-                    return st
-            return OK
+        """Synchronises and returns the device status of the last run."""
         return workspace_status(self.workspace)
 
     def run(self, check=False):
-        if self._parts:
-            for _, part in self._parts:
-                part.run(check=check)
-            return self.outputs
         with torch.cuda.device(self.device):
             _check(lib().fgx_batched_run(ctypes.byref(self.plan), _stream()), "fgx_batched_run")
             if check:

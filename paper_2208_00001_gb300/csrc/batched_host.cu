@@ -113,12 +113,26 @@ int check_instance(const fgx_instance& it) {
     return FGX_OK;
 }
 
+// Options of the 3D instances of a batch: tile_lines and tile_width shape the
+// 2D line tiles (an autotuned batch carries them), so the 3D instances keep
+// the plane-tile kernel's own geometry; tile_height, a 3D tile extent, sends
+// them to the tiled engine with all three.
+const fgx_options* options_3d(const fgx_options* opt, fgx_options* buf) {
+    if (!opt || opt->tile_height) return opt;
+    *buf = *opt;
+    buf->tile_lines = 0;
+    buf->tile_width = 0;
+    return buf;
+}
+
 // Builds descriptors and the round/wave work list; pointers are checked only
 // when `check_ptrs`.
 int build_schedule(const fgx_instance* items, int n, const fgx_options* opt, bool check_ptrs,
                    Schedule* S) {
     if (n < 0 || (n > 0 && !items)) return FGX_ERR_ARG;
     if (n > 32767) return FGX_ERR_UNSUPPORTED;
+    fgx_options o3;
+    const fgx_options* opt3 = options_3d(opt, &o3);
     int sms = 0;
     int max_tiles_any = 1, flags_total = 0;
     S->desc.clear();
@@ -168,13 +182,13 @@ int build_schedule(const fgx_instance* items, int n, const fgx_options* opt, boo
             if (d < im + N * it.channels * 4 && im < d + N * 4) return FGX_ERR_ARG;
         }
         SweepArgs a;
-        st = plan_instance(it.ndim, it.channels, it.D, it.H, it.W, it.spacing, it.lambda, opt, &a,
-                           &sms);
+        st = plan_instance(it.ndim, it.channels, it.D, it.H, it.W, it.spacing, it.lambda,
+                           it.ndim == 3 ? opt3 : opt, &a, &sms);
         if (st != FGX_OK) return st;
         if (it.ndim == 3) {
             size_t xb = 0, wb = 0;
             int ci = 0, mt = 0, tiles[kMaxPasses];
-            if (vol3d_instance_desc(nullptr, it, a, opt, sms, nullptr, nullptr, nullptr, nullptr,
+            if (vol3d_instance_desc(nullptr, it, a, opt3, sms, nullptr, nullptr, nullptr, nullptr,
                                     &xb, &wb, &ci, &mt, tiles)) {
                 if (check_ptrs) {
                     if (!it.image || !it.mask || !it.dist) return FGX_ERR_ARG;
@@ -376,8 +390,10 @@ int fgx_batched_prepare(const fgx_instance* items, int n, void* workspace,
     for (size_t k = 0; k < S.v_index.size(); ++k) {
         size_t xb = 0, wb = 0;
         int ci = 0, mt = 0, tiles[kMaxPasses];
+        fgx_options o3;
         if (!vol3d_instance_desc(vdesc.data() + k * vol3d_desc_size(), items[S.v_index[k]],
-                                 S.v_args[k], opt, S.sms, w, (int*)(w + S.v_flag_off) + k,
+                                 S.v_args[k], options_3d(opt, &o3), S.sms, w,
+                                 (int*)(w + S.v_flag_off) + k,
                                  w + S.v_xbuf_off + S.v_xoff[k], w + S.v_work_off + S.v_woff[k],
                                  &xb, &wb, &ci, &mt, tiles))
             return FGX_ERR_UNSUPPORTED;
@@ -473,6 +489,54 @@ int fgx_batched_run(const fgx_batched_plan* plan, void* stream) {
     int st = batched_max_blocks_per_sm((size_t)plan->smem_bytes, &per_sm);
     if (st != FGX_OK) return st;
     return launch_batched(a, plan->grid, (size_t)plan->smem_bytes, stream);
+}
+
+int fgx_batched_autotune(const fgx_instance* items, int n, void* workspace,
+                         size_t workspace_bytes, const fgx_options* candidates, int ncand,
+                         int reps, int* best_index, float* best_ms, void* stream) {
+    if (!candidates || ncand < 1 || reps < 1 || !best_index || !best_ms) return FGX_ERR_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess) return FGX_ERR_CUDA;
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return FGX_ERR_CUDA;
+    }
+    int st = FGX_OK, best = -1;
+    float best_t = 0.f;
+    for (int i = 0; i < ncand && st == FGX_OK; ++i) {
+        size_t need = 0;
+        int r = fgx_batched_workspace_size(items, n, candidates + i, &need);
+        if (r == FGX_ERR_UNSUPPORTED || (r == FGX_OK && need > workspace_bytes)) continue;
+        if (r != FGX_OK) { st = r; break; }
+        fgx_batched_plan plan;
+        r = fgx_batched_prepare(items, n, workspace, workspace_bytes, candidates + i, &plan,
+                                stream);
+        if (r == FGX_ERR_UNSUPPORTED) continue;
+        if (r == FGX_OK) r = fgx_batched_run(&plan, stream);  // warm-up
+        if (r != FGX_OK) { st = r; break; }
+        if (cudaEventRecord(e0, s) != cudaSuccess) { st = FGX_ERR_CUDA; break; }
+        for (int k = 0; k < reps && r == FGX_OK; ++k) r = fgx_batched_run(&plan, stream);
+        if (r != FGX_OK) { st = r; break; }
+        float ms = 0.f;
+        if (cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+            cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+            st = FGX_ERR_CUDA;
+            break;
+        }
+        ms /= (float)reps;
+        if (best < 0 || ms < best_t) {
+            best = i;
+            best_t = ms;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (st != FGX_OK) return st;
+    if (best < 0) return FGX_ERR_UNSUPPORTED;
+    *best_index = best;
+    *best_ms = best_t;
+    return FGX_OK;
 }
 
 int fgx_geodesic_batched(const fgx_instance* items, int n, void* workspace,

@@ -61,7 +61,8 @@ def _small_mixed(seed=0):
     return cases
 
 
-@pytest.mark.parametrize("opts", [None, dict(max_blocks=24, tile_width=16, tile_lines=4)])
+@pytest.mark.parametrize("opts", [None, dict(max_blocks=24, tile_width=16, tile_lines=4),
+                                  dict(max_blocks=24, tile_width=16, tile_lines=4, tile_height=8)])
 def test_batched_small_mixed_bit_exact(fgx, opts):
     cases = _small_mixed()
     outs = fgx.geodesic_batched(_to_gpu(cases), options=opts, check=True)
