@@ -295,3 +295,25 @@ def test_error_codes(fgx):
     assert L.fgx_geodesic3d(P(d3), P(d3), P(o3), 1, 1, 2, 8, 8, sp, 1.0, 0.5, 1, P(ws), WS,
                             None, s) == fgx.ERR_ARG
     torch.cuda.synchronize()
+
+
+@pytest.mark.parametrize("shape,C", [((20, 36, 44), 1), ((17, 40, 28), 2), ((9, 64, 96), 3)])
+def test_cost_tables_3d(fgx, shape, C):
+    """The general 3D cost read from the per-call edge-cost tables (shapes
+    whose rows suit tensor copies) and computed in every pass
+    (no_cost_tables) both equal the oracle bit for bit, also with a forced
+    ring width and with parent codes."""
+    rng = np.random.default_rng(sum(shape) + C)
+    sp = tuple(float(x) for x in rng.uniform(0.5, 3.0, size=3))
+    case = workloads.random_case(rng, 3, shape, channels=C, lam=0.65, iterations=2, soft=True,
+                                 v=20.0, spacing=sp)
+    want = oracle_run(case)
+    for opts in (None, dict(no_cost_tables=1), dict(tile_lines=8), dict(tile_lines=4)):
+        assert_bit_exact(gpu_run(fgx, case, options=opts), want)
+    img = torch.from_numpy(case.image).cuda()
+    m = torch.from_numpy(case.mask).cuda()
+    d, saved = fgx.forward_train(img, m, case.v, case.lam, case.iterations, spacing=case.spacing)
+    dw, cw = oracle.gdt(case.image, case.mask, case.v, case.lam, case.iterations,
+                        spacing=case.spacing, return_codes=True, threads=THREADS)
+    assert_bit_exact(d.cpu().numpy(), dw)
+    assert np.array_equal(saved.cpu().numpy().reshape(cw.shape), cw)
