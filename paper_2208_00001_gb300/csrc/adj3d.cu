@@ -553,7 +553,11 @@ Adj3DKernel adj_kernel(bool store_a) {
 bool plan_adj3d(const SweepArgs& f, int iterations, const fgx_options* opt, int sms,
                 Adj3DPlan* p) {
     if (f.ndim != 3 || iterations <= 0) return false;
-    if (opt && (opt->tile_lines || opt->tile_width || opt->tile_height)) return false;
+    // the forward's ring-width option (tile_lines 4 or 8 alone) does not
+    // concern the reverse sweep's fixed ring; other tile options select the
+    // tiled engine
+    if (opt && (opt->tile_width || opt->tile_height)) return false;
+    if (opt && opt->tile_lines && opt->tile_lines != 4 && opt->tile_lines != 8) return false;
     // offsets within one instance (image channels included) are int
     if (f.C * f.N >= ((int64_t)1 << 31)) return false;
     int max_tiles = 1;

@@ -150,7 +150,10 @@ int plan_forward(int ndim, int64_t B, int64_t C, int64_t D, int64_t H, int64_t W
         pass_extents(axis, ext, &g);
         pass_offsets_t(ndim, axis, sp, lambda, g.t);
         for (int k = 0; k < 9; ++k) g.c[k] = std::sqrt(g.t[k]);  // IEEE square root
-        int K = (opt && opt->tile_lines) ? opt->tile_lines : (ndim == 3 ? 4 : 16);
+        // 3D tile_lines alone sets the plane-tile kernel's ring width: the
+        // tiled engine keeps its own default then
+        const bool ring_only = ndim == 3 && opt && !opt->tile_width && !opt->tile_height;
+        int K = (opt && opt->tile_lines && !ring_only) ? opt->tile_lines : (ndim == 3 ? 4 : 16);
         int tq = (opt && opt->tile_width) ? opt->tile_width : (ndim == 3 ? 16 : 128);
         int tp = ndim == 3 ? ((opt && opt->tile_height) ? opt->tile_height : 16) : 1;
         tq = (int)std::max<int64_t>(1, std::min<int64_t>(tq, std::max<int64_t>(g.Q, 1)));
