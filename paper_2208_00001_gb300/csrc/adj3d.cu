@@ -36,9 +36,10 @@ constexpr int kCW = 8;                    // compute warps
 constexpr int kPW = 4;                    // producer warps
 constexpr int kRP = kRows * kCW;          // region rows
 constexpr int kRQ = 32;                   // region columns (one per lane)
-constexpr int kRing = 4;                  // ring width = steps between refreshes
-constexpr int kTP = kRP - 2 * kRing;      // owned rows of a tile
-constexpr int kTQ = kRQ - 2 * kRing;      // owned columns of a tile
+constexpr int kRing = 4;                  // narrow ring width = steps between refreshes
+constexpr int kRingWide = 8;              // wide ring width (fewer refreshes, more tiles)
+constexpr int kTP = kRP - 2 * kRing;      // owned rows of a narrow-ring tile (the most)
+constexpr int kTQ = kRQ - 2 * kRing;      // owned columns of a narrow-ring tile
 constexpr int kPlane = kRP * kRQ;         // region voxels
 constexpr int kChunk = kRing;             // planes per staging chunk
 constexpr int kNst = 3;                   // chunks in the staging ring
@@ -95,6 +96,7 @@ struct Tile3 {
     const float* img;  // intensities of this instance in the pass's layout
     int64_t csl, csp, csq;  // strides of line, p and q in the image order of the codes
     int jp, jq, ntq, tile;
+    int K, tp, tq;     // ring width and owned extents (tp = tq = 32 - 2K)
     int64_t b;
     int L, nch;
     int64_t p0, q0;  // plane coordinates of region row 0 and column 0
@@ -116,7 +118,8 @@ __device__ bool exchange3(const XLink3& a, const Tile3& t, int w, unsigned int t
     const int lane = threadIdx.x & 31;
     unsigned long long* base = a.xbuf + (size_t)t.b * a.max_tiles * 2 * kXWords;
     unsigned long long* mine = base + ((size_t)t.tile * 2 + par) * kXWords;
-    const bool qown = lane >= kRing && lane < kRing + kTQ;
+    const int K = t.K, tp = t.tp, tq = t.tq;
+    const bool qown = lane >= K && lane < K + tq;
     const int64_t q = t.q0 + lane;
     const bool qin = q >= 0 && q < g.Q;
     const unsigned long long* src[kRows];
@@ -124,17 +127,17 @@ __device__ bool exchange3(const XLink3& a, const Tile3& t, int w, unsigned int t
 #pragma unroll
     for (int i = 0; i < kRows; ++i) {
         const int r = w * kRows + i;
-        const bool pown = r >= kRing && r < kRing + kTP;
+        const bool pown = r >= K && r < K + tp;
         const unsigned long long word =
             ((unsigned long long)tg << 32) | (unsigned int)__float_as_uint(d[i]);
-        if (pown && qown) st_relaxed_u64(mine + (r - kRing) * kTQ + (lane - kRing), word);
+        if (pown && qown) st_relaxed_u64(mine + (r - K) * tq + (lane - K), word);
         const int64_t p = t.p0 + r;
         need[i] = !(pown && qown) && qin && p >= 0 && p < g.P;
         src[i] = nullptr;
         if (need[i]) {
-            const int op = (int)(p / kTP), oq = (int)(q / kTQ);
-            const int lr = (int)(p - (int64_t)op * kTP), lq = (int)(q - (int64_t)oq * kTQ);
-            src[i] = base + ((size_t)(op * t.ntq + oq) * 2 + par) * kXWords + lr * kTQ + lq;
+            const int op = (int)(p / tp), oq = (int)(q / tq);
+            const int lr = (int)(p - (int64_t)op * tp), lq = (int)(q - (int64_t)oq * tq);
+            src[i] = base + ((size_t)(op * t.ntq + oq) * 2 + par) * kXWords + lr * tq + lq;
         }
     }
     long long t0 = 0;
@@ -183,6 +186,7 @@ struct Adj3DArgs {
     int in_first;             // adjoint of application t_hi-1: -1 = grad_dist, else G[in_first]
     PassGeom pass[kMaxPasses];
     int ntp[kMaxPasses], ntq[kMaxPasses];
+    int ring[kMaxPasses];     // ring width K of each pass (4 or 8)
     int max_tiles;
     unsigned long long* xbuf;
     unsigned int* barrier;
@@ -263,14 +267,15 @@ __device__ bool adj_compute3(const Adj3DArgs& a, const Tile3& t, int t_app, AdjH
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int64_t q = t.q0 + lane;
     const bool qin = q >= 0 && q < g.Q;
-    const bool qown = lane >= kRing && lane < kRing + kTQ;
+    const int K = t.K, tp = t.tp, tq = t.tq;
+    const bool qown = lane >= K && lane < K + tq;
     bool own[kRows];
     int64_t goff[kRows];
 #pragma unroll
     for (int i = 0; i < kRows; ++i) {
         const int r = w * kRows + i;
         const int64_t p = t.p0 + r;
-        own[i] = qin && p >= 0 && p < g.P && qown && r >= kRing && r < kRing + kTP;
+        own[i] = qin && p >= 0 && p < g.P && qown && r >= K && r < K + tp;
         goff[i] = p * g.sp + q * g.sq;
     }
     const int cl = max(lane - 1, 0), cr = min(lane + 1, kRQ - 1);
@@ -352,7 +357,7 @@ __device__ bool adj_compute3(const Adj3DArgs& a, const Tile3& t, int t_app, AdjH
         }
 #pragma unroll
         for (int i = 0; i < kRows; ++i) ap[i] = na[i];
-        if (s >= kRing && s % kRing == 0 && s + 1 < t.L) {
+        if (s >= K && s % K == 0 && s + 1 < t.L) {
             if (!failed && !exchange3(XLink3{a.xbuf, a.max_tiles, a.status, a.timeout_ns}, t, w,
                                       tag_base | (unsigned int)(xi + 1), xi & 1, ap))
                 failed = true;
@@ -518,8 +523,10 @@ __global__ void __launch_bounds__(kBlock3, 1) adj3d_kernel(const Adj3DArgs a) {
             t.b = b;
             t.L = L;
             t.nch = nch;
-            t.p0 = (int64_t)t.jp * kTP - kRing;
-            t.q0 = (int64_t)t.jq * kTQ - kRing;
+            t.K = a.ring[pass];
+            t.tp = t.tq = kRP - 2 * t.K;
+            t.p0 = (int64_t)t.jp * t.tp - t.K;
+            t.q0 = (int64_t)t.jq * t.tq - t.K;
             const float* gsrc = (in_idx < 0 ? a.grad_dist : a.G[in_idx]) + b * a.N;
             if ((int)(threadIdx.x >> 5) >= kCW) {
                 adj_producer3(a, t, gsrc,
@@ -541,7 +548,7 @@ __global__ void __launch_bounds__(kBlock3, 1) adj3d_kernel(const Adj3DArgs a) {
 
 struct Adj3DPlan {
     int grid = 0, max_tiles = 0;
-    int ntp[kMaxPasses] = {}, ntq[kMaxPasses] = {};
+    int ntp[kMaxPasses] = {}, ntq[kMaxPasses] = {}, ring[kMaxPasses] = {};
     size_t xbuf_off = 0, g_off[2] = {}, a_off = 0, total = 0;
 };
 
@@ -560,15 +567,6 @@ bool plan_adj3d(const SweepArgs& f, int iterations, const fgx_options* opt, int 
     if (opt && opt->tile_lines && opt->tile_lines != 4 && opt->tile_lines != 8) return false;
     // offsets within one instance (image channels included) are int
     if (f.C * f.N >= ((int64_t)1 << 31)) return false;
-    int max_tiles = 1;
-    for (int i = 0; i < kMaxPasses; ++i) {
-        const PassGeom& g = f.pass[i];
-        p->ntp[i] = (int)std::max<int64_t>(1, (g.P + kTP - 1) / kTP);
-        p->ntq[i] = (int)std::max<int64_t>(1, (g.Q + kTQ - 1) / kTQ);
-        if ((int64_t)p->ntp[i] * p->ntq[i] > (1 << 20)) return false;
-        max_tiles = std::max(max_tiles, p->ntp[i] * p->ntq[i]);
-    }
-    p->max_tiles = max_tiles;
     const size_t smem = adj3_smem_bytes();
     for (Adj3DKernel k : {adj_kernel(false), adj_kernel(true)})
         if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
@@ -579,9 +577,32 @@ bool plan_adj3d(const SweepArgs& f, int iterations, const fgx_options* opt, int 
                                                       smem) != cudaSuccess ||
         per_sm < 1)
         return false;
-    int64_t grid = (int64_t)per_sm * sms;
-    if (opt && opt->max_blocks) grid = std::min<int64_t>(grid, opt->max_blocks);
-    grid = std::min<int64_t>(grid, std::max<int64_t>(1, f.B * max_tiles));
+    int64_t cap = (int64_t)per_sm * sms;
+    if (opt && opt->max_blocks) cap = std::min<int64_t>(cap, opt->max_blocks);
+    // per pass the ring is 8 wide (16 x 16 owned, half the refreshes) where
+    // its tiles still fit the grid in about as few waves as the narrow
+    // ring's (the rule of the forward plane tiles)
+    const int64_t B = std::max<int64_t>(f.B, 1);
+    auto tiles = [](const PassGeom& g, int K) {
+        const int64_t t = kRP - 2 * K;
+        return std::max<int64_t>(1, (g.P + t - 1) / t) * std::max<int64_t>(1, (g.Q + t - 1) / t);
+    };
+    auto waves = [&](int64_t n) { return (B + cap / n - 1) / (cap / n); };
+    int max_tiles = 1;
+    for (int i = 0; i < kMaxPasses; ++i) {
+        const PassGeom& g = f.pass[i];
+        const int64_t n4 = tiles(g, kRing), n8 = tiles(g, kRingWide);
+        if (n4 > (1 << 20) || n4 > cap) return false;
+        int K = kRing;
+        if (n8 <= cap && 3 * waves(n8) <= 4 * waves(n4)) K = kRingWide;
+        const int t = kRP - 2 * K;
+        p->ring[i] = K;
+        p->ntp[i] = (int)std::max<int64_t>(1, (g.P + t - 1) / t);
+        p->ntq[i] = (int)std::max<int64_t>(1, (g.Q + t - 1) / t);
+        max_tiles = std::max(max_tiles, p->ntp[i] * p->ntq[i]);
+    }
+    p->max_tiles = max_tiles;
+    int64_t grid = std::min<int64_t>(cap, B * max_tiles);
     if (grid < max_tiles) return false;
     p->grid = (int)grid;
     auto al = [](size_t x) { return (x + 255) & ~size_t(255); };
@@ -642,6 +663,7 @@ int run_adj3d(const SweepArgs& f, const float* grad_dist, const float* image,
         a.pass[i] = f.pass[i];
         a.ntp[i] = p.ntp[i];
         a.ntq[i] = p.ntq[i];
+        a.ring[i] = p.ring[i];
     }
     a.max_tiles = p.max_tiles;
     a.xbuf = (unsigned long long*)(w + p.xbuf_off);
