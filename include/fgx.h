@@ -434,7 +434,8 @@ int fgx_geodesic3d_bwd_checkpoint(const float* grad_dist, const float* image, co
                                   size_t workspace_bytes, const fgx_options* opt, void* stream);
 
 /* Scratch bytes of fgx_geodesic_bwd_params: the reverse sweep's workspace
- * (fgx_backward_workspace_size) plus three arrays of B*D*H*W floats. */
+ * (fgx_backward_workspace_size) plus three arrays of B*D*H*W floats and 8 KB
+ * of float64 partial sums. */
 int fgx_params_workspace_size(int ndim, int64_t B, int64_t C, int64_t D, int64_t H, int64_t W,
                               int iterations, const fgx_options* opt, size_t* bytes);
 

@@ -698,18 +698,20 @@ int check_3d_args(const float spacing[3], float v, float lambda, int iterations)
 }
 
 struct ParamsLayout {
-    size_t g0_off, lt_off, vt_off, total;
+    size_t g0_off, lt_off, vt_off, part_off, total;
 };
 
 // Workspace of the parameter gradients: the reverse sweep's workspace, then
-// G0 and scratch for the two per-element term arrays.
+// G0, scratch for the two per-element term arrays and the float64 partial
+// sums.
 ParamsLayout params_layout(size_t bwd, int64_t n) {
     ParamsLayout l;
     const size_t arr = align256((size_t)std::max<int64_t>(n, 1) * sizeof(float));
     l.g0_off = align256(bwd);
     l.lt_off = l.g0_off + arr;
     l.vt_off = l.lt_off + arr;
-    l.total = l.vt_off + arr;
+    l.part_off = l.vt_off + arr;
+    l.total = l.part_off + align256(param_partials_bytes());
     return l;
 }
 
@@ -924,7 +926,8 @@ int fgx_geodesic_bwd_params(int ndim, const float* grad_dist, const float* image
     if (st != FGX_OK) return st;
     DeviceInfo dev;
     if ((st = current_device(&dev)) != FGX_OK) return st;
-    return run_param_sums(mask, g0, vt, lt, grad_lambda, grad_v, n, dev.sms, stream);
+    return run_param_sums(mask, g0, vt, lt, grad_lambda, grad_v, (double*)(w + l.part_off), n,
+                          dev.sms, stream);
 }
 
 

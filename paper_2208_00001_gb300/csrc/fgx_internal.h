@@ -223,8 +223,11 @@ int run_adj3d(const SweepArgs& f, const float* grad_dist, const float* image,
 // Parameter gradients (param_grads.cu): v_terms = mask * g0 per element, then
 // grad_lambda / grad_v (device doubles, nullable) = float64 sums of
 // lambda_terms / v_terms by a fixed-shape tree.
+// float64 partial sums of the parameter gradients (bytes of the scratch)
+size_t param_partials_bytes();
 int run_param_sums(const float* mask, const float* g0, float* v_terms, const float* lambda_terms,
-                   double* grad_lambda, double* grad_v, int64_t n, int sms, void* stream);
+                   double* grad_lambda, double* grad_v, double* partials, int64_t n, int sms,
+                   void* stream);
 
 // Failure-detection check (wait_probe.cu): one bounded wait on a tag that
 // nothing writes.

@@ -942,23 +942,20 @@ __device__ void transpose_round(const Vol3DBatch& bt, int r, bool back, float* s
 __global__ void __launch_bounds__(256) init3d_batched_kernel(const Vol3DArgs* desc) {
     const Vol3DArgs& a = desc[blockIdx.y];
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    const int64_t HW = a.H * a.W;
     const float* img = a.image_src ? a.image_src : a.image;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.N; i += stride) {
-        const float d0 = __fmul_rn(a.v, a.mask[i]);
-        if (a.out) {
-            const int64_t z = i / HW, y = (i - z * HW) / a.W, x = i - z * HW - y * a.W;
-            a.dist[(z * a.H + y) * a.Wp + x] = d0;
-        } else {
-            a.dist[i] = d0;
-        }
-    }
+    // one warp per row of W voxels (rows of the caller's layout to rows of
+    // the pitched copy), lanes along the row
+    const int lane = threadIdx.x & 31;
+    const int64_t w0 = (int64_t)blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
+    const int64_t nw = (int64_t)gridDim.x * (blockDim.x / 32);
+    const int64_t rows = a.D * a.H;
+    for (int64_t r = w0; r < rows; r += nw)
+        for (int64_t x = lane; x < a.W; x += 32)
+            a.dist[r * a.Wp + x] = __fmul_rn(a.v, a.mask[r * a.W + x]);
     if (a.image_src && a.mode != kModeConst)
-        for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.C * a.N;
-             i += stride) {
-            const int64_t z = i / HW, y = (i - z * HW) / a.W, x = i - z * HW - y * a.W;
-            const_cast<float*>(a.image)[(z * a.H + y) * a.Wp + x] = a.image_src[i];
-        }
+        for (int64_t r = w0; r < a.C * rows; r += nw)
+            for (int64_t x = lane; x < a.W; x += 32)
+                const_cast<float*>(a.image)[r * a.Wp + x] = a.image_src[r * a.W + x];
     if (a.mode != kModeAbs) return;
     int* flag = const_cast<int*>(a.range_flag);
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.C * a.N; i += stride) {
@@ -990,12 +987,11 @@ __global__ void __launch_bounds__(256) transpose_image3d_batched_kernel(const Vo
 __global__ void __launch_bounds__(256) finish3d_batched_kernel(const Vol3DArgs* desc) {
     const Vol3DArgs& a = desc[blockIdx.y];
     if (!a.out) return;
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    const int64_t HW = a.H * a.W;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.N; i += stride) {
-        const int64_t z = i / HW, y = (i - z * HW) / a.W, x = i - z * HW - y * a.W;
-        a.out[i] = __ldcg(a.dist + (z * a.H + y) * a.Wp + x);
-    }
+    const int lane = threadIdx.x & 31;
+    const int64_t w0 = (int64_t)blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
+    const int64_t nw = (int64_t)gridDim.x * (blockDim.x / 32);
+    for (int64_t r = w0; r < a.D * a.H; r += nw)
+        for (int64_t x = lane; x < a.W; x += 32) a.out[r * a.W + x] = __ldcg(a.dist + r * a.Wp + x);
 }
 
 // Cost tables of the batched instances with C channels that read them
