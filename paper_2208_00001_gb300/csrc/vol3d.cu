@@ -444,6 +444,7 @@ __device__ bool compute3(const Vol3DArgs& a, const Tile3& t, int t_app, Head3& h
     constexpr int PF = Stage3<CI>::kPlaneF;
     constexpr int kNst = Ring3<R>::kNst, kChunk = Ring3<R>::kChunk, kSlots = Ring3<R>::kSlots;
     const PassGeom& g = *t.g;
+    const bool early = kTab && g.dir > 0;  // the previous plane's slot is released a step early
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int rows0 = w * kRows;
     const int q = t.q0 + lane;
@@ -512,10 +513,15 @@ __device__ bool compute3(const Vol3DArgs& a, const Tile3& t, int t_app, Head3& h
         h.rowtop[rb][w][lane] = d[0];
         h.rowbot[rb][w][lane] = d[kRows - 1];
         compute_sync();
-        // plane s-2 is no longer read by any compute warp: its chunk slot is
+        // plane s-2 is no longer read by any compute warp (plane s-1 already,
+        // in a forward sweep reading cost tables: its costs sit at the
+        // voxel, so the previous plane's slot is not read): its chunk slot is
         // free once it was the chunk's last plane
-        if (threadIdx.x == 0 && s >= 2 && ((s - 2) & (kChunk - 1)) == kChunk - 1)
-            mbar_arrive3(&h.empty[(cb + (s - 2) / kChunk) % kNst]);
+        if (threadIdx.x == 0) {
+            const int fp = s - (early ? 1 : 2);
+            if (fp >= 0 && (fp & (kChunk - 1)) == kChunk - 1)
+                mbar_arrive3(&h.empty[(cb + fp / kChunk) % kNst]);
+        }
         float col[kRows + 2], lft[kRows + 2], rgt[kRows + 2];
         col[0] = w > 0 ? h.rowbot[rb][w - 1][lane] : kInf3;
 #pragma unroll
@@ -601,10 +607,12 @@ __device__ bool compute3(const Vol3DArgs& a, const Tile3& t, int t_app, Head3& h
     }
     compute_sync();
     if (threadIdx.x == 0) {
-        // free the chunks still held (those whose last plane is one of the last two)
+        // free the chunks still held (those whose last plane is one of the
+        // last two, or the last one)
+        const int held = early ? 1 : 2;
         for (int c = max(0, t.nch - 2); c < t.nch; ++c) {
             const int last = min(c * kChunk + kChunk - 1, t.L - 1);
-            if (last >= t.L - 2) mbar_arrive3(&h.empty[(cb + c) % kNst]);
+            if (last >= t.L - held) mbar_arrive3(&h.empty[(cb + c) % kNst]);
         }
     }
     return !failed;
