@@ -137,6 +137,9 @@ struct Vol3DArgs {  // aligned as CUtensorMap (the descriptor arrays of batched 
     float* out;
     const float* image_src;
     float* tables;  // batched cost tables: D axis, H axis ([9][D][H][Wp] each), W axis ([9][W][D][Hp])
+    // strides of line, p and q of every pass in the caller's [D][H][W] order
+    // (the codes' layout)
+    int64_t csl[kMaxPasses], csp[kMaxPasses], csq[kMaxPasses];
 };
 
 struct Head3 {
@@ -229,6 +232,7 @@ struct Tile3 {
     const float* img;  // intensities of this instance in the pass's layout (channel stride N)
     uint8_t* codes;    // this application's codes of the instance (image order), or null
     int64_t csl, csp, csq;  // strides of line, p and q in the image order of the codes
+    int64_t cst;       // channel stride of the intensities in the pass's layout
     int tile, ntq, L, nch;
     int K, tp, tq;     // ring width and owned extents (tp = tq = 32 - 2K)
     int p0, q0;        // plane coordinates of region row 0 and column 0
@@ -349,7 +353,7 @@ __device__ bool producer3(const Vol3DArgs& a, const Tile3& t, Head3& h, float* s
 #pragma unroll
                 for (int ch = 0; ch < CI; ++ch)
                     cp_async4(dr + (unsigned int)((1 + ch) * kArr) * 4u,
-                              in ? (const void*)(img + ch * a.N + off) : (const void*)g_zero4v);
+                              in ? (const void*)(img + ch * t.cst + off) : (const void*)g_zero4v);
             }
             lo += dsl;
         }
@@ -637,6 +641,55 @@ __global__ void __launch_bounds__(256) init3d_kernel(const float* mask, float* d
     }
 }
 
+// One 32 x 32 tile of a transpose between the two pitched layouts of an
+// instance, by one warp: forward from [D][H][sp] to [W][D][dp] (sp, dp: row
+// pitches), back the other way.  unit = (d, tile row, tile column) over the
+// H x W plane of slice d.  `tile`: this warp's 32 x 33 floats of shared
+// memory.  The sources may have been written by other blocks of the same
+// launch: read through L2.
+__device__ void transpose_unit(const float* src, float* dst, int64_t D, int64_t H, int64_t W,
+                               int64_t sp, int64_t dp, bool back, int64_t unit, float* tile) {
+    const int lane = threadIdx.x & 31;
+    const int64_t th = (H + 31) / 32, tw = (W + 31) / 32;
+    const int64_t d = unit / (th * tw), rem = unit - d * (th * tw);
+    const int64_t h0 = (rem / tw) * 32, w0 = (rem % tw) * 32;
+    float v[32];
+    if (!back) {
+        // rows h0 + y, columns w0 + lane of slice d
+#pragma unroll
+        for (int y = 0; y < 32; ++y) {
+            const int64_t h = h0 + y, w = w0 + lane;
+            v[y] = (h < H && w < W) ? __ldcg(src + (d * H + h) * sp + w) : 0.0f;
+        }
+    } else {
+        // rows w0 + y, columns h0 + lane of the transposed slice d
+#pragma unroll
+        for (int y = 0; y < 32; ++y) {
+            const int64_t w = w0 + y, h = h0 + lane;
+            v[y] = (h < H && w < W) ? __ldcg(src + (w * D + d) * sp + h) : 0.0f;
+        }
+    }
+#pragma unroll
+    for (int y = 0; y < 32; ++y) tile[y * 33 + lane] = v[y];
+    __syncwarp();
+#pragma unroll
+    for (int y = 0; y < 32; ++y) {
+        const float x = tile[lane * 33 + y];
+        if (!back) {
+            const int64_t w = w0 + y, h = h0 + lane;
+            if (w < W && h < H) dst[(w * D + d) * dp + h] = x;
+        } else {
+            const int64_t h = h0 + y, w = w0 + lane;
+            if (w < W && h < H) dst[(d * H + h) * dp + w] = x;
+        }
+    }
+    __syncwarp();
+}
+
+__device__ __forceinline__ int64_t transpose_units(const Vol3DArgs& a) {
+    return a.D * ((a.H + 31) / 32) * ((a.W + 31) / 32);
+}
+
 // Transposes `count` arrays of R x W floats (R = D*H) into W x R (back:
 // W x R into R x W).  Each of `nwarps` warps of a block moves whole 32 x 32
 // tiles through its own 32 x 33 shared tile (32 loads in flight per lane);
@@ -676,13 +729,87 @@ __device__ void transpose_rw(const float* src, float* dst, int64_t count, int64_
     __syncthreads();
 }
 
-// The image in the W passes' layout, once per call (all SMs, before the
+// The distance transposes of a single call around the W passes: every
+// instance between [D][H][Wp] (the working distances) and [W][D][Hp], 32 x 32
+// tiles spread over kTransposeWarps warps of every block (dense layouts as
+// one tall matrix per instance, which runs faster).
+__device__ void transpose_single(const Vol3DArgs& a, bool back, float* smem) {
+    if (a.Wp == a.W && a.Hp == a.H) {
+        // dense layouts: one [D*H][W] matrix per instance
+        transpose_rw(back ? a.distT : a.dist, back ? a.dist : a.distT, a.B, a.D * a.H, a.W, back,
+                     smem, kTransposeWarps);
+        return;
+    }
+    const int warp = threadIdx.x >> 5;
+    if (warp < kTransposeWarps) {
+        float* tile = smem + warp * (32 * 33);
+        const int64_t nw = (int64_t)gridDim.x * kTransposeWarps;
+        const int64_t per = transpose_units(a);
+        const int64_t nd = a.D * a.H * a.Wp, nt = a.W * a.D * a.Hp;
+        for (int64_t u = (int64_t)blockIdx.x * kTransposeWarps + warp; u < a.B * per; u += nw) {
+            const int64_t b = u / per;
+            const float* src = back ? a.distT + b * nt : a.dist + b * nd;
+            float* dst = back ? a.dist + b * nd : a.distT + b * nt;
+            transpose_unit(src, dst, a.D, a.H, a.W, back ? a.Hp : a.Wp, back ? a.Wp : a.Hp, back,
+                           u - b * per, tile);
+        }
+    }
+    __syncthreads();
+}
+
+// The image of a single call in the W passes' layout [nimg][C][W][D][Hp], once
+// per call from the caller's [nimg][C][D][H][W] (all SMs, before the
 // persistent launch).
 __global__ void __launch_bounds__(256) transpose_image3d_kernel(const float* image, float* imageT,
-                                                                int64_t count, int64_t R,
-                                                                int64_t W) {
+                                                                int64_t count, int64_t D,
+                                                                int64_t H, int64_t W,
+                                                                int64_t Hp) {
     __shared__ float smem[8 * 32 * 33];
-    transpose_rw(image, imageT, count, R, W, false, smem, 8);
+    if (Hp == H) {
+        transpose_rw(image, imageT, count, D * H, W, false, smem, 8);
+        return;
+    }
+    const int warp = threadIdx.x >> 5;
+    const int64_t per = D * ((H + 31) / 32) * ((W + 31) / 32);
+    for (int64_t u = (int64_t)blockIdx.x * 8 + warp; u < count * per; u += (int64_t)gridDim.x * 8) {
+        const int64_t c = u / per;
+        transpose_unit(image + c * D * H * W, imageT + c * W * D * Hp, D, H, W, W, Hp, false,
+                       u - c * per, smem + warp * (32 * 33));
+    }
+}
+
+// Pitched working copies of a single call (instance blockIdx.y): the
+// distances [D][H][Wp] (D0 = v * M, or the caller's distances when the call
+// resumes from them) and, for instances below nimg, the image; one warp per
+// row of W voxels.
+__global__ void __launch_bounds__(256) pitch3d_kernel(const Vol3DArgs a, bool resume) {
+    const int64_t b = blockIdx.y;
+    const int lane = threadIdx.x & 31;
+    const int64_t w0 = (int64_t)blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
+    const int64_t nw = (int64_t)gridDim.x * (blockDim.x / 32);
+    const int64_t rows = a.D * a.H, nd = rows * a.Wp;
+    for (int64_t r = w0; r < rows; r += nw)
+        for (int64_t x = lane; x < a.W; x += 32) {
+            const int64_t i = b * a.N + r * a.W + x;
+            a.dist[b * nd + r * a.Wp + x] = resume ? a.out[i] : __fmul_rn(a.v, a.mask[i]);
+        }
+    if (a.image_src && b < a.nimg)
+        for (int64_t r = w0; r < a.C * rows; r += nw)
+            for (int64_t x = lane; x < a.W; x += 32)
+                const_cast<float*>(a.image)[b * a.C * nd + r * a.Wp + x] =
+                    a.image_src[b * a.C * a.N + r * a.W + x];
+}
+
+// The caller's distances from the pitched working copies (instance blockIdx.y).
+__global__ void __launch_bounds__(256) unpitch3d_kernel(const Vol3DArgs a) {
+    const int64_t b = blockIdx.y;
+    const int lane = threadIdx.x & 31;
+    const int64_t w0 = (int64_t)blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
+    const int64_t nw = (int64_t)gridDim.x * (blockDim.x / 32);
+    const int64_t rows = a.D * a.H, nd = rows * a.Wp;
+    for (int64_t r = w0; r < rows; r += nw)
+        for (int64_t x = lane; x < a.W; x += 32)
+            a.out[b * a.N + r * a.W + x] = __ldcg(a.dist + b * nd + r * a.Wp + x);
 }
 
 // Edge-cost tables of one axis (the general cost, once per call instead of in
@@ -804,14 +931,15 @@ __global__ void __launch_bounds__(TMA ? (kCW + kTW) * 32 : (kCW + kPW) * 32, 1)
     const int napps = a.iterations * kMaxPasses;
     bool alive = true;
     const bool tw = a.distT != nullptr;
-    const int64_t DH = a.D * a.H;  // rows of the transposes
+    // instance strides of the working and transposed layouts
+    const int64_t nd = a.D * a.H * a.Wp, nt = a.W * a.D * a.Hp;
 
     for (int t_app = 0; t_app < napps && alive; ++t_app) {
         const int pass = t_app % kMaxPasses;
         const PassGeom& g = a.pass[pass];
         const bool on_t = tw && pass >= 4;  // this pass runs on the transposed copies
         if (tw && pass == 4) {
-            transpose_rw(a.dist, a.distT, a.B, DH, a.W, false, stage, kTransposeWarps);
+            transpose_single(a, false, stage);
             if (!(alive = grid_barrier(a.barrier, epoch++, a.status, a.timeout_ns))) break;
         }
         const int ntiles = a.ntp[pass] * a.ntq[pass];
@@ -829,12 +957,13 @@ __global__ void __launch_bounds__(TMA ? (kCW + kTW) * 32 : (kCW + kPW) * 32, 1)
             t.tile = blockIdx.x % ntiles;
             t.ntq = a.ntq[pass];
             t.b = b;
-            t.dist = (on_t ? a.distT : a.dist) + b * a.N;
-            t.img = (on_t ? a.imageT : a.image) + (b % a.nimg) * a.C * a.N;
+            t.dist = on_t ? a.distT + b * nt : a.dist + b * nd;
+            t.img = on_t ? a.imageT + (b % a.nimg) * a.C * nt : a.image + (b % a.nimg) * a.C * nd;
             t.codes = CODES ? a.codes + ((int64_t)t_app * a.B + b) * a.N : nullptr;
-            t.csl = on_t ? 1 : g.sl;
-            t.csp = on_t ? a.H * a.W : g.sp;
-            t.csq = on_t ? a.W : g.sq;
+            t.csl = a.csl[pass];
+            t.csp = a.csp[pass];
+            t.csq = a.csq[pass];
+            t.cst = on_t ? nt : nd;
             t.L = L;
             t.nch = nch;
             t.K = a.ring[pass];
@@ -849,7 +978,7 @@ __global__ void __launch_bounds__(TMA ? (kCW + kTW) * 32 : (kCW + kPW) * 32, 1)
         }
         alive = grid_barrier(a.barrier, epoch++, a.status, a.timeout_ns);
         if (alive && tw && pass == 5) {
-            transpose_rw(a.distT, a.dist, a.B, DH, a.W, true, stage, kTransposeWarps);
+            transpose_single(a, true, stage);
             alive = grid_barrier(a.barrier, epoch++, a.status, a.timeout_ns);
         }
         if (blockIdx.x == 0 && threadIdx.x == 0 && t_app + 1 < 16)
@@ -872,55 +1001,6 @@ struct Vol3DBatch {
     int* status;
     long long timeout_ns;
 };
-
-// One 32 x 32 tile of a transpose between the two pitched layouts of an
-// instance, by one warp: forward from [D][H][sp] to [W][D][dp] (sp, dp: row
-// pitches), back the other way.  unit = (d, tile row, tile column) over the
-// H x W plane of slice d.  `tile`: this warp's 32 x 33 floats of shared
-// memory.  The sources may have been written by other blocks of the same
-// launch: read through L2.
-__device__ void transpose_unit(const float* src, float* dst, int64_t D, int64_t H, int64_t W,
-                               int64_t sp, int64_t dp, bool back, int64_t unit, float* tile) {
-    const int lane = threadIdx.x & 31;
-    const int64_t th = (H + 31) / 32, tw = (W + 31) / 32;
-    const int64_t d = unit / (th * tw), rem = unit - d * (th * tw);
-    const int64_t h0 = (rem / tw) * 32, w0 = (rem % tw) * 32;
-    float v[32];
-    if (!back) {
-        // rows h0 + y, columns w0 + lane of slice d
-#pragma unroll
-        for (int y = 0; y < 32; ++y) {
-            const int64_t h = h0 + y, w = w0 + lane;
-            v[y] = (h < H && w < W) ? __ldcg(src + (d * H + h) * sp + w) : 0.0f;
-        }
-    } else {
-        // rows w0 + y, columns h0 + lane of the transposed slice d
-#pragma unroll
-        for (int y = 0; y < 32; ++y) {
-            const int64_t w = w0 + y, h = h0 + lane;
-            v[y] = (h < H && w < W) ? __ldcg(src + (w * D + d) * sp + h) : 0.0f;
-        }
-    }
-#pragma unroll
-    for (int y = 0; y < 32; ++y) tile[y * 33 + lane] = v[y];
-    __syncwarp();
-#pragma unroll
-    for (int y = 0; y < 32; ++y) {
-        const float x = tile[lane * 33 + y];
-        if (!back) {
-            const int64_t w = w0 + y, h = h0 + lane;
-            if (w < W && h < H) dst[(w * D + d) * dp + h] = x;
-        } else {
-            const int64_t h = h0 + y, w = w0 + lane;
-            if (w < W && h < H) dst[(d * H + h) * dp + w] = x;
-        }
-    }
-    __syncwarp();
-}
-
-__device__ __forceinline__ int64_t transpose_units(const Vol3DArgs& a) {
-    return a.D * ((a.H + 31) / 32) * ((a.W + 31) / 32);
-}
 
 // The distance transposes of round r of a batched launch: every instance
 // that applies pass 4 in this round (forward) or applied pass 5 (back).
@@ -1076,6 +1156,7 @@ __global__ void __launch_bounds__(kBlockBatched3, 1) vol3d_batched_kernel(const 
             t.img = on_t ? a.imageT : a.image;
             t.codes = nullptr;
             t.csl = t.csp = t.csq = 0;
+            t.cst = on_t ? a.W * a.D * a.Hp : a.D * a.H * a.Wp;
             t.L = (int)g.L;
             t.nch = t.L > 1 ? (t.L + Ring3<R>::kChunk - 1) / Ring3<R>::kChunk : 0;
             t.K = a.ring[pass];
@@ -1151,15 +1232,16 @@ bool make_map(CUtensorMap* m, const void* base, uint64_t d0, uint64_t d1, uint64
 bool make_maps(Vol3DArgs& a) {
     const uint64_t D = (uint64_t)a.D, H = (uint64_t)a.H, W = (uint64_t)a.W;
     const uint64_t B = (uint64_t)a.B, BC = (uint64_t)(a.nimg * a.C);
-    if (W % 4 || H % 4 || !a.distT) return false;
+    const uint64_t Wp = (uint64_t)a.Wp, Hp = (uint64_t)a.Hp;
+    if (Wp % 4 || Hp % 4 || !a.distT) return false;
     if (D > (1u << 30) || H > (1u << 30) || W > (1u << 30) || BC > (1u << 30)) return false;
-    bool ok = make_map(&a.tmap[kMapDistD], a.dist, W, H, D, B, kRQ, kRP, 1, true) &&
-              make_map(&a.tmap[kMapDistH], a.dist, W, H, D, B, kRQ, 1, kRP, true) &&
-              make_map(&a.tmap[kMapDistW], a.distT, H, D, W, B, kRQ, kRP, 1, true);
+    bool ok = make_map(&a.tmap[kMapDistD], a.dist, W, H, D, B, kRQ, kRP, 1, true, Wp) &&
+              make_map(&a.tmap[kMapDistH], a.dist, W, H, D, B, kRQ, 1, kRP, true, Wp) &&
+              make_map(&a.tmap[kMapDistW], a.distT, H, D, W, B, kRQ, kRP, 1, true, Hp);
     if (ok && a.mode != kModeConst)
-        ok = make_map(&a.tmap[kMapImgD], a.image, W, H, D, BC, kRQ, kRP, 1, false) &&
-             make_map(&a.tmap[kMapImgH], a.image, W, H, D, BC, kRQ, 1, kRP, false) &&
-             make_map(&a.tmap[kMapImgW], a.imageT, H, D, W, BC, kRQ, kRP, 1, false);
+        ok = make_map(&a.tmap[kMapImgD], a.image, W, H, D, BC, kRQ, kRP, 1, false, Wp) &&
+             make_map(&a.tmap[kMapImgH], a.image, W, H, D, BC, kRQ, 1, kRP, false, Wp) &&
+             make_map(&a.tmap[kMapImgW], a.imageT, H, D, W, BC, kRQ, kRP, 1, false, Hp);
     return ok;
 }
 
@@ -1169,10 +1251,12 @@ struct Vol3DPlan {
     size_t smem = 0, ws_bytes = 0;
     size_t zero_bytes = 0;             // header and exchange words (cleared per call)
     size_t distT_off = 0, imageT_off = 0;  // transposed copies for the W passes
-    // cost tables (general cost on tensor-copy layouts): [B][9][N] for the D
-    // axis, then the H axis, then the W axis in its [W][D][H] layout;
+    // cost tables (general cost on tensor-copy layouts): [B][9][D][H][Wp] for
+    // the D axis, then the H axis, then the W axis in its [W][D][Hp] layout;
     // ws_bytes includes them when tab_bytes > 0, ws_min_bytes does not
     size_t tab_off = 0, tab_bytes = 0, ws_min_bytes = 0;
+    int64_t Wp = 0, Hp = 0;            // row pitches of the working and transposed layouts
+    size_t pd_off = 0, pi_off = 0;     // pitched working copies of the distances and image (or 0)
 };
 
 int64_t tiles_of(const PassGeom& g, int K) {
@@ -1248,19 +1332,33 @@ bool plan_vol3d(const SweepArgs& f, const fgx_options* opt, int sms, Vol3DPlan* 
     vp->grid = (int)std::min<int64_t>(cap, B * max_tiles);
     auto al = [](size_t x) { return (x + 255) & ~size_t(255); };
     vp->zero_bytes = kHeaderBytes + (size_t)B * xtiles * 2 * kXWords * 8;
+    // rows padded to 16 bytes (pitches Wp, Hp) so that every plane stages by
+    // tensor copies: the W passes' transposed copies always carry the pitch
+    // Hp; with W not a multiple of 4 the distances and the image also get
+    // pitched working copies (results copied back after the launch).  A
+    // volume with W = 1 has no W passes and keeps the caller's arrays.
+    const int64_t D = f.pass[0].L, H = f.pass[2].L, W = f.pass[4].L;
+    vp->Wp = W > 1 ? (W + 3) / 4 * 4 : W;
+    vp->Hp = W > 1 ? (H + 3) / 4 * 4 : H;
+    const size_t nd = (size_t)D * H * vp->Wp, nt = (size_t)W * D * vp->Hp;
     vp->distT_off = al(vp->zero_bytes);
-    vp->imageT_off = vp->distT_off + al((size_t)f.B * f.N * 4);
-    vp->ws_bytes = vp->imageT_off + al((size_t)f.B * f.C * f.N * 4);
+    vp->imageT_off = vp->distT_off + al((size_t)f.B * nt * 4);
+    vp->ws_bytes = vp->imageT_off + al((size_t)f.B * f.C * nt * 4);
+    vp->pd_off = vp->pi_off = 0;
+    if (vp->Wp != W) {
+        vp->pd_off = vp->ws_bytes;
+        vp->pi_off = vp->pd_off + al((size_t)f.B * nd * 4);
+        vp->ws_bytes = vp->pi_off + al((size_t)f.B * f.C * nd * 4);
+    }
     vp->ws_min_bytes = vp->ws_bytes;
-    // the general cost reads tables when every staged row is 16-byte aligned
-    // (the tensor-copy path); a size query (any_mode) covers them
-    const int64_t W = f.pass[4].L, H = f.pass[2].L;
-    const bool tab = (any_mode || vp->mode == kModeGeneral) && W % 4 == 0 && H % 4 == 0 &&
-                     W > 1 && !(opt && opt->no_cost_tables) &&
-                     (int64_t)kTabArrays * f.N < ((int64_t)1 << 31);
+    // the general cost reads tables on the tensor-copy path (W > 1); a size
+    // query (any_mode) covers them
+    const bool tab = (any_mode || vp->mode == kModeGeneral) && W > 1 &&
+                     !(opt && opt->no_cost_tables) &&
+                     (int64_t)kTabArrays * (int64_t)std::max(nd, nt) < ((int64_t)1 << 31);
     if (tab) {
         vp->tab_off = vp->ws_bytes;
-        vp->tab_bytes = al((size_t)f.B * 3 * 9 * f.N * 4);
+        vp->tab_bytes = al((size_t)f.B * 9 * (2 * nd + nt) * 4);
         vp->ws_bytes += vp->tab_bytes;
     }
     return true;
@@ -1360,13 +1458,37 @@ int run_vol3d(const SweepArgs& f, const float* image, const float* mask, float* 
     a.D = f.pass[0].L;
     a.H = f.pass[2].L;
     a.W = f.pass[4].L;
+    a.Wp = vp.Wp;
+    a.Hp = vp.Hp;
+    // the codes keep the caller's element order: (line, p, q) strides of
+    // every pass in [D][H][W] (the W passes' lines are columns)
+    for (int i = 0; i < kMaxPasses; ++i) {
+        a.csl[i] = i < 4 ? f.pass[i].sl : 1;
+        a.csp[i] = i < 4 ? f.pass[i].sp : a.H * a.W;
+        a.csq[i] = i < 4 ? f.pass[i].sq : a.W;
+    }
     if (a.W > 1) {
-        // the W passes run on [W][D][H] copies: their planes' rows are contiguous
+        // the W passes run on [W][D][Hp] copies: their planes' rows are contiguous
         a.distT = (float*)(w + vp.distT_off);
         a.imageT = vp.mode == kModeConst ? nullptr : (float*)(w + vp.imageT_off);
         for (int i = 4; i < 6; ++i) {
-            a.pass[i].sl = a.D * a.H;
-            a.pass[i].sp = a.H;
+            a.pass[i].sl = a.D * a.Hp;
+            a.pass[i].sp = a.Hp;
+            a.pass[i].sq = 1;
+        }
+    }
+    if (vp.pd_off) {
+        // rows of W floats are not 16-byte aligned: the passes run on pitched
+        // working copies [D][H][Wp] and the results are copied back
+        a.dist = (float*)(w + vp.pd_off);
+        a.out = dist;
+        if (vp.mode != kModeConst) {
+            a.image = (const float*)(w + vp.pi_off);
+            a.image_src = image;
+        }
+        for (int i = 0; i < 4; ++i) {
+            a.pass[i].sl = i < 2 ? a.H * a.Wp : a.Wp;
+            a.pass[i].sp = i < 2 ? a.Wp : a.H * a.Wp;
             a.pass[i].sq = 1;
         }
     }
@@ -1377,15 +1499,16 @@ int run_vol3d(const SweepArgs& f, const float* image, const float* mask, float* 
     size_t smem = vp.smem;
     const bool tab = tma && vp.mode == kModeGeneral && vp.tab_bytes > 0 && ws_bytes >= vp.ws_bytes;
     float* tabs[3] = {nullptr, nullptr, nullptr};
+    const int64_t nd = a.D * a.H * a.Wp, nt = a.W * a.D * a.Hp;
     if (tab) {
         const uint64_t D = (uint64_t)a.D, H = (uint64_t)a.H, W = (uint64_t)a.W;
         const uint64_t n9 = (uint64_t)a.nimg * kTabArrays;
         tabs[0] = (float*)(w + vp.tab_off);
-        tabs[1] = tabs[0] + n9 * (uint64_t)f.N;
-        tabs[2] = tabs[1] + n9 * (uint64_t)f.N;
-        if (make_map(&a.tmap[kMapImgD], tabs[0], W, H, D, n9, kRQ, kRP, 1, false) &&
-            make_map(&a.tmap[kMapImgH], tabs[1], W, H, D, n9, kRQ, 1, kRP, false) &&
-            make_map(&a.tmap[kMapImgW], tabs[2], H, D, W, n9, kRQ, kRP, 1, false)) {
+        tabs[1] = tabs[0] + n9 * (uint64_t)nd;
+        tabs[2] = tabs[1] + n9 * (uint64_t)nd;
+        if (make_map(&a.tmap[kMapImgD], tabs[0], W, H, D, n9, kRQ, kRP, 1, false, a.Wp) &&
+            make_map(&a.tmap[kMapImgH], tabs[1], W, H, D, n9, kRQ, 1, kRP, false, a.Wp) &&
+            make_map(&a.tmap[kMapImgW], tabs[2], H, D, W, n9, kRQ, kRP, 1, false, a.Hp)) {
             a.mode = kModeTable;
             smem = stage_bytes(kTabArrays, 1);
         } else if (!make_maps(a)) {
@@ -1400,13 +1523,20 @@ int run_vol3d(const SweepArgs& f, const float* image, const float* mask, float* 
         return FGX_ERR_CUDA;
     const int64_t n = f.B * f.N;
     const int ig = (int)std::min<int64_t>((n + 255) / 256, (int64_t)sms * 16);
-    init3d_kernel<<<std::max(ig, 1), 256, 0, s>>>(mask, resume ? nullptr : dist, v, n, image,
-                                                 a.nimg * f.C * f.N,
+    // D0 (into the caller's distances unless they are pitched or the call
+    // resumes) and the intensity range test
+    init3d_kernel<<<std::max(ig, 1), 256, 0, s>>>(mask, resume || a.out ? nullptr : dist, v, n,
+                                                 image, a.nimg * f.C * f.N,
                                                  vp.mode == kModeAbs ? range_flag : nullptr);
     if (cudaGetLastError() != cudaSuccess) return FGX_ERR_CUDA;
+    if (a.out) {
+        pitch3d_kernel<<<dim3((unsigned)std::max(1, sms * 4), (unsigned)f.B), 256, 0, s>>>(a,
+                                                                                      resume);
+        if (cudaGetLastError() != cudaSuccess) return FGX_ERR_CUDA;
+    }
     if (a.imageT && f.iterations > 0) {
-        transpose_image3d_kernel<<<sms * 8, 256, 0, s>>>(image, a.imageT, a.nimg * f.C,
-                                                          a.D * a.H, a.W);
+        transpose_image3d_kernel<<<sms * 8, 256, 0, s>>>(image, a.imageT, a.nimg * f.C, a.D, a.H,
+                                                          a.W, a.Hp);
         if (cudaGetLastError() != cudaSuccess) return FGX_ERR_CUDA;
     }
     if (f.iterations == 0) return FGX_OK;
@@ -1415,13 +1545,14 @@ int run_vol3d(const SweepArgs& f, const float* image, const float* mask, float* 
         std::memset(&ct, 0, sizeof(ct));
         const int src_pass[3] = {0, 2, 4};
         for (int ax = 0; ax < 3; ++ax) {
-            ct.img[ax] = ax < 2 ? image : a.imageT;
+            const int64_t pl = ax < 2 ? nd : nt;
+            ct.img[ax] = ax < 2 ? a.image : a.imageT;
             ct.tab[ax] = tabs[ax];
             ct.g[ax] = a.pass[src_pass[ax]];
-            ct.cstride[ax] = f.N;
-            ct.kstride[ax] = f.N;
-            ct.istride[ax] = f.C * f.N;
-            ct.tstride[ax] = kTabArrays * f.N;
+            ct.cstride[ax] = pl;
+            ct.kstride[ax] = pl;
+            ct.istride[ax] = f.C * pl;
+            ct.tstride[ax] = kTabArrays * pl;
         }
         ct.count = a.nimg;
         ct.C = (int)f.C;
@@ -1450,6 +1581,10 @@ int run_vol3d(const SweepArgs& f, const float* image, const float* mask, float* 
         return FGX_ERR_CUDA;
     if (cudaLaunchKernelEx(&cfg, k, a) != cudaSuccess)
         return FGX_ERR_CUDA;
+    if (a.out) {
+        unpitch3d_kernel<<<dim3((unsigned)std::max(1, sms * 4), (unsigned)f.B), 256, 0, s>>>(a);
+        if (cudaGetLastError() != cudaSuccess) return FGX_ERR_CUDA;
+    }
     return FGX_OK;
 }
 
