@@ -24,29 +24,35 @@
 // warp edge (the shuffle returns the lane's own value there); it lies outside
 // the exact cone from the first step on, so no owned voxel depends on it.
 //
-// Staging.  Old distances and intensities of upcoming planes sit in a shared
-// ring of kNst chunks of kChunk planes; each staged array has a spare row
-// above and below the region, so every parent load of a lane is one base
-// register plus a constant offset.  Two ways to fill it:
-//  * tensor memory accelerator (when every plane row of the pass layout is
-//    16-byte aligned): one producer warp copies the plane tiles of a chunk
+// Staging.  Old distances and intensities (or cost tables) of upcoming
+// planes sit in a shared ring of kNst chunks of kChunk planes (Ring3); each
+// staged array has a spare row above and below the region, so every parent
+// load of a lane is one base register plus a constant offset.  Rows of the
+// pass layouts are padded to 16 bytes where needed (pitched working copies
+// of the distances and image, transposed copies for the W passes).  Two
+// ways to fill the ring:
+//  * tensor memory accelerator (every volume with W > 1): one producer warp
+//    copies the plane tiles of a chunk
 //    as boxes (cp.async.bulk.tensor, one box per lane) as soon as the chunk
 //    slot is free, completed on the slot's mbarrier by transaction count;
 //    outside the volume the copy fills distances with NaN (a NaN candidate
 //    never wins fminf, exactly like +inf) and intensities with 0.  Issuing
 //    the copies from a compute thread put them on the plane steps' critical
 //    path (about a quarter of the step time, measured);
-//  * otherwise four producer warps copy the tile with per-lane 4-byte
-//    cp.async (voxels outside the volume: distance +inf, intensity 0).
+//  * otherwise (W = 1, or no tensor-map encoder) four producer warps copy
+//    the tile with per-lane 4-byte cp.async (voxels outside the volume:
+//    distance +inf, intensity 0).
 //
-// Edge costs are evaluated on the fly in the fixed order of the method:
+// Edge costs, in the fixed order of the method:
 //  constant (lambda = 0): sqrt(t_k), one constant per stencil offset;
 //  absolute (lambda = 1, one channel): |I(x) - I(y)|, which equals
 //    sqrt_rn(fl(d*d)) for d = 0 and 2^-63 <= |d| <= 2^63; a first kernel
 //    checks that every intensity is 0 or has magnitude in [2^-40, 2^62],
 //    which bounds every difference to that range; otherwise each candidate
 //    is checked and falls back to the square root;
-//  general: sqrt_rn(t_k + lambda * sum_ch (I(x)-I(y))^2);
+//  general: sqrt_rn(t_k + lambda * sum_ch (I(x)-I(y))^2), read from tables
+//    written once per call (nine per voxel and axis) on the tensor-copy
+//    path, else evaluated in every pass;
 //  fast (fast-math option, forward without codes): the general formula with
 //    fused multiply-adds and the approximate square root.
 #include <cuda.h>  // CUtensorMap and its encoder's signature (the encoder is looked up at run time)
