@@ -297,12 +297,13 @@ def test_error_codes(fgx):
     torch.cuda.synchronize()
 
 
-@pytest.mark.parametrize("shape,C", [((20, 36, 44), 1), ((17, 40, 28), 2), ((9, 64, 96), 3)])
+@pytest.mark.parametrize("shape,C", [((20, 36, 44), 1), ((17, 40, 28), 2), ((9, 64, 96), 3),
+                                     ((15, 37, 29), 1), ((11, 30, 45), 2)])
 def test_cost_tables_3d(fgx, shape, C):
-    """The general 3D cost read from the per-call edge-cost tables (shapes
-    whose rows suit tensor copies) and computed in every pass
-    (no_cost_tables) both equal the oracle bit for bit, also with a forced
-    ring width and with parent codes."""
+    """The general 3D cost read from the per-call edge-cost tables and
+    computed in every pass (no_cost_tables) both equal the oracle bit for
+    bit, also with a forced ring width and with parent codes; W or H not a
+    multiple of 4 runs on pitched working copies."""
     rng = np.random.default_rng(sum(shape) + C)
     sp = tuple(float(x) for x in rng.uniform(0.5, 3.0, size=3))
     case = workloads.random_case(rng, 3, shape, channels=C, lam=0.65, iterations=2, soft=True,
