@@ -88,6 +88,17 @@ typedef struct fgx_options {
                              * whose size query then includes them; a workspace too
                              * small for them computes the costs in every pass instead,
                              * with identical results); 1 = never (smaller workspace) */
+    int32_t split_sms;    /* batches holding both 2D instances (line-chain launch) and
+                           * 3D instances (plane-tile launch): the two launches run at
+                           * the same time, the 2D one on a stream of the library's own
+                           * forked from and joined back into the caller's stream,
+                           * each with one thread block per SM of its share; n = the
+                           * SMs of the 2D launch (the 3D launch gets the rest;
+                           * clamped so that the largest instance of each launch has
+                           * all its tiles resident, else one launch after the other),
+                           * 0 = shares estimated from the work of each part, -1 = one
+                           * launch after the other, each on every SM.  Results are
+                           * the same bit for bit whatever the shares */
 } fgx_options;
 
 /* Human-readable name of a status code (static string). */
@@ -292,7 +303,8 @@ typedef struct fgx_batched_plan {
     int32_t n3d, grid3d, rounds3d, smem3d;
     uint64_t desc3d_off, waves3d_off, items3d_off;
     int32_t tables3d;       /* 1: some 3D instance reads cost tables (staging ring of single planes) */
-    int32_t reserved3d;
+    int32_t concurrent;     /* 1: the line-chain and plane-tile launches run at the same
+                             * time on disjoint SM shares (grid2d + grid3d <= SMs) */
 } fgx_batched_plan;
 
 /* Workspace bytes for a batched launch of these instances. */
@@ -308,9 +320,16 @@ int fgx_batched_prepare(const fgx_instance* items, int n, void* workspace,
                         size_t workspace_bytes, const fgx_options* opt,
                         fgx_batched_plan* plan, void* stream);
 
-/* Runs a prepared plan: clears the plan's progress tags and launches the one
- * persistent kernel that computes every instance.  Allocates nothing and
- * copies nothing from the host, so it can be captured in a CUDA graph. */
+/* Runs a prepared plan: clears the plan's progress tags and launches the
+ * persistent kernels that compute every instance (line chain, plane tiles,
+ * tiled engine: those the plan holds).  With plan->concurrent the line-chain
+ * launch runs on a stream of the library's own, created with two events per
+ * host thread and device on first use (fgx_batched_prepare creates them for
+ * its thread) and kept until the thread exits; it waits for the caller's
+ * stream and the caller's stream waits for it, so the call stays ordered on
+ * `stream` as a whole.  Allocates nothing and copies nothing from the host,
+ * so it can be captured in a CUDA graph (the fork and join become graph
+ * edges). */
 int fgx_batched_run(const fgx_batched_plan* plan, void* stream);
 
 /* fgx_batched_prepare followed by fgx_batched_run.  Results equal n separate

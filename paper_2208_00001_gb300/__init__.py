@@ -47,12 +47,12 @@ class Options(ctypes.Structure):
                 ("tile_width", ctypes.c_int32), ("tile_height", ctypes.c_int32),
                 ("max_blocks", ctypes.c_int32), ("timeout_ms", ctypes.c_int32),
                 ("segments", ctypes.c_int32), ("fast_math", ctypes.c_int32),
-                ("no_cost_tables", ctypes.c_int32)]
+                ("no_cost_tables", ctypes.c_int32), ("split_sms", ctypes.c_int32)]
 
     def __init__(self, tile_lines=0, tile_width=0, tile_height=0, max_blocks=0, timeout_ms=0,
-                 segments=0, fast_math=0, no_cost_tables=0):
+                 segments=0, fast_math=0, no_cost_tables=0, split_sms=0):
         super().__init__(ctypes.sizeof(Options), tile_lines, tile_width, tile_height, max_blocks,
-                         timeout_ms, segments, fast_math, no_cost_tables)
+                         timeout_ms, segments, fast_math, no_cost_tables, split_sms)
 
 
 class Instance(ctypes.Structure):
@@ -80,7 +80,7 @@ class BatchedPlanC(ctypes.Structure):
                 ("n3d", ctypes.c_int32), ("grid3d", ctypes.c_int32), ("rounds3d", ctypes.c_int32),
                 ("smem3d", ctypes.c_int32), ("desc3d_off", ctypes.c_uint64),
                 ("waves3d_off", ctypes.c_uint64), ("items3d_off", ctypes.c_uint64),
-                ("tables3d", ctypes.c_int32), ("reserved3d", ctypes.c_int32)]
+                ("tables3d", ctypes.c_int32), ("concurrent", ctypes.c_int32)]
 
 
 _i64, _i32, _f32, _vp, _sz = (ctypes.c_int64, ctypes.c_int, ctypes.c_float, ctypes.c_void_p,
@@ -244,6 +244,10 @@ TILE_CANDIDATES_2D = ((0, 0), (32, 64), (24, 80), (16, 96), (8, 112))
 # 3D: ring widths of the plane-tile kernel (0: the planner's per-pass choice,
 # 4: every pass narrow, 8: every pass wide where its tiles fit the grid).
 RING_CANDIDATES_3D = (0, 4, 8)
+# Batches of 2D and 3D instances: SM shares of the 2D launch tried beside the
+# library's estimate (0) and one launch after the other (-1), as fractions of
+# the SM count.
+SPLIT_FRACTIONS = (0.2, 0.26, 0.32, 0.4)
 _tuned = {}
 
 
@@ -706,10 +710,24 @@ class BatchedPlan:
         if isinstance(options, str):
             if options != "auto":
                 raise ValueError("options: a dict, Options, None or 'auto'")
-            # the tuned 2D line-tile geometry; the library keeps the plane
-            # tiles of the 3D instances whatever 2D geometry the options carry
-            i2 = [i for i, inst in enumerate(self.instances) if inst[0].dim() == 4]
-            options = self._tune([self.instances[i] for i in i2]) if i2 else None
+            # the tuned 2D line-tile geometry (the library keeps the plane
+            # tiles of the 3D instances whatever 2D geometry the options
+            # carry), then, with 2D and 3D instances, the SM share of the 2D
+            # launch running beside the 3D one
+            i2 = [inst for inst in self.instances if inst[0].dim() == 4]
+            has3 = len(i2) < len(self.instances)
+            options = {}
+            if i2:
+                cands = [dict(tile_lines=k, tile_width=t) if (k, t) != (0, 0) else {}
+                         for k, t in TILE_CANDIDATES_2D]
+                options = cands[self._tune(i2, cands)]
+            if i2 and has3:
+                dev = self.instances[0][0].device
+                sms = torch.cuda.get_device_properties(dev).multi_processor_count
+                splits = [0, -1] + [max(1, round(f * sms)) for f in SPLIT_FRACTIONS]
+                cands = [dict(options, split_sms=x) for x in splits]
+                options = cands[self._tune(self.instances, cands)]
+            options = options or None
         self.options = options
         self.outputs = []
         arr = (Instance * max(1, len(self.instances)))()
@@ -742,11 +760,10 @@ class BatchedPlan:
         self.device = dev
 
     @staticmethod
-    def _tune(instances, reps=2):
-        """The fastest 2D line-tile geometry for this batch (fgx_batched_autotune
-        over the 2D candidates; the 3D instances keep the plane tiles)."""
-        cands = TILE_CANDIDATES_2D
-        opts = (Options * len(cands))(*[Options(tile_lines=k, tile_width=t) for k, t in cands])
+    def _tune(instances, cands, reps=2):
+        """Index of the fastest option set of `cands` (dicts) for this batch
+        (fgx_batched_autotune)."""
+        opts = (Options * len(cands))(*[Options(**c) for c in cands])
         arr = (Instance * max(1, len(instances)))()
         outs = []
         dev = None
@@ -775,8 +792,7 @@ class BatchedPlan:
                                               len(cands), int(reps), ctypes.byref(best),
                                               ctypes.byref(ms), _stream()),
                    "fgx_batched_autotune")
-        k, t = cands[best.value]
-        return None if (k, t) == (0, 0) else dict(tile_lines=k, tile_width=t)
+        return best.value
 
     def status(self):
         """Synchronises and returns the device status of the last run."""

@@ -5,11 +5,19 @@
 // passes per iteration, FastGeodis Implementation section).  2D instances
 // run on the line-chain kernel, 3D instances on the plane-tile kernel, the
 // rest (tile options, more channels than it stages) on the tiled engine: up
-// to three persistent launches on the caller's stream.  In each, instances advance one
-// pass application per round; a round packs whole instances into waves of
+// to three persistent launches.  In each, instances advance one pass
+// application per round; a round packs whole instances into waves of
 // co-resident thread blocks (first fit), so the tiles of an instance that
 // wait on one another always run together; rounds are separated by a grid
 // barrier inside the launch.
+//
+// The line-chain and plane-tile launches of a batch holding both run at the
+// same time: the 2D one on a side stream forked from the caller's stream,
+// each with one block per SM of a disjoint share.  Their blocks never share
+// an SM (neither kernel leaves room for a block of the other) and together
+// they number at most the SM count, so every block of both launches is
+// resident at once and neither launch waits for SMs the other holds; each
+// waits only on its own blocks, with its own grid-barrier counter.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -49,6 +57,9 @@ struct Schedule {
     std::vector<int> v_round_waves, v_wave_items;
     int v_grid = 0, v_rounds = 0, v_ci = 0, v_max_tiles = 0;
     int sms = 0;
+    // line-chain and plane-tile launches at the same time: SM shares
+    bool concurrent = false;
+    int c_sms = 0, v_sms = 0;
     size_t v_smem = 0, v_xbuf_bytes = 0, v_work_bytes = 0, v_work_off = 0;
     size_t v_flag_off = 0, v_xbuf_off = 0, v_desc_off = 0, v_waves_off = 0, v_items_off = 0;
 };
@@ -123,6 +134,56 @@ const fgx_options* options_3d(const fgx_options* opt, fgx_options* buf) {
     buf->tile_lines = 0;
     buf->tile_width = 0;
     return buf;
+}
+
+// SMs for the line-chain launch when it runs beside the plane-tile launch:
+// the share of the estimated work of the 2D part, counted in tile steps (one
+// line of a 2D tile, one plane of a 3D tile) weighted 0.3 : 1.7, the ratio
+// that put the split of the 64 + 16 instance batch (2D sides 128..1024, 3D
+// 64..192) near its measured best on GB300.  An estimate: the batch
+// autotuner times shares around it.
+int split_estimate(const Schedule& S, const fgx_instance* items, int sms) {
+    double w2 = 0.0, w3 = 0.0;
+    for (size_t k = 0; k < S.c_index.size(); ++k) {
+        const fgx_instance& it = items[S.c_index[k]];
+        w2 += 2.0 * it.iterations * ((double)S.c_tiles_v[k] * it.H + (double)S.c_tiles_h[k] * it.W);
+    }
+    for (size_t k = 0; k < S.v_index.size(); ++k)
+        for (int r = 0; r < kMaxPasses; ++r)
+            w3 += (double)items[S.v_index[k]].iterations * S.v_tiles[k][r] *
+                  (double)S.v_args[k].pass[r].L;
+    w2 *= 0.3;
+    w3 *= 1.7;
+    if (!(w2 + w3 > 0.0)) return sms / 2;
+    return (int)std::lround(sms * w2 / (w2 + w3));
+}
+
+// Plans the plane tiles of the 3D instances again for `share` SMs (ring
+// widths and tile counts); false, with the schedule unchanged, when an
+// instance needs more tiles than that.
+bool replan_vol3d(const fgx_instance* items, const fgx_options* opt3, int share, Schedule* S) {
+    const size_t n = S->v_index.size();
+    std::vector<std::vector<int>> tiles(n);
+    std::vector<size_t> xoff(n);
+    size_t xbytes = 0;
+    int max_tiles = 0;
+    for (size_t k = 0; k < n; ++k) {
+        size_t xb = 0, wb = 0;
+        int ci = 0, mt = 0, t[kMaxPasses];
+        if (!vol3d_instance_desc(nullptr, items[S->v_index[k]], S->v_args[k], opt3, share, nullptr,
+                                 nullptr, nullptr, nullptr, &xb, &wb, &ci, &mt, t))
+            return false;
+        tiles[k].assign(t, t + kMaxPasses);
+        xoff[k] = xbytes;
+        xbytes += al256(xb);
+        max_tiles = std::max(max_tiles, mt);
+    }
+    if (max_tiles > share) return false;
+    S->v_tiles = tiles;
+    S->v_xoff = xoff;
+    S->v_xbuf_bytes = xbytes;
+    S->v_max_tiles = max_tiles;
+    return true;
 }
 
 // Builds descriptors and the round/wave work list; pointers are checked only
@@ -273,11 +334,32 @@ int build_schedule(const fgx_instance* items, int n, const fgx_options* opt, boo
                     return d.pass[r % d.npass].L;
                 },
                 &S->round_waves, &S->wave_items);
+    // line-chain and plane-tile instances together: both launches run at
+    // once, each on its own share of the SMs with one block per SM
+    S->c_sms = S->v_sms = sms;
+    if (!S->c_index.empty() && !S->v_index.empty() && sms > 1 &&
+        !(opt && opt->split_sms < 0)) {
+        // the largest instance of each launch needs all its tiles resident
+        int need2 = 1, need3 = 1;
+        for (size_t k = 0; k < S->c_index.size(); ++k)
+            need2 = std::max({need2, S->c_tiles_v[k], S->c_tiles_h[k]});
+        for (const std::vector<int>& t : S->v_tiles)
+            for (int x : t) need3 = std::max(need3, x);
+        int s2 = (opt && opt->split_sms > 0) ? opt->split_sms
+                                             : split_estimate(*S, items, sms);
+        s2 = std::max(need2, std::min(s2, sms - need3));
+        if (s2 < sms && replan_vol3d(items, opt3, sms - s2, S)) {
+            S->concurrent = true;
+            S->c_sms = s2;
+            S->v_sms = sms - s2;
+        }
+    }
     // the plane-tile launch for the 3D instances
     if (!S->v_index.empty()) {
-        const int st = vol3d_batched_geometry(sms, S->v_ci, S->v_ci > kMaxChannels3 ? 1 : 0, opt,
-                                              &S->v_grid, &S->v_smem);
+        const int st = vol3d_batched_geometry(S->v_sms, S->v_ci, S->v_ci > kMaxChannels3 ? 1 : 0,
+                                              opt, &S->v_grid, &S->v_smem);
         if (st != FGX_OK) return st;
+        if (S->concurrent) S->v_grid = std::min(S->v_grid, S->v_sms);
         if (S->v_max_tiles > S->v_grid) return FGX_ERR_UNSUPPORTED;
         pack_rounds((int)S->v_index.size(), S->v_rounds, S->v_grid,
                     [&](int k, int r) {
@@ -301,8 +383,10 @@ int build_schedule(const fgx_instance* items, int n, const fgx_options* opt, boo
             const int st = plan_instance(2, 1, 1, 8, 8, unit, 0.5f, opt, &tmp, &sms);
             if (st != FGX_OK) return st;
         }
-        const int st = chain2d_batched_geometry(sms, opt, &S->c_grid, &S->c_smem);
+        const int st = chain2d_batched_geometry(S->concurrent ? S->c_sms : sms, opt, &S->c_grid,
+                                                &S->c_smem);
         if (st != FGX_OK) return st;
+        if (S->concurrent) S->c_grid = std::min(S->c_grid, S->c_sms);
         for (size_t k = 0; k < S->c_index.size(); ++k)
             if (std::max(S->c_tiles_v[k], S->c_tiles_h[k]) > S->c_grid) return FGX_ERR_UNSUPPORTED;
         const int nc = (int)S->c_index.size();
@@ -341,6 +425,49 @@ int build_schedule(const fgx_instance* items, int n, const fgx_options* opt, boo
     S->v_work_off = S->c_sec_off + al256(S->c_sec_bytes);
     S->total = S->v_work_off + al256(S->v_work_bytes);
     return FGX_OK;
+}
+
+// The side stream of the concurrent batched launches, with its fork and join
+// events: one set per host thread and device, so that calls from different
+// threads never share an event (an event wait refers to the last record);
+// released when the thread exits.
+struct SideStreams {
+    static constexpr int kDevices = 64;
+    cudaStream_t stream[kDevices] = {};
+    cudaEvent_t fork[kDevices] = {}, join[kDevices] = {};
+    ~SideStreams() {
+        for (int i = 0; i < kDevices; ++i) {
+            if (fork[i]) cudaEventDestroy(fork[i]);
+            if (join[i]) cudaEventDestroy(join[i]);
+            if (stream[i]) cudaStreamDestroy(stream[i]);
+        }
+    }
+};
+thread_local SideStreams tl_side;
+
+bool side_stream(cudaStream_t* s, cudaEvent_t* fork, cudaEvent_t* join) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= SideStreams::kDevices)
+        return false;
+    SideStreams& t = tl_side;
+    if (!t.stream[dev]) {
+        cudaStream_t st = nullptr;
+        cudaEvent_t f = nullptr, j = nullptr;
+        if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) return false;
+        if (cudaEventCreateWithFlags(&f, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&j, cudaEventDisableTiming) != cudaSuccess) {
+            if (f) cudaEventDestroy(f);
+            cudaStreamDestroy(st);
+            return false;
+        }
+        t.stream[dev] = st;
+        t.fork[dev] = f;
+        t.join[dev] = j;
+    }
+    *s = t.stream[dev];
+    *fork = t.fork[dev];
+    *join = t.join[dev];
+    return true;
 }
 
 }  // namespace
@@ -392,7 +519,7 @@ int fgx_batched_prepare(const fgx_instance* items, int n, void* workspace,
         int ci = 0, mt = 0, tiles[kMaxPasses];
         fgx_options o3;
         if (!vol3d_instance_desc(vdesc.data() + k * vol3d_desc_size(), items[S.v_index[k]],
-                                 S.v_args[k], options_3d(opt, &o3), S.sms, w,
+                                 S.v_args[k], options_3d(opt, &o3), S.v_sms, w,
                                  (int*)(w + S.v_flag_off) + k,
                                  w + S.v_xbuf_off + S.v_xoff[k], w + S.v_work_off + S.v_woff[k],
                                  &xb, &wb, &ci, &mt, tiles))
@@ -442,6 +569,12 @@ int fgx_batched_prepare(const fgx_instance* items, int n, void* workspace,
     plan->waves3d_off = S.v_waves_off;
     plan->items3d_off = S.v_items_off;
     plan->tables3d = S.v_ci > kMaxChannels3 ? 1 : 0;
+    plan->concurrent = S.concurrent ? 1 : 0;
+    if (S.concurrent) {
+        cudaStream_t s2;
+        cudaEvent_t f, j;
+        if (!side_stream(&s2, &f, &j)) return FGX_ERR_CUDA;
+    }
     return FGX_OK;
 }
 
@@ -451,26 +584,44 @@ int fgx_batched_run(const fgx_batched_plan* plan, void* stream) {
     char* w = (char*)plan->workspace;
     if (cudaMemsetAsync(w, 0, plan->clear_bytes, s) != cudaSuccess) return FGX_ERR_CUDA;
     const long long timeout_ns = (long long)plan->timeout_ms * 1000000LL;
-    if (plan->n2d > 0) {
-        const int st = launch_chain2d_batched(
+    const bool both = plan->concurrent && plan->n2d > 0 && plan->n3d > 0;
+    cudaStream_t s2 = s;
+    cudaEvent_t join = nullptr;
+    if (both) {
+        // fork: the line-chain launch runs on the side stream after
+        // everything before it on the caller's stream (the clear above)
+        cudaEvent_t fork = nullptr;
+        if (!side_stream(&s2, &fork, &join) || cudaEventRecord(fork, s) != cudaSuccess ||
+            cudaStreamWaitEvent(s2, fork, 0) != cudaSuccess)
+            return FGX_ERR_CUDA;
+    }
+    int st = FGX_OK;
+    if (plan->n2d > 0)
+        st = launch_chain2d_batched(
             w + plan->desc2d_off, plan->n2d, plan->channels2d, plan->max_wp2d, plan->max_hp2d,
             plan->rounds2d, (const int*)(w + plan->waves2d_off),
-            (const int*)(w + plan->items2d_off), plan->grid2d, w, timeout_ns, stream);
-        if (st != FGX_OK) return st;
-    }
-    if (plan->n3d > 0) {
-        if (plan->n2d > 0 && cudaMemsetAsync(w + 64, 0, 4, s) != cudaSuccess)
-            return FGX_ERR_CUDA;  // fresh grid-barrier counter for this launch
+            (const int*)(w + plan->items2d_off), plan->grid2d, w, timeout_ns, s2);
+    if (st == FGX_OK && plan->n3d > 0) {
+        // one after the other the launches reuse one grid-barrier counter; at
+        // the same time the plane-tile launch counts in the next word
         int dev = 0, sms = 0;
-        if (cudaGetDevice(&dev) != cudaSuccess ||
+        if ((plan->n2d > 0 && !both && cudaMemsetAsync(w + 64, 0, 4, s) != cudaSuccess) ||
+            cudaGetDevice(&dev) != cudaSuccess ||
             cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
-            return FGX_ERR_CUDA;
-        const int st = launch_vol3d_batched(
-            w + plan->desc3d_off, plan->n3d, plan->rounds3d, (const int*)(w + plan->waves3d_off),
-            (const int*)(w + plan->items3d_off), plan->grid3d, (size_t)plan->smem3d,
-            plan->tables3d, w, timeout_ns, sms, stream);
-        if (st != FGX_OK) return st;
+            st = FGX_ERR_CUDA;
+        else
+            st = launch_vol3d_batched(
+                w + plan->desc3d_off, plan->n3d, plan->rounds3d,
+                (const int*)(w + plan->waves3d_off), (const int*)(w + plan->items3d_off),
+                plan->grid3d, (size_t)plan->smem3d, plan->tables3d, w,
+                (unsigned int*)(w + (both ? 128 : 64)), timeout_ns, sms, stream);
     }
+    // join (also after a failed launch): the caller's stream waits for the
+    // line-chain launch
+    if (both && (cudaEventRecord(join, s2) != cudaSuccess ||
+                 cudaStreamWaitEvent(s, join, 0) != cudaSuccess))
+        return FGX_ERR_CUDA;
+    if (st != FGX_OK) return st;
     if (plan->n == 0) return FGX_OK;
     if ((plan->n2d > 0 || plan->n3d > 0) && cudaMemsetAsync(w + 64, 0, 4, s) != cudaSuccess)
         return FGX_ERR_CUDA;  // fresh grid-barrier counter for this launch
@@ -486,7 +637,7 @@ int fgx_batched_run(const fgx_batched_plan* plan, void* stream) {
     a.status = (int*)w;
     a.timeout_ns = timeout_ns;
     int per_sm = 0;
-    int st = batched_max_blocks_per_sm((size_t)plan->smem_bytes, &per_sm);
+    st = batched_max_blocks_per_sm((size_t)plan->smem_bytes, &per_sm);
     if (st != FGX_OK) return st;
     return launch_batched(a, plan->grid, (size_t)plan->smem_bytes, stream);
 }

@@ -187,9 +187,11 @@ bool vol3d_instance_desc(void* desc, const fgx_instance& it, const SweepArgs& f,
 constexpr int kMaxChannels3 = 3;
 int vol3d_batched_geometry(int sms, int max_ci, int tables, const fgx_options* opt, int* grid,
                            size_t* smem);
+// `hdr` holds the status word; `barrier` is the launch's grid-barrier
+// counter (zero at launch).
 int launch_vol3d_batched(const void* desc, int n, int rounds, const int* round_waves,
                          const int* wave_items, int grid, size_t smem, int tables, char* hdr,
-                         long long timeout_ns, int sms, void* stream);
+                         unsigned int* barrier, long long timeout_ns, int sms, void* stream);
 
 // 2D reverse sweep on warp chains (adj2d.cu).
 size_t adj2d_workspace_bytes(int64_t B, int64_t H, int64_t W, int iterations,

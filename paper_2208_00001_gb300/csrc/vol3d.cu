@@ -1720,7 +1720,7 @@ int vol3d_batched_geometry(int sms, int max_ci, int tables, const fgx_options* o
 
 int launch_vol3d_batched(const void* desc, int n, int rounds, const int* round_waves,
                          const int* wave_items, int grid, size_t smem, int tables, char* hdr,
-                         long long timeout_ns, int sms, void* stream) {
+                         unsigned int* barrier, long long timeout_ns, int sms, void* stream) {
     cudaStream_t s = (cudaStream_t)stream;
     const Vol3DArgs* d = (const Vol3DArgs*)desc;
     const dim3 per_inst((unsigned)std::max(1, sms * 4), (unsigned)n);
@@ -1741,7 +1741,7 @@ int launch_vol3d_batched(const void* desc, int n, int rounds, const int* round_w
     bt.rounds = rounds;
     bt.round_waves = round_waves;
     bt.wave_items = wave_items;
-    bt.barrier = (unsigned int*)(hdr + 64);
+    bt.barrier = barrier;
     bt.status = (int*)hdr;
     bt.timeout_ns = timeout_ns;
     cudaLaunchConfig_t cfg = {};

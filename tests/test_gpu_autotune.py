@@ -68,6 +68,8 @@ def test_batched_auto_options_match_plain_calls(fgx):
     inst = [(torch.from_numpy(c.image).to(dev), torch.from_numpy(c.mask).to(dev), c.v, c.lam,
              c.iterations, c.spacing or (1.0, 1.0, 1.0)) for c in cases]
     plan = fgx.BatchedPlan(inst, options="auto")
+    # 2D and 3D instances: the tuner also chose the SM share of the 2D launch
+    assert "split_sms" in plan.options
     outs = plan.run(check=True)
     for c, o in zip(cases, outs):
         want = oracle.gdt(c.image, c.mask, c.v, c.lam, c.iterations, spacing=c.spacing,

@@ -89,6 +89,34 @@ def test_batched_config_matches_plain_calls(fgx):
         _bits(outs[k].cpu().numpy(), want, c.name + " vs oracle")
 
 
+@pytest.mark.parametrize("split", [-1, 0, 1, 7, 10_000])
+def test_batched_concurrent_launches(fgx, split):
+    """A batch with 2D and 3D instances runs its line-chain and plane-tile
+    launches at the same time on disjoint SM shares (split_sms > 0 sets the
+    2D launch's share, clamped so that the largest instance of each launch
+    has its tiles resident; 0 estimates it; -1 runs them one after the
+    other): every share gives the oracle's results bit for bit, also on
+    replay."""
+    cases = _small_mixed(seed=5)
+    plan = fgx.BatchedPlan(_to_gpu(cases), options=dict(split_sms=split))
+    p = plan.plan
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    assert p.n2d > 0 and p.n3d > 0
+    assert p.concurrent == (0 if split == -1 else 1)
+    if p.concurrent:
+        assert p.grid2d + p.grid3d <= sms
+        if split == 10_000:
+            assert p.grid3d == 1
+    for rep in range(2):
+        for o in plan.outputs:
+            o.fill_(-1.0)
+        outs = plan.run(check=True)
+        for c, o in zip(cases, outs):
+            want = oracle.gdt(c.image, c.mask, c.v, c.lam, c.iterations, spacing=c.spacing,
+                              threads=THREADS)
+            _bits(o.cpu().numpy(), want, f"{c.name} split {split} run {rep}")
+
+
 def test_batched_replay_and_graph_capture(fgx):
     cases = _small_mixed(seed=3)
     plan = fgx.BatchedPlan(_to_gpu(cases))
