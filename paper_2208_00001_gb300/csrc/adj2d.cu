@@ -54,6 +54,10 @@ constexpr int kChA = 8;                  // lines per chunk
 constexpr int kNciA = 5;                 // chunks in the input ring
 constexpr int kNoA = 3;                  // chunks in the output ring
 constexpr int kOutLdA = kRegionA + 4;    // floats per output row
+// The flusher waits for chunks on the input ring's barriers by phase parity:
+// the chain, at most kNoA chunks ahead of it, must not complete two phases
+// of one input slot in between.
+static_assert(kNoA <= kNciA, "output ring deeper than the input ring");
 constexpr int kTileA = 32;               // layout kernel tile
 #define kNegZero __int_as_float(0x80000000)
 
@@ -189,15 +193,25 @@ __device__ bool adj_producer(const Adj2DArgs& a, const AdjGeo& g, AdjSmem& sm, u
 // Flusher warp: writes the owned columns of each finished chunk: the masked
 // adjoint (rows, or transposed when the next application runs along the
 // other axis; v times it into dL/dM after the first application) and A.
+// The chunk goes to registers first and its output slot is handed back
+// before the global stores, so the chain never waits for them.
 __device__ bool adj_flusher(const Adj2DArgs& a, const AdjGeo& g, AdjSmem& sm, unsigned int cb) {
+    static_assert(kChA == 8, "transposed stores: 8 lines x 4 column groups per warp");
     const int lane = threadIdx.x & 31;
     const int c0 = g.r0 + 4 * lane;
     bool owned[4];
 #pragma unroll
     for (int i = 0; i < 4; ++i) owned[i] = (c0 + i >= g.q0) && (c0 + i < g.q1);
+    // rows of the padded pass layouts start on 16 bytes (K and T are
+    // multiples of 4), image-order rows need not
     const bool all_owned = owned[0] && owned[3];
     const int ncol = g.q1 - g.q0;
     const int off = g.q0 - g.r0;
+    const bool rows_g = g.gdst && !g.gdst_transposed;
+    const bool cols_g = g.gdst && g.gdst_transposed;
+    // transposed: lane (jj, cg) writes line jj of columns cg, cg + 4, ...
+    const int jj = lane & (kChA - 1);
+    const int cg = lane >> 3;
     for (int c = 0; c < g.nch; ++c) {
         const unsigned int gc = cb + c;
         const int slot = slot_of(gc, kNoA);
@@ -206,42 +220,65 @@ __device__ bool adj_flusher(const Adj2DArgs& a, const AdjGeo& g, AdjSmem& sm, un
             return false;
         const int s0 = c * kChA;
         const int nl = min(kChA, g.L - s0);
-        // rows in the pass layout: A, and the adjoint when it keeps the layout
-        for (int j = 0; j < nl; ++j) {
-            const int64_t row = (int64_t)line_of(g, s0 + j);
-            if (g.adst) {
-                const float4 v = *reinterpret_cast<const float4*>(&sm.outa[slot][j][4 * lane]);
-                float* p = g.adst + row * g.ld + c0;
-                if (all_owned) {
-                    *reinterpret_cast<float4*>(p) = v;
-                } else {
-                    if (owned[0]) p[0] = v.x;
-                    if (owned[1]) p[1] = v.y;
-                    if (owned[2]) p[2] = v.z;
-                    if (owned[3]) p[3] = v.w;
-                }
-            }
-            if (g.gmask || g.g0 || (g.gdst && !g.gdst_transposed)) {
-                const float4 v = *reinterpret_cast<const float4*>(&sm.outg[slot][j][4 * lane]);
-                const float vv[4] = {v.x, v.y, v.z, v.w};
+        float4 va[kChA], vg[kChA];
 #pragma unroll
-                for (int i = 0; i < 4; ++i) {
-                    if (!owned[i]) continue;
-                    if (g.gmask) g.gmask[row * a.W + c0 + i] = __fmul_rn(a.v, vv[i]);
-                    if (g.g0) g.g0[row * a.W + c0 + i] = vv[i];
-                    if (g.gdst && !g.gdst_transposed) g.gdst[row * g.gdst_ld + c0 + i] = vv[i];
-                }
-            }
+        for (int j = 0; j < kChA; ++j) {
+            va[j] = *reinterpret_cast<const float4*>(&sm.outa[slot][j][4 * lane]);
+            vg[j] = *reinterpret_cast<const float4*>(&sm.outg[slot][j][4 * lane]);
         }
-        if (g.gdst && g.gdst_transposed) {
-            // consecutive lanes write consecutive lines of one column
-            const int jj = lane & (kChA - 1);
-            const int line = line_of(g, s0 + jj);
-            for (int col = lane >> 3; col < ncol; col += 4)
-                if (jj < nl) g.gdst[(int64_t)(g.q0 + col) * g.gdst_ld + line] = sm.outg[slot][jj][off + col];
+        float vt[kRegionA / 4];
+        if (cols_g) {
+#pragma unroll
+            for (int k = 0; k < kRegionA / 4; ++k) {
+                const int col = cg + 4 * k;
+                vt[k] = col < ncol ? sm.outg[slot][jj][off + col] : 0.0f;
+            }
         }
         __syncwarp();
         if (lane == 0) mbar_arrive(&sm.out_empty[slot]);
+#pragma unroll
+        for (int j = 0; j < kChA; ++j) {
+            if (j >= nl) break;
+            const int64_t row = (int64_t)line_of(g, s0 + j);
+            const float a4[4] = {va[j].x, va[j].y, va[j].z, va[j].w};
+            const float g4[4] = {vg[j].x, vg[j].y, vg[j].z, vg[j].w};
+            if (g.adst) {
+                float* p = g.adst + row * g.ld + c0;
+                if (all_owned) {
+                    *reinterpret_cast<float4*>(p) = va[j];
+                } else {
+#pragma unroll
+                    for (int i = 0; i < 4; ++i)
+                        if (owned[i]) p[i] = a4[i];
+                }
+            }
+            if (rows_g) {
+                float* p = g.gdst + row * g.gdst_ld + c0;
+                if (all_owned) {
+                    *reinterpret_cast<float4*>(p) = vg[j];
+                } else {
+#pragma unroll
+                    for (int i = 0; i < 4; ++i)
+                        if (owned[i]) p[i] = g4[i];
+                }
+            }
+            if (g.gmask || g.g0) {
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    if (!owned[i]) continue;
+                    if (g.gmask) g.gmask[row * a.W + c0 + i] = __fmul_rn(a.v, g4[i]);
+                    if (g.g0) g.g0[row * a.W + c0 + i] = g4[i];
+                }
+            }
+        }
+        if (cols_g && jj < nl) {
+            float* p = g.gdst + (int64_t)g.q0 * g.gdst_ld + line_of(g, s0 + jj);
+#pragma unroll
+            for (int k = 0; k < kRegionA / 4; ++k) {
+                const int col = cg + 4 * k;
+                if (col < ncol) p[(int64_t)col * g.gdst_ld] = vt[k];
+            }
+        }
     }
     return true;
 }

@@ -118,6 +118,10 @@ constexpr int kNci = 4;             // chunks in the input ring
 constexpr int kNo = 3;              // chunks in the output ring
 constexpr int kRow = kRegion + 8;   // floats per input row: 4 pad | 128 | 4 pad
 constexpr int kOutLd = kRegion + 4; // floats per output row (conflict-free transposes)
+// The flusher waits for chunks on the input ring's barriers by phase parity:
+// the chain, at most kNo chunks ahead of it, must not complete two phases of
+// one input slot in between.
+static_assert(kNo <= kNci, "output ring deeper than the input ring");
 
 struct TileSmem {
     // in_full: the producer's copies of a chunk have landed; done: the chain
