@@ -540,10 +540,12 @@ __device__ __forceinline__ void chain_step(float (&dp)[4], float left, float rig
         nd[i] = (!masked || valid[i]) ? best : kInf;
         if (codes) {
             // 0: kept its value; else 1 + the lowest parent index reaching the
-            // (strictly smaller) minimum
-            const unsigned int code =
-                nd[i] < c.dold[i] ? (y0 == nd[i] ? 1u : (x1 == nd[i] ? 2u : 3u)) : 0u;
-            packed |= code << (8 * i);
+            // (strictly smaller) minimum, in integer arithmetic (no branch on
+            // the data in the chain step)
+            const unsigned int lt = nd[i] < c.dold[i] ? 1u : 0u;
+            const unsigned int ne0 = y0 != nd[i] ? 1u : 0u;
+            const unsigned int ne1 = x1 != nd[i] ? 1u : 0u;
+            packed |= (lt * (1u + ne0 + (ne0 & ne1))) << (8 * i);
         }
     }
 #pragma unroll
