@@ -224,6 +224,13 @@ __device__ bool adj_producer3(const Adj3DArgs& a, const Tile3& t, const float* g
     const int lane = threadIdx.x & 31, pw = (threadIdx.x >> 5) - kCW;
     const int64_t q = t.q0 + lane;
     const bool qin = q >= 0 && q < g.Q;
+    // lines contiguous in memory (the W passes) with every chunk whole and
+    // aligned: a chunk's planes come as one 16-byte load of adjoints and one
+    // 4-byte load of codes per voxel instead of four of each, strided
+    static_assert(kChunk == 4, "vector loads of four planes");
+    const bool vec = g.sl == 1 && (t.L % kChunk) == 0 && (g.sp % kChunk) == 0 &&
+                     (g.sq % kChunk) == 0 && ((uintptr_t)gsrc & 15u) == 0 &&
+                     ((uintptr_t)csrc & 3u) == 0;
     for (int c = 0; c < t.nch; ++c) {
         const unsigned int gc = cb + c;
         const int slot = (int)(gc % kNst);
@@ -233,17 +240,39 @@ __device__ bool adj_producer3(const Adj3DArgs& a, const Tile3& t, const float* g
             return false;
         float gv[kChunk][kRP / kPW];
         unsigned int cv[kChunk][kRP / kPW];
-#pragma unroll
-        for (int j = 0; j < kChunk; ++j) {
-            const int s = c * kChunk + j;
-            const int64_t line = g.dir > 0 ? (t.L - 1 - s) : s;
+        if (vec) {
+            // the chunk's four planes are four consecutive elements of memory
+            const int64_t lo = g.dir > 0 ? (int64_t)(t.L - kChunk - c * kChunk) : c * kChunk;
 #pragma unroll
             for (int rr = 0; rr < kRP / kPW; ++rr) {
                 const int64_t p = t.p0 + pw + kPW * rr;
-                const bool in = s < t.L && qin && p >= 0 && p < g.P;
-                const int64_t off = line * g.sl + p * g.sp + q * g.sq;
-                gv[j][rr] = in ? __ldcg(gsrc + off) : 0.0f;
-                cv[j][rr] = in ? (unsigned int)__ldg(csrc + off) : 0u;
+                const bool in = qin && p >= 0 && p < g.P;
+                const int64_t off = lo + p * g.sp + q * g.sq;
+                const float4 v = in ? __ldcg(reinterpret_cast<const float4*>(gsrc + off))
+                                    : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+                const unsigned int cw =
+                    in ? __ldg(reinterpret_cast<const unsigned int*>(csrc + off)) : 0u;
+                const float f[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+                for (int j = 0; j < kChunk; ++j) {
+                    const int k = g.dir > 0 ? kChunk - 1 - j : j;
+                    gv[j][rr] = f[k];
+                    cv[j][rr] = (cw >> (8 * k)) & 0xffu;
+                }
+            }
+        } else {
+#pragma unroll
+            for (int j = 0; j < kChunk; ++j) {
+                const int s = c * kChunk + j;
+                const int64_t line = g.dir > 0 ? (t.L - 1 - s) : s;
+#pragma unroll
+                for (int rr = 0; rr < kRP / kPW; ++rr) {
+                    const int64_t p = t.p0 + pw + kPW * rr;
+                    const bool in = s < t.L && qin && p >= 0 && p < g.P;
+                    const int64_t off = line * g.sl + p * g.sp + q * g.sq;
+                    gv[j][rr] = in ? __ldcg(gsrc + off) : 0.0f;
+                    cv[j][rr] = in ? (unsigned int)__ldg(csrc + off) : 0u;
+                }
             }
         }
 #pragma unroll
