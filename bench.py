@@ -349,7 +349,7 @@ def measure_extras(fgx, dev, flush, stream, peak, steps=5, only=None):
 
 
 def _batched_extra(fgx, dev, flush, stream, peak, steps, fwd_bytes):
-    """Batched workload: one persistent launch vs the same instances as
+    """Batched workload: one prepared plan (its persistent launches) vs the same instances as
     sequential calls."""
     import torch
     import workloads

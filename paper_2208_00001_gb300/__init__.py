@@ -702,7 +702,8 @@ class BatchedPlan:
     """A prepared batched launch over instances of uneven shapes (2D and 3D
     mixed).  ``instances`` is a list of (image, mask, v, lam, iterations,
     spacing) with image (1, C, ...) and mask (1, 1, ...) CUDA float32
-    tensors.  :meth:`run` launches the one persistent kernel (replayable, also
+    tensors.  :meth:`run` launches the persistent kernels (2D line chains and
+    3D plane tiles side by side on disjoint SM shares; replayable, also
     inside a captured CUDA graph); results are in :attr:`outputs`."""
 
     def __init__(self, instances, options=None):
@@ -807,6 +808,7 @@ class BatchedPlan:
 
 
 def geodesic_batched(instances, options=None, check=False):
-    """One persistent launch over all instances; returns their distance maps."""
+    """Prepares and runs one batched plan over all instances; returns their
+    distance maps."""
     plan = BatchedPlan(instances, options)
     return plan.run(check=check)

@@ -1,9 +1,11 @@
 """Batched launch of uneven instances (GPU).
 
-One persistent launch computes every instance of a mixed 2D/3D list; each
-result must equal the oracle's bit for bit and the plain single-instance call
-bit for bit, also when instances are spread over several waves and when the
-prepared launch is replayed or captured in a CUDA graph.
+One prepared plan computes every instance of a mixed 2D/3D list (the 2D line
+chains and the 3D plane tiles as two persistent launches side by side, or
+one after the other); each result must equal the oracle's bit for bit and the
+plain single-instance call bit for bit, also when instances are spread over
+several waves, for every SM share, and when the prepared launch is replayed
+or captured in a CUDA graph.
 """
 import ctypes
 import os
@@ -74,7 +76,7 @@ def test_batched_small_mixed_bit_exact(fgx, opts):
 
 def test_batched_config_matches_plain_calls(fgx):
     """The batched workload (64 2D images, sides 128..1024, and 16 volumes,
-    sides 64..192): one launch equals 80 plain calls and the oracle, bit for
+    sides 64..192): one plan equals 80 plain calls and the oracle, bit for
     bit, on every instance."""
     cases = workloads.batched()
     gpu = _to_gpu(cases)
