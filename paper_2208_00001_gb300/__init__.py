@@ -711,23 +711,24 @@ class BatchedPlan:
         if isinstance(options, str):
             if options != "auto":
                 raise ValueError("options: a dict, Options, None or 'auto'")
-            # the tuned 2D line-tile geometry (the library keeps the plane
-            # tiles of the 3D instances whatever 2D geometry the options
-            # carry), then, with 2D and 3D instances, the SM share of the 2D
-            # launch running beside the 3D one
+            # the 2D line-tile geometry (the library keeps the plane tiles of
+            # the 3D instances whatever 2D geometry the options carry); with
+            # 2D and 3D instances jointly with the SM share of the 2D launch
+            # running beside the 3D one, since the best geometry on a share
+            # of the SMs need not be the best on all of them
             i2 = [inst for inst in self.instances if inst[0].dim() == 4]
             has3 = len(i2) < len(self.instances)
             options = {}
-            if i2:
-                cands = [dict(tile_lines=k, tile_width=t) if (k, t) != (0, 0) else {}
-                         for k, t in TILE_CANDIDATES_2D]
-                options = cands[self._tune(i2, cands)]
+            geos = [dict(tile_lines=k, tile_width=t) if (k, t) != (0, 0) else {}
+                    for k, t in TILE_CANDIDATES_2D]
             if i2 and has3:
                 dev = self.instances[0][0].device
                 sms = torch.cuda.get_device_properties(dev).multi_processor_count
                 splits = [0, -1] + [max(1, round(f * sms)) for f in SPLIT_FRACTIONS]
-                cands = [dict(options, split_sms=x) for x in splits]
+                cands = [dict(geo, split_sms=x) for geo in geos for x in splits]
                 options = cands[self._tune(self.instances, cands)]
+            elif i2:
+                options = geos[self._tune(i2, geos)]
             options = options or None
         self.options = options
         self.outputs = []
