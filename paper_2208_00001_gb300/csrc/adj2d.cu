@@ -544,15 +544,24 @@ __global__ void __launch_bounds__(256) grad2d_kernel(const Grad2DArgs a) {
             auto at = [&](int ln, int qq) -> int64_t {
                 return vert ? (int64_t)ln * a.W + qq : (int64_t)qq * a.W + ln;
             };
-            // children on the next line of the forward sweep, offset order
+            // children on the next line of the forward sweep, offset order:
+            // the offsets whose child chose this element are collected first,
+            // then visited in increasing order, so that a warp evaluates one
+            // cost per step for all its lanes instead of one per offset any
+            // lane needs
             const int cl = line + dir;
             if (IMG && cl >= 0 && cl < L) {
+                unsigned int chose = 0u;
 #pragma unroll
                 for (int k = 0; k < 3; ++k) {
                     const int cq = q + 1 - k;
-                    if (cq < 0 || cq >= Q) continue;
+                    if (cq >= 0 && cq < Q && cd[at(cl, cq)] == k + 1) chose |= 1u << k;
+                }
+                while (chose) {
+                    const int k = __ffs(chose) - 1;
+                    chose &= chose - 1u;
+                    const int cq = q + 1 - k;
                     const int64_t x = at(cl, cq);
-                    if (cd[x] != k + 1) continue;
                     const float c = grad_cost(img, x, e, C, N, tk[k], lam);
                     if (c > 0.0f) {
                         const float wgt =

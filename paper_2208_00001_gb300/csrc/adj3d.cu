@@ -465,15 +465,23 @@ __device__ void grad_app3(const Adj3DArgs& a, int t) {
         const int line = g.axis == 0 ? dd : (g.axis == 1 ? hh : ww);
         const int p = g.axis == 0 ? hh : dd;
         const int q = g.axis == 2 ? hh : ww;
-        // children on the next plane of the forward sweep, offset order
+        // children on the next plane of the forward sweep, offset order: the
+        // offsets whose child chose this voxel are collected first, then
+        // visited in increasing order, so that a warp evaluates one cost per
+        // step for all its lanes instead of one per offset any lane needs
         const int cl = line + g.dir;
         if (gout && cl >= 0 && cl < L) {
+            unsigned int chose = 0u;
 #pragma unroll
             for (int k = 0; k < 9; ++k) {
                 const int cp = p - (k / 3 - 1), cq = q - (k % 3 - 1);
                 if (cp < 0 || cp >= P || cq < 0 || cq >= Q) continue;
-                const int x = cl * sl + cp * sp + cq * sq;
-                if (cd[x] != k + 1) continue;
+                if (cd[cl * sl + cp * sp + cq * sq] == k + 1) chose |= 1u << k;
+            }
+            while (chose) {
+                const int k = __ffs(chose) - 1;
+                chose &= chose - 1u;
+                const int x = cl * sl + (p - (k / 3 - 1)) * sp + (q - (k % 3 - 1)) * sq;
                 const float c = grad_cost3(img, x, e, C, n, g.t[k], lam);
                 if (c > 0.0f) add_term(__fdiv_rn(__fmul_rn(A[x], lam), c), x, e, true);
             }
